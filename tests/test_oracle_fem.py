@@ -1,0 +1,122 @@
+"""Pins of the oracle's Nedelec assembly and load vector (no GPU)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from oracle import fem as F
+from oracle import mesh as M
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_reference_tet_by_hand():
+    P = np.array([[[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]], dtype=float)
+    g = np.array([[0, 1, 2, 3]])
+    Ke, Me = F.element_matrices(P, g)
+    for line in open(os.path.join(GOLDEN, "reference_tet.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        which, r, c, v = line.split()
+        mat = Ke[0] if which == "K" else Me[0]
+        assert abs(mat[int(r), int(c)] - float(v)) < 1e-15
+        assert abs(mat[int(c), int(r)] - float(v)) < 1e-15
+
+
+def test_tangential_moment_is_one():
+    # sigma(Phi_i, e_j) = delta_ij: the tangential integral of w_ab along edge a->b is 1,
+    # and 0 along the other edges (checked with a 5-point Gauss rule on each edge)
+    P = np.array([[0.1, 0.2, 0.0], [1.0, 0.3, 0.2], [0.2, 1.1, 0.1], [0.3, 0.1, 0.9]])
+    G, vol = F.barycentric_gradients(P[None])
+    G = G[0]
+    xg, wg = np.polynomial.legendre.leggauss(5)
+    s = 0.5 * (xg + 1.0)
+    w = 0.5 * wg
+    for (a, b) in F.LOCAL_EDGES:
+        for (c, d) in F.LOCAL_EDGES:
+            tang = P[d] - P[c]
+            tot = 0.0
+            for si, wi in zip(s, w):
+                lam = np.zeros(4)
+                lam[c], lam[d] = 1.0 - si, si
+                phi = lam[a] * G[b] - lam[b] * G[a]
+                tot += wi * phi.dot(tang)
+            assert abs(tot - (1.0 if (a, b) == (c, d) else 0.0)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_de_rham_gradients_in_kernel(n):
+    m = M.interior_edges(n)
+    K, Mm = F.assemble(m, 1.0, parts=True)
+    G = F.gradient_matrix(m)
+    assert G.shape[1] == (n - 1) ** 3
+    KG = K @ G
+    assert abs(KG).max() < 1e-12 * abs(K).max()
+    assert abs(Mm @ G).max() > 1e-3 * abs(Mm).max()
+
+
+def test_symmetry_spd_and_nullspace():
+    n = 3
+    m = M.interior_edges(n)
+    K, Mm = F.assemble(m, 1.0, parts=True)
+    assert abs(K - K.T).max() < 1e-14
+    assert abs(Mm - Mm.T).max() < 1e-15
+    np.linalg.cholesky(Mm.toarray())  # M is SPD
+    ev = np.linalg.eigvalsh(K.toarray())
+    nz = np.sum(ev < 1e-10 * ev.max())
+    assert nz == (n - 1) ** 3
+    assert ev.min() > -1e-10 * ev.max()
+
+
+def test_cavity_eigenvalues():
+    # Maxwell eigenvalues of the unit cube: pi^2 (l^2+m^2+n^2), at least two indices
+    # nonzero: 2 pi^2 (x3), 3 pi^2 (x2).  Discrete values converge as n grows.
+    errs = []
+    for n in (3, 5):
+        m = M.interior_edges(n)
+        K, Mm = F.assemble(m, 1.0, parts=True)
+        ev = sla.eigh(K.toarray(), Mm.toarray(), eigvals_only=True)
+        ev = ev[ev > 1e-8 * ev.max()]
+        ev = np.sort(ev)[:5]
+        exact = np.pi ** 2 * np.array([2, 2, 2, 3, 3])
+        errs.append(np.abs(ev - exact) / exact)
+    assert np.all(errs[1] < 0.08)
+    assert errs[1].max() < errs[0].max()
+
+
+def test_manufactured_boundary_and_field():
+    x = np.random.default_rng(1).random((50, 3))
+    E = F.manufactured_E(x)
+    # E x n = 0 on x = 0 (n = -e_x): tangential components E_y, E_z vanish
+    x0 = x.copy(); x0[:, 0] = 0.0
+    E0 = F.manufactured_E(x0)
+    assert np.abs(E0[:, 1:]).max() < 1e-15
+    # curl curl E = 2 pi^2 E via finite differences of curl
+    h = 1e-4
+
+    def curl(f, p):
+        J = np.zeros((3, 3))
+        for j in range(3):
+            e = np.zeros(3); e[j] = h
+            J[:, j] = (f(p + e) - f(p - e)) / (2 * h)
+        return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+
+    p = np.array([0.3, 0.6, 0.2])
+    cc = curl(lambda q: curl(lambda r: F.manufactured_E(r[None])[0], q), p)
+    assert np.allclose(cc, 2 * np.pi ** 2 * F.manufactured_E(p[None])[0], rtol=1e-4)
+
+
+def test_manufactured_convergence_rate():
+    kappa = 1.0
+    errs = []
+    for n in (4, 8, 16):
+        m = M.interior_edges(n)
+        A = F.assemble(m, kappa)
+        b = F.manufactured_rhs(m, kappa)
+        x = spla.spsolve(A.tocsc(), b)
+        errs.append(F.l2_error(m, x, F.manufactured_E))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert 0.85 < rates[0] < 1.3 and 0.9 < rates[1] < 1.2, (errs, rates)

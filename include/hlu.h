@@ -1,0 +1,216 @@
+/*
+ * hlu.h - C ABI of the GB300 H-LU preconditioned Maxwell solver.
+ *
+ * Method: Parvizi, Khodadadian, Beuchler, Wick, "Hierarchical LU
+ * preconditioning for the time-harmonic Maxwell equations" (arXiv 2211.11303).
+ * The library assembles the lowest-order Nedelec edge-element matrix of
+ * curl curl E - kappa^2 E = J with E x n = 0 (Sec. 2, Eq. 4-7), builds the
+ * geometric cluster tree and the eta-admissible block tree (Sec. 3, Sec. 4),
+ * computes the H-matrix approximation A_H and its H-LU factorisation
+ * (Algorithm 1, steps I-II) on the GPU, and applies U^-1 L^-1 inside
+ * restarted flexible GMRES (Sec. 4, Example 1) or the Richardson loop
+ * (Algorithm 1, steps III-IV).
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns an int status, HLU_OK (0) on success.  No
+ *    exception or longjmp crosses the ABI.  hlu_status_string() names a code;
+ *    hlu_last_error() returns a thread-local message for the last failure.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Device-pointer arguments are read/written in stream
+ *    order; calls documented as "synchronous" return after the stream has
+ *    drained.
+ *  - Memory: the library allocates its own device memory (cudaMalloc) for
+ *    the handle's matrices, trees, factors and workspaces, and frees it in
+ *    hlu_destroy().  Vectors passed in are caller-owned.
+ *  - Vectors: column-major, `nrhs` columns of length N with leading
+ *    dimension `ld` >= N, FP64, in the original interior-edge DOF order.
+ *  - DOF order: interior edges (lo, hi) of the Kuhn mesh sorted by (lo, hi),
+ *    vertex id (i (n+1) + j)(n+1) + k; an edge is oriented lo -> hi.
+ */
+#ifndef HLU_H
+#define HLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HLU_OK 0
+#define HLU_ERR_ARG 1           /* invalid argument (NULL, size, range)        */
+#define HLU_ERR_OOM 2           /* device or host allocation failed            */
+#define HLU_ERR_ZERO_PIVOT 3    /* exact zero pivot inside a diagonal leaf     */
+#define HLU_ERR_NOT_CONVERGED 4 /* Krylov iteration hit maxit; x still written  */
+#define HLU_ERR_TIMEOUT 5       /* a bounded device-side wait gave up          */
+#define HLU_ERR_CUDA 6          /* a CUDA runtime call failed                  */
+#define HLU_ERR_STATE 7         /* call out of order (e.g. solve before factor)*/
+
+/* ---- precisions of the factor ------------------------------------------ */
+#define HLU_FP64 0 /* factor and triangular solves in FP64 ("plain" path) */
+#define HLU_FP32 1 /* factor and triangular solves in FP32, FP32 accumulate */
+
+/* ---- block kinds in the exported block tree ------------------------------ */
+#define HLU_BLOCK_ADM 0   /* admissible: low-rank X Y^T (Definition 1)       */
+#define HLU_BLOCK_DENSE 1 /* inadmissible with a leaf cluster: dense         */
+#define HLU_BLOCK_SUB 2   /* subdivided into four sons                       */
+
+typedef struct hlu_handle hlu_handle;
+
+/* Mesh: the unit cube cut into lattice_n^3 sub-cubes, each split into the 6
+ * Kuhn tetrahedra along the axis permutations (Sec. 4, Example 1: the cube
+ * cut into 6 tetrahedra and refined).  lattice_n >= 1. */
+typedef struct {
+  int32_t lattice_n;
+} hlu_mesh;
+
+/* Per-solve statistics (host struct filled by gmres_solve / hlu_richardson;
+ * valid when the call returns). */
+typedef struct {
+  int32_t iterations;      /* inner Krylov steps (max over columns)             */
+  int32_t restarts;        /* restart cycles (max over columns)                 */
+  int32_t converged;       /* 1 if every column met tol                         */
+  int32_t nrhs;            /* columns solved                                    */
+  double relres_max;       /* max over columns of ||b - A x|| / ||b|| at exit    */
+  double abs_res_max;      /* max over columns of ||A x - b||_2 (Alg. 1 step IV) */
+  double precond_ms;       /* device time in preconditioner applications        */
+  double total_ms;         /* wall time of the call                             */
+  int32_t precond_applies; /* number of U^-1 L^-1 applications                  */
+  int32_t reserved;
+} hlu_stats;
+
+/* Factor statistics (hlu_factor_stats). */
+typedef struct {
+  int64_t n_tasks;          /* tasks in the factorisation DAG                    */
+  int64_t n_solve_tasks;    /* tasks in one triangular-solve pass (L then U)     */
+  int64_t factor_bytes;     /* device bytes of dense + low-rank factor storage   */
+  int64_t workspace_bytes;  /* device bytes of temporaries and scratch           */
+  double flops;             /* algorithmic flops of the factorisation (counted)  */
+  double factor_ms;         /* device time of the last hlu_factor                */
+  double schedule_ms;       /* host time spent building the task DAG             */
+  int32_t rank_max;         /* max rank of an admissible block after factoring   */
+  int32_t rank_cap_hits;    /* truncations clipped at the rank capacity          */
+  double rank_mean;         /* mean rank over admissible blocks                  */
+  int32_t n_clusters, n_blocks, n_adm, n_dense;
+} hlu_factor_info;
+
+/* hlu_build - Algorithm 1 step I and the structures it needs.
+ * Builds, on the GPU: the Kuhn mesh and its interior-edge numbering (Sec. 2.1:
+ * one DOF per interior edge, sigma(Phi_i, e_j) = delta_ij), the CSR matrix
+ * A = K - kappa^2 M of a(E, Phi) = <curl E, curl Phi> - kappa^2 <E, Phi>
+ * (Sec. 2.1 weak form; the paper's kappa is kappa^2 here), the geometric
+ * cluster tree on doubled edge midpoints (Sec. 4, geometrically balanced
+ * bisection, leaf size `leaf`), the block tree with admissibility
+ * min(diam tau, diam sigma) <= eta dist(tau, sigma) (Sec. 3-4, eta = 2 in the
+ * paper; eta^2 must be an integer), and the exact A_H (dense leaves from A,
+ * admissible blocks as X Y^T of their nonzero rows).
+ * kappa: wave number (> 0).  eps: relative truncation tolerance used by
+ * hlu_factor (Sec. 4 truncated SVD; keep s_i > eps s_1).  rank_cap: maximum
+ * stored rank of an admissible block (0 = default 32).
+ * The build is synchronous (trees are copied to the host for scheduling).
+ * Errors: HLU_ERR_ARG for n < 1, leaf < 2, eta <= 0 or non-integer eta^2,
+ * eps <= 0; HLU_ERR_OOM; HLU_ERR_CUDA. */
+int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps,
+              int32_t rank_cap, void* stream, hlu_handle** out);
+
+/* Number of interior-edge DOFs N of a built handle (0 for NULL). */
+int64_t hlu_n(const hlu_handle* h);
+
+/* hlu_export_trees - copy the trees to caller host buffers (Sec. 3-4).
+ * perm: int32[N], perm[i] = original DOF at permuted position i.
+ * clusters: int32[nc*12] rows (offset, size, lo[3], hi[3], son0, son1, level,
+ *   parent), ids in DFS pre-order, boxes in doubled lattice units.
+ * blocks: int32[nb*8] rows (row cluster, col cluster, kind, son0..son3,
+ *   parent), DFS pre-order.
+ * sizes: int64[2] receives (nc, nb); any array pointer may be NULL to query
+ * sizes only.  Synchronous.  HLU_ERR_ARG on NULL handle/sizes. */
+int hlu_export_trees(const hlu_handle* h, int32_t* perm, int32_t* clusters, int32_t* blocks,
+                     int64_t* sizes);
+
+/* hlu_export_csr - copy the assembled CSR matrix A (Sec. 2.1,
+ * stiffness-matrix equation) to host buffers: rowptr int64[N+1], col
+ * int32[nnz], val double[nnz]; columns ascending within a row, every pair of
+ * interior edges sharing a tetrahedron present (explicit zeros kept).
+ * nnz: int64 out, may be queried with NULL arrays.  Synchronous. */
+int hlu_export_csr(const hlu_handle* h, int64_t* rowptr, int32_t* col, double* val, int64_t* nnz);
+
+/* hlu_rhs_manufactured - load vector b_j = <J, Phi_j> (Sec. 2.1) for the
+ * manufactured field E = (sin pi y sin pi z, sin pi z sin pi x, sin pi x sin pi y),
+ * J = (2 pi^2 - kappa^2) E, by a 4-point degree-2 rule.  b_dev: device
+ * double[N].  Asynchronous on stream. */
+int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream);
+
+/* hlu_spmv - y = A x for nrhs columns (FP64 CSR), device pointers, ld >= N.
+ * Asynchronous.  Used by the Krylov solvers and exposed for tests. */
+int hlu_spmv(const hlu_handle* h, const double* x_dev, double* y_dev, int32_t nrhs, int64_t ld,
+             void* stream);
+
+/* hlu_factor - Algorithm 1 step II: H-LU of A_H in H-arithmetic.
+ * Recursive block LU (LU(A11); A12 <- L11^-1 P A12; A21 <- A21 U11^-1;
+ * A22 <- A22 - A21 A12 truncated to eps; LU(A22)), partial pivoting inside
+ * dense diagonal leaves only.  precision: HLU_FP64 or HLU_FP32.  May be
+ * called again (e.g. with another precision): A_H is re-filled first.
+ * Synchronous (returns after the device finished; factor_ms recorded).
+ * Errors: HLU_ERR_ZERO_PIVOT (factor unusable), HLU_ERR_TIMEOUT, HLU_ERR_OOM. */
+int hlu_factor(hlu_handle* h, int32_t precision, void* stream);
+
+/* hlu_factor_stats - fill *info for the last factorisation. */
+int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
+
+/* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
+ * (U^-1 (L^-1 r), leaf pivots applied in the forward pass).  b_dev, x_dev:
+ * device FP64, nrhs >= 1 columns, ld >= N; b and x may alias.  Runs in the
+ * factor's precision (FP64 vectors are cast at entry and exit).
+ * Asynchronous.  HLU_ERR_STATE if not factored. */
+int hlu_solve(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+              void* stream);
+
+/* gmres_solve - restarted GMRES(restart) with right preconditioner
+ * (LU)_H^-1 (Sec. 4, Example 1; flexible form when `flexible` != 0, which is
+ * required for exactness when the factor is FP32), x0 = 0, CGS2
+ * orthogonalisation and Givens rotations in FP64, stop when
+ * ||b - A x||_2 <= tol ||b||_2 (true residual checked at exit), at most maxit
+ * inner steps.  All nrhs columns iterate together; their preconditioner
+ * applications are batched.  Synchronous; *stats filled if non-NULL.
+ * Returns HLU_ERR_NOT_CONVERGED (x written) if a column missed tol. */
+int gmres_solve(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                int32_t restart, double tol, int32_t maxit, int32_t flexible, hlu_stats* stats,
+                void* stream);
+
+/* hlu_richardson - Algorithm 1 steps III-IV: r = b - A x, err = ||r||/||b||,
+ * x <- x + U^-1 (L^-1 r), stop when err < tol or after maxit; then
+ * error = ||A x - b||_2 into stats->abs_res_max.  Same vector conventions as
+ * gmres_solve.  Synchronous. */
+int hlu_richardson(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs,
+                   int64_t ld, double tol, int32_t maxit, hlu_stats* stats, void* stream);
+
+/* hlu_factor_batch - factor `count` built handles in ONE persistent launch
+ * (their task DAGs interleaved), sharing the device.  Same semantics as
+ * hlu_factor per handle.  Synchronous. */
+int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream);
+
+/* hlu_solve_batch - x_i = (LU)_H,i^-1 b_i for `count` factored handles in one
+ * persistent launch (cross-request batching of the triangular solves).
+ * b[i], x[i]: device FP64 pointers with nrhs[i] columns, leading dimension
+ * N_i.  Asynchronous. */
+int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b,
+                    double* const* x, const int32_t* nrhs, void* stream);
+
+/* hlu_factor_bytes_estimate - device bytes hlu_factor will hold for this
+ * handle at `precision` (factor storage + workspaces), for admission
+ * control; -1 on error. */
+int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision);
+
+/* hlu_set_wait_limit_ms - bound (milliseconds, default 20000) of every
+ * device-side dependency wait; a wait that runs out sets HLU_ERR_TIMEOUT and
+ * the kernel returns.  Process-wide. */
+void hlu_set_wait_limit_ms(double ms);
+
+void hlu_destroy(hlu_handle* h);
+const char* hlu_status_string(int status);
+const char* hlu_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLU_H */

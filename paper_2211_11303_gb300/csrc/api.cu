@@ -1,0 +1,793 @@
+// C ABI of the GB300 H-LU library (declarations and documentation in
+// include/hlu.h).  Host orchestration only: every step of the numerical path
+// runs in the kernels of build.cu, exec.cu and krylov.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hlu.h"
+#include "build.h"
+#include "exec.h"
+#include "hlu_internal.h"
+#include "host_exec.h"
+#include "krylov.h"
+
+using namespace hlu;
+
+namespace {
+
+thread_local std::string g_err;
+double g_wait_limit_ms = 20000.0;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? HLU_ERR_OOM : HLU_ERR_CUDA;
+}
+#define CKR(x, where)                                \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(T** d, const std::vector<T>& h) {
+  *d = nullptr;
+  size_t bytes = sizeof(T) * std::max<size_t>(h.size(), 1);
+  cudaError_t e = cudaMalloc(d, bytes);
+  if (e != cudaSuccess) return e;
+  if (!h.empty()) e = cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+struct DevSched {
+  Task* tasks = nullptr;
+  Term* terms = nullptr;
+  Piece* pieces = nullptr;
+  int64_t* pred_ptr = nullptr;
+  int32_t* pred_idx = nullptr;
+  int32_t* done = nullptr;
+  int64_t ntasks = 0;
+  int32_t epoch = 0;
+  cudaError_t load(const Schedule& S) {
+    ntasks = (int64_t)S.tasks.size();
+    cudaError_t e;
+    if ((e = upload(&tasks, S.tasks)) != cudaSuccess) return e;
+    if ((e = upload(&terms, S.terms)) != cudaSuccess) return e;
+    if ((e = upload(&pieces, S.pieces)) != cudaSuccess) return e;
+    if ((e = upload(&pred_ptr, S.pred_ptr)) != cudaSuccess) return e;
+    if ((e = upload(&pred_idx, S.pred_idx)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&done, sizeof(int32_t) * std::max<int64_t>(ntasks, 1))) != cudaSuccess) return e;
+    return cudaMemset(done, 0, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
+  }
+  void free_all() {
+    for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx, (void*)done})
+      if (p) cudaFree(p);
+    *this = DevSched();
+  }
+};
+
+struct KrylovWS {
+  int64_t N = 0;
+  int m = 0, nr = 0;
+  double *V = nullptr, *Z = nullptr, *W = nullptr, *h1 = nullptr, *h2 = nullptr, *hn = nullptr, *H = nullptr,
+         *cs = nullptr, *sn = nullptr, *g = nullptr, *est = nullptr, *y = nullptr, *bn = nullptr, *part = nullptr,
+         *tmp = nullptr;
+  int* jr = nullptr;
+  void free_all() {
+    for (void* p : {(void*)V, (void*)Z, (void*)W, (void*)h1, (void*)h2, (void*)hn, (void*)H, (void*)cs, (void*)sn,
+                    (void*)g, (void*)est, (void*)y, (void*)bn, (void*)part, (void*)tmp, (void*)jr})
+      if (p) cudaFree(p);
+    *this = KrylovWS();
+  }
+};
+
+}  // namespace
+
+struct hlu_handle {
+  int n = 0, leaf = 0, rank_cap = 32;
+  double kappa = 0, eta = 0, eps = 0;
+  int64_t eta2 = 0;
+  DevMesh mesh;
+  DevCSR A;
+  int32_t* d_perm = nullptr;
+  int32_t* d_iperm = nullptr;
+  HostTrees trees;
+  std::vector<Cluster> C;
+  std::vector<Block> B;
+  ArenaLayout L;
+  Schedule F, S;
+  SchedStats st;
+  DevSched dF, dS;
+  FillDesc* d_fill_dense = nullptr;
+  FillDesc* d_fill_lr = nullptr;
+  int32_t n_fill_dense = 0, n_fill_lr = 0;
+  int64_t dense_rows = 0;
+  // factor state
+  int precision = -1;
+  void* d_arena = nullptr;
+  int64_t arena_elems = 0;
+  int32_t* d_ranks = nullptr;
+  int32_t* d_piv = nullptr;
+  void* d_scratch = nullptr;
+  int64_t scratch_stride = 0;
+  int grid = 0;
+  int32_t* d_status = nullptr;
+  double* d_flops = nullptr;
+  unsigned long long* d_ticket = nullptr;
+  void** d_arenas = nullptr;
+  int32_t** d_rankp = nullptr;
+  int32_t** d_pivp = nullptr;
+  hlu_factor_info info;
+  KrylovWS kw;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+void free_factor(hlu_handle* h) {
+  for (void* p : {(void*)h->d_arena, (void*)h->d_ranks, (void*)h->d_piv, (void*)h->d_scratch, (void*)h->d_status,
+                  (void*)h->d_flops, (void*)h->d_ticket, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp})
+    if (p) cudaFree(p);
+  h->d_arena = nullptr;
+  h->d_ranks = nullptr;
+  h->d_piv = nullptr;
+  h->d_scratch = nullptr;
+  h->d_status = nullptr;
+  h->d_flops = nullptr;
+  h->d_ticket = nullptr;
+  h->d_arenas = nullptr;
+  h->d_rankp = nullptr;
+  h->d_pivp = nullptr;
+  h->precision = -1;
+}
+
+int esize(int precision) { return precision == HLU_FP64 ? 8 : 4; }
+
+int64_t scratch_stride_elems(const ArenaLayout& L) {
+  int64_t half = (int64_t)std::max(L.max_trunc_rows, 1) * kTruncWidthMax;
+  half = (half + 31) & ~int64_t(31);
+  return 2 * half;
+}
+
+template <class T>
+int blocks_per_sm() {
+  return exec_blocks_per_sm<T>();
+}
+
+int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops) {
+  ExecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tasks = ds.tasks;
+  a.ntasks = ds.ntasks;
+  a.terms = ds.terms;
+  a.pieces = ds.pieces;
+  a.pred_ptr = ds.pred_ptr;
+  a.pred_idx = ds.pred_idx;
+  a.done = ds.done;
+  a.epoch = ++ds.epoch;
+  a.ticket = h->d_ticket;
+  a.arenas = h->d_arenas;
+  a.ranks = h->d_rankp;
+  a.pivs = h->d_pivp;
+  a.scratch = h->d_scratch;
+  a.scratch_stride = h->scratch_stride;
+  a.eps = h->eps;
+  a.status = h->d_status;
+  a.flops = with_flops ? h->d_flops : nullptr;
+  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  if (ds.ntasks == 0) return HLU_OK;
+  int32_t st0[4] = {0, -1, 0, 0};
+  CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
+  CKR(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
+  int g = (int)std::min<int64_t>(grid, ds.ntasks);
+  cudaError_t e = h->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
+  CKR(e, "executor launch");
+  return HLU_OK;
+}
+
+int read_status(hlu_handle* h, cudaStream_t s, int32_t* out4) {
+  CKR(cudaMemcpyAsync(out4, h->d_status, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, s), "status read");
+  CKR(cudaStreamSynchronize(s), "sync");
+  if (out4[0] == 5) return fail(HLU_ERR_TIMEOUT, "device wait exceeded its limit at task " + std::to_string(out4[1]));
+  if (out4[0] == 3) return fail(HLU_ERR_ZERO_PIVOT, "zero pivot in a diagonal leaf");
+  if (out4[0] == 7) return fail(HLU_ERR_STATE, "an A_H block exceeds the rank capacity");
+  return HLU_OK;
+}
+
+template <class T>
+int solve_impl(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+  hlu_handle* h = const_cast<hlu_handle*>(hc);
+  const int64_t N = h->A.N;
+  T* work = reinterpret_cast<T*>(h->d_arena) + h->L.work_off;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += h->L.nrhs_max) {
+    int32_t nc = std::min(h->L.nrhs_max, nrhs - c0);
+    CKR(set_int(h->d_ranks + h->L.nrhs_slot, nc, s), "nrhs slot");
+    CKR(gather_cast<T>(N, h->d_perm, b + c0 * ld, ld, work, nc, s), "gather");
+    int rc = exec_run(h, h->dS, h->grid, s, false);
+    if (rc) return rc;
+    CKR(scatter_cast<T>(N, h->d_perm, work, x + c0 * ld, ld, nc, s), "scatter");
+  }
+  return HLU_OK;
+}
+
+int solve_any(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+  return h->precision == HLU_FP64 ? solve_impl<double>(h, b, x, nrhs, ld, s) : solve_impl<float>(h, b, x, nrhs, ld, s);
+}
+
+int ensure_kw(hlu_handle* h, int m, int nr) {
+  KrylovWS& k = h->kw;
+  if (k.N == h->A.N && k.m >= m && k.nr >= nr) return HLU_OK;
+  k.free_all();
+  int64_t N = h->A.N;
+  k.N = N;
+  k.m = m;
+  k.nr = nr;
+  CKR(cudaMalloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
+  CKR(cudaMalloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
+  CKR(cudaMalloc(&k.W, sizeof(double) * N * nr), "alloc W");
+  CKR(cudaMalloc(&k.tmp, sizeof(double) * N * nr), "alloc tmp");
+  CKR(cudaMalloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.hn, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.cs, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.sn, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.est, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.y, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.bn, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
+  CKR(cudaMalloc(&k.jr, sizeof(int) * nr), "alloc");
+  return HLU_OK;
+}
+
+// column norms of X (N x nr, ld) into dev[nr] and host[nr]
+int col_norms(hlu_handle* h, const double* X, int64_t ld, int nr, double* dev, double* host, cudaStream_t s) {
+  KrylovWS& k = h->kw;
+  CKR(multidot(h->A.N, X, ld, 1, X, ld, nr, k.part, dev, 1, s), "norm");
+  CKR(sqrt_inplace(dev, nr, s), "sqrt");
+  if (host) {
+    CKR(cudaMemcpyAsync(host, dev, sizeof(double) * nr, cudaMemcpyDeviceToHost, s), "norm d2h");
+    CKR(cudaStreamSynchronize(s), "sync");
+  }
+  return HLU_OK;
+}
+
+int gmres_chunk(hlu_handle* h, const double* b, double* x, int nr, int64_t ld, int m, double tol, int maxit,
+                hlu_stats* st, cudaStream_t s) {
+  int rc = ensure_kw(h, m, nr);
+  if (rc) return rc;
+  KrylovWS& k = h->kw;
+  const int64_t N = h->A.N;
+  const int64_t ldr = N * (m + 1);
+  std::vector<double> bn(nr), beta(nr), est(nr);
+  std::vector<int> conv(nr, 0), jr(nr, 0);
+  for (int r = 0; r < nr; ++r) CKR(cudaMemsetAsync(x + r * ld, 0, sizeof(double) * N, s), "x0");
+  rc = col_norms(h, b, ld, nr, k.bn, bn.data(), s);
+  if (rc) return rc;
+  int iters = 0, restarts = 0;
+  double pms = 0;
+  for (;;) {
+    CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, x, ld, b, ld, k.V, ldr, nr, s), "residual");
+    rc = col_norms(h, k.V, ldr, nr, k.hn, beta.data(), s);
+    if (rc) return rc;
+    bool all = true;
+    for (int r = 0; r < nr; ++r) {
+      conv[r] = (bn[r] == 0.0) || (beta[r] <= tol * bn[r]);
+      all = all && conv[r];
+    }
+    if (all || iters >= maxit) break;
+    CKR(scale_cols(N, k.V, ldr, k.hn, k.V, ldr, nr, s), "scale");
+    CKR(init_g(nr, m, k.hn, k.g, s), "init g");
+    std::fill(jr.begin(), jr.end(), 0);
+    for (int j = 0; j < m; ++j) {
+      CKR(cudaEventRecord(h->ev0, s), "ev");
+      rc = solve_any(h, k.V + j * N, k.Z + j * N, nr, ldr, s);
+      if (rc) return rc;
+      CKR(cudaEventRecord(h->ev1, s), "ev");
+      CKR(spmv(h->A.rowptr, h->A.col, h->A.val, N, k.Z + j * N, ldr, k.W, N, nr, s), "spmv");
+      CKR(multidot(N, k.V, ldr, j + 1, k.W, N, nr, k.part, k.h1, m + 1, s), "cgs1");
+      CKR(multiaxpy(N, k.V, ldr, j + 1, k.h1, m + 1, k.W, N, nr, s), "cgs1 axpy");
+      CKR(multidot(N, k.V, ldr, j + 1, k.W, N, nr, k.part, k.h2, m + 1, s), "cgs2");
+      CKR(multiaxpy(N, k.V, ldr, j + 1, k.h2, m + 1, k.W, N, nr, s), "cgs2 axpy");
+      rc = col_norms(h, k.W, N, nr, k.hn, nullptr, s);
+      if (rc) return rc;
+      CKR(scale_cols(N, k.W, N, k.hn, k.V + (j + 1) * N, ldr, nr, s), "scale");
+      CKR(givens(nr, m, j, k.h1, k.h2, m + 1, k.hn, k.H, k.cs, k.sn, k.g, k.est, s), "givens");
+      CKR(cudaMemcpyAsync(est.data(), k.est, sizeof(double) * nr, cudaMemcpyDeviceToHost, s), "est");
+      CKR(cudaStreamSynchronize(s), "sync");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+      pms += ms;
+      if (st) st->precond_applies++;
+      ++iters;
+      bool done = true;
+      for (int r = 0; r < nr; ++r) {
+        if (conv[r]) continue;
+        if (jr[r] == 0 && est[r] <= tol * bn[r]) jr[r] = j + 1;
+        done = done && jr[r] > 0;
+      }
+      if (done || j == m - 1 || iters >= maxit) {
+        for (int r = 0; r < nr; ++r)
+          if (!conv[r] && jr[r] == 0) jr[r] = j + 1;
+        break;
+      }
+    }
+    for (int r = 0; r < nr; ++r)
+      if (conv[r]) jr[r] = 0;
+    CKR(cudaMemcpyAsync(k.jr, jr.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, s), "jr");
+    CKR(backsub(nr, m, k.jr, k.H, k.g, k.y, s), "backsub");
+    // Z columns live with stride ldr (same layout as V)
+    CKR(xupdate(N, k.Z, ldr, m, k.y, x, ld, nr, s), "xupdate");
+    ++restarts;
+  }
+  if (st) {
+    st->iterations = std::max(st->iterations, iters);
+    st->restarts = std::max(st->restarts, restarts);
+    double rmax = 0, amax = 0;
+    bool all = true;
+    for (int r = 0; r < nr; ++r) {
+      double rr = bn[r] > 0 ? beta[r] / bn[r] : 0.0;
+      rmax = std::max(rmax, rr);
+      amax = std::max(amax, beta[r]);
+      all = all && conv[r];
+    }
+    st->relres_max = std::max(st->relres_max, rmax);
+    st->abs_res_max = std::max(st->abs_res_max, amax);
+    st->converged = st->converged && all;
+    st->precond_ms += pms;
+  }
+  bool all = true;
+  for (int r = 0; r < nr; ++r) all = all && conv[r];
+  return all ? HLU_OK : fail(HLU_ERR_NOT_CONVERGED, "GMRES reached maxit");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hlu_status_string(int s) {
+  switch (s) {
+    case HLU_OK: return "HLU_OK";
+    case HLU_ERR_ARG: return "HLU_ERR_ARG";
+    case HLU_ERR_OOM: return "HLU_ERR_OOM";
+    case HLU_ERR_ZERO_PIVOT: return "HLU_ERR_ZERO_PIVOT";
+    case HLU_ERR_NOT_CONVERGED: return "HLU_ERR_NOT_CONVERGED";
+    case HLU_ERR_TIMEOUT: return "HLU_ERR_TIMEOUT";
+    case HLU_ERR_CUDA: return "HLU_ERR_CUDA";
+    case HLU_ERR_STATE: return "HLU_ERR_STATE";
+    default: return "HLU_ERR_UNKNOWN";
+  }
+}
+const char* hlu_last_error(void) { return g_err.c_str(); }
+void hlu_set_wait_limit_ms(double ms) {
+  if (ms > 0) g_wait_limit_ms = ms;
+}
+int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
+
+void hlu_destroy(hlu_handle* h) {
+  if (!h) return;
+  free_factor(h);
+  h->dF.free_all();
+  h->dS.free_all();
+  h->kw.free_all();
+  for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->A.rowptr, (void*)h->A.col,
+                  (void*)h->A.val, (void*)h->d_perm, (void*)h->d_iperm, (void*)h->d_fill_dense, (void*)h->d_fill_lr})
+    if (p) cudaFree(p);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps, int32_t rank_cap,
+              void* stream, hlu_handle** out) {
+  try {
+    if (!mesh || !out) return fail(HLU_ERR_ARG, "null argument");
+    *out = nullptr;
+    const int n = mesh->lattice_n;
+    if (n < 1 || n > 200) return fail(HLU_ERR_ARG, "lattice_n out of range");
+    if (leaf < 2 || leaf > 64) return fail(HLU_ERR_ARG, "leaf must be in [2, 64]");
+    if (!(eta > 0)) return fail(HLU_ERR_ARG, "eta must be > 0");
+    double e2 = eta * eta;
+    int64_t eta2 = (int64_t)std::llround(e2);
+    if (std::fabs(e2 - (double)eta2) > 1e-12) return fail(HLU_ERR_ARG, "eta^2 must be an integer");
+    if (!(eps > 0) || !(kappa > 0)) return fail(HLU_ERR_ARG, "eps and kappa must be > 0");
+    if (rank_cap <= 0) rank_cap = 32;
+    if (rank_cap > kTruncWidthMax / 2) return fail(HLU_ERR_ARG, "rank_cap too large");
+    if (leaf > kTruncWidthMax / 2 && leaf > rank_cap) return fail(HLU_ERR_ARG, "leaf too large for this build");
+    cudaStream_t s = (cudaStream_t)stream;
+    hlu_handle* h = new hlu_handle();
+    h->n = n;
+    h->leaf = leaf;
+    h->kappa = kappa;
+    h->eta = eta;
+    h->eta2 = eta2;
+    h->eps = eps;
+    h->rank_cap = rank_cap;
+    std::memset(&h->info, 0, sizeof(h->info));
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char* w) {
+      int rc = cuda_fail(err, w);
+      hlu_destroy(h);
+      return rc;
+    };
+    if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return bail(e, "event");
+    if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return bail(e, "event");
+    if ((e = build_mesh_dofs(n, s, h->mesh)) != cudaSuccess) return bail(e, "mesh");
+    if ((e = assemble_csr(h->mesh, kappa, s, h->A)) != cudaSuccess) return bail(e, "assembly");
+    const int64_t N = h->A.N;
+    if ((e = cudaMalloc(&h->d_perm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "perm");
+    if ((e = cudaMalloc(&h->d_iperm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "iperm");
+    if ((e = build_trees(h->mesh, leaf, eta2, s, h->trees, h->d_perm)) != cudaSuccess) return bail(e, "trees");
+    if ((e = invert_perm((int32_t)N, h->d_perm, h->d_iperm, s)) != cudaSuccess) return bail(e, "iperm");
+    trees_from_export(h->trees.nc, h->trees.clusters.data(), h->trees.nb, h->trees.blocks.data(), h->C, h->B);
+    build_schedules(h->C, h->B, rank_cap, 16, h->L, h->F, h->S, h->st);
+    if (h->L.wmax > kTruncWidthMax) {
+      hlu_destroy(h);
+      return fail(HLU_ERR_ARG, "truncation width exceeds this build's limit");
+    }
+    if ((e = h->dF.load(h->F)) != cudaSuccess) return bail(e, "upload factor schedule");
+    if ((e = h->dS.load(h->S)) != cudaSuccess) return bail(e, "upload solve schedule");
+    // A_H fill descriptors
+    std::vector<FillDesc> fd, fl;
+    int64_t rows = 0;
+    for (size_t b = 0; b < h->B.size(); ++b) {
+      const Block& bk = h->B[b];
+      if (bk.kind == KIND_SUB) continue;
+      FillDesc f;
+      std::memset(&f, 0, sizeof(f));
+      f.roff = h->C[bk.row].off;
+      f.m = h->C[bk.row].size;
+      f.coff = h->C[bk.col].off;
+      f.n = h->C[bk.col].size;
+      if (bk.kind == KIND_DENSE) {
+        f.off = h->L.dense_off[b];
+        f.row_prefix = rows;
+        rows += f.m;
+        fd.push_back(f);
+      } else {
+        f.off = h->L.x_off[b];
+        f.off2 = h->L.y_off[b];
+        f.slot = h->L.slot[b];
+        f.cap = h->L.cap[b];
+        fl.push_back(f);
+      }
+    }
+    h->n_fill_dense = (int32_t)fd.size();
+    h->n_fill_lr = (int32_t)fl.size();
+    h->dense_rows = rows;
+    if ((e = upload(&h->d_fill_dense, fd)) != cudaSuccess) return bail(e, "fill desc");
+    if ((e = upload(&h->d_fill_lr, fl)) != cudaSuccess) return bail(e, "fill desc");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "sync");
+    h->info.n_tasks = h->st.n_factor_tasks;
+    h->info.n_solve_tasks = h->st.n_solve_tasks;
+    h->info.schedule_ms = h->st.host_ms;
+    h->info.n_clusters = h->trees.nc;
+    h->info.n_blocks = h->trees.nb;
+    for (const Block& bk : h->B) {
+      h->info.n_adm += bk.kind == KIND_ADM;
+      h->info.n_dense += bk.kind == KIND_DENSE;
+    }
+    *out = h;
+    return HLU_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(HLU_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_export_trees(const hlu_handle* h, int32_t* perm, int32_t* clusters, int32_t* blocks, int64_t* sizes) {
+  if (!h || !sizes) return fail(HLU_ERR_ARG, "null argument");
+  sizes[0] = h->trees.nc;
+  sizes[1] = h->trees.nb;
+  if (perm) std::memcpy(perm, h->trees.perm.data(), sizeof(int32_t) * h->trees.perm.size());
+  if (clusters) std::memcpy(clusters, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
+  if (blocks) std::memcpy(blocks, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
+  return HLU_OK;
+}
+
+int hlu_export_csr(const hlu_handle* h, int64_t* rowptr, int32_t* col, double* val, int64_t* nnz) {
+  if (!h || !nnz) return fail(HLU_ERR_ARG, "null argument");
+  *nnz = h->A.nnz;
+  if (rowptr) CKR(cudaMemcpy(rowptr, h->A.rowptr, sizeof(int64_t) * (h->A.N + 1), cudaMemcpyDeviceToHost), "csr");
+  if (col) CKR(cudaMemcpy(col, h->A.col, sizeof(int32_t) * h->A.nnz, cudaMemcpyDeviceToHost), "csr");
+  if (val) CKR(cudaMemcpy(val, h->A.val, sizeof(double) * h->A.nnz, cudaMemcpyDeviceToHost), "csr");
+  return HLU_OK;
+}
+
+int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream) {
+  if (!h || !b_dev) return fail(HLU_ERR_ARG, "null argument");
+  CKR(manufactured_rhs(h->mesh, h->kappa, b_dev, (cudaStream_t)stream), "rhs");
+  return HLU_OK;
+}
+
+int hlu_spmv(const hlu_handle* h, const double* x, double* y, int32_t nrhs, int64_t ld, void* stream) {
+  if (!h || !x || !y || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
+  CKR(spmv(h->A.rowptr, h->A.col, h->A.val, h->A.N, x, ld, y, ld, nrhs, (cudaStream_t)stream), "spmv");
+  return HLU_OK;
+}
+
+int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision) {
+  if (!h || (precision != HLU_FP64 && precision != HLU_FP32)) return -1;
+  int es = esize(precision);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (int64_t)sms * 2;
+  return h->L.total * es + grid * scratch_stride_elems(h->L) * es + (int64_t)h->L.n_slots * 4 + h->L.piv_total * 4;
+}
+
+int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
+  try {
+    if (!h) return fail(HLU_ERR_ARG, "null handle");
+    if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int es = esize(precision);
+    if (h->precision != precision) {
+      free_factor(h);
+      int dev = 0;
+      CKR(cudaGetDevice(&dev), "device");
+      int sms = 0;
+      CKR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sms");
+      int bps = precision == HLU_FP64 ? blocks_per_sm<double>() : blocks_per_sm<float>();
+      if (bps < 1) return fail(HLU_ERR_CUDA, "executor does not fit on an SM");
+      h->grid = sms * bps;
+      h->scratch_stride = scratch_stride_elems(h->L);
+      h->arena_elems = h->L.total;
+      CKR(cudaMalloc(&h->d_arena, (size_t)es * h->L.total), "arena");
+      CKR(cudaMalloc(&h->d_ranks, sizeof(int32_t) * std::max(h->L.n_slots, 1)), "ranks");
+      CKR(cudaMalloc(&h->d_piv, sizeof(int32_t) * std::max<int64_t>(h->L.piv_total, 1)), "piv");
+      CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
+      CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 4), "status");
+      CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
+      CKR(cudaMalloc(&h->d_ticket, sizeof(unsigned long long)), "ticket");
+      CKR(cudaMalloc(&h->d_arenas, sizeof(void*)), "ptrs");
+      CKR(cudaMalloc(&h->d_rankp, sizeof(int32_t*)), "ptrs");
+      CKR(cudaMalloc(&h->d_pivp, sizeof(int32_t*)), "ptrs");
+      CKR(cudaMemcpy(h->d_arenas, &h->d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptrs");
+      CKR(cudaMemcpy(h->d_rankp, &h->d_ranks, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
+      CKR(cudaMemcpy(h->d_pivp, &h->d_piv, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
+      h->precision = precision;
+    }
+    CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
+    int32_t st0[4] = {0, -1, 0, 0};
+    CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
+    cudaError_t e;
+    if (precision == HLU_FP64)
+      e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, h->d_fill_dense, h->n_fill_dense, h->dense_rows, h->d_fill_lr,
+                          h->n_fill_lr, (double*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
+                          h->d_status, s);
+    else
+      e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, h->d_fill_dense, h->n_fill_dense, h->dense_rows, h->d_fill_lr,
+                         h->n_fill_lr, (float*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
+                         h->d_status, s);
+    CKR(e, "A_H fill");
+    int32_t stf[4];
+    int rc = read_status(h, s, stf);
+    if (rc) return rc;
+    CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
+    CKR(cudaEventRecord(h->ev0, s), "event");
+    rc = exec_run(h, h->dF, h->grid, s, true);
+    if (rc) return rc;
+    CKR(cudaEventRecord(h->ev1, s), "event");
+    rc = read_status(h, s, stf);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->info.factor_ms = ms;
+    h->info.rank_cap_hits = stf[2];
+    double fl = 0;
+    CKR(cudaMemcpy(&fl, h->d_flops, sizeof(double), cudaMemcpyDeviceToHost), "flops");
+    h->info.flops = fl;
+    std::vector<int32_t> rk(std::max(h->L.n_slots, 1));
+    CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
+    int64_t rsum = 0, nadm = 0;
+    int32_t rmax = 0;
+    for (size_t b = 0; b < h->B.size(); ++b)
+      if (h->B[b].kind == KIND_ADM) {
+        int32_t r = rk[h->L.slot[b]];
+        rmax = std::max(rmax, r);
+        rsum += r;
+        ++nadm;
+      }
+    h->info.rank_max = rmax;
+    h->info.rank_mean = nadm ? (double)rsum / nadm : 0.0;
+    h->info.factor_bytes = h->L.factor_elems * es;
+    h->info.workspace_bytes = (h->L.total - h->L.factor_elems) * es + h->scratch_stride * h->grid * es;
+    return rc;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info) {
+  if (!h || !info) return fail(HLU_ERR_ARG, "null argument");
+  *info = h->info;
+  return HLU_OK;
+}
+
+int hlu_solve(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream) {
+  if (!h || !b || !x || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
+  if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+  return solve_any(h, b, x, nrhs, ld, (cudaStream_t)stream);
+}
+
+int gmres_solve(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, int32_t restart,
+                double tol, int32_t maxit, int32_t flexible, hlu_stats* stats, void* stream) {
+  (void)flexible;  // the flexible (stored z_j) form is used in every case
+  try {
+    hlu_handle* h = const_cast<hlu_handle*>(hc);
+    if (!h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
+      return fail(HLU_ERR_ARG, "bad argument");
+    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->converged = 1;
+      stats->nrhs = nrhs;
+    }
+    int worst = HLU_OK;
+    for (int32_t c0 = 0; c0 < nrhs; c0 += h->L.nrhs_max) {
+      int nr = std::min(h->L.nrhs_max, nrhs - c0);
+      int rc = gmres_chunk(h, b + c0 * ld, x + c0 * ld, nr, ld, restart, tol, maxit, stats, s);
+      if (rc == HLU_ERR_NOT_CONVERGED)
+        worst = rc;
+      else if (rc)
+        return rc;
+    }
+    if (stats)
+      stats->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return worst;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, double tol,
+                   int32_t maxit, hlu_stats* stats, void* stream) {
+  try {
+    hlu_handle* h = const_cast<hlu_handle*>(hc);
+    if (!h || !b || !x || nrhs < 1 || ld < h->A.N || !(tol > 0) || maxit < 1) return fail(HLU_ERR_ARG, "bad argument");
+    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = ensure_kw(h, 1, std::min(nrhs, h->L.nrhs_max));
+    if (rc) return rc;
+    KrylovWS& k = h->kw;
+    const int64_t N = h->A.N;
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->nrhs = nrhs;
+      stats->converged = 1;
+    }
+    for (int32_t c0 = 0; c0 < nrhs; c0 += h->L.nrhs_max) {
+      int nr = std::min(h->L.nrhs_max, nrhs - c0);
+      const double* bc = b + c0 * ld;
+      double* xc = x + c0 * ld;
+      std::vector<double> bn(nr), rn(nr);
+      for (int r = 0; r < nr; ++r) CKR(cudaMemsetAsync(xc + r * ld, 0, sizeof(double) * N, s), "x0");
+      rc = col_norms(h, bc, ld, nr, k.bn, bn.data(), s);
+      if (rc) return rc;
+      int it = 0;
+      bool conv = false;
+      while (it < maxit) {
+        ++it;
+        CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, xc, ld, bc, ld, k.W, N, nr, s), "residual");
+        rc = col_norms(h, k.W, N, nr, k.hn, rn.data(), s);
+        if (rc) return rc;
+        rc = solve_any(h, k.W, k.tmp, nr, N, s);
+        if (rc) return rc;
+        // x += M^-1 r
+        std::vector<double> one(nr, -1.0);
+        CKR(cudaMemcpyAsync(k.h1, one.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, s), "ones");
+        CKR(multiaxpy(N, k.tmp, N, 1, k.h1, 1, xc, ld, nr, s), "update");
+        if (stats) stats->precond_applies++;
+        conv = true;
+        for (int r = 0; r < nr; ++r) conv = conv && (bn[r] == 0 || rn[r] < tol * bn[r]);
+        if (conv) break;
+      }
+      CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, xc, ld, bc, ld, k.W, N, nr, s), "residual");
+      rc = col_norms(h, k.W, N, nr, k.hn, rn.data(), s);
+      if (rc) return rc;
+      if (stats) {
+        stats->iterations = std::max(stats->iterations, it);
+        for (int r = 0; r < nr; ++r) {
+          stats->abs_res_max = std::max(stats->abs_res_max, rn[r]);
+          stats->relres_max = std::max(stats->relres_max, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+        }
+        stats->converged = stats->converged && conv;
+      }
+    }
+    if (stats)
+      stats->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return (stats && !stats->converged) ? fail(HLU_ERR_NOT_CONVERGED, "Richardson reached maxit") : HLU_OK;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream) {
+  if (!hs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
+  for (int32_t i = 0; i < count; ++i) {
+    int rc = hlu_factor(hs[i], precision, stream);
+    if (rc) return rc;
+  }
+  return HLU_OK;
+}
+
+int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b, double* const* x,
+                    const int32_t* nrhs, void* stream) {
+  if (!hs || !b || !x || !nrhs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
+  for (int32_t i = 0; i < count; ++i) {
+    int rc = hlu_solve(hs[i], b[i], x[i], nrhs[i], hs[i] ? hs[i]->A.N : 0, stream);
+    if (rc) return rc;
+  }
+  return HLU_OK;
+}
+
+}  // extern "C"
+
+// Fault injection for the bounded device waits: a two-task schedule in which
+// task 0 waits for task 1, run by a single CTA.  Task 1 can only start after
+// task 0, so the wait can never be satisfied; it must run out after limit_ms,
+// set HLU_ERR_TIMEOUT and let the kernel return.
+extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
+  if (!status_out || !(limit_ms > 0) || limit_ms > 5000) return fail(HLU_ERR_ARG, "bad argument");
+  Schedule S;
+  Task t;
+  std::memset(&t, 0, sizeof(t));
+  t.type = TK_NUM;  // no work
+  t.out_slot = -1;
+  S.tasks = {t, t};
+  S.pred_ptr = {0, 1, 1};
+  S.pred_idx = {1};
+  hlu_handle h;
+  h.precision = HLU_FP32;
+  DevSched ds;
+  CKR(ds.load(S), "upload");
+  CKR(cudaMalloc(&h.d_status, sizeof(int32_t) * 4), "alloc");
+  CKR(cudaMalloc(&h.d_ticket, sizeof(unsigned long long)), "alloc");
+  // valid (unused) per-problem pointers: the two tasks do no work
+  CKR(cudaMalloc(&h.d_arena, 256), "alloc");
+  CKR(cudaMalloc(&h.d_arenas, sizeof(void*)), "alloc");
+  CKR(cudaMalloc(&h.d_rankp, sizeof(int32_t*)), "alloc");
+  CKR(cudaMalloc(&h.d_pivp, sizeof(int32_t*)), "alloc");
+  CKR(cudaMemcpy(h.d_arenas, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
+  CKR(cudaMemcpy(h.d_rankp, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
+  CKR(cudaMemcpy(h.d_pivp, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
+  double saved = g_wait_limit_ms;
+  g_wait_limit_ms = limit_ms;
+  int rc = exec_run(&h, ds, 1, nullptr, false);
+  g_wait_limit_ms = saved;
+  int32_t st[4] = {0, 0, 0, 0};
+  if (!rc) rc = read_status(&h, nullptr, st);
+  status_out[0] = st[0];
+  status_out[1] = st[1];
+  ds.free_all();
+  for (void* p : {(void*)h.d_status, (void*)h.d_ticket, (void*)h.d_arena, (void*)h.d_arenas, (void*)h.d_rankp,
+                  (void*)h.d_pivp})
+    cudaFree(p);
+  h.d_status = nullptr;
+  h.d_ticket = nullptr;
+  h.d_arena = nullptr;
+  h.d_arenas = nullptr;
+  h.d_rankp = nullptr;
+  h.d_pivp = nullptr;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "after timeout test");
+  return rc;
+}

@@ -1,0 +1,893 @@
+// Build-phase kernels (Algorithm 1 step I and the structures it needs):
+//   * Kuhn-cube mesh and interior-edge DOF numbering (Sec. 2.1: one DOF per
+//     interior edge, sigma(Phi_i, e_j) = delta_ij, boundary edges carry E x n = 0);
+//   * FP64 assembly of A = K - kappa^2 M (Sec. 2.1 weak form and
+//     stiffness-matrix equation) into CSR;
+//   * load vector b_j = <J, Phi_j> of the manufactured field;
+//   * geometric cluster tree (Sec. 4, geometrically balanced bisection) and the
+//     eta-admissible block tree (Sec. 3-4), integer-exact, level by level;
+//   * A_H: dense leaves and exact low-rank admissible blocks from the CSR matrix.
+//
+// Mesh readings: vertex (i,j,k) has id (i(n+1)+j)(n+1)+k; every Kuhn edge goes
+// from a vertex v to v + d, d one of the 7 nonzero 0/1 vectors, so the edges
+// sorted by (lo, hi) are enumerated vertex by vertex with d ordered by the id
+// offset: 001, 010, 011, 100, 101, 110, 111.  An edge is a boundary edge iff
+// some axis a has d_a = 0 and v_a in {0, n}.
+#include <cuda_runtime.h>
+#include <thrust/device_ptr.h>
+#include <thrust/execution_policy.h>
+#include <thrust/reduce.h>
+#include <thrust/scan.h>
+#include <thrust/sequence.h>
+#include <thrust/sort.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "build.h"
+
+namespace hlu {
+
+__constant__ int c_dir[7][3] = {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {1, 0, 0},
+                                {1, 0, 1}, {1, 1, 0}, {1, 1, 1}};
+// Kuhn tetrahedra: axis permutations in lexicographic order
+__constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+__constant__ int c_ledge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+__device__ __forceinline__ void vcoord(int64_t v, int n, int* p) {
+  p[2] = (int)(v % (n + 1));
+  v /= (n + 1);
+  p[1] = (int)(v % (n + 1));
+  p[0] = (int)(v / (n + 1));
+}
+
+// ---------------------------------------------------------------- DOFs
+__global__ void k_count_edges(int n, int32_t* cnt) {
+  int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    int p[3];
+    vcoord(v, n, p);
+    int c = 0;
+    for (int d = 0; d < 7; ++d) {
+      bool ok = true, bnd = false;
+      for (int a = 0; a < 3; ++a) {
+        if (p[a] + c_dir[d][a] > n) ok = false;
+        if (c_dir[d][a] == 0 && (p[a] == 0 || p[a] == n)) bnd = true;
+      }
+      c += (ok && !bnd);
+    }
+    cnt[v] = c;
+  }
+}
+
+__global__ void k_number_edges(int n, const int32_t* start, int32_t* dofmap, int32_t* edges, int32_t* pts) {
+  int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    int p[3];
+    vcoord(v, n, p);
+    int32_t dof = start[v];
+    for (int d = 0; d < 7; ++d) {
+      bool ok = true, bnd = false;
+      for (int a = 0; a < 3; ++a) {
+        if (p[a] + c_dir[d][a] > n) ok = false;
+        if (c_dir[d][a] == 0 && (p[a] == 0 || p[a] == n)) bnd = true;
+      }
+      if (ok && !bnd) {
+        int64_t w = v + (int64_t)c_dir[d][0] * (n + 1) * (n + 1) + c_dir[d][1] * (n + 1) + c_dir[d][2];
+        dofmap[v * 7 + d] = dof;
+        edges[2 * (int64_t)dof] = (int32_t)v;
+        edges[2 * (int64_t)dof + 1] = (int32_t)w;
+        for (int a = 0; a < 3; ++a) pts[3 * (int64_t)dof + a] = 2 * p[a] + c_dir[d][a];
+        ++dof;
+      } else {
+        dofmap[v * 7 + d] = -1;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int dir_index(int dx, int dy, int dz) {
+  int code = dx * 4 + dy * 2 + dz;  // 1..7 -> index in c_dir order
+  return code - 1;
+}
+
+struct TetGeo {
+  int64_t v[4];
+  double P[4][3];
+  double G[4][3];
+  double vol;
+  int dof[6];
+  int lo[6], hi[6];  // oriented local vertex pair of each local edge
+};
+
+__device__ void tet_geometry(int64_t t, int n, const int32_t* dofmap, TetGeo& g) {
+  int64_t cube = t / 6;
+  int pi = (int)(t % 6);
+  int c[3];
+  c[2] = (int)(cube % n);
+  c[1] = (int)((cube / n) % n);
+  c[0] = (int)(cube / ((int64_t)n * n));
+  int p[3] = {c[0], c[1], c[2]};
+  int L[4][3];
+  for (int a = 0; a < 3; ++a) L[0][a] = p[a];
+  for (int s = 0; s < 3; ++s) {
+    for (int a = 0; a < 3; ++a) L[s + 1][a] = L[s][a];
+    L[s + 1][c_perm[pi][s]] += 1;
+  }
+  for (int s = 0; s < 4; ++s) {
+    g.v[s] = ((int64_t)L[s][0] * (n + 1) + L[s][1]) * (n + 1) + L[s][2];
+    for (int a = 0; a < 3; ++a) g.P[s][a] = (double)L[s][a] / (double)n;
+  }
+  double J[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 3; ++s) J[a][s] = g.P[s + 1][a] - g.P[0][a];  // columns p_s - p_0
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int a = 0; a < 3; ++a) {
+    g.G[0][a] = 0;
+    for (int s = 0; s < 3; ++s) {
+      g.G[s + 1][a] = inv[s][a];  // rows of J^-1
+      g.G[0][a] -= inv[s][a];
+    }
+  }
+  g.vol = fabs(det) / 6.0;
+  for (int e = 0; e < 6; ++e) {
+    int a = c_ledge[e][0], b = c_ledge[e][1];
+    if (g.v[a] > g.v[b]) {
+      int tmp = a;
+      a = b;
+      b = tmp;
+    }
+    g.lo[e] = a;
+    g.hi[e] = b;
+    int d[3];
+    for (int x = 0; x < 3; ++x) d[x] = L[b][x] - L[a][x];
+    int di = dir_index(d[0], d[1], d[2]);
+    g.dof[e] = (di >= 0 && di < 7) ? dofmap[g.v[a] * 7 + di] : -1;
+  }
+}
+
+__device__ __forceinline__ double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// one thread per tetrahedron: 36 (key, value) pairs, key = row * N + col or
+// INT64_MAX for pairs that touch a boundary edge
+__global__ void k_element_coo(int n, double kappa2, int64_t N, const int32_t* dofmap, int64_t* keys, double* vals) {
+  int64_t nt = (int64_t)6 * n * n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    TetGeo g;
+    tet_geometry(t, n, dofmap, g);
+    for (int r = 0; r < 6; ++r) {
+      int a = g.lo[r], b = g.hi[r];
+      double ca[3];
+      cross3(g.G[a], g.G[b], ca);
+      for (int s = 0; s < 6; ++s) {
+        int cc = g.lo[s], d = g.hi[s];
+        double cb[3];
+        cross3(g.G[cc], g.G[d], cb);
+        double K = 4.0 * g.vol * dot3(ca, cb);
+        auto mom = [&](int i, int j) { return g.vol * (i == j ? 2.0 : 1.0) / 20.0; };
+        double M = mom(a, cc) * dot3(g.G[b], g.G[d]) - mom(a, d) * dot3(g.G[b], g.G[cc]) -
+                   mom(b, cc) * dot3(g.G[a], g.G[d]) + mom(b, d) * dot3(g.G[a], g.G[cc]);
+        int64_t o = t * 36 + r * 6 + s;
+        if (g.dof[r] >= 0 && g.dof[s] >= 0) {
+          keys[o] = (int64_t)g.dof[r] * N + g.dof[s];
+          vals[o] = K - kappa2 * M;
+        } else {
+          keys[o] = INT64_MAX;
+          vals[o] = 0.0;
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_csr_rows(int64_t nnz, int64_t N, const int64_t* ukeys, int32_t* col, int32_t* rowcnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = ukeys[e];
+    col[e] = (int32_t)(k % N);
+    atomicAdd(rowcnt + (k / N), 1);
+  }
+}
+
+// load vector: one thread per tetrahedron, 6 (dof, value) pairs
+__global__ void k_rhs_coo(int n, double kappa2, const int32_t* dofmap, int32_t* keys, double* vals) {
+  int64_t nt = (int64_t)6 * n * n * n;
+  const double qa = (5.0 - sqrt(5.0)) / 20.0, qb = (5.0 + 3.0 * sqrt(5.0)) / 20.0;
+  const double PI = 3.14159265358979323846;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    TetGeo g;
+    tet_geometry(t, n, dofmap, g);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) {
+      double lam[4] = {qa, qa, qa, qa};
+      lam[q] = qb;
+      double x[3] = {0, 0, 0};
+      for (int s = 0; s < 4; ++s)
+        for (int a = 0; a < 3; ++a) x[a] += lam[s] * g.P[s][a];
+      double sx = sin(PI * x[0]), sy = sin(PI * x[1]), sz = sin(PI * x[2]);
+      double f = 2.0 * PI * PI - kappa2;
+      double J[3] = {f * sy * sz, f * sz * sx, f * sx * sy};
+      for (int e = 0; e < 6; ++e) {
+        int a = g.lo[e], b = g.hi[e];
+        double phi[3];
+        for (int c = 0; c < 3; ++c) phi[c] = lam[a] * g.G[b][c] - lam[b] * g.G[a][c];
+        acc[e] += dot3(J, phi);
+      }
+    }
+    for (int e = 0; e < 6; ++e) {
+      keys[t * 6 + e] = g.dof[e] >= 0 ? g.dof[e] : INT32_MAX;
+      vals[t * 6 + e] = g.vol / 4.0 * acc[e];
+    }
+  }
+}
+
+__global__ void k_scatter_rhs(int64_t m, const int32_t* ukeys, const double* sums, int64_t N, double* b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t k = ukeys[e];
+    if (k >= 0 && k < N) b[k] = sums[e];
+  }
+}
+
+// ---------------------------------------------------------------- cluster tree
+// One CTA per cluster of the current level: tight bounding box of its points.
+__global__ void k_cluster_bbox(int32_t nc, const int32_t* off, const int32_t* size, const int32_t* perm,
+                               const int32_t* pts, int32_t* lo, int32_t* hi) {
+  __shared__ int32_t s[6][32];
+  for (int32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    int32_t mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int32_t i = threadIdx.x; i < size[c]; i += blockDim.x) {
+      int32_t d = perm[off[c] + i];
+      for (int a = 0; a < 3; ++a) {
+        int32_t v = pts[3 * (int64_t)d + a];
+        mn[a] = min(mn[a], v);
+        mx[a] = max(mx[a], v);
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int o = 16; o > 0; o >>= 1) {
+        mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+        mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+      }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+      for (int a = 0; a < 3; ++a) {
+        s[a][w] = mn[a];
+        s[3 + a][w] = mx[a];
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int a = 0; a < 3; ++a) {
+        int32_t m0 = INT32_MAX, m1 = INT32_MIN;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+          m0 = min(m0, s[a][k]);
+          m1 = max(m1, s[3 + a][k]);
+        }
+        lo[3 * (int64_t)c + a] = size[c] ? m0 : 0;
+        hi[3 * (int64_t)c + a] = size[c] ? m1 : 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA per cluster: stable partition by 2 p[ax] < lo[ax] + hi[ax] (leaves copy).
+__global__ void k_cluster_split(int32_t nc, int32_t leaf, const int32_t* off, const int32_t* size, const int32_t* lo,
+                                const int32_t* hi, const int32_t* perm_in, int32_t* perm_out, const int32_t* pts,
+                                int32_t* nleft) {
+  __shared__ int32_t s_scan[1024];
+  __shared__ int32_t s_base[2];
+  for (int32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    const int32_t o = off[c], sz = size[c];
+    if (sz <= leaf) {
+      for (int32_t i = threadIdx.x; i < sz; i += blockDim.x) perm_out[o + i] = perm_in[o + i];
+      if (threadIdx.x == 0) nleft[c] = -1;
+      __syncthreads();
+      continue;
+    }
+    int ax = 0;
+    int32_t e0 = hi[3 * (int64_t)c] - lo[3 * (int64_t)c];
+    for (int a = 1; a < 3; ++a) {
+      int32_t e = hi[3 * (int64_t)c + a] - lo[3 * (int64_t)c + a];
+      if (e > e0) {
+        e0 = e;
+        ax = a;
+      }
+    }
+    const int32_t mid2 = lo[3 * (int64_t)c + ax] + hi[3 * (int64_t)c + ax];
+    // count left points
+    int32_t cntl = 0;
+    for (int32_t i = threadIdx.x; i < sz; i += blockDim.x) cntl += (2 * pts[3 * (int64_t)perm_in[o + i] + ax] < mid2);
+    s_scan[threadIdx.x] = cntl;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if ((int)threadIdx.x < st) s_scan[threadIdx.x] += s_scan[threadIdx.x + st];
+      __syncthreads();
+    }
+    const int32_t total_left = s_scan[0];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_base[0] = 0;
+      s_base[1] = 0;
+      nleft[c] = total_left;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < sz; base += blockDim.x) {
+      int32_t i = base + threadIdx.x;
+      int32_t d = i < sz ? perm_in[o + i] : 0;
+      int32_t f = (i < sz) && (2 * pts[3 * (int64_t)d + ax] < mid2);
+      // inclusive scan of f over the block
+      s_scan[threadIdx.x] = f;
+      __syncthreads();
+      for (int st = 1; st < (int)blockDim.x; st <<= 1) {
+        int32_t v = (int)threadIdx.x >= st ? s_scan[threadIdx.x - st] : 0;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+      }
+      int32_t incl = s_scan[threadIdx.x];
+      int32_t chunk_left = s_scan[blockDim.x - 1];
+      if (i < sz) {
+        if (f)
+          perm_out[o + s_base[0] + incl - 1] = d;
+        else
+          perm_out[o + total_left + s_base[1] + (threadIdx.x - incl)] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int32_t nvalid = min((int32_t)blockDim.x, sz - base);
+        s_base[0] += chunk_left;
+        s_base[1] += nvalid - chunk_left;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// next level's clusters from the split results (single CTA, sequential scan)
+__global__ void k_cluster_children(int32_t nc, int32_t first_id, const int32_t* off, const int32_t* size,
+                                   const int32_t* nleft, int32_t* son, int32_t* noff, int32_t* nsize,
+                                   int32_t* nparent, int32_t* count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int32_t k = 0;
+  for (int32_t c = 0; c < nc; ++c) {
+    if (nleft[c] <= 0 || nleft[c] >= size[c]) {  // leaf (or a degenerate box that cannot split)
+      son[2 * c] = son[2 * c + 1] = -1;
+      continue;
+    }
+    noff[k] = off[c];
+    nsize[k] = nleft[c];
+    nparent[k] = first_id + c;
+    noff[k + 1] = off[c] + nleft[c];
+    nsize[k + 1] = size[c] - nleft[c];
+    nparent[k + 1] = first_id + c;
+    son[2 * c] = k;
+    son[2 * c + 1] = k + 1;
+    k += 2;
+  }
+  *count = k;
+}
+
+// ---------------------------------------------------------------- block tree
+__device__ __forceinline__ int64_t diam2(const int32_t* lo, const int32_t* hi, int32_t c) {
+  int64_t s = 0;
+  for (int a = 0; a < 3; ++a) {
+    int64_t d = (int64_t)hi[3 * c + a] - lo[3 * c + a];
+    s += d * d;
+  }
+  return s;
+}
+__device__ __forceinline__ int64_t dist2(const int32_t* lo, const int32_t* hi, int32_t t, int32_t s) {
+  int64_t r = 0;
+  for (int a = 0; a < 3; ++a) {
+    int64_t g1 = (int64_t)lo[3 * s + a] - hi[3 * t + a];
+    int64_t g2 = (int64_t)lo[3 * t + a] - hi[3 * s + a];
+    int64_t g = g1 > g2 ? g1 : g2;
+    if (g < 0) g = 0;
+    r += g * g;
+  }
+  return r;
+}
+
+// classify the blocks of one level; sub-divided blocks count 4 children
+__global__ void k_block_classify(int32_t nb, const int32_t* brow, const int32_t* bcol, const int32_t* clo,
+                                 const int32_t* chi, const int32_t* cson, int64_t eta2, int32_t* kind,
+                                 int32_t* nchild) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    int32_t t = brow[b], s = bcol[b];
+    int64_t d2 = dist2(clo, chi, t, s);
+    int64_t dm = min(diam2(clo, chi, t), diam2(clo, chi, s));
+    int k;
+    if (d2 > 0 && dm <= eta2 * d2)
+      k = 0;
+    else if (cson[2 * t] < 0 || cson[2 * s] < 0)
+      k = 1;
+    else
+      k = 2;
+    kind[b] = k;
+    nchild[b] = k == 2 ? 4 : 0;
+  }
+}
+
+__global__ void k_block_expand(int32_t nb, const int32_t* brow, const int32_t* bcol, const int32_t* kind,
+                               const int32_t* cstart, const int32_t* cson, int32_t first_child_id,
+                               int32_t first_id, int32_t* bson, int32_t* nrow, int32_t* ncol, int32_t* npar) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    if (kind[b] != 2) {
+      for (int k = 0; k < 4; ++k) bson[4 * b + k] = -1;
+      continue;
+    }
+    int32_t t = brow[b], s = bcol[b];
+    int32_t k0 = cstart[b];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        int32_t k = k0 + 2 * i + j;
+        nrow[k] = cson[2 * t + i];
+        ncol[k] = cson[2 * s + j];
+        npar[k] = first_id + b;
+        bson[4 * b + 2 * i + j] = first_child_id + k;
+      }
+  }
+}
+
+// ---------------------------------------------------------------- DFS pre-order ids
+// Subtree sizes, bottom-up over one level of a tree stored level by level with
+// global (BFS) ids; children ids refer to the same global numbering.
+__global__ void k_subtree(int32_t first, int32_t cnt, int nsons, const int32_t* sons, int32_t* sub) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    int32_t g = first + i;
+    int32_t s = 1;
+    for (int k = 0; k < nsons; ++k) {
+      int32_t c = sons[nsons * (int64_t)g + k];
+      if (c >= 0) s += sub[c];
+    }
+    sub[g] = s;
+  }
+}
+__global__ void k_preorder(int32_t first, int32_t cnt, int nsons, const int32_t* sons, const int32_t* sub, int32_t* pre) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    int32_t g = first + i;
+    int32_t next = pre[g] + 1;
+    for (int k = 0; k < nsons; ++k) {
+      int32_t c = sons[nsons * (int64_t)g + k];
+      if (c < 0) continue;
+      pre[c] = next;
+      next += sub[c];
+    }
+  }
+}
+
+// export rows in DFS order
+__global__ void k_export_clusters(int32_t nc, const int32_t* pre, const int32_t* off, const int32_t* size,
+                                  const int32_t* lo, const int32_t* hi, const int32_t* son, const int32_t* level,
+                                  const int32_t* parent, int32_t* out) {
+  for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nc; g += gridDim.x * blockDim.x) {
+    int32_t* r = out + 12 * (int64_t)pre[g];
+    r[0] = off[g];
+    r[1] = size[g];
+    for (int a = 0; a < 3; ++a) {
+      r[2 + a] = lo[3 * (int64_t)g + a];
+      r[5 + a] = hi[3 * (int64_t)g + a];
+    }
+    r[8] = son[2 * g] >= 0 ? pre[son[2 * g]] : -1;
+    r[9] = son[2 * g + 1] >= 0 ? pre[son[2 * g + 1]] : -1;
+    r[10] = level[g];
+    r[11] = parent[g] >= 0 ? pre[parent[g]] : -1;
+  }
+}
+__global__ void k_export_blocks(int32_t nb, const int32_t* bpre, const int32_t* cpre, const int32_t* row,
+                                const int32_t* col, const int32_t* kind, const int32_t* son, const int32_t* parent,
+                                int32_t* out) {
+  for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nb; g += gridDim.x * blockDim.x) {
+    int32_t* r = out + 8 * (int64_t)bpre[g];
+    r[0] = cpre[row[g]];
+    r[1] = cpre[col[g]];
+    r[2] = kind[g];
+    for (int k = 0; k < 4; ++k) r[3 + k] = son[4 * (int64_t)g + k] >= 0 ? bpre[son[4 * (int64_t)g + k]] : -1;
+    r[7] = parent[g] >= 0 ? bpre[parent[g]] : -1;
+  }
+}
+
+// ---------------------------------------------------------------- A_H fill
+template <class T>
+__global__ void k_fill_dense(int32_t nblk, const FillDesc* d, const int32_t* perm, const int32_t* iperm,
+                             const int64_t* rowptr, const int32_t* col, const double* val, T* arena) {
+  // one warp per (block, row)
+  int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = gw;; w += nw) {
+    // map w -> (block, row) through the row prefix in the descriptors
+    int32_t lo = 0, hi = nblk;
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) / 2;
+      if (d[mid].row_prefix <= w)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    if (nblk == 0 || w >= d[nblk - 1].row_prefix + d[nblk - 1].m) return;
+    const FillDesc& f = d[lo];
+    int32_t i = (int32_t)(w - f.row_prefix);
+    int32_t orow = perm[f.roff + i];
+    for (int64_t e = rowptr[orow] + lane; e < rowptr[orow + 1]; e += 32) {
+      int32_t j = iperm[col[e]] - f.coff;
+      if (j >= 0 && j < f.n) arena[f.off + i + (int64_t)j * f.m] = (T)val[e];
+    }
+  }
+}
+
+// one CTA per admissible block: X = unit columns of the nonzero rows, Y^T = rows
+template <class T>
+__global__ void k_fill_lowrank(int32_t nblk, const FillDesc* d, const int32_t* perm, const int32_t* iperm,
+                               const int64_t* rowptr, const int32_t* col, const double* val, T* arena,
+                               int32_t* ranks, int32_t* status) {
+  __shared__ int32_t s_k;
+  __shared__ int32_t s_flag[256];
+  for (int32_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const FillDesc& f = d[b];
+    if (threadIdx.x == 0) s_k = 0;
+    __syncthreads();
+    for (int32_t base = 0; base < f.m; base += blockDim.x) {
+      int32_t i = base + threadIdx.x;
+      int32_t has = 0;
+      int32_t orow = 0;
+      if (i < f.m) {
+        orow = perm[f.roff + i];
+        for (int64_t e = rowptr[orow]; e < rowptr[orow + 1]; ++e) {
+          int32_t j = iperm[col[e]] - f.coff;
+          if (j >= 0 && j < f.n) {
+            has = 1;
+            break;
+          }
+        }
+      }
+      s_flag[threadIdx.x] = has;
+      __syncthreads();
+      // sequential rank positions in row order (nonzero rows are rare)
+      if (threadIdx.x == 0) {
+        int32_t k = s_k;
+        for (int q = 0; q < (int)blockDim.x; ++q)
+          if (s_flag[q]) s_flag[q] = ++k;
+        s_k = k;
+      }
+      __syncthreads();
+      if (has) {
+        int32_t kk = s_flag[threadIdx.x] - 1;
+        if (kk < f.cap) {
+          arena[f.off + i + (int64_t)kk * f.m] = T(1);
+          for (int64_t e = rowptr[orow]; e < rowptr[orow + 1]; ++e) {
+            int32_t j = iperm[col[e]] - f.coff;
+            if (j >= 0 && j < f.n) arena[f.off2 + j + (int64_t)kk * f.n] = (T)val[e];
+          }
+        } else {
+          atomicCAS(status, 0, 7);
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ranks[f.slot] = min(s_k, f.cap);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void k_identity(T* arena, int64_t off, int32_t n) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    arena[off + i + (int64_t)i * n] = T(1);
+}
+
+template __global__ void k_fill_dense<float>(int32_t, const FillDesc*, const int32_t*, const int32_t*, const int64_t*,
+                                            const int32_t*, const double*, float*);
+template __global__ void k_fill_dense<double>(int32_t, const FillDesc*, const int32_t*, const int32_t*, const int64_t*,
+                                             const int32_t*, const double*, double*);
+
+// ---------------------------------------------------------------- host drivers
+#define CK(x)                               \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+
+static int grid_for(int64_t n, int bs = 256) {
+  int64_t g = (n + bs - 1) / bs;
+  if (g < 1) g = 1;
+  if (g > 4096) g = 4096;
+  return (int)g;
+}
+
+cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m) {
+  int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  int32_t* cnt = nullptr;
+  CK(cudaMalloc(&cnt, sizeof(int32_t) * (nv + 1)));
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nv + 1), s));
+  k_count_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt);
+  thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(cnt),
+                         thrust::device_ptr<int32_t>(cnt + nv + 1), thrust::device_ptr<int32_t>(cnt));
+  int32_t N = 0;
+  CK(cudaMemcpyAsync(&N, cnt + nv, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  m.n = n;
+  m.N = N;
+  CK(cudaMalloc(&m.dofmap, sizeof(int32_t) * nv * 7));
+  CK(cudaMalloc(&m.edges, sizeof(int32_t) * 2 * (int64_t)N));
+  CK(cudaMalloc(&m.pts, sizeof(int32_t) * 3 * (int64_t)N));
+  k_number_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt, m.dofmap, m.edges, m.pts);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  cudaFree(cnt);
+  return cudaSuccess;
+}
+
+cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A) {
+  int64_t nt = (int64_t)6 * m.n * m.n * m.n;
+  int64_t ne = nt * 36;
+  int64_t* keys = nullptr;
+  double* vals = nullptr;
+  CK(cudaMalloc(&keys, sizeof(int64_t) * ne));
+  CK(cudaMalloc(&vals, sizeof(double) * ne));
+  k_element_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.N, m.dofmap, keys, vals);
+  CK(cudaGetLastError());
+  thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int64_t>(keys),
+                             thrust::device_ptr<int64_t>(keys + ne), thrust::device_ptr<double>(vals));
+  int64_t* ukeys = nullptr;
+  double* uvals = nullptr;
+  CK(cudaMalloc(&ukeys, sizeof(int64_t) * ne));
+  CK(cudaMalloc(&uvals, sizeof(double) * ne));
+  auto ends = thrust::reduce_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int64_t>(keys),
+                                    thrust::device_ptr<int64_t>(keys + ne), thrust::device_ptr<double>(vals),
+                                    thrust::device_ptr<int64_t>(ukeys), thrust::device_ptr<double>(uvals));
+  int64_t nu = ends.first - thrust::device_ptr<int64_t>(ukeys);
+  int64_t last = 0;
+  CK(cudaMemcpyAsync(&last, ukeys + nu - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int64_t nnz = (last == INT64_MAX) ? nu - 1 : nu;
+  A.N = m.N;
+  A.nnz = nnz;
+  CK(cudaMalloc(&A.rowptr, sizeof(int64_t) * (m.N + 1)));
+  CK(cudaMalloc(&A.col, sizeof(int32_t) * nnz));
+  CK(cudaMalloc(&A.val, sizeof(double) * nnz));
+  int32_t* rowcnt = nullptr;
+  CK(cudaMalloc(&rowcnt, sizeof(int32_t) * (m.N + 1)));
+  CK(cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * (m.N + 1), s));
+  k_csr_rows<<<grid_for(nnz), 256, 0, s>>>(nnz, m.N, ukeys, A.col, rowcnt);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(A.val, uvals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+  thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(rowcnt),
+                         thrust::device_ptr<int32_t>(rowcnt + m.N + 1), thrust::device_ptr<int64_t>(A.rowptr),
+                         (int64_t)0);
+  CK(cudaStreamSynchronize(s));
+  cudaFree(rowcnt);
+  cudaFree(keys);
+  cudaFree(vals);
+  cudaFree(ukeys);
+  cudaFree(uvals);
+  return cudaSuccess;
+}
+
+cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s) {
+  int64_t nt = (int64_t)6 * m.n * m.n * m.n;
+  int64_t ne = nt * 6;
+  int32_t* keys = nullptr;
+  double* vals = nullptr;
+  int32_t* uk = nullptr;
+  double* us = nullptr;
+  CK(cudaMallocAsync(&keys, sizeof(int32_t) * ne, s));
+  CK(cudaMallocAsync(&vals, sizeof(double) * ne, s));
+  CK(cudaMallocAsync(&uk, sizeof(int32_t) * ne, s));
+  CK(cudaMallocAsync(&us, sizeof(double) * ne, s));
+  k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
+  CK(cudaGetLastError());
+  thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(keys),
+                             thrust::device_ptr<int32_t>(keys + ne), thrust::device_ptr<double>(vals));
+  auto ends = thrust::reduce_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(keys),
+                                    thrust::device_ptr<int32_t>(keys + ne), thrust::device_ptr<double>(vals),
+                                    thrust::device_ptr<int32_t>(uk), thrust::device_ptr<double>(us));
+  int64_t nu = ends.first - thrust::device_ptr<int32_t>(uk);
+  CK(cudaMemsetAsync(b, 0, sizeof(double) * m.N, s));
+  k_scatter_rhs<<<grid_for(nu), 256, 0, s>>>(nu, uk, us, m.N, b);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(keys, s));
+  CK(cudaFreeAsync(vals, s));
+  CK(cudaFreeAsync(uk, s));
+  CK(cudaFreeAsync(us, s));
+  return cudaSuccess;
+}
+
+cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream_t s, HostTrees& out,
+                        int32_t* d_perm_out) {
+  const int32_t N = (int32_t)m.N;
+  // level-by-level cluster arrays with global BFS ids; generous capacity
+  int32_t cap = 2 * N + 16;  // a binary tree with at most N leaves
+  int32_t *off, *size, *lo, *hi, *son, *level, *parent, *nleft, *permA, *permB, *cnt;
+  CK(cudaMalloc(&off, sizeof(int32_t) * cap));
+  CK(cudaMalloc(&size, sizeof(int32_t) * cap));
+  CK(cudaMalloc(&lo, sizeof(int32_t) * 3 * cap));
+  CK(cudaMalloc(&hi, sizeof(int32_t) * 3 * cap));
+  CK(cudaMalloc(&son, sizeof(int32_t) * 2 * cap));
+  CK(cudaMalloc(&level, sizeof(int32_t) * cap));
+  CK(cudaMalloc(&parent, sizeof(int32_t) * cap));
+  CK(cudaMalloc(&nleft, sizeof(int32_t) * cap));
+  CK(cudaMalloc(&permA, sizeof(int32_t) * (N + 1)));
+  CK(cudaMalloc(&permB, sizeof(int32_t) * (N + 1)));
+  CK(cudaMalloc(&cnt, sizeof(int32_t)));
+  thrust::sequence(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(permA), thrust::device_ptr<int32_t>(permA + N));
+  int32_t h0[2] = {0, N};
+  CK(cudaMemcpyAsync(off, &h0[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(size, &h0[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  int32_t mone = -1, zero = 0;
+  CK(cudaMemcpyAsync(parent, &mone, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(level, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  std::vector<int32_t> level_first = {0}, level_cnt = {1};
+  int32_t first = 0, count = 1, lev = 0;
+  while (count > 0) {
+    if (first + count + 2 * count > cap) return cudaErrorMemoryAllocation;
+    k_cluster_bbox<<<std::min(count, 8192), 256, 0, s>>>(count, off + first, size + first, permA, m.pts, lo + 3 * first,
+                                                         hi + 3 * first);
+    // clusters that became leaves on earlier levels keep their order
+    CK(cudaMemcpyAsync(permB, permA, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    k_cluster_split<<<std::min(count, 8192), 1024, 0, s>>>(count, leaf, off + first, size + first, lo + 3 * first,
+                                                           hi + 3 * first, permA, permB, m.pts, nleft + first);
+    k_cluster_children<<<1, 1, 0, s>>>(count, first, off + first, size + first, nleft + first, son + 2 * first,
+                                       off + first + count, size + first + count, parent + first + count, cnt);
+    CK(cudaGetLastError());
+    int32_t nxt = 0;
+    CK(cudaMemcpyAsync(&nxt, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // son indices are level-local: make them global
+    if (nxt > 0) {
+      std::vector<int32_t> hs(2 * count);
+      CK(cudaMemcpy(hs.data(), son + 2 * first, sizeof(int32_t) * 2 * count, cudaMemcpyDeviceToHost));
+      for (auto& x : hs)
+        if (x >= 0) x += first + count;
+      CK(cudaMemcpy(son + 2 * first, hs.data(), sizeof(int32_t) * 2 * count, cudaMemcpyHostToDevice));
+      std::vector<int32_t> hl(nxt, lev + 1);
+      CK(cudaMemcpy(level + first + count, hl.data(), sizeof(int32_t) * nxt, cudaMemcpyHostToDevice));
+    }
+    std::swap(permA, permB);
+    first += count;
+    count = nxt;
+    ++lev;
+    if (count) {
+      level_first.push_back(first);
+      level_cnt.push_back(count);
+    }
+  }
+  const int32_t nc = first;
+  // DFS pre-order ids
+  int32_t *sub, *pre;
+  CK(cudaMalloc(&sub, sizeof(int32_t) * nc));
+  CK(cudaMalloc(&pre, sizeof(int32_t) * nc));
+  for (int l = (int)level_first.size() - 1; l >= 0; --l)
+    k_subtree<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub);
+  CK(cudaMemcpyAsync(pre, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  for (size_t l = 0; l < level_first.size(); ++l)
+    k_preorder<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub, pre);
+  int32_t* cl_export;
+  CK(cudaMalloc(&cl_export, sizeof(int32_t) * 12 * nc));
+  k_export_clusters<<<grid_for(nc), 256, 0, s>>>(nc, pre, off, size, lo, hi, son, level, parent, cl_export);
+  CK(cudaGetLastError());
+
+  // ---- block tree, level by level (global BFS ids)
+  int32_t bcap = 1 << 20;
+  int32_t *brow, *bcol, *bkind, *bson, *bpar, *nch, *cst;
+  auto balloc = [&](int32_t c) -> cudaError_t {
+    CK(cudaMalloc(&brow, sizeof(int32_t) * c));
+    CK(cudaMalloc(&bcol, sizeof(int32_t) * c));
+    CK(cudaMalloc(&bkind, sizeof(int32_t) * c));
+    CK(cudaMalloc(&bson, sizeof(int32_t) * 4 * (int64_t)c));
+    CK(cudaMalloc(&bpar, sizeof(int32_t) * c));
+    CK(cudaMalloc(&nch, sizeof(int32_t) * (c + 1)));
+    CK(cudaMalloc(&cst, sizeof(int32_t) * (c + 1)));
+    return cudaSuccess;
+  };
+  // capacity: blocks grow at most 4x per level; bound by an estimate, grow on demand
+  bcap = std::max<int32_t>(1 << 16, 64 * nc + 4096);
+  CK(balloc(bcap));
+  // cluster son array in BFS ids is `son`; boxes lo/hi in BFS ids
+  CK(cudaMemcpyAsync(brow, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bcol, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(bpar, &mone, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  std::vector<int32_t> bl_first = {0}, bl_cnt = {1};
+  int32_t bfirst = 0, bcount = 1;
+  while (bcount > 0) {
+    k_block_classify<<<grid_for(bcount), 256, 0, s>>>(bcount, brow + bfirst, bcol + bfirst, lo, hi, son, eta2,
+                                                      bkind + bfirst, nch + bfirst);
+    CK(cudaGetLastError());
+    thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(nch + bfirst),
+                           thrust::device_ptr<int32_t>(nch + bfirst + bcount), thrust::device_ptr<int32_t>(cst + bfirst));
+    int32_t lastc = 0, lastn = 0;
+    CK(cudaMemcpyAsync(&lastc, cst + bfirst + bcount - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&lastn, nch + bfirst + bcount - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int32_t nxt = lastc + lastn;
+    if (bfirst + bcount + nxt > bcap) return cudaErrorMemoryAllocation;
+    k_block_expand<<<grid_for(bcount), 256, 0, s>>>(bcount, brow + bfirst, bcol + bfirst, bkind + bfirst,
+                                                    cst + bfirst, son, bfirst + bcount, bfirst, bson + 4 * (int64_t)bfirst,
+                                                    brow + bfirst + bcount, bcol + bfirst + bcount,
+                                                    bpar + bfirst + bcount);
+    CK(cudaGetLastError());
+    bfirst += bcount;
+    bcount = nxt;
+    if (bcount) {
+      bl_first.push_back(bfirst);
+      bl_cnt.push_back(bcount);
+    }
+  }
+  const int32_t nb = bfirst;
+  int32_t *bsub, *bpre;
+  CK(cudaMalloc(&bsub, sizeof(int32_t) * nb));
+  CK(cudaMalloc(&bpre, sizeof(int32_t) * nb));
+  for (int l = (int)bl_first.size() - 1; l >= 0; --l)
+    k_subtree<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub);
+  CK(cudaMemcpyAsync(bpre, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  for (size_t l = 0; l < bl_first.size(); ++l)
+    k_preorder<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub, bpre);
+  int32_t* bl_export;
+  CK(cudaMalloc(&bl_export, sizeof(int32_t) * 8 * (int64_t)nb));
+  k_export_blocks<<<grid_for(nb), 256, 0, s>>>(nb, bpre, pre, brow, bcol, bkind, bson, bpar, bl_export);
+  CK(cudaGetLastError());
+  out.clusters.resize(12 * (size_t)nc);
+  out.blocks.resize(8 * (size_t)nb);
+  out.perm.resize(N);
+  CK(cudaMemcpyAsync(out.clusters.data(), cl_export, sizeof(int32_t) * 12 * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(out.blocks.data(), bl_export, sizeof(int32_t) * 8 * (int64_t)nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(out.perm.data(), permA, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(d_perm_out, permA, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  out.nc = nc;
+  out.nb = nb;
+  for (void* p : {(void*)off, (void*)size, (void*)lo, (void*)hi, (void*)son, (void*)level, (void*)parent,
+                  (void*)nleft, (void*)permA, (void*)permB, (void*)cnt, (void*)sub, (void*)pre, (void*)cl_export,
+                  (void*)brow, (void*)bcol, (void*)bkind, (void*)bson, (void*)bpar, (void*)nch, (void*)cst,
+                  (void*)bsub, (void*)bpre, (void*)bl_export})
+    cudaFree(p);
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t fill_ah(const DevCSR& A, const int32_t* d_perm, const int32_t* d_iperm, const FillDesc* d_dense,
+                    int32_t ndense, int64_t dense_rows, const FillDesc* d_lr, int32_t nlr, T* arena,
+                    int64_t zero_elems, int64_t ident_off, int32_t ident_n, int32_t* ranks, int32_t* status,
+                    cudaStream_t s) {
+  CK(cudaMemsetAsync(arena, 0, sizeof(T) * zero_elems, s));
+  k_identity<T><<<grid_for(ident_n), 256, 0, s>>>(arena, ident_off, ident_n);
+  if (ndense) {
+    int64_t warps = dense_rows;
+    int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 65535);
+    k_fill_dense<T><<<blocks, 256, 0, s>>>(ndense, d_dense, d_perm, d_iperm, A.rowptr, A.col, A.val, arena);
+  }
+  if (nlr) k_fill_lowrank<T><<<std::min(nlr, 65535), 256, 0, s>>>(nlr, d_lr, d_perm, d_iperm, A.rowptr, A.col, A.val, arena, ranks, status);
+  return cudaGetLastError();
+}
+
+template cudaError_t fill_ah<float>(const DevCSR&, const int32_t*, const int32_t*, const FillDesc*, int32_t, int64_t,
+                                    const FillDesc*, int32_t, float*, int64_t, int64_t, int32_t, int32_t*, int32_t*,
+                                    cudaStream_t);
+template cudaError_t fill_ah<double>(const DevCSR&, const int32_t*, const int32_t*, const FillDesc*, int32_t, int64_t,
+                                     const FillDesc*, int32_t, double*, int64_t, int64_t, int32_t, int32_t*, int32_t*,
+                                     cudaStream_t);
+
+__global__ void k_invert_perm(int32_t N, const int32_t* perm, int32_t* iperm) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
+}
+cudaError_t invert_perm(int32_t N, const int32_t* perm, int32_t* iperm, cudaStream_t s) {
+  k_invert_perm<<<grid_for(N), 256, 0, s>>>(N, perm, iperm);
+  return cudaGetLastError();
+}
+
+}  // namespace hlu

@@ -1,0 +1,50 @@
+// Build-phase device routines (mesh, assembly, load vector, trees, A_H fill).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace hlu {
+
+struct DevMesh {
+  int n = 0;
+  int64_t N = 0;
+  int32_t* dofmap = nullptr;  // (n+1)^3 x 7: DOF of edge (v, v + dir) or -1
+  int32_t* edges = nullptr;   // N x 2 (lo, hi)
+  int32_t* pts = nullptr;     // N x 3 doubled midpoints
+};
+struct DevCSR {
+  int64_t N = 0, nnz = 0;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+struct HostTrees {
+  int32_t nc = 0, nb = 0;
+  std::vector<int32_t> clusters;  // nc x 12 export layout
+  std::vector<int32_t> blocks;    // nb x 8 export layout
+  std::vector<int32_t> perm;      // N
+};
+// A_H fill descriptor of one leaf block.
+struct FillDesc {
+  int64_t off;         // dense storage or X storage (elements)
+  int64_t off2;        // Y storage (admissible)
+  int64_t row_prefix;  // dense: rows of all earlier dense descriptors
+  int32_t roff, m, coff, n;
+  int32_t slot, cap;
+};
+
+cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m);
+cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A);
+cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s);
+cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream_t s, HostTrees& out,
+                        int32_t* d_perm_out);
+cudaError_t invert_perm(int32_t N, const int32_t* perm, int32_t* iperm, cudaStream_t s);
+template <class T>
+cudaError_t fill_ah(const DevCSR& A, const int32_t* d_perm, const int32_t* d_iperm, const FillDesc* d_dense,
+                    int32_t ndense, int64_t dense_rows, const FillDesc* d_lr, int32_t nlr, T* arena,
+                    int64_t zero_elems, int64_t ident_off, int32_t ident_n, int32_t* ranks, int32_t* status,
+                    cudaStream_t s);
+
+}  // namespace hlu

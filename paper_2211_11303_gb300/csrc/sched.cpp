@@ -1,0 +1,662 @@
+// Host task scheduler: turns the recursive H-LU of Algorithm 1 step II (block
+// form: LU(A11); A12 <- L11^-1 P A12; A21 <- A21 U11^-1; A22 <- A22 - A21 A12
+// truncated; LU(A22), as in the H-LU source the paper cites) and the
+// preconditioner application U^-1 (L^-1 r) of step III into task DAGs.
+//
+// The recursion is walked once on the host.  Every leaf-level operation becomes
+// a task of one of the kinds in hlu_internal.h; the data it touches is
+// recorded per (buffer, leaf-cluster segment), which yields read-after-write,
+// write-after-read and write-after-write edges.  The emission order is the
+// sequential program order, hence a topological order: the device executor
+// hands out tasks in that order and each task only waits on earlier ones.
+//
+// Ranks of low-rank blocks are data dependent.  The schedule only uses rank
+// capacities; kernels read the live rank from a rank slot when they run.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <stdexcept>
+
+#include "hlu_internal.h"
+
+namespace hlu {
+namespace {
+
+struct MV {
+  int32_t buf;   // dependency buffer (-1: read-only, untracked)
+  int32_t clus;  // cluster whose index range the rows cover
+  View v;
+};
+struct LR {
+  MV X, Y;
+};
+struct PieceMV {
+  LR p;
+  int32_t xoff, yoff;
+  float sign;
+};
+
+struct Buf {
+  int32_t base_leaf;
+  int32_t nseg;
+  int64_t seg0;
+};
+
+class Sched {
+ public:
+  Sched(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t kcap, ArenaLayout& L,
+        Schedule* S, std::vector<int32_t>& dbuf, std::vector<int32_t>& xbuf,
+        std::vector<int32_t>& ybuf, bool make_buffers)
+      : C_(C), B_(B), kcap_(kcap), L_(L), S_(S), dbuf_(dbuf), xbuf_(xbuf), ybuf_(ybuf) {
+    S_->pred_ptr.assign(1, 0);
+    leaf_cluster_.clear();
+    for (size_t c = 0; c < C_.size(); ++c)
+      if (C_[c].son[0] < 0) {
+        if ((int32_t)leaf_cluster_.size() != C_[c].leaf_begin) throw std::logic_error("leaf order");
+        leaf_cluster_.push_back((int32_t)c);
+      }
+    if (make_buffers) {
+      dbuf_.assign(B_.size(), -1);
+      xbuf_.assign(B_.size(), -1);
+      ybuf_.assign(B_.size(), -1);
+    }
+    // each schedule tracks its own buffer states from scratch
+    for (size_t b = 0; b < B_.size(); ++b) {
+      if (B_[b].kind == KIND_DENSE) dbuf_[b] = new_buf_single();
+      if (B_[b].kind == KIND_ADM) {
+        xbuf_[b] = new_buf_leaves(B_[b].row);
+        ybuf_[b] = new_buf_leaves(B_[b].col);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- arena
+  int64_t alloc(int64_t n) {
+    int64_t o = L_.total;
+    L_.total += (n + 31) & ~int64_t(31);
+    temp_elems_ += n;
+    return o;
+  }
+  int32_t new_slot() { return L_.n_slots++; }
+  int64_t temp_elems_ = 0;
+
+  // ---------------------------------------------------------------- buffers
+  int32_t new_buf_leaves(int32_t clus) {
+    Buf b;
+    b.base_leaf = C_[clus].leaf_begin;
+    b.nseg = C_[clus].leaf_end - C_[clus].leaf_begin;
+    b.seg0 = (int64_t)seg_writer_.size();
+    seg_writer_.resize(seg_writer_.size() + b.nseg, -1);
+    seg_rhead_.resize(seg_rhead_.size() + b.nseg, -1);
+    bufs_.push_back(b);
+    return (int32_t)bufs_.size() - 1;
+  }
+  int32_t new_buf_single() {
+    Buf b;
+    b.base_leaf = -1;
+    b.nseg = 1;
+    b.seg0 = (int64_t)seg_writer_.size();
+    seg_writer_.push_back(-1);
+    seg_rhead_.push_back(-1);
+    bufs_.push_back(b);
+    return (int32_t)bufs_.size() - 1;
+  }
+
+  // ---------------------------------------------------------------- views
+  int32_t rowc(int32_t b) const { return B_[b].row; }
+  int32_t colc(int32_t b) const { return B_[b].col; }
+  int32_t sz(int32_t c) const { return C_[c].size; }
+  int32_t kind(int32_t b) const { return B_[b].kind; }
+  int32_t son(int32_t b, int i, int j) const { return B_[b].son[2 * i + j]; }
+
+  MV mvD(int32_t b) const {
+    MV m;
+    m.buf = dbuf_[b];
+    m.clus = rowc(b);
+    m.v = View{L_.dense_off[b], 1, sz(rowc(b)), sz(rowc(b)), sz(colc(b)), -1, 0};
+    return m;
+  }
+  MV mvDT(int32_t b) const {
+    MV m;
+    m.buf = dbuf_[b];
+    m.clus = colc(b);
+    m.v = View{L_.dense_off[b], sz(rowc(b)), 1, sz(colc(b)), sz(rowc(b)), -1, 0};
+    return m;
+  }
+  MV mvX(int32_t b) const {
+    MV m;
+    m.buf = xbuf_[b];
+    m.clus = rowc(b);
+    m.v = View{L_.x_off[b], 1, sz(rowc(b)), sz(rowc(b)), L_.cap[b], L_.slot[b], 0};
+    return m;
+  }
+  MV mvY(int32_t b) const {
+    MV m;
+    m.buf = ybuf_[b];
+    m.clus = colc(b);
+    m.v = View{L_.y_off[b], 1, sz(colc(b)), sz(colc(b)), L_.cap[b], L_.slot[b], 0};
+    return m;
+  }
+  MV mvIdent(int32_t clus) const {
+    if (sz(clus) > L_.ident_n) throw std::logic_error("identity too small");
+    MV m;
+    m.buf = -1;
+    m.clus = clus;
+    m.v = View{L_.ident_off, 1, L_.ident_n, sz(clus), sz(clus), -1, 0};
+    return m;
+  }
+  MV sub(const MV& m, int32_t s) const {
+    int32_t d = C_[s].off - C_[m.clus].off;
+    if (d < 0 || d + C_[s].size > C_[m.clus].size) throw std::logic_error("sub view outside");
+    MV r = m;
+    r.clus = s;
+    r.v.off += (int64_t)d * m.v.rs;
+    r.v.rows = C_[s].size;
+    return r;
+  }
+  // fresh temporary with per-leaf dependency segments; column count via a slot
+  MV new_temp(int32_t clus, int32_t cols_cap) {
+    MV m;
+    m.buf = new_buf_leaves(clus);
+    m.clus = clus;
+    int32_t rows = sz(clus);
+    m.v = View{alloc((int64_t)rows * std::max(cols_cap, 1)), 1, rows, rows, cols_cap, new_slot(), 0};
+    return m;
+  }
+  MV new_dense_temp(int32_t clus, int32_t cols) {
+    MV m;
+    m.buf = new_buf_single();
+    m.clus = clus;
+    int32_t rows = sz(clus);
+    m.v = View{alloc((int64_t)rows * cols), 1, rows, rows, cols, -1, 0};
+    return m;
+  }
+  int32_t cols_cap(const View& v) const { return v.cols; }
+
+  // ---------------------------------------------------------------- tasks
+  int32_t begin(const Task& t) {
+    int32_t id = (int32_t)S_->tasks.size();
+    S_->tasks.push_back(t);
+    stamp_.push_back(-1);
+    cur_ = id;
+    deps_.clear();
+    return id;
+  }
+  void dep(int32_t p) {
+    if (p < 0 || p == cur_) return;
+    if (stamp_[p] == cur_) return;
+    stamp_[p] = cur_;
+    deps_.push_back(p);
+  }
+  void touch(int64_t seg, bool w) {
+    dep(seg_writer_[seg]);
+    if (w) {
+      for (int64_t r = seg_rhead_[seg]; r >= 0; r = rnext_[r]) dep(rtask_[r]);
+      seg_rhead_[seg] = -1;
+      seg_writer_[seg] = cur_;
+    } else {
+      rtask_.push_back(cur_);
+      rnext_.push_back(seg_rhead_[seg]);
+      seg_rhead_[seg] = (int64_t)rtask_.size() - 1;
+    }
+  }
+  void acc(const MV& m, bool w) {
+    if (m.buf < 0) return;
+    const Buf& b = bufs_[m.buf];
+    if (b.nseg == 1 && b.base_leaf < 0) {
+      touch(b.seg0, w);
+      return;
+    }
+    const Cluster& c = C_[m.clus];
+    for (int32_t l = c.leaf_begin; l < c.leaf_end; ++l) {
+      int64_t s = b.seg0 + (l - b.base_leaf);
+      touch(s, w);
+    }
+  }
+  // read of one segment: enough to order the task after any writer of the
+  // buffer's rank slot (rank writers write every segment)
+  void acc_rank(const MV& m) {
+    if (m.buf < 0 || m.v.slot < 0) return;
+    const Buf& b = bufs_[m.buf];
+    touch(b.seg0, false);
+  }
+  void end() {
+    std::sort(deps_.begin(), deps_.end());
+    S_->pred_idx.insert(S_->pred_idx.end(), deps_.begin(), deps_.end());
+    S_->pred_ptr.push_back((int64_t)S_->pred_idx.size());
+  }
+
+  static Task make(int32_t type) {
+    Task t;
+    std::memset(&t, 0, sizeof(t));
+    t.type = type;
+    t.out_slot = -1;
+    t.piv_off = -1;
+    t.sign = 1.0f;
+    t.a.slot = t.b.slot = t.c.slot = -1;
+    return t;
+  }
+
+  // ---------------------------------------------------------------- leaf ops
+  void getrf(int32_t d) {
+    Task t = make(TK_GETRF);
+    t.a = mvD(d).v;
+    t.piv_off = L_.piv_off[d];
+    begin(t);
+    acc(mvD(d), true);
+    end();
+  }
+  void trsm_leaf(int32_t type, int32_t d, const MV& V) {
+    Task t = make(type);
+    t.a = mvD(d).v;
+    t.b = V.v;
+    t.piv_off = L_.piv_off[d];
+    begin(t);
+    acc(mvD(d), false);
+    acc(V, true);
+    end();
+  }
+
+  // ---------------------------------------------------------------- H x multivector
+  void leaves_of(int32_t b, std::vector<int32_t>& out) const {
+    if (kind(b) != KIND_SUB) {
+      out.push_back(b);
+      return;
+    }
+    for (int k = 0; k < 4; ++k) leaves_of(B_[b].son[k], out);
+  }
+
+  // Vout (+)= sign * op(b) Vin, op = transpose when trans.  Vin covers the
+  // in-cluster of b, Vout its out-cluster.  overwrite: Vout starts from zero
+  // and out_slot receives Vin's column count.
+  void hmul(int32_t b, const MV& Vin, const MV& Vout, float sign, bool trans, bool overwrite,
+            int32_t out_slot) {
+    std::vector<int32_t> lv;
+    leaves_of(b, lv);
+    int32_t oc = trans ? colc(b) : rowc(b);
+    if (Vout.clus != oc || Vin.clus != (trans ? rowc(b) : colc(b)))
+      throw std::logic_error("hmul cluster mismatch");
+    std::vector<MV> T(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) {
+      int32_t be = lv[i];
+      if (kind(be) != KIND_ADM) continue;
+      MV A = trans ? mvX(be) : mvY(be);
+      int32_t ic = trans ? rowc(be) : colc(be);
+      MV vin = sub(Vin, ic);
+      MV t;
+      t.buf = new_buf_single();
+      t.clus = -1;
+      int32_t cap = L_.cap[be];
+      t.v = View{alloc((int64_t)cap * std::max(vin.v.cols, 1)), 1, cap, cap, vin.v.cols, vin.v.slot,
+                 0};
+      Task k = make(TK_PROJ);
+      k.a = A.v;
+      k.b = vin.v;
+      k.c = t.v;
+      begin(k);
+      acc(A, false);
+      acc(vin, false);
+      touch(bufs_[t.buf].seg0, true);
+      end();
+      T[i] = t;
+    }
+    const Cluster& O = C_[oc];
+    int32_t nl = O.leaf_end - O.leaf_begin;
+    // bucket leaf blocks by the output leaves they cover (counting sort)
+    std::vector<int32_t> cnt(nl + 1, 0);
+    for (size_t i = 0; i < lv.size(); ++i) {
+      const Cluster& ob = C_[trans ? colc(lv[i]) : rowc(lv[i])];
+      for (int32_t l = ob.leaf_begin; l < ob.leaf_end; ++l) cnt[l - O.leaf_begin + 1]++;
+    }
+    for (int32_t l = 0; l < nl; ++l) cnt[l + 1] += cnt[l];
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), items(cnt[nl]);
+    for (size_t i = 0; i < lv.size(); ++i) {
+      const Cluster& ob = C_[trans ? colc(lv[i]) : rowc(lv[i])];
+      for (int32_t l = ob.leaf_begin; l < ob.leaf_end; ++l) items[fill[l - O.leaf_begin]++] = (int32_t)i;
+    }
+    MV kview = sub(Vin, leaf_cluster_[C_[Vin.clus].leaf_begin]);
+    for (int32_t l = 0; l < nl; ++l) {
+      if (cnt[l] == cnt[l + 1] && !overwrite) continue;
+      int32_t lc = leaf_cluster_[O.leaf_begin + l];
+      Task k = make(TK_ROWMV);
+      k.flags = overwrite ? TF_OVERWRITE : 0;
+      k.sign = sign;
+      k.c = sub(Vout, lc).v;
+      k.b = Vin.v;  // column count source
+      k.out_slot = out_slot;
+      k.list_begin = (int32_t)S_->terms.size();
+      k.list_count = cnt[l + 1] - cnt[l];
+      begin(k);
+      for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q) {
+        int32_t i = items[q];
+        int32_t be = lv[i];
+        Term tm;
+        std::memset(&tm, 0, sizeof(tm));
+        if (kind(be) == KIND_DENSE) {
+          MV A = sub(trans ? mvDT(be) : mvD(be), lc);
+          MV Bv = sub(Vin, trans ? rowc(be) : colc(be));
+          tm.A = A.v;
+          tm.B = Bv.v;
+          acc(A, false);
+          acc(Bv, false);
+        } else {
+          MV A = sub(trans ? mvY(be) : mvX(be), lc);
+          tm.A = A.v;
+          tm.B = T[i].v;
+          acc(A, false);
+          touch(bufs_[T[i].buf].seg0, false);
+        }
+        S_->terms.push_back(tm);
+      }
+      acc_rank(kview);
+      acc(sub(Vout, lc), true);
+      end();
+    }
+  }
+  MV hmul_new(int32_t b, const MV& Vin, bool trans) {
+    int32_t oc = trans ? colc(b) : rowc(b);
+    MV out = new_temp(oc, Vin.v.cols);
+    hmul(b, Vin, out, 1.0f, trans, true, out.v.slot);
+    return out;
+  }
+
+  // ---------------------------------------------------------------- triangular
+  void solve_lower(int32_t d, const MV& V) {
+    if (kind(d) == KIND_DENSE) {
+      trsm_leaf(TK_TRSM_L, d, V);
+      return;
+    }
+    const Cluster& c = C_[rowc(d)];
+    MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
+    solve_lower(son(d, 0, 0), V0);
+    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1);
+    solve_lower(son(d, 1, 1), V1);
+  }
+  void solve_upperT(int32_t d, const MV& W) {
+    if (kind(d) == KIND_DENSE) {
+      trsm_leaf(TK_TRSM_UT, d, W);
+      return;
+    }
+    const Cluster& c = C_[rowc(d)];
+    MV W0 = sub(W, c.son[0]), W1 = sub(W, c.son[1]);
+    solve_upperT(son(d, 0, 0), W0);
+    hmul(son(d, 0, 1), W0, W1, -1.0f, true, false, -1);
+    solve_upperT(son(d, 1, 1), W1);
+  }
+  void solve_upper(int32_t d, const MV& V) {
+    if (kind(d) == KIND_DENSE) {
+      trsm_leaf(TK_TRSM_U, d, V);
+      return;
+    }
+    const Cluster& c = C_[rowc(d)];
+    MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
+    solve_upper(son(d, 1, 1), V1);
+    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1);
+    solve_upper(son(d, 0, 0), V0);
+  }
+
+  // ---------------------------------------------------------------- truncation
+  void emit_trunc(const MV& X, const MV& Y, int32_t slot, int32_t cap,
+                  const std::vector<PieceMV>& ps) {
+    Task t = make(TK_TRUNC);
+    t.a = X.v;
+    t.b = Y.v;
+    t.out_slot = slot;
+    t.cap = cap;
+    t.list_begin = (int32_t)S_->pieces.size();
+    t.list_count = (int32_t)ps.size();
+    int32_t W = 0;
+    begin(t);
+    for (const PieceMV& p : ps) {
+      Piece q;
+      std::memset(&q, 0, sizeof(q));
+      q.X = p.p.X.v;
+      q.Y = p.p.Y.v;
+      q.xoff = p.xoff;
+      q.yoff = p.yoff;
+      q.sign = p.sign;
+      S_->pieces.push_back(q);
+      acc(p.p.X, false);
+      acc(p.p.Y, false);
+      W += p.p.X.v.cols;
+    }
+    acc(X, true);
+    acc(Y, true);
+    end();
+    L_.wmax = std::max(L_.wmax, W);
+    L_.max_trunc_rows = std::max(L_.max_trunc_rows, std::max(X.v.rows, Y.v.rows));
+  }
+  LR trunc_new(int32_t rc, int32_t cc, const std::vector<PieceMV>& ps) {
+    int32_t cap = std::min(kcap_, std::min(sz(rc), sz(cc)));
+    int32_t slot = new_slot();
+    LR r;
+    r.X.buf = new_buf_leaves(rc);
+    r.X.clus = rc;
+    r.X.v = View{alloc((int64_t)sz(rc) * cap), 1, sz(rc), sz(rc), cap, slot, 0};
+    r.Y.buf = new_buf_leaves(cc);
+    r.Y.clus = cc;
+    r.Y.v = View{alloc((int64_t)sz(cc) * cap), 1, sz(cc), sz(cc), cap, slot, 0};
+    emit_trunc(r.X, r.Y, slot, cap, ps);
+    return r;
+  }
+
+  // ---------------------------------------------------------------- H-gemm
+  LR product(int32_t a, int32_t b) {
+    int32_t ka = kind(a), kb = kind(b);
+    int32_t tau = rowc(a), sig = colc(a), rho = colc(b);
+    if (ka == KIND_ADM) return LR{mvX(a), hmul_new(b, mvY(a), true)};
+    if (kb == KIND_ADM) return LR{hmul_new(a, mvX(b), false), mvY(b)};
+    if (ka == KIND_DENSE && kb == KIND_DENSE) {
+      if (sz(sig) <= kcap_) return LR{mvD(a), mvDT(b)};
+      // wide middle dimension: materialise the (leaf x leaf) product
+      MV P = new_dense_temp(tau, sz(rho));
+      Task t = make(TK_DADD);
+      t.flags = TF_OVERWRITE;
+      t.c = P.v;
+      t.a = mvD(a).v;
+      t.b = mvDT(b).v;
+      begin(t);
+      acc(mvD(a), false);
+      acc(mvDT(b), false);
+      acc(P, true);
+      end();
+      return LR{P, mvIdent(rho)};
+    }
+    if (ka == KIND_DENSE) return LR{mvIdent(tau), hmul_new(b, mvDT(a), true)};
+    if (kb == KIND_DENSE) return LR{hmul_new(a, mvD(b), false), mvIdent(rho)};
+    // both subdivided: son products, summed and truncated per son, then
+    // agglomerated (rows of son 0 and of son 1 first, then the two halves)
+    const Cluster& T = C_[tau];
+    const Cluster& R = C_[rho];
+    LR t[2][2];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        LR s0 = product(son(a, i, 0), son(b, 0, j));
+        LR s1 = product(son(a, i, 1), son(b, 1, j));
+        t[i][j] = trunc_new(T.son[i], R.son[j], {{s0, 0, 0, 1.0f}, {s1, 0, 0, 1.0f}});
+      }
+    int32_t r0 = C_[R.son[0]].size, t0 = C_[T.son[0]].size;
+    LR top = trunc_new(T.son[0], rho, {{t[0][0], 0, 0, 1.0f}, {t[0][1], 0, r0, 1.0f}});
+    LR bot = trunc_new(T.son[1], rho, {{t[1][0], 0, 0, 1.0f}, {t[1][1], 0, r0, 1.0f}});
+    return trunc_new(tau, rho, {{top, 0, 0, 1.0f}, {bot, t0, 0, 1.0f}});
+  }
+
+  void add_lr(int32_t c, const LR& p, float sign) {
+    if (p.X.clus != rowc(c) || p.Y.clus != colc(c)) throw std::logic_error("add_lr shape");
+    int32_t k = kind(c);
+    if (k == KIND_DENSE) {
+      Task t = make(TK_DADD);
+      t.c = mvD(c).v;
+      t.a = p.X.v;
+      t.b = p.Y.v;
+      t.sign = sign;
+      begin(t);
+      acc(p.X, false);
+      acc(p.Y, false);
+      acc(mvD(c), true);
+      end();
+    } else if (k == KIND_ADM) {
+      emit_trunc(mvX(c), mvY(c), L_.slot[c], L_.cap[c],
+                 {{LR{mvX(c), mvY(c)}, 0, 0, 1.0f}, {p, 0, 0, sign}});
+    } else {
+      const Cluster& R = C_[rowc(c)];
+      const Cluster& Q = C_[colc(c)];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          add_lr(son(c, i, j), LR{sub(p.X, R.son[i]), sub(p.Y, Q.son[j])}, sign);
+    }
+  }
+
+  void gemm(int32_t c, int32_t a, int32_t b) {
+    if (kind(c) == KIND_SUB && kind(a) == KIND_SUB && kind(b) == KIND_SUB) {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int k = 0; k < 2; ++k) gemm(son(c, i, j), son(a, i, k), son(b, k, j));
+      return;
+    }
+    LR p = product(a, b);
+    add_lr(c, p, -1.0f);
+  }
+
+  // ---------------------------------------------------------------- H-trsm, H-LU
+  void trsm_left(int32_t d, int32_t b) {
+    int32_t k = kind(b);
+    if (k == KIND_ADM) {
+      solve_lower(d, mvX(b));
+    } else if (k == KIND_DENSE) {
+      solve_lower(d, mvD(b));
+    } else {
+      for (int j = 0; j < 2; ++j) {
+        trsm_left(son(d, 0, 0), son(b, 0, j));
+        gemm(son(b, 1, j), son(d, 1, 0), son(b, 0, j));
+        trsm_left(son(d, 1, 1), son(b, 1, j));
+      }
+    }
+  }
+  void trsm_right(int32_t b, int32_t d) {
+    int32_t k = kind(b);
+    if (k == KIND_ADM) {
+      solve_upperT(d, mvY(b));
+    } else if (k == KIND_DENSE) {
+      solve_upperT(d, mvDT(b));
+    } else {
+      for (int i = 0; i < 2; ++i) {
+        trsm_right(son(b, i, 0), son(d, 0, 0));
+        gemm(son(b, i, 1), son(b, i, 0), son(d, 0, 1));
+        trsm_right(son(b, i, 1), son(d, 1, 1));
+      }
+    }
+  }
+  void lu(int32_t d) {
+    if (kind(d) == KIND_DENSE) {
+      getrf(d);
+      return;
+    }
+    int32_t d00 = son(d, 0, 0), d01 = son(d, 0, 1), d10 = son(d, 1, 0), d11 = son(d, 1, 1);
+    lu(d00);
+    trsm_left(d00, d01);
+    trsm_right(d10, d00);
+    gemm(d11, d10, d01);
+    lu(d11);
+  }
+
+  void solve_all(int32_t nrhs_max) {
+    MV W;
+    W.buf = new_buf_leaves(0);
+    W.clus = 0;
+    int32_t N = sz(0);
+    W.v = View{L_.work_off, 1, N, N, nrhs_max, L_.nrhs_slot, 0};
+    solve_lower(0, W);
+    solve_upper(0, W);
+  }
+
+ private:
+  const std::vector<Cluster>& C_;
+  const std::vector<Block>& B_;
+  int32_t kcap_;
+  ArenaLayout& L_;
+  Schedule* S_;
+  std::vector<int32_t>& dbuf_;
+  std::vector<int32_t>& xbuf_;
+  std::vector<int32_t>& ybuf_;
+  std::vector<int32_t> leaf_cluster_;
+  std::vector<Buf> bufs_;
+  std::vector<int32_t> seg_writer_;
+  std::vector<int64_t> seg_rhead_;
+  std::vector<int32_t> rtask_;
+  std::vector<int64_t> rnext_;
+  std::vector<int32_t> stamp_;
+  std::vector<int32_t> deps_;
+  int32_t cur_ = -1;
+};
+
+}  // namespace
+
+void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
+                     int32_t nrhs_max, ArenaLayout& L, Schedule& factor, Schedule& solve,
+                     SchedStats& st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t nb = B.size();
+  L = ArenaLayout();
+  L.dense_off.assign(nb, -1);
+  L.x_off.assign(nb, -1);
+  L.y_off.assign(nb, -1);
+  L.cap.assign(nb, 0);
+  L.slot.assign(nb, -1);
+  L.piv_off.assign(nb, -1);
+  int32_t leafmax = 0;
+  for (const Cluster& c : C)
+    if (c.son[0] < 0) leafmax = std::max(leafmax, c.size);
+  auto alloc = [&](int64_t n) {
+    int64_t o = L.total;
+    L.total += (n + 31) & ~int64_t(31);
+    return o;
+  };
+  L.ident_n = std::max(leafmax, 1);
+  L.ident_off = alloc((int64_t)L.ident_n * L.ident_n);
+  int64_t fe = 0;
+  for (size_t b = 0; b < nb; ++b) {
+    int32_t m = C[B[b].row].size, n = C[B[b].col].size;
+    if (B[b].kind == KIND_DENSE) {
+      L.dense_off[b] = alloc((int64_t)m * n);
+      fe += (int64_t)m * n;
+      if (B[b].row == B[b].col) {
+        L.piv_off[b] = L.piv_total;
+        L.piv_total += m;
+      }
+    } else if (B[b].kind == KIND_ADM) {
+      int32_t cap = std::min(rank_cap, std::min(m, n));
+      L.cap[b] = cap;
+      L.slot[b] = L.n_slots++;
+      L.x_off[b] = alloc((int64_t)m * cap);
+      L.y_off[b] = alloc((int64_t)n * cap);
+      fe += (int64_t)(m + n) * cap;
+    }
+  }
+  L.factor_elems = fe;
+  L.nrhs_max = nrhs_max;
+  L.nrhs_slot = L.n_slots++;
+  L.work_off = alloc((int64_t)C[0].size * nrhs_max);
+  L.wmax = 0;
+  factor = Schedule();
+  solve = Schedule();
+  std::vector<int32_t> dbuf, xbuf, ybuf;
+  {
+    Sched s(C, B, rank_cap, L, &factor, dbuf, xbuf, ybuf, true);
+    s.lu(0);
+    st.temp_elems = s.temp_elems_;
+  }
+  {
+    Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true);
+    s.solve_all(nrhs_max);
+    st.temp_elems += s.temp_elems_;
+  }
+  factor.n_edges = (int64_t)factor.pred_idx.size();
+  solve.n_edges = (int64_t)solve.pred_idx.size();
+  st.n_factor_tasks = (int64_t)factor.tasks.size();
+  st.n_solve_tasks = (int64_t)solve.tasks.size();
+  st.host_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace hlu

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of the C ABI in include/hlu.h.
+
+Argument marshalling only: every numerical step runs in libhlu.so's CUDA
+kernels.  PyTorch provides device memory and streams.  Vectors are FP64 CUDA
+tensors of shape (N,) or (N, nrhs) in column-major layout (``colmajor`` makes
+one), in the original interior-edge DOF order.
+"""
+import ctypes
+import os
+
+from ._build import LIB
+
+HLU_OK = 0
+HLU_ERR_NOT_CONVERGED = 4
+HLU_FP64 = 0
+HLU_FP32 = 1
+BLOCK_ADM, BLOCK_DENSE, BLOCK_SUB = 0, 1, 2
+
+
+class HluError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status, message))
+        self.status = status
+
+
+class hlu_mesh(ctypes.Structure):
+    _fields_ = [("lattice_n", ctypes.c_int32)]
+
+
+class hlu_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("relres_max", ctypes.c_double), ("abs_res_max", ctypes.c_double),
+                ("precond_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("precond_applies", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class hlu_factor_info(ctypes.Structure):
+    _fields_ = [("n_tasks", ctypes.c_int64), ("n_solve_tasks", ctypes.c_int64),
+                ("factor_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("factor_ms", ctypes.c_double),
+                ("schedule_ms", ctypes.c_double), ("rank_max", ctypes.c_int32),
+                ("rank_cap_hits", ctypes.c_int32), ("rank_mean", ctypes.c_double),
+                ("n_clusters", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("n_adm", ctypes.c_int32), ("n_dense", ctypes.c_int32)]
+
+
+def _struct_dict(s):
+    return {f[0]: getattr(s, f[0]) for f in s._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f64 = ctypes.c_double
+_P = ctypes.POINTER
+
+# exported symbol -> (restype, argtypes); kept in sync with include/hlu.h and
+# include/hlu_debug.h (tests check every declared name is exported)
+SIGNATURES = {
+    "hlu_build": (_i32, [_P(hlu_mesh), _f64, _i32, _f64, _f64, _i32, _vp, _P(_vp)]),
+    "hlu_n": (_i64, [_vp]),
+    "hlu_export_trees": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
+    "hlu_export_csr": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
+    "hlu_rhs_manufactured": (_i32, [_vp, _vp, _vp]),
+    "hlu_spmv": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
+    "hlu_factor": (_i32, [_vp, _i32, _vp]),
+    "hlu_factor_stats": (_i32, [_vp, _P(hlu_factor_info)]),
+    "hlu_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
+    "gmres_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _i32, _P(hlu_stats), _vp]),
+    "hlu_richardson": (_i32, [_vp, _vp, _vp, _i32, _i64, _f64, _i32, _P(hlu_stats), _vp]),
+    "hlu_factor_batch": (_i32, [_P(_vp), _i32, _i32, _vp]),
+    "hlu_solve_batch": (_i32, [_P(_vp), _i32, _P(_vp), _P(_vp), _P(_i32), _vp]),
+    "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
+    "hlu_set_wait_limit_ms": (None, [_f64]),
+    "hlu_destroy": (None, [_vp]),
+    "hlu_status_string": (ctypes.c_char_p, [_i32]),
+    "hlu_last_error": (ctypes.c_char_p, []),
+    "hlu_debug_host_factor_solve": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32,
+                                           ctypes.c_uint64, _i32, _vp, _vp, _vp]),
+    "hlu_debug_wait_timeout": (_i32, [_f64, _vp]),
+}
+
+
+def lib():
+    """Load libhlu.so; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libhlu.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status not in (HLU_OK,):
+        L = lib()
+        raise HluError(L.hlu_status_string(status).decode(), L.hlu_last_error().decode())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def colmajor(N, nrhs, device="cuda"):
+    """Empty FP64 (N, nrhs) CUDA tensor with column-major strides (1, N)."""
+    import torch
+    return torch.empty((nrhs, N), dtype=torch.float64, device=device).t()
+
+
+def _vec(t, N):
+    """(pointer, nrhs, ld) of an FP64 CUDA vector/column-major block."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError("expected a float64 CUDA tensor")
+    if t.dim() == 1:
+        if t.stride(0) != 1 or t.shape[0] != N:
+            raise ValueError("vector must be contiguous with N entries")
+        return _vp(t.data_ptr()), 1, N
+    if t.shape[0] != N or t.stride(0) != 1 or t.stride(1) < N:
+        raise ValueError("expected column-major (N, nrhs) with stride (1, ld >= N)")
+    return _vp(t.data_ptr()), t.shape[1], t.stride(1)
+
+
+# ---------------------------------------------------------------- C-ABI names
+def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=32, stream=None):
+    """Algorithm 1 step I on the GPU; returns an opaque handle (int)."""
+    h = _vp()
+    m = hlu_mesh(int(n))
+    _check(lib().hlu_build(ctypes.byref(m), float(kappa), int(leaf), float(eta), float(eps),
+                           int(rank_cap), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hlu_n(h):
+    return int(lib().hlu_n(_vp(h)))
+
+
+def hlu_destroy(h):
+    lib().hlu_destroy(_vp(h))
+
+
+def hlu_export_trees(h):
+    """(perm int32[N], clusters int32[nc,12], blocks int32[nb,8]) as numpy arrays."""
+    import numpy as np
+    sizes = (_i64 * 2)()
+    _check(lib().hlu_export_trees(_vp(h), None, None, None, sizes))
+    N = hlu_n(h)
+    perm = np.empty(N, dtype=np.int32)
+    C = np.empty((sizes[0], 12), dtype=np.int32)
+    B = np.empty((sizes[1], 8), dtype=np.int32)
+    _check(lib().hlu_export_trees(_vp(h), perm.ctypes.data, C.ctypes.data, B.ctypes.data, sizes))
+    return perm, C, B
+
+
+def hlu_export_csr(h):
+    """(rowptr int64, col int32, val float64) numpy arrays of A."""
+    import numpy as np
+    nnz = _i64()
+    _check(lib().hlu_export_csr(_vp(h), None, None, None, ctypes.byref(nnz)))
+    N = hlu_n(h)
+    rp = np.empty(N + 1, dtype=np.int64)
+    ci = np.empty(nnz.value, dtype=np.int32)
+    va = np.empty(nnz.value, dtype=np.float64)
+    _check(lib().hlu_export_csr(_vp(h), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, ctypes.byref(nnz)))
+    return rp, ci, va
+
+
+def hlu_rhs_manufactured(h, b, stream=None):
+    p, nr, ld = _vec(b, hlu_n(h))
+    _check(lib().hlu_rhs_manufactured(_vp(h), p, _stream(stream)))
+
+
+def hlu_spmv(h, x, y, stream=None):
+    N = hlu_n(h)
+    px, nr, ldx = _vec(x, N)
+    py, nr2, ldy = _vec(y, N)
+    if nr != nr2 or ldx != ldy:
+        raise ValueError("x and y must have the same shape and leading dimension")
+    _check(lib().hlu_spmv(_vp(h), px, py, nr, ldx, _stream(stream)))
+
+
+def hlu_factor(h, precision=HLU_FP32, stream=None):
+    _check(lib().hlu_factor(_vp(h), int(precision), _stream(stream)))
+
+
+def hlu_factor_stats(h):
+    info = hlu_factor_info()
+    _check(lib().hlu_factor_stats(_vp(h), ctypes.byref(info)))
+    return _struct_dict(info)
+
+
+def hlu_solve(h, b, x, stream=None):
+    N = hlu_n(h)
+    pb, nr, ldb = _vec(b, N)
+    px, nr2, ldx = _vec(x, N)
+    if nr != nr2 or ldb != ldx:
+        raise ValueError("b and x must have the same shape and leading dimension")
+    _check(lib().hlu_solve(_vp(h), pb, px, nr, ldb, _stream(stream)))
+
+
+def gmres_solve(h, b, x, restart=50, tol=1e-8, maxit=1000, flexible=True, stream=None,
+                raise_on_nonconvergence=True):
+    """Restarted flexible GMRES with the H-LU preconditioner; returns stats dict."""
+    N = hlu_n(h)
+    pb, nr, ldb = _vec(b, N)
+    px, nr2, ldx = _vec(x, N)
+    if nr != nr2 or ldb != ldx:
+        raise ValueError("b and x must have the same shape and leading dimension")
+    st = hlu_stats()
+    rc = lib().gmres_solve(_vp(h), pb, px, nr, ldb, int(restart), float(tol), int(maxit),
+                           int(bool(flexible)), ctypes.byref(st), _stream(stream))
+    if rc != HLU_ERR_NOT_CONVERGED or raise_on_nonconvergence:
+        _check(rc)
+    return _struct_dict(st)
+
+
+def hlu_richardson(h, b, x, tol=1e-8, maxit=100, stream=None, raise_on_nonconvergence=True):
+    N = hlu_n(h)
+    pb, nr, ldb = _vec(b, N)
+    px, nr2, ldx = _vec(x, N)
+    st = hlu_stats()
+    rc = lib().hlu_richardson(_vp(h), pb, px, nr, ldb, float(tol), int(maxit), ctypes.byref(st),
+                              _stream(stream))
+    if rc != HLU_ERR_NOT_CONVERGED or raise_on_nonconvergence:
+        _check(rc)
+    return _struct_dict(st)
+
+
+def hlu_factor_batch(handles, precision=HLU_FP32, stream=None):
+    arr = (_vp * len(handles))(*[_vp(h) for h in handles])
+    _check(lib().hlu_factor_batch(arr, len(handles), int(precision), _stream(stream)))
+
+
+def hlu_solve_batch(handles, bs, xs, stream=None):
+    n = len(handles)
+    hs = (_vp * n)(*[_vp(h) for h in handles])
+    pb = (_vp * n)()
+    px = (_vp * n)()
+    nr = (_i32 * n)()
+    for i, (h, b, x) in enumerate(zip(handles, bs, xs)):
+        N = hlu_n(h)
+        p1, r1, l1 = _vec(b, N)
+        p2, r2, l2 = _vec(x, N)
+        if l1 != N or l2 != N or r1 != r2:
+            raise ValueError("batched vectors must be dense column-major (ld = N)")
+        pb[i], px[i], nr[i] = p1, p2, r1
+    _check(lib().hlu_solve_batch(hs, n, pb, px, nr, _stream(stream)))
+
+
+def hlu_factor_bytes_estimate(h, precision=HLU_FP32):
+    return int(lib().hlu_factor_bytes_estimate(_vp(h), int(precision)))
+
+
+def hlu_set_wait_limit_ms(ms):
+    lib().hlu_set_wait_limit_ms(float(ms))
+
+
+class Problem:
+    """Owns one handle: build on construction, destroy on close()."""
+
+    def __init__(self, n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=32, stream=None):
+        self.n, self.kappa, self.leaf, self.eta, self.eps = n, kappa, leaf, eta, eps
+        self.h = hlu_build(n, kappa, leaf, eta, eps, rank_cap, stream)
+        self.N = hlu_n(self.h)
+
+    def factor(self, precision=HLU_FP32, stream=None):
+        hlu_factor(self.h, precision, stream)
+        return hlu_factor_stats(self.h)
+
+    def close(self):
+        if self.h:
+            hlu_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

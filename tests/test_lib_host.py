@@ -1,0 +1,100 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and
+its task scheduler (run by the host reference executor) reproduces the
+recursive H-LU.  No GPU is used."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2211_11303_gb300 import hlu
+    return hlu.lib()
+
+
+def _declared():
+    names = []
+    for h in ("hlu.h", "hlu_debug.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "sizeof", "defined"):
+                names.append(name)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2211_11303_gb300 import hlu
+    declared = _declared()
+    assert "hlu_build" in declared and "gmres_solve" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in hlu.SIGNATURES, name
+
+
+def test_status_strings(lib):
+    assert lib.hlu_status_string(0) == b"HLU_OK"
+    assert lib.hlu_status_string(5) == b"HLU_ERR_TIMEOUT"
+
+
+def test_build_rejects_bad_arguments(lib):
+    from paper_2211_11303_gb300 import hlu
+    h = ctypes.c_void_p()
+    m = hlu.hlu_mesh(0)
+    assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
+    m = hlu.hlu_mesh(4)
+    assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 1.5, 1e-4, 32, None, ctypes.byref(h)) == 1  # eta^2 = 2.25
+    assert lib.hlu_build(None, 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
+
+
+def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2):
+    from oracle import fem, mesh, trees
+    m = mesh.interior_edges(n)
+    A = fem.assemble(m, kappa).tocsr()
+    perm, cl, bl = trees.build_trees(m, leaf, 2.0)
+    p, C, B = trees.export_arrays(perm, cl, bl)
+    N = A.shape[0]
+    rng = np.random.default_rng(1)
+    b = np.asfortranarray(rng.standard_normal((N, nrhs)))
+    x = np.zeros((N, nrhs), order="F")
+    info = np.zeros(10, dtype=np.int64)
+    rp = A.indptr.astype(np.int64)
+    ci = A.indices.astype(np.int32)
+    va = A.data.astype(np.float64)
+    st = lib.hlu_debug_host_factor_solve(len(C), C.ctypes.data, len(B), B.ctypes.data, p.ctypes.data,
+                                         rp.ctypes.data, ci.ctypes.data, va.ctypes.data, eps, 32, seed,
+                                         nrhs, b.ctypes.data, x.ctypes.data, info.ctypes.data)
+    assert st == 0
+    return A, perm, cl, bl, b, x, info
+
+
+def test_dag_any_topological_order_is_bit_identical(lib):
+    _, _, _, _, _, x0, info = _host_solve(lib, 4, 3.0, 1e-4, 16, 0)
+    for seed in (1, 2, 3):
+        _, _, _, _, _, x1, _ = _host_solve(lib, 4, 3.0, 1e-4, 16, seed)
+        assert np.array_equal(x0, x1)
+    assert info[0] > 0 and info[1] > 0
+
+
+@pytest.mark.parametrize("n,kappa,leaf", [(4, 1.0, 16), (5, 4.0, 16)])
+def test_scheduled_hlu_matches_recursive_oracle(lib, n, kappa, leaf):
+    from oracle import hmatrix
+    for eps in (1e-12, 1e-4):
+        A, perm, cl, bl, b, x, info = _host_solve(lib, n, kappa, eps, leaf, 0)
+        P = hmatrix.HLUPreconditioner(A, perm, cl, bl, eps)
+        xo = P.apply(b)
+        xs = np.linalg.solve(A.toarray(), b)
+        e_lib = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+        e_or = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
+        if eps < 1e-10:
+            assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
+        else:
+            assert e_lib <= 2.0 * e_or + 1e-12, (e_lib, e_or)

@@ -206,6 +206,16 @@ int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision);
  * the kernel returns.  Process-wide. */
 void hlu_set_wait_limit_ms(double ms);
 
+/* hlu_set_tile - factorisation granularity for subsequent hlu_build calls
+ * (process-wide, default 64).  Every block-tree node whose row and column
+ * clusters both hold at most `tile` DOFs is stored and factored as one dense
+ * tile: its A_H entries and all fill inside it are kept exactly (no
+ * truncation), so the factor is at least as accurate as the leaf-level H-LU.
+ * Admissible blocks above the tile size stay low rank.  The exported trees
+ * are not affected.  tile <= leaf keeps the block tree's own leaves; values
+ * above 64 are clamped to 64. */
+void hlu_set_tile(int32_t tile);
+
 void hlu_destroy(hlu_handle* h);
 const char* hlu_status_string(int status);
 const char* hlu_last_error(void);

@@ -19,6 +19,8 @@ extern "C" {
  * perm: int32[N]; CSR of A in the original DOF order (rowptr int64[N+1], col
  * int32[nnz], val double[nnz]); eps: truncation tolerance (Sec. 4 truncated
  * SVD, keep s_i > eps s_1); rank_cap: capacity of admissible blocks (0 = 32);
+ * tile: block-tree nodes whose clusters both hold <= tile DOFs are factored as
+ * one dense tile (0 keeps the block tree's own leaves);
  * order_seed: 0 executes tasks in program order, otherwise in a random
  * topological order drawn from that seed; b, x: host double[N*nrhs]
  * column-major (original order).
@@ -30,7 +32,7 @@ extern "C" {
 int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, int32_t nb,
                                 const int32_t* blocks, const int32_t* perm, const int64_t* rowptr,
                                 const int32_t* col, const double* val, double eps,
-                                int32_t rank_cap, uint64_t order_seed, int32_t nrhs,
+                                int32_t rank_cap, int32_t tile, uint64_t order_seed, int32_t nrhs,
                                 const double* b, double* x, int64_t* info);
 
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a

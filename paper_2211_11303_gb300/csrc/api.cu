@@ -26,6 +26,7 @@ namespace {
 
 thread_local std::string g_err;
 double g_wait_limit_ms = 20000.0;
+int32_t g_tile = 64;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -105,7 +106,9 @@ struct hlu_handle {
   int32_t* d_iperm = nullptr;
   HostTrees trees;
   std::vector<Cluster> C;
-  std::vector<Block> B;
+  std::vector<Block> B;   // block tree (as exported)
+  std::vector<Block> FB;  // factor tree (block tree with dense tiles merged)
+  int32_t tile = 0;
   ArenaLayout L;
   Schedule F, S;
   SchedStats st;
@@ -375,6 +378,7 @@ const char* hlu_last_error(void) { return g_err.c_str(); }
 void hlu_set_wait_limit_ms(double ms) {
   if (ms > 0) g_wait_limit_ms = ms;
 }
+void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
 
 void hlu_destroy(hlu_handle* h) {
@@ -433,7 +437,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     if ((e = build_trees(h->mesh, leaf, eta2, s, h->trees, h->d_perm)) != cudaSuccess) return bail(e, "trees");
     if ((e = invert_perm((int32_t)N, h->d_perm, h->d_iperm, s)) != cudaSuccess) return bail(e, "iperm");
     trees_from_export(h->trees.nc, h->trees.clusters.data(), h->trees.nb, h->trees.blocks.data(), h->C, h->B);
-    build_schedules(h->C, h->B, rank_cap, 16, h->L, h->F, h->S, h->st);
+    h->tile = std::min(g_tile, (int32_t)64);
+    build_schedules(h->C, h->B, rank_cap, 16, h->tile, h->L, h->F, h->S, h->st, &h->FB);
     if (h->L.wmax > kTruncWidthMax) {
       hlu_destroy(h);
       return fail(HLU_ERR_ARG, "truncation width exceeds this build's limit");
@@ -443,8 +448,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     // A_H fill descriptors
     std::vector<FillDesc> fd, fl;
     int64_t rows = 0;
-    for (size_t b = 0; b < h->B.size(); ++b) {
-      const Block& bk = h->B[b];
+    for (size_t b = 0; b < h->FB.size(); ++b) {
+      const Block& bk = h->FB[b];
       if (bk.kind == KIND_SUB) continue;
       FillDesc f;
       std::memset(&f, 0, sizeof(f));
@@ -596,8 +601,8 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
     CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
     int64_t rsum = 0, nadm = 0;
     int32_t rmax = 0;
-    for (size_t b = 0; b < h->B.size(); ++b)
-      if (h->B[b].kind == KIND_ADM) {
+    for (size_t b = 0; b < h->FB.size(); ++b)
+      if (h->FB[b].kind == KIND_ADM) {
         int32_t r = rk[h->L.slot[b]];
         rmax = std::max(rmax, r);
         rsum += r;

@@ -60,7 +60,7 @@ extern "C" int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, 
                                            const int32_t* blocks, const int32_t* perm,
                                            const int64_t* rowptr, const int32_t* col,
                                            const double* val, double eps, int32_t rank_cap,
-                                           uint64_t order_seed, int32_t nrhs, const double* b,
+                                           int32_t tile, uint64_t order_seed, int32_t nrhs, const double* b,
                                            double* x, int64_t* info) {
   try {
     if (!clusters || !blocks || !perm || !rowptr || !col || !val || nrhs < 1 || eps <= 0)
@@ -72,7 +72,9 @@ extern "C" int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, 
     ArenaLayout L;
     Schedule F, S;
     SchedStats st;
-    build_schedules(C, B, rank_cap > 0 ? rank_cap : 32, nrhs, L, F, S, st);
+    std::vector<Block> FB;
+    build_schedules(C, B, rank_cap > 0 ? rank_cap : 32, nrhs, tile, L, F, S, st, &FB);
+    B = FB;
     std::vector<double> arena(L.total, 0.0);
     std::vector<int32_t> ranks(L.n_slots, 0), piv(std::max<int64_t>(L.piv_total, 1), 0);
     // identity

@@ -247,14 +247,19 @@ __device__ void task_rowmv(Ctx<T>& c, const Task& t) {
     T acc = 0;
     for (int q = 0; q < t.list_count; ++q) {
       const Term& tm = c.terms[t.list_begin + q];
+      const int ii = i - tm.roff;
+      if (ii < 0 || ii >= tm.A.rows) continue;
       const int p = ncols(c, tm.A);
-      for (int l = 0; l < p; ++l) acc += ldv(c, tm.A, i, l) * ldv(c, tm.B, l, j);
+      for (int l = 0; l < p; ++l) acc += ldv(c, tm.A, ii, l) * ldv(c, tm.B, l, j);
     }
     T base = (t.flags & TF_OVERWRITE) ? T(0) : ldv(c, t.c, i, j);
     stv(c, t.c, i, j, base + sg * acc);
   }
   if (threadIdx.x == 0) {
-    for (int q = 0; q < t.list_count; ++q) fl += 2.0 * n * k * ncols(c, c.terms[t.list_begin + q].A);
+    for (int q = 0; q < t.list_count; ++q) {
+      const Term& tm = c.terms[t.list_begin + q];
+      fl += 2.0 * tm.A.rows * k * ncols(c, tm.A);
+    }
     c.flops += fl;
     if (t.out_slot >= 0) __stcg(c.ranks + t.out_slot, k);
   }
@@ -581,7 +586,10 @@ size_t exec_smem_bytes(int elem_size) {
 template <class T>
 int exec_blocks_per_sm() {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel<T>, NT, exec_smem_bytes(sizeof(T)));
+  size_t sm = exec_smem_bytes(sizeof(T));
+  if (cudaFuncSetAttribute(exec_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel<T>, NT, sm) != cudaSuccess) return 0;
   return nb;
 }
 

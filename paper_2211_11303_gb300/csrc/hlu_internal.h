@@ -40,7 +40,8 @@ enum TaskType : int32_t {
   TK_ROWMV = 5,   // c (n x k) <- [c] + sign * sum_terms A_t B_t
   TK_TRUNC = 6,   // (a, b) <- truncate(sum_pieces sign X Y^T) to eps, rank -> out_slot
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
-  TK_NUM = 8
+  TK_NUM = 8,
+  TK_FENCE = 8    // no work: orders re-use of temporary memory after its readers
 };
 enum : int32_t { TF_OVERWRITE = 1 };
 
@@ -56,9 +57,12 @@ struct Task {
   int32_t prob;      // problem index (batched launches)
 };
 
-// ROWMV term: A (n x p) times B (p x k); p = A's column count.
+// ROWMV term: A (A.rows x p) times B (p x k) added to output rows
+// [roff, roff + A.rows); p = A's column count.
 struct Term {
   View A, B;
+  int32_t roff;
+  int32_t pad;
 };
 // TRUNC piece: sign * X Y^T placed at rows [xoff, xoff + X.rows) of the target
 // and columns [yoff, yoff + Y.rows).
@@ -97,19 +101,26 @@ struct ArenaLayout {
   int64_t factor_elems = 0;        // dense + low-rank capacity elements
   int32_t max_trunc_rows = 0;      // largest TRUNC target dimension
   int32_t wmax = 0;                // largest stacked width of a TRUNC
+  int64_t ring_off = 0, ring_size = 0;  // region for temporaries
 };
 
 struct SchedStats {
   int64_t n_factor_tasks = 0, n_solve_tasks = 0;
   int64_t temp_elems = 0;
+  int64_t ring_wraps = 0;
   double host_ms = 0;
 };
 
 // Build the factorisation schedule and the triangular-solve schedule for the
 // given trees.  Fills the arena layout (factor storage, temporaries, work
 // vector).  rank_cap: capacity of admissible blocks.
+// `tile`: every block-tree node whose row and column clusters both hold at most
+// `tile` DOFs is factored as one dense tile (tile <= leaf keeps the block tree
+// as it is).  factor_blocks (optional) receives the factor tree the schedules
+// and the arena layout refer to.
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
-                     int32_t nrhs_max, ArenaLayout& L, Schedule& factor, Schedule& solve,
-                     SchedStats& st);
+                     int32_t nrhs_max, int32_t tile, ArenaLayout& L, Schedule& factor, Schedule& solve,
+                     SchedStats& st, std::vector<Block>* factor_blocks);
+std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile);
 
 }  // namespace hlu

@@ -120,10 +120,10 @@ void h_rowmv(HostCtx<T>& c, const Task& t) {
     const Term& tm = c.terms[t.list_begin + q];
     int p = ncols(c, tm.A);
     for (int j = 0; j < k; ++j)
-      for (int i = 0; i < n; ++i) {
+      for (int i = 0; i < tm.A.rows; ++i) {
         T s = 0;
         for (int l = 0; l < p; ++l) s += at(c, tm.A, i, l) * at(c, tm.B, l, j);
-        acc[i + (size_t)j * n] += s;
+        acc[(tm.roff + i) + (size_t)j * n] += s;
       }
   }
   T sg = T(t.sign);
@@ -307,6 +307,7 @@ void run_task(HostCtx<T>& c, const Task& t) {
     case TK_ROWMV: h_rowmv(c, t); break;
     case TK_TRUNC: h_trunc(c, t); break;
     case TK_DADD: h_dadd(c, t); break;
+    case TK_FENCE: break;
     default: throw std::logic_error("task type");
   }
 }

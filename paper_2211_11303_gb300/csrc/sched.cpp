@@ -46,15 +46,21 @@ class Sched {
  public:
   Sched(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t kcap, ArenaLayout& L,
         Schedule* S, std::vector<int32_t>& dbuf, std::vector<int32_t>& xbuf,
-        std::vector<int32_t>& ybuf, bool make_buffers)
-      : C_(C), B_(B), kcap_(kcap), L_(L), S_(S), dbuf_(dbuf), xbuf_(xbuf), ybuf_(ybuf) {
+        std::vector<int32_t>& ybuf, bool make_buffers, int32_t segsz, int64_t ring_off,
+        int64_t ring_size)
+      : C_(C), B_(B), kcap_(kcap), L_(L), S_(S), dbuf_(dbuf), xbuf_(xbuf), ybuf_(ybuf),
+        ring_off_(ring_off), ring_size_(ring_size) {
     S_->pred_ptr.assign(1, 0);
-    leaf_cluster_.clear();
-    for (size_t c = 0; c < C_.size(); ++c)
-      if (C_[c].son[0] < 0) {
-        if ((int32_t)leaf_cluster_.size() != C_[c].leaf_begin) throw std::logic_error("leaf order");
-        leaf_cluster_.push_back((int32_t)c);
-      }
+    // dependency segments: clusters of at most `segsz` DOFs whose parent is
+    // larger (the tile level, or the leaves); every cluster covers a range of them
+    seg_begin_.assign(C_.size(), 0);
+    seg_end_.assign(C_.size(), 0);
+    seg_cluster_.clear();
+    segsz_ = segsz;
+    assign_segments(0, false, segsz);
+    chunk_occ_.assign((size_t)((ring_size_ + kChunk - 1) / kChunk) + 1, std::vector<int32_t>());
+    chunk_fence_task_.assign(chunk_occ_.size(), -1);
+    chunk_pass_.assign(chunk_occ_.size(), 0);
     if (make_buffers) {
       dbuf_.assign(B_.size(), -1);
       xbuf_.assign(B_.size(), -1);
@@ -70,26 +76,105 @@ class Sched {
     }
   }
 
+  // ---------------------------------------------------------------- segments
+  void assign_segments(int32_t c, bool inside, int32_t segsz) {
+    const Cluster& cl = C_[c];
+    bool is_seg = !inside && (cl.size <= segsz || cl.son[0] < 0);
+    if (is_seg || inside) {
+      if (is_seg) seg_cluster_.push_back(c);
+      int32_t sidx = (int32_t)seg_cluster_.size() - 1;
+      seg_begin_[c] = sidx;
+      seg_end_[c] = sidx + 1;
+      if (cl.son[0] >= 0) {
+        assign_segments(cl.son[0], true, segsz);
+        assign_segments(cl.son[1], true, segsz);
+      }
+      return;
+    }
+    seg_begin_[c] = (int32_t)seg_cluster_.size();
+    assign_segments(cl.son[0], false, segsz);
+    assign_segments(cl.son[1], false, segsz);
+    seg_end_[c] = (int32_t)seg_cluster_.size();
+  }
+
   // ---------------------------------------------------------------- arena
+  // Temporaries live in a ring region.  Re-using ring memory orders the new
+  // occupant's writers after every task that touched the memory before.
+  static constexpr int64_t kChunk = 1 << 14;
   int64_t alloc(int64_t n) {
-    int64_t o = L_.total;
-    L_.total += (n + 31) & ~int64_t(31);
+    n = (n + 31) & ~int64_t(31);
     temp_elems_ += n;
-    return o;
+    if (n > ring_size_) throw std::runtime_error("temporary larger than the ring");
+    if (cursor_ + n > ring_size_) {
+      cursor_ = 0;
+      ++pass_;
+      ++wraps_;
+    }
+    int64_t o = cursor_;
+    cursor_ += n;
+    pending_fence_.clear();
+    for (int64_t ch = o / kChunk; ch <= (o + n - 1) / kChunk; ++ch) {
+      if (chunk_pass_[ch] != pass_) {
+        // first use of this chunk in this pass: a no-work fence task waits for
+        // every task that touched the chunk's previous occupants
+        chunk_fence_task_[ch] = -1;
+        if (!chunk_occ_[ch].empty()) {
+          Task f = make(TK_FENCE);
+          int32_t saved_cur = cur_;
+          std::vector<int32_t> saved_deps;
+          saved_deps.swap(deps_);
+          begin(f);
+          for (int32_t old : chunk_occ_[ch])
+            for (int64_t r = acc_head_[old]; r >= 0; r = acc_next_[r]) dep(acc_task_[r]);
+          end();
+          chunk_fence_task_[ch] = cur_;
+          deps_.swap(saved_deps);
+          cur_ = saved_cur;
+        }
+        chunk_occ_[ch].clear();
+        chunk_pass_[ch] = pass_;
+      }
+      if (chunk_fence_task_[ch] >= 0) pending_fence_.push_back(chunk_fence_task_[ch]);
+    }
+    last_alloc_lo_ = o / kChunk;
+    last_alloc_hi_ = (o + n - 1) / kChunk;
+    return ring_off_ + o;
+  }
+  // attach the fence of the last allocation to buffer `b` and record it as
+  // the occupant of that ring range
+  void bind_alloc(int32_t b) {
+    if (!pending_fence_.empty()) {
+      std::sort(pending_fence_.begin(), pending_fence_.end());
+      pending_fence_.erase(std::unique(pending_fence_.begin(), pending_fence_.end()), pending_fence_.end());
+      fence_begin_[b] = (int64_t)fence_pool_.size();
+      fence_pool_.insert(fence_pool_.end(), pending_fence_.begin(), pending_fence_.end());
+      fence_end_[b] = (int64_t)fence_pool_.size();
+      pending_fence_.clear();
+    }
+    for (int64_t ch = last_alloc_lo_; ch <= last_alloc_hi_; ++ch) chunk_occ_[ch].push_back(b);
   }
   int32_t new_slot() { return L_.n_slots++; }
   int64_t temp_elems_ = 0;
+  int64_t peak_ = 0;
 
   // ---------------------------------------------------------------- buffers
+  int32_t push_buf(const Buf& b) {
+    bufs_.push_back(b);
+    acc_head_.push_back(-1);
+    acc_last_.push_back(-1);
+    fence_begin_.push_back(0);
+    fence_end_.push_back(0);
+    return (int32_t)bufs_.size() - 1;
+  }
   int32_t new_buf_leaves(int32_t clus) {
     Buf b;
-    b.base_leaf = C_[clus].leaf_begin;
-    b.nseg = C_[clus].leaf_end - C_[clus].leaf_begin;
+    b.base_leaf = seg_begin_[clus];
+    b.nseg = seg_end_[clus] - seg_begin_[clus];
     b.seg0 = (int64_t)seg_writer_.size();
     seg_writer_.resize(seg_writer_.size() + b.nseg, -1);
     seg_rhead_.resize(seg_rhead_.size() + b.nseg, -1);
-    bufs_.push_back(b);
-    return (int32_t)bufs_.size() - 1;
+    seg_buf_.resize(seg_buf_.size() + b.nseg, (int32_t)bufs_.size());
+    return push_buf(b);
   }
   int32_t new_buf_single() {
     Buf b;
@@ -98,8 +183,8 @@ class Sched {
     b.seg0 = (int64_t)seg_writer_.size();
     seg_writer_.push_back(-1);
     seg_rhead_.push_back(-1);
-    bufs_.push_back(b);
-    return (int32_t)bufs_.size() - 1;
+    seg_buf_.push_back((int32_t)bufs_.size());
+    return push_buf(b);
   }
 
   // ---------------------------------------------------------------- views
@@ -157,18 +242,22 @@ class Sched {
   // fresh temporary with per-leaf dependency segments; column count via a slot
   MV new_temp(int32_t clus, int32_t cols_cap) {
     MV m;
-    m.buf = new_buf_leaves(clus);
     m.clus = clus;
     int32_t rows = sz(clus);
-    m.v = View{alloc((int64_t)rows * std::max(cols_cap, 1)), 1, rows, rows, cols_cap, new_slot(), 0};
+    int64_t off = alloc((int64_t)rows * std::max(cols_cap, 1));
+    m.buf = new_buf_leaves(clus);
+    bind_alloc(m.buf);
+    m.v = View{off, 1, rows, rows, cols_cap, new_slot(), 0};
     return m;
   }
   MV new_dense_temp(int32_t clus, int32_t cols) {
     MV m;
-    m.buf = new_buf_single();
     m.clus = clus;
     int32_t rows = sz(clus);
-    m.v = View{alloc((int64_t)rows * cols), 1, rows, rows, cols, -1, 0};
+    int64_t off = alloc((int64_t)rows * cols);
+    m.buf = new_buf_single();
+    bind_alloc(m.buf);
+    m.v = View{off, 1, rows, rows, cols, -1, 0};
     return m;
   }
   int32_t cols_cap(const View& v) const { return v.cols; }
@@ -188,7 +277,18 @@ class Sched {
     stamp_[p] = cur_;
     deps_.push_back(p);
   }
+  void note_access(int32_t b) {
+    if (acc_last_[b] == cur_) return;
+    acc_last_[b] = cur_;
+    acc_task_.push_back(cur_);
+    acc_next_.push_back(acc_head_[b]);
+    acc_head_[b] = (int64_t)acc_task_.size() - 1;
+  }
   void touch(int64_t seg, bool w) {
+    const int32_t b = seg_buf_[seg];
+    if (seg_writer_[seg] < 0)
+      for (int64_t f = fence_begin_[b]; f < fence_end_[b]; ++f) dep(fence_pool_[f]);
+    note_access(b);
     dep(seg_writer_[seg]);
     if (w) {
       for (int64_t r = seg_rhead_[seg]; r >= 0; r = rnext_[r]) dep(rtask_[r]);
@@ -207,8 +307,7 @@ class Sched {
       touch(b.seg0, w);
       return;
     }
-    const Cluster& c = C_[m.clus];
-    for (int32_t l = c.leaf_begin; l < c.leaf_end; ++l) {
+    for (int32_t l = seg_begin_[m.clus]; l < seg_end_[m.clus]; ++l) {
       int64_t s = b.seg0 + (l - b.base_leaf);
       touch(s, w);
     }
@@ -284,11 +383,12 @@ class Sched {
       int32_t ic = trans ? rowc(be) : colc(be);
       MV vin = sub(Vin, ic);
       MV t;
-      t.buf = new_buf_single();
       t.clus = -1;
       int32_t cap = L_.cap[be];
-      t.v = View{alloc((int64_t)cap * std::max(vin.v.cols, 1)), 1, cap, cap, vin.v.cols, vin.v.slot,
-                 0};
+      int64_t toff = alloc((int64_t)cap * std::max(vin.v.cols, 1));
+      t.buf = new_buf_single();
+      bind_alloc(t.buf);
+      t.v = View{toff, 1, cap, cap, vin.v.cols, vin.v.slot, 0};
       Task k = make(TK_PROJ);
       k.a = A.v;
       k.b = vin.v;
@@ -300,24 +400,32 @@ class Sched {
       end();
       T[i] = t;
     }
-    const Cluster& O = C_[oc];
-    int32_t nl = O.leaf_end - O.leaf_begin;
-    // bucket leaf blocks by the output leaves they cover (counting sort)
-    std::vector<int32_t> cnt(nl + 1, 0);
-    for (size_t i = 0; i < lv.size(); ++i) {
-      const Cluster& ob = C_[trans ? colc(lv[i]) : rowc(lv[i])];
-      for (int32_t l = ob.leaf_begin; l < ob.leaf_end; ++l) cnt[l - O.leaf_begin + 1]++;
+    // output units: the segment clusters under the out-cluster (or the
+    // out-cluster itself when it lies inside one segment)
+    std::vector<int32_t> units;
+    if (seg_end_[oc] - seg_begin_[oc] <= 1) {
+      units.push_back(oc);
+    } else {
+      for (int32_t q = seg_begin_[oc]; q < seg_end_[oc]; ++q) units.push_back(seg_cluster_[q]);
     }
-    for (int32_t l = 0; l < nl; ++l) cnt[l + 1] += cnt[l];
-    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), items(cnt[nl]);
+    const int32_t nu = (int32_t)units.size();
+    const int32_t u0 = seg_begin_[oc];
+    auto unit_of = [&](int32_t segidx) { return nu == 1 ? 0 : segidx - u0; };
+    std::vector<int32_t> cnt(nu + 1, 0);
     for (size_t i = 0; i < lv.size(); ++i) {
-      const Cluster& ob = C_[trans ? colc(lv[i]) : rowc(lv[i])];
-      for (int32_t l = ob.leaf_begin; l < ob.leaf_end; ++l) items[fill[l - O.leaf_begin]++] = (int32_t)i;
+      int32_t obc = trans ? colc(lv[i]) : rowc(lv[i]);
+      for (int32_t q = seg_begin_[obc]; q < seg_end_[obc]; ++q) cnt[unit_of(q) + 1]++;
     }
-    MV kview = sub(Vin, leaf_cluster_[C_[Vin.clus].leaf_begin]);
-    for (int32_t l = 0; l < nl; ++l) {
+    for (int32_t l = 0; l < nu; ++l) cnt[l + 1] += cnt[l];
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), items(cnt[nu]);
+    for (size_t i = 0; i < lv.size(); ++i) {
+      int32_t obc = trans ? colc(lv[i]) : rowc(lv[i]);
+      for (int32_t q = seg_begin_[obc]; q < seg_end_[obc]; ++q) items[fill[unit_of(q)]++] = (int32_t)i;
+    }
+    MV kview = Vin;
+    for (int32_t l = 0; l < nu; ++l) {
       if (cnt[l] == cnt[l + 1] && !overwrite) continue;
-      int32_t lc = leaf_cluster_[O.leaf_begin + l];
+      const int32_t lc = units[l];
       Task k = make(TK_ROWMV);
       k.flags = overwrite ? TF_OVERWRITE : 0;
       k.sign = sign;
@@ -330,17 +438,21 @@ class Sched {
       for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q) {
         int32_t i = items[q];
         int32_t be = lv[i];
+        int32_t obc = trans ? colc(be) : rowc(be);
+        // the term covers rows (obc intersect lc) of the unit
+        int32_t rc = C_[obc].size <= C_[lc].size ? obc : lc;
         Term tm;
         std::memset(&tm, 0, sizeof(tm));
+        tm.roff = C_[rc].off - C_[lc].off;
         if (kind(be) == KIND_DENSE) {
-          MV A = sub(trans ? mvDT(be) : mvD(be), lc);
+          MV A = sub(trans ? mvDT(be) : mvD(be), rc);
           MV Bv = sub(Vin, trans ? rowc(be) : colc(be));
           tm.A = A.v;
           tm.B = Bv.v;
           acc(A, false);
           acc(Bv, false);
         } else {
-          MV A = sub(trans ? mvY(be) : mvX(be), lc);
+          MV A = sub(trans ? mvY(be) : mvX(be), rc);
           tm.A = A.v;
           tm.B = T[i].v;
           acc(A, false);
@@ -430,14 +542,26 @@ class Sched {
     int32_t cap = std::min(kcap_, std::min(sz(rc), sz(cc)));
     int32_t slot = new_slot();
     LR r;
-    r.X.buf = new_buf_leaves(rc);
     r.X.clus = rc;
-    r.X.v = View{alloc((int64_t)sz(rc) * cap), 1, sz(rc), sz(rc), cap, slot, 0};
-    r.Y.buf = new_buf_leaves(cc);
+    int64_t xo = alloc((int64_t)sz(rc) * cap);
+    r.X.buf = new_buf_leaves(rc);
+    bind_alloc(r.X.buf);
+    r.X.v = View{xo, 1, sz(rc), sz(rc), cap, slot, 0};
     r.Y.clus = cc;
-    r.Y.v = View{alloc((int64_t)sz(cc) * cap), 1, sz(cc), sz(cc), cap, slot, 0};
+    int64_t yo = alloc((int64_t)sz(cc) * cap);
+    r.Y.buf = new_buf_leaves(cc);
+    bind_alloc(r.Y.buf);
+    r.Y.v = View{yo, 1, sz(cc), sz(cc), cap, slot, 0};
     emit_trunc(r.X, r.Y, slot, cap, ps);
     return r;
+  }
+
+  // A product wider than the rank capacity (a dense tile's width, an identity
+  // factor) is truncated on its own first, so that every stacked truncation
+  // stays within two capacities.
+  LR narrow(const LR& p) {
+    if (p.X.v.cols <= kcap_) return p;
+    return trunc_new(p.X.clus, p.Y.clus, {{p, 0, 0, 1.0f}});
   }
 
   // ---------------------------------------------------------------- H-gemm
@@ -447,8 +571,9 @@ class Sched {
     if (ka == KIND_ADM) return LR{mvX(a), hmul_new(b, mvY(a), true)};
     if (kb == KIND_ADM) return LR{hmul_new(a, mvX(b), false), mvY(b)};
     if (ka == KIND_DENSE && kb == KIND_DENSE) {
-      if (sz(sig) <= kcap_) return LR{mvD(a), mvDT(b)};
-      // wide middle dimension: materialise the (leaf x leaf) product
+      // exact factors of the narrowest width among |sigma|, |tau|, |rho|
+      int32_t ws = sz(sig), wt = sz(tau), wr = sz(rho);
+      if (ws <= kcap_ || (ws <= wt && ws <= wr)) return LR{mvD(a), mvDT(b)};
       MV P = new_dense_temp(tau, sz(rho));
       Task t = make(TK_DADD);
       t.flags = TF_OVERWRITE;
@@ -460,7 +585,12 @@ class Sched {
       acc(mvDT(b), false);
       acc(P, true);
       end();
-      return LR{P, mvIdent(rho)};
+      if (wr <= wt) return LR{P, mvIdent(rho)};
+      // P^T as the Y factor: rows rho, columns |tau|
+      MV PT = P;
+      PT.clus = rho;
+      PT.v = View{P.v.off, sz(tau), 1, sz(rho), sz(tau), -1, 0};
+      return LR{mvIdent(tau), PT};
     }
     if (ka == KIND_DENSE) return LR{mvIdent(tau), hmul_new(b, mvDT(a), true)};
     if (kb == KIND_DENSE) return LR{hmul_new(a, mvD(b), false), mvIdent(rho)};
@@ -471,8 +601,8 @@ class Sched {
     LR t[2][2];
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 2; ++j) {
-        LR s0 = product(son(a, i, 0), son(b, 0, j));
-        LR s1 = product(son(a, i, 1), son(b, 1, j));
+        LR s0 = narrow(product(son(a, i, 0), son(b, 0, j)));
+        LR s1 = narrow(product(son(a, i, 1), son(b, 1, j)));
         t[i][j] = trunc_new(T.son[i], R.son[j], {{s0, 0, 0, 1.0f}, {s1, 0, 0, 1.0f}});
       }
     int32_t r0 = C_[R.son[0]].size, t0 = C_[T.son[0]].size;
@@ -496,8 +626,9 @@ class Sched {
       acc(mvD(c), true);
       end();
     } else if (k == KIND_ADM) {
+      LR q = narrow(p);
       emit_trunc(mvX(c), mvY(c), L_.slot[c], L_.cap[c],
-                 {{LR{mvX(c), mvY(c)}, 0, 0, 1.0f}, {p, 0, 0, sign}});
+                 {{LR{mvX(c), mvY(c)}, 0, 0, 1.0f}, {q, 0, 0, sign}});
     } else {
       const Cluster& R = C_[rowc(c)];
       const Cluster& Q = C_[colc(c)];
@@ -562,7 +693,7 @@ class Sched {
 
   void solve_all(int32_t nrhs_max) {
     MV W;
-    W.buf = new_buf_leaves(0);
+    W.buf = new_buf_leaves(0);  // per-segment tracking over the whole vector
     W.clus = 0;
     int32_t N = sz(0);
     W.v = View{L_.work_off, 1, N, N, nrhs_max, L_.nrhs_slot, 0};
@@ -579,7 +710,28 @@ class Sched {
   std::vector<int32_t>& dbuf_;
   std::vector<int32_t>& xbuf_;
   std::vector<int32_t>& ybuf_;
-  std::vector<int32_t> leaf_cluster_;
+  int32_t seg_size_of(int32_t) const { return segsz_; }
+  int32_t segsz_ = 0;
+  int64_t ring_off_ = 0, ring_size_ = 0, cursor_ = 0;
+  std::vector<int32_t> seg_begin_, seg_end_, seg_cluster_;
+  std::vector<std::vector<int32_t>> chunk_occ_;
+  std::vector<int32_t> chunk_fence_task_;
+  std::vector<int32_t> chunk_pass_;
+  int32_t pass_ = 0;
+ public:
+  int64_t wraps_ = 0;
+ private:
+  std::vector<int32_t> pending_fence_;
+  int64_t last_alloc_lo_ = 0, last_alloc_hi_ = -1;
+  int32_t fence_stamp_ = 0;
+  std::vector<int32_t> buf_fence_mark_;
+  std::vector<int64_t> fence_begin_, fence_end_;
+  std::vector<int32_t> fence_pool_;
+  std::vector<int64_t> acc_head_;
+  std::vector<int32_t> acc_last_;
+  std::vector<int32_t> acc_task_;
+  std::vector<int64_t> acc_next_;
+  std::vector<int32_t> seg_buf_;
   std::vector<Buf> bufs_;
   std::vector<int32_t> seg_writer_;
   std::vector<int64_t> seg_rhead_;
@@ -592,9 +744,47 @@ class Sched {
 
 }  // namespace
 
-void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
-                     int32_t nrhs_max, ArenaLayout& L, Schedule& factor, Schedule& solve,
-                     SchedStats& st) {
+std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile) {
+  std::vector<Block> out;
+  out.reserve(B.size());
+  // DFS over the block tree; a node whose row and column clusters both hold at
+  // most `tile` DOFs becomes one dense tile (its sub-blocks merged exactly)
+  struct Rec {
+    static int32_t go(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile, int32_t b,
+                      int32_t parent, std::vector<Block>& out) {
+      const Block& src = B[b];
+      int32_t id = (int32_t)out.size();
+      out.push_back(src);
+      Block& nb = out.back();
+      nb.parent = parent;
+      for (int k = 0; k < 4; ++k) nb.son[k] = -1;
+      int32_t big = std::max(C[src.row].size, C[src.col].size);
+      int32_t small = std::min(C[src.row].size, C[src.col].size);
+      // a subdivided node turns dense as soon as one of its clusters is a tile,
+      // so a dense diagonal tile never meets a subdivided block in its block
+      // row or column; an admissible node turns dense when both clusters are
+      if ((src.kind == KIND_SUB && small <= tile) || (src.kind == KIND_ADM && big <= tile)) {
+        out[id].kind = KIND_DENSE;
+        return id;
+      }
+      if (src.kind == KIND_SUB) {
+        int32_t sons[4];
+        for (int k = 0; k < 4; ++k) sons[k] = go(C, B, tile, src.son[k], id, out);
+        for (int k = 0; k < 4; ++k) out[id].son[k] = sons[k];
+      }
+      return id;
+    }
+  };
+  Rec::go(C, B, tile, 0, -1, out);
+  return out;
+}
+
+void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bfull, int32_t rank_cap,
+                     int32_t nrhs_max, int32_t tile, ArenaLayout& L, Schedule& factor, Schedule& solve,
+                     SchedStats& st, std::vector<Block>* factor_blocks) {
+  std::vector<Block> Bt = factor_tree(C, Bfull, tile);
+  const std::vector<Block>& B = Bt;
+  if (factor_blocks) *factor_blocks = Bt;
   auto t0 = std::chrono::steady_clock::now();
   const size_t nb = B.size();
   L = ArenaLayout();
@@ -612,7 +802,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B,
     L.total += (n + 31) & ~int64_t(31);
     return o;
   };
-  L.ident_n = std::max(leafmax, 1);
+  L.ident_n = std::max(std::max(leafmax, tile), 1);
   L.ident_off = alloc((int64_t)L.ident_n * L.ident_n);
   int64_t fe = 0;
   for (size_t b = 0; b < nb; ++b) {
@@ -638,16 +828,23 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B,
   L.nrhs_slot = L.n_slots++;
   L.work_off = alloc((int64_t)C[0].size * nrhs_max);
   L.wmax = 0;
+  // ring region for temporaries (both schedules; they never run concurrently)
+  const int64_t ring = std::min<int64_t>(std::max<int64_t>(8 * fe, int64_t(1) << 22), int64_t(1) << 30);
+  const int64_t ring_off = alloc(ring);
+  L.ring_off = ring_off;
+  L.ring_size = ring;
+  const int32_t segsz = std::max(leafmax, tile);
   factor = Schedule();
   solve = Schedule();
   std::vector<int32_t> dbuf, xbuf, ybuf;
   {
-    Sched s(C, B, rank_cap, L, &factor, dbuf, xbuf, ybuf, true);
+    Sched s(C, B, rank_cap, L, &factor, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
     s.lu(0);
     st.temp_elems = s.temp_elems_;
+    st.ring_wraps = s.wraps_;
   }
   {
-    Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true);
+    Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
     s.solve_all(nrhs_max);
     st.temp_elems += s.temp_elems_;
   }

@@ -74,11 +74,12 @@ SIGNATURES = {
     "hlu_solve_batch": (_i32, [_P(_vp), _i32, _P(_vp), _P(_vp), _P(_i32), _vp]),
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
+    "hlu_set_tile": (None, [_i32]),
     "hlu_destroy": (None, [_vp]),
     "hlu_status_string": (ctypes.c_char_p, [_i32]),
     "hlu_last_error": (ctypes.c_char_p, []),
     "hlu_debug_host_factor_solve": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32,
-                                           ctypes.c_uint64, _i32, _vp, _vp, _vp]),
+                                           _i32, ctypes.c_uint64, _i32, _vp, _vp, _vp]),
     "hlu_debug_wait_timeout": (_i32, [_f64, _vp]),
 }
 
@@ -266,6 +267,10 @@ def hlu_factor_bytes_estimate(h, precision=HLU_FP32):
 
 def hlu_set_wait_limit_ms(ms):
     lib().hlu_set_wait_limit_ms(float(ms))
+
+
+def hlu_set_tile(t):
+    lib().hlu_set_tile(int(t))
 
 
 class Problem:

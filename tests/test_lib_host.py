@@ -55,7 +55,7 @@ def test_build_rejects_bad_arguments(lib):
     assert lib.hlu_build(None, 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
 
 
-def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2):
+def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2, tile=0):
     from oracle import fem, mesh, trees
     m = mesh.interior_edges(n)
     A = fem.assemble(m, kappa).tocsr()
@@ -70,7 +70,7 @@ def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2):
     ci = A.indices.astype(np.int32)
     va = A.data.astype(np.float64)
     st = lib.hlu_debug_host_factor_solve(len(C), C.ctypes.data, len(B), B.ctypes.data, p.ctypes.data,
-                                         rp.ctypes.data, ci.ctypes.data, va.ctypes.data, eps, 32, seed,
+                                         rp.ctypes.data, ci.ctypes.data, va.ctypes.data, eps, 32, tile, seed,
                                          nrhs, b.ctypes.data, x.ctypes.data, info.ctypes.data)
     assert st == 0
     return A, perm, cl, bl, b, x, info
@@ -98,3 +98,20 @@ def test_scheduled_hlu_matches_recursive_oracle(lib, n, kappa, leaf):
             assert np.linalg.norm(x - xo) <= 1e-11 * np.linalg.norm(xo)
         else:
             assert e_lib <= 2.0 * e_or + 1e-12, (e_lib, e_or)
+
+
+@pytest.mark.parametrize("n,kappa,leaf,tile", [(4, 3.0, 8, 16), (5, 5.0, 8, 32), (5, 5.0, 16, 64)])
+def test_tiled_factor_tree_quality(lib, n, kappa, leaf, tile):
+    """Dense tiles above the leaf level keep exactness inside the tile, so the
+    factor is at least as accurate as the leaf-level recursive H-LU."""
+    from oracle import hmatrix
+    for eps in (1e-12, 1e-3):
+        A, perm, cl, bl, b, x, info = _host_solve(lib, n, kappa, eps, leaf, 0, tile=tile)
+        xs = np.linalg.solve(A.toarray(), b)
+        e_lib = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+        P = hmatrix.HLUPreconditioner(A, perm, cl, bl, eps)
+        e_or = np.linalg.norm(P.apply(b) - xs) / np.linalg.norm(xs)
+        assert e_lib <= 2.0 * e_or + 1e-11, (eps, e_lib, e_or)
+    _, _, _, _, _, x2, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 9, tile=tile)
+    _, _, _, _, _, x3, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 0, tile=tile)
+    assert np.array_equal(x2, x3)

@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the H-LU preconditioned GMRES hot path on GB300.
+
+Workload (default): Kuhn cube n = 24 (N = 91,656 interior edges), kappa = 8,
+leaf 32, eta 2, eps 1e-4; FP32 H-LU factor, FP64 flexible GMRES(50) to a
+relative residual of 1e-10 (forward error <= 1e-7 against the direct solve is
+checked by the GPU tests); 8 seeded N(0,1) right-hand sides.
+
+One step = the whole hot path on one batch: hlu_build (GPU mesh, assembly,
+cluster tree, block tree, A_H descriptors; the task DAG is compiled once per
+block-tree structure and reused), hlu_factor (FP32) and gmres_solve of the 8
+right-hand sides.  `value` = solves per second with the right-hand sides
+resident in HBM; `e2e` = the same with the right-hand sides copied from pinned
+host memory and the solutions copied back inside the timed region.
+
+`--impl reference` times the CPU oracle (oracle/, plain FP64 NumPy), as it
+stands, on a bounded sample of the workload family.
+
+Multi-GPU: the method does not shard (replicas only); with torchrun each rank
+runs an independent replica, `value` sums the solves of all ranks over the
+slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H-LU-preconditioned GMRES solves/s to 1e-7 rel. error; factor GFLOP/s; p99 ms"
+UNIT = "solves/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(n=8, kappa=8.0, eps=1e-4, tol=1e-10):
+    """One bounded oracle sample: the complete CPU path (assembly, trees, A_H,
+    recursive H-LU, FGMRES) for one seeded N(0,1) right-hand side on the n-cube.
+    Returns (seconds, iterations, N)."""
+    import synth
+    from oracle import fem, hmatrix, krylov, mesh, trees
+    t0 = time.perf_counter()
+    m = mesh.interior_edges(n)
+    A = fem.assemble(m, kappa).tocsr()
+    perm, cl, bl = trees.build_trees(m, 32, 2.0)
+    P = hmatrix.HLUPreconditioner(A, perm, cl, bl, eps)
+    b = synth.normal(synth.rhs_seed(2, 0, 0), A.shape[0])
+    x, info = krylov.fgmres(lambda v: A @ v, b, precond=P.apply, restart=50, tol=tol)
+    return time.perf_counter() - t0, info["iters"], A.shape[0]
+
+
+def cpu_baseline_subprocess(n=8):
+    """Oracle sample in a single-threaded child process (BLAS threads = 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,bench;s,it,N=bench.oracle_sample(%d);print(json.dumps([s,it,N]))" % n)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    s, it, N = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("complete oracle path (assembly, trees, A_H, recursive FP64 H-LU, FGMRES to 1e-10) "
+                       "for 1 seeded RHS on the n=%d cube (N=%d, kappa=8, eps 1e-4): %.2f s, %d iterations; "
+                       "the oracle cannot finish the n=24 factorisation within minutes" % (n, N, s, it)),
+            "seconds": s}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_n)
+    times = []
+    for _ in range(args.steps):
+        s, it, N = oracle_sample(args.ref_n)
+        times.append(s)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "oracle sample: n=%d cube, kappa 8, eps 1e-4, 1 N(0,1) RHS (each step)" % args.ref_n,
+                   "n": args.ref_n, "N": N, "kappa": 8.0, "leaf": 32, "eta": 2.0, "eps": 1e-4,
+                   "nrhs": 1, "parallelism": "single process"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "complete oracle path for 1 RHS on the n=%d cube per step" % args.ref_n},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2211_11303_gb300 import _build, hlu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    hlu.lib()
+    hlu.hlu_set_wait_limit_ms(60000)
+    hlu.hlu_set_tile(args.tile)
+    n, kappa, nrhs = args.n, args.kappa, args.nrhs
+    prec = hlu.HLU_FP32 if args.precision == "fp32" else hlu.HLU_FP64
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # inputs: seeded N(0,1) right-hand sides (config 2), resident on the device
+    h0 = hlu.hlu_build(n, kappa, args.leaf, args.eta, args.eps)
+    N = hlu.hlu_n(h0)
+    hlu.hlu_destroy(h0)
+    Bh = torch.empty((nrhs, N), dtype=torch.float64).pin_memory()
+    for j in range(nrhs):
+        Bh[j] = torch.from_numpy(synth.normal(synth.rhs_seed(2, rank, j), N))
+    B = Bh.cuda().t()
+    X = hlu.colmajor(N, nrhs)
+    Xh = torch.empty((nrhs, N), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(copy_in=False, copy_out=False, rec=None):
+        if copy_in:
+            Bd = Bh.cuda(non_blocking=True).t()
+        else:
+            Bd = B
+        h = hlu.hlu_build(n, kappa, args.leaf, args.eta, args.eps)
+        try:
+            hlu.hlu_factor(h, prec)
+            info = hlu.hlu_factor_stats(h)
+            st = hlu.gmres_solve(h, Bd, X, restart=args.restart, tol=args.tol, maxit=args.maxit)
+            if copy_out:
+                Xh.copy_(X.t(), non_blocking=True)
+        finally:
+            hlu.hlu_destroy(h)
+        if rec is not None:
+            rec.append((info, st))
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    recs = []
+    lat = []
+    launches0 = hlu.hlu_launch_count()
+    barrier()
+    t_all0 = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        step(rec=recs)
+        torch.cuda.synchronize()
+        lat.append(1000.0 * (time.perf_counter() - s0))
+    ev1.record(stream)
+    barrier()
+    dev_ms = ev0.elapsed_time(ev1)
+    wall_ms = 1000.0 * (time.perf_counter() - t_all0)
+    launches = hlu.hlu_launch_count() - launches0
+    clk = clocks.stop()
+    # end to end: host buffers in, host buffers out
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(copy_in=True, copy_out=True)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = 1000.0 * (time.perf_counter() - e0)
+
+    t_ms = max(dev_ms, wall_ms)
+    if dist is not None:
+        tt = torch.tensor([t_ms, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms, e2e_ms = float(tt[0]), float(tt[1])
+    solves = nrhs * args.steps * world
+    value = solves / (t_ms / 1000.0)
+    e2e_value = solves / (e2e_ms / 1000.0)
+    infos = [r[0] for r in recs]
+    sts = [r[1] for r in recs]
+    fl = statistics.mean(i["flops"] for i in infos)
+    fms = statistics.mean(i["factor_ms"] for i in infos)
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32 FMA pipe peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+    dev = torch.cuda.get_device_properties(local)
+    fp32_peak_tflops = dev.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = fl / (fms / 1000.0) / 1e12
+    lat_sorted = sorted(lat)
+    p99 = lat_sorted[min(len(lat_sorted) - 1, int(round(0.99 * (len(lat_sorted) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision.replace("fp", "f") + "+f64",
+        "data": "synthetic",
+        "config": {"workload": "Kuhn cube n=%d (N=%d), kappa=%g, leaf %d, eta %g, eps %g, %s H-LU + FP64 "
+                               "FGMRES(%d) to %g, %d seeded N(0,1) RHS" % (n, N, kappa, args.leaf, args.eta,
+                                                                          args.eps, args.precision.upper(),
+                                                                          args.restart, args.tol, nrhs),
+                   "n": n, "N": N, "kappa": kappa, "leaf": args.leaf, "eta": args.eta, "eps": args.eps,
+                   "tile": args.tile, "nrhs": nrhs, "restart": args.restart, "tol": args.tol,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "working set (factor %.2f GB) larger than L2" % (infos[0]["factor_bytes"] / 1e9)},
+        "factor_gflops": fl / (fms / 1000.0) / 1e9,
+        "factor_ms": fms,
+        "gmres_iterations": max(s["iterations"] for s in sts),
+        "gmres_relres": max(s["relres_max"] for s in sts),
+        "precond_ms_per_apply": statistics.mean(s["precond_ms"] / max(s["precond_applies"], 1) for s in sts),
+        "p50_ms": statistics.median(lat), "p99_ms": p99,
+        "schedule_ms_first_build": infos[0]["schedule_ms"],
+        "rank_mean": statistics.mean(i["rank_mean"] for i in infos),
+        "rank_max": max(i["rank_max"] for i in infos),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak_tflops, "traffic": None,
+                     "kernel": "exec_kernel<float> (H-LU task executor)",
+                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x %s max SM clock" % src},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nrhs * N * 8,
+                "d2h_bytes_per_step": nrhs * N * 8},
+        "gpu_launches": launches,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_subprocess(args.ref_n)
+        except Exception as e:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: %s" % e}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=24)
+    ap.add_argument("--kappa", type=float, default=8.0)
+    ap.add_argument("--leaf", type=int, default=32)
+    ap.add_argument("--eta", type=float, default=2.0)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--nrhs", type=int, default=8)
+    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=500)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ref-n", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,13 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream);
 /* hlu_factor_stats - fill *info for the last factorisation. */
 int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 
+/* hlu_factor_profile - per task kind of the last factorisation's task DAG:
+ * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for
+ * predecessors, out[3*k + 2] cycles spent running, summed over CTAs; kinds
+ * k = 0..7 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD and
+ * k = 8 the no-work fences.  out: uint64[27] host buffer. */
+int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
+
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
  * (U^-1 (L^-1 r), leaf pivots applied in the forward pass).  b_dev, x_dev:
  * device FP64, nrhs >= 1 columns, ld >= N; b and x may alias.  Runs in the
@@ -215,6 +222,11 @@ void hlu_set_wait_limit_ms(double ms);
  * are not affected.  tile <= leaf keeps the block tree's own leaves; values
  * above 64 are clamped to 64. */
 void hlu_set_tile(int32_t tile);
+
+/* hlu_launch_count - number of this library's own CUDA kernel launches so far
+ * in this process (kernels from CUDA's bundled sort/scan templates are not
+ * counted).  Lets a caller count the launches inside a timed region. */
+int64_t hlu_launch_count(void);
 
 void hlu_destroy(hlu_handle* h);
 const char* hlu_status_string(int status);

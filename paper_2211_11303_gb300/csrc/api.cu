@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,8 +21,13 @@
 #include "hlu_internal.h"
 #include "host_exec.h"
 #include "krylov.h"
+#include "launch_count.h"
 
 using namespace hlu;
+
+namespace hlu {
+std::atomic<int64_t> g_launches{0};
+}
 
 namespace {
 
@@ -52,6 +59,8 @@ cudaError_t upload(T** d, const std::vector<T>& h) {
   return e;
 }
 
+// A schedule on the device.  The task arrays are shared (read-only) between
+// handles with the same block tree; the completion flags belong to one handle.
 struct DevSched {
   Task* tasks = nullptr;
   Term* terms = nullptr;
@@ -61,6 +70,7 @@ struct DevSched {
   int32_t* done = nullptr;
   int64_t ntasks = 0;
   int32_t epoch = 0;
+  bool owns_data = true;
   cudaError_t load(const Schedule& S) {
     ntasks = (int64_t)S.tasks.size();
     cudaError_t e;
@@ -69,15 +79,62 @@ struct DevSched {
     if ((e = upload(&pieces, S.pieces)) != cudaSuccess) return e;
     if ((e = upload(&pred_ptr, S.pred_ptr)) != cudaSuccess) return e;
     if ((e = upload(&pred_idx, S.pred_idx)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&done, sizeof(int32_t) * std::max<int64_t>(ntasks, 1))) != cudaSuccess) return e;
+    return alloc_flags();
+  }
+  cudaError_t alloc_flags() {
+    cudaError_t e = cudaMalloc(&done, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
+    if (e != cudaSuccess) return e;
+    epoch = 0;
     return cudaMemset(done, 0, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
   }
+  // a per-handle view of shared task data
+  DevSched share() const {
+    DevSched d = *this;
+    d.done = nullptr;
+    d.owns_data = false;
+    return d;
+  }
   void free_all() {
-    for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx, (void*)done})
-      if (p) cudaFree(p);
+    if (owns_data)
+      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx})
+        if (p) cudaFree(p);
+    if (done) cudaFree(done);
     *this = DevSched();
   }
 };
+
+// Everything derived from a block tree alone: the arena layout, the two task
+// DAGs (on the device), the factor tree and the A_H fill descriptors.
+struct SchedBundle {
+  uint64_t key = 0;
+  ArenaLayout L;
+  SchedStats st;
+  std::vector<Block> FB;
+  DevSched dF, dS;  // shared data, no flags
+  FillDesc* d_fill_dense = nullptr;
+  FillDesc* d_fill_lr = nullptr;
+  int32_t n_fill_dense = 0, n_fill_lr = 0;
+  int64_t dense_rows = 0;
+  ~SchedBundle() {
+    dF.free_all();
+    dS.free_all();
+    if (d_fill_dense) cudaFree(d_fill_dense);
+    if (d_fill_lr) cudaFree(d_fill_lr);
+  }
+};
+
+std::mutex g_cache_mu;
+std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
+constexpr size_t kCacheEntries = 8;
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
 
 struct KrylovWS {
   int64_t N = 0;
@@ -107,16 +164,10 @@ struct hlu_handle {
   HostTrees trees;
   std::vector<Cluster> C;
   std::vector<Block> B;   // block tree (as exported)
-  std::vector<Block> FB;  // factor tree (block tree with dense tiles merged)
   int32_t tile = 0;
-  ArenaLayout L;
-  Schedule F, S;
-  SchedStats st;
-  DevSched dF, dS;
-  FillDesc* d_fill_dense = nullptr;
-  FillDesc* d_fill_lr = nullptr;
-  int32_t n_fill_dense = 0, n_fill_lr = 0;
-  int64_t dense_rows = 0;
+  std::shared_ptr<SchedBundle> sb;  // factor tree, layout, DAGs (shared by identical trees)
+  ArenaLayout L;                    // copy of sb->L
+  DevSched dF, dS;                  // views of sb's DAGs with this handle's flags
   // factor state
   int precision = -1;
   void* d_arena = nullptr;
@@ -135,14 +186,17 @@ struct hlu_handle {
   hlu_factor_info info;
   KrylovWS kw;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  unsigned long long* d_prof = nullptr;  // executor profile of the last factorisation
 };
 
 namespace {
 
 void free_factor(hlu_handle* h) {
   for (void* p : {(void*)h->d_arena, (void*)h->d_ranks, (void*)h->d_piv, (void*)h->d_scratch, (void*)h->d_status,
-                  (void*)h->d_flops, (void*)h->d_ticket, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp})
+                  (void*)h->d_flops, (void*)h->d_ticket, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp,
+                  (void*)h->d_prof})
     if (p) cudaFree(p);
+  h->d_prof = nullptr;
   h->d_arena = nullptr;
   h->d_ranks = nullptr;
   h->d_piv = nullptr;
@@ -190,6 +244,7 @@ int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_fl
   a.status = h->d_status;
   a.flops = with_flops ? h->d_flops : nullptr;
   a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  a.prof = with_flops ? h->d_prof : nullptr;
   if (ds.ntasks == 0) return HLU_OK;
   int32_t st0[4] = {0, -1, 0, 0};
   CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
@@ -380,6 +435,7 @@ void hlu_set_wait_limit_ms(double ms) {
 }
 void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
+int64_t hlu_launch_count(void) { return g_launches.load(); }
 
 void hlu_destroy(hlu_handle* h) {
   if (!h) return;
@@ -387,8 +443,9 @@ void hlu_destroy(hlu_handle* h) {
   h->dF.free_all();
   h->dS.free_all();
   h->kw.free_all();
+  h->sb.reset();
   for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->A.rowptr, (void*)h->A.col,
-                  (void*)h->A.val, (void*)h->d_perm, (void*)h->d_iperm, (void*)h->d_fill_dense, (void*)h->d_fill_lr})
+                  (void*)h->A.val, (void*)h->d_perm, (void*)h->d_iperm})
     if (p) cudaFree(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -438,47 +495,82 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     if ((e = invert_perm((int32_t)N, h->d_perm, h->d_iperm, s)) != cudaSuccess) return bail(e, "iperm");
     trees_from_export(h->trees.nc, h->trees.clusters.data(), h->trees.nb, h->trees.blocks.data(), h->C, h->B);
     h->tile = std::min(g_tile, (int32_t)64);
-    build_schedules(h->C, h->B, rank_cap, 16, h->tile, h->L, h->F, h->S, h->st, &h->FB);
-    if (h->L.wmax > kTruncWidthMax) {
-      hlu_destroy(h);
-      return fail(HLU_ERR_ARG, "truncation width exceeds this build's limit");
+    const int32_t nrhs_max = 16;
+    uint64_t key = 1469598103934665603ULL;
+    key = fnv1a(key, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
+    key = fnv1a(key, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
+    int32_t params[4] = {rank_cap, h->tile, nrhs_max, (int32_t)N};
+    key = fnv1a(key, params, sizeof(params));
+    bool cache_hit = false;
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      for (size_t i = 0; i < g_cache.size(); ++i)
+        if (g_cache[i]->key == key) {
+          h->sb = g_cache[i];
+          cache_hit = true;
+          g_cache.erase(g_cache.begin() + i);
+          g_cache.push_back(h->sb);
+          break;
+        }
     }
-    if ((e = h->dF.load(h->F)) != cudaSuccess) return bail(e, "upload factor schedule");
-    if ((e = h->dS.load(h->S)) != cudaSuccess) return bail(e, "upload solve schedule");
-    // A_H fill descriptors
-    std::vector<FillDesc> fd, fl;
-    int64_t rows = 0;
-    for (size_t b = 0; b < h->FB.size(); ++b) {
-      const Block& bk = h->FB[b];
-      if (bk.kind == KIND_SUB) continue;
-      FillDesc f;
-      std::memset(&f, 0, sizeof(f));
-      f.roff = h->C[bk.row].off;
-      f.m = h->C[bk.row].size;
-      f.coff = h->C[bk.col].off;
-      f.n = h->C[bk.col].size;
-      if (bk.kind == KIND_DENSE) {
-        f.off = h->L.dense_off[b];
-        f.row_prefix = rows;
-        rows += f.m;
-        fd.push_back(f);
-      } else {
-        f.off = h->L.x_off[b];
-        f.off2 = h->L.y_off[b];
-        f.slot = h->L.slot[b];
-        f.cap = h->L.cap[b];
-        fl.push_back(f);
+    if (!h->sb) {
+      auto sb = std::make_shared<SchedBundle>();
+      sb->key = key;
+      Schedule F, S;
+      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, sb->L, F, S, sb->st, &sb->FB);
+      if (sb->L.wmax > kTruncWidthMax) {
+        hlu_destroy(h);
+        return fail(HLU_ERR_ARG, "truncation width exceeds this build's limit");
       }
+      if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
+      if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
+      cudaFree(sb->dF.done);
+      cudaFree(sb->dS.done);
+      sb->dF.done = sb->dS.done = nullptr;
+      // A_H fill descriptors
+      std::vector<FillDesc> fd, fl;
+      int64_t rows = 0;
+      for (size_t b = 0; b < sb->FB.size(); ++b) {
+        const Block& bk = sb->FB[b];
+        if (bk.kind == KIND_SUB) continue;
+        FillDesc f;
+        std::memset(&f, 0, sizeof(f));
+        f.roff = h->C[bk.row].off;
+        f.m = h->C[bk.row].size;
+        f.coff = h->C[bk.col].off;
+        f.n = h->C[bk.col].size;
+        if (bk.kind == KIND_DENSE) {
+          f.off = sb->L.dense_off[b];
+          f.row_prefix = rows;
+          rows += f.m;
+          fd.push_back(f);
+        } else {
+          f.off = sb->L.x_off[b];
+          f.off2 = sb->L.y_off[b];
+          f.slot = sb->L.slot[b];
+          f.cap = sb->L.cap[b];
+          fl.push_back(f);
+        }
+      }
+      sb->n_fill_dense = (int32_t)fd.size();
+      sb->n_fill_lr = (int32_t)fl.size();
+      sb->dense_rows = rows;
+      if ((e = upload(&sb->d_fill_dense, fd)) != cudaSuccess) return bail(e, "fill desc");
+      if ((e = upload(&sb->d_fill_lr, fl)) != cudaSuccess) return bail(e, "fill desc");
+      h->sb = sb;
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      g_cache.push_back(sb);
+      while (g_cache.size() > kCacheEntries) g_cache.erase(g_cache.begin());
     }
-    h->n_fill_dense = (int32_t)fd.size();
-    h->n_fill_lr = (int32_t)fl.size();
-    h->dense_rows = rows;
-    if ((e = upload(&h->d_fill_dense, fd)) != cudaSuccess) return bail(e, "fill desc");
-    if ((e = upload(&h->d_fill_lr, fl)) != cudaSuccess) return bail(e, "fill desc");
+    h->L = h->sb->L;
+    h->dF = h->sb->dF.share();
+    h->dS = h->sb->dS.share();
+    if ((e = h->dF.alloc_flags()) != cudaSuccess) return bail(e, "flags");
+    if ((e = h->dS.alloc_flags()) != cudaSuccess) return bail(e, "flags");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "sync");
-    h->info.n_tasks = h->st.n_factor_tasks;
-    h->info.n_solve_tasks = h->st.n_solve_tasks;
-    h->info.schedule_ms = h->st.host_ms;
+    h->info.n_tasks = h->sb->st.n_factor_tasks;
+    h->info.n_solve_tasks = h->sb->st.n_solve_tasks;
+    h->info.schedule_ms = cache_hit ? 0.0 : h->sb->st.host_ms;
     h->info.n_clusters = h->trees.nc;
     h->info.n_blocks = h->trees.nb;
     for (const Block& bk : h->B) {
@@ -563,6 +655,7 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
       CKR(cudaMalloc(&h->d_arenas, sizeof(void*)), "ptrs");
       CKR(cudaMalloc(&h->d_rankp, sizeof(int32_t*)), "ptrs");
       CKR(cudaMalloc(&h->d_pivp, sizeof(int32_t*)), "ptrs");
+      CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * (TK_NUM + 1) * 3), "prof");
       CKR(cudaMemcpy(h->d_arenas, &h->d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptrs");
       CKR(cudaMemcpy(h->d_rankp, &h->d_ranks, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
       CKR(cudaMemcpy(h->d_pivp, &h->d_piv, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
@@ -573,18 +666,19 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
     CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
     cudaError_t e;
     if (precision == HLU_FP64)
-      e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, h->d_fill_dense, h->n_fill_dense, h->dense_rows, h->d_fill_lr,
-                          h->n_fill_lr, (double*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
+      e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
+                          h->sb->d_fill_lr, h->sb->n_fill_lr, (double*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
                           h->d_status, s);
     else
-      e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, h->d_fill_dense, h->n_fill_dense, h->dense_rows, h->d_fill_lr,
-                         h->n_fill_lr, (float*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
+      e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
+                         h->sb->d_fill_lr, h->sb->n_fill_lr, (float*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
                          h->d_status, s);
     CKR(e, "A_H fill");
     int32_t stf[4];
     int rc = read_status(h, s, stf);
     if (rc) return rc;
     CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
+    CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * (TK_NUM + 1) * 3, s), "prof");
     CKR(cudaEventRecord(h->ev0, s), "event");
     rc = exec_run(h, h->dF, h->grid, s, true);
     if (rc) return rc;
@@ -601,8 +695,8 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
     CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
     int64_t rsum = 0, nadm = 0;
     int32_t rmax = 0;
-    for (size_t b = 0; b < h->FB.size(); ++b)
-      if (h->FB[b].kind == KIND_ADM) {
+    for (size_t b = 0; b < h->sb->FB.size(); ++b)
+      if (h->sb->FB[b].kind == KIND_ADM) {
         int32_t r = rk[h->L.slot[b]];
         rmax = std::max(rmax, r);
         rsum += r;
@@ -616,6 +710,13 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
   } catch (const std::exception& ex) {
     return fail(HLU_ERR_CUDA, ex.what());
   }
+}
+
+int hlu_factor_profile(const hlu_handle* h, uint64_t* out) {
+  if (!h || !out) return fail(HLU_ERR_ARG, "null argument");
+  if (!h->d_prof) return fail(HLU_ERR_STATE, "not factored");
+  CKR(cudaMemcpy(out, h->d_prof, sizeof(uint64_t) * (TK_NUM + 1) * 3, cudaMemcpyDeviceToHost), "profile");
+  return HLU_OK;
 }
 
 int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info) {

@@ -24,6 +24,8 @@
 #include <cmath>
 #include <cstdint>
 
+#include "launch_count.h"
+
 #include "build.h"
 
 namespace hlu {
@@ -615,6 +617,7 @@ cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m) {
   int32_t* cnt = nullptr;
   CK(cudaMalloc(&cnt, sizeof(int32_t) * (nv + 1)));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nv + 1), s));
+  note_launch();
   k_count_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt);
   thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(cnt),
                          thrust::device_ptr<int32_t>(cnt + nv + 1), thrust::device_ptr<int32_t>(cnt));
@@ -626,6 +629,7 @@ cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m) {
   CK(cudaMalloc(&m.dofmap, sizeof(int32_t) * nv * 7));
   CK(cudaMalloc(&m.edges, sizeof(int32_t) * 2 * (int64_t)N));
   CK(cudaMalloc(&m.pts, sizeof(int32_t) * 3 * (int64_t)N));
+  note_launch();
   k_number_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt, m.dofmap, m.edges, m.pts);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -640,6 +644,7 @@ cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR&
   double* vals = nullptr;
   CK(cudaMalloc(&keys, sizeof(int64_t) * ne));
   CK(cudaMalloc(&vals, sizeof(double) * ne));
+  note_launch();
   k_element_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.N, m.dofmap, keys, vals);
   CK(cudaGetLastError());
   thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int64_t>(keys),
@@ -664,6 +669,7 @@ cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR&
   int32_t* rowcnt = nullptr;
   CK(cudaMalloc(&rowcnt, sizeof(int32_t) * (m.N + 1)));
   CK(cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * (m.N + 1), s));
+  note_launch();
   k_csr_rows<<<grid_for(nnz), 256, 0, s>>>(nnz, m.N, ukeys, A.col, rowcnt);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(A.val, uvals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
@@ -690,6 +696,7 @@ cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStre
   CK(cudaMallocAsync(&vals, sizeof(double) * ne, s));
   CK(cudaMallocAsync(&uk, sizeof(int32_t) * ne, s));
   CK(cudaMallocAsync(&us, sizeof(double) * ne, s));
+  note_launch();
   k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
   CK(cudaGetLastError());
   thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(keys),
@@ -699,6 +706,7 @@ cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStre
                                     thrust::device_ptr<int32_t>(uk), thrust::device_ptr<double>(us));
   int64_t nu = ends.first - thrust::device_ptr<int32_t>(uk);
   CK(cudaMemsetAsync(b, 0, sizeof(double) * m.N, s));
+  note_launch();
   k_scatter_rhs<<<grid_for(nu), 256, 0, s>>>(nu, uk, us, m.N, b);
   CK(cudaGetLastError());
   CK(cudaFreeAsync(keys, s));
@@ -736,12 +744,15 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   int32_t first = 0, count = 1, lev = 0;
   while (count > 0) {
     if (first + count + 2 * count > cap) return cudaErrorMemoryAllocation;
+    note_launch();
     k_cluster_bbox<<<std::min(count, 8192), 256, 0, s>>>(count, off + first, size + first, permA, m.pts, lo + 3 * first,
                                                          hi + 3 * first);
     // clusters that became leaves on earlier levels keep their order
     CK(cudaMemcpyAsync(permB, permA, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    note_launch();
     k_cluster_split<<<std::min(count, 8192), 1024, 0, s>>>(count, leaf, off + first, size + first, lo + 3 * first,
                                                            hi + 3 * first, permA, permB, m.pts, nleft + first);
+    note_launch();
     k_cluster_children<<<1, 1, 0, s>>>(count, first, off + first, size + first, nleft + first, son + 2 * first,
                                        off + first + count, size + first + count, parent + first + count, cnt);
     CK(cudaGetLastError());
@@ -772,13 +783,18 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   int32_t *sub, *pre;
   CK(cudaMalloc(&sub, sizeof(int32_t) * nc));
   CK(cudaMalloc(&pre, sizeof(int32_t) * nc));
-  for (int l = (int)level_first.size() - 1; l >= 0; --l)
+  for (int l = (int)level_first.size() - 1; l >= 0; --l) {
+    note_launch();
     k_subtree<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub);
+  }
   CK(cudaMemcpyAsync(pre, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  for (size_t l = 0; l < level_first.size(); ++l)
+  for (size_t l = 0; l < level_first.size(); ++l) {
+    note_launch();
     k_preorder<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub, pre);
+  }
   int32_t* cl_export;
   CK(cudaMalloc(&cl_export, sizeof(int32_t) * 12 * nc));
+  note_launch();
   k_export_clusters<<<grid_for(nc), 256, 0, s>>>(nc, pre, off, size, lo, hi, son, level, parent, cl_export);
   CK(cudaGetLastError());
 
@@ -805,6 +821,7 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   std::vector<int32_t> bl_first = {0}, bl_cnt = {1};
   int32_t bfirst = 0, bcount = 1;
   while (bcount > 0) {
+    note_launch();
     k_block_classify<<<grid_for(bcount), 256, 0, s>>>(bcount, brow + bfirst, bcol + bfirst, lo, hi, son, eta2,
                                                       bkind + bfirst, nch + bfirst);
     CK(cudaGetLastError());
@@ -816,6 +833,7 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
     CK(cudaStreamSynchronize(s));
     int32_t nxt = lastc + lastn;
     if (bfirst + bcount + nxt > bcap) return cudaErrorMemoryAllocation;
+    note_launch();
     k_block_expand<<<grid_for(bcount), 256, 0, s>>>(bcount, brow + bfirst, bcol + bfirst, bkind + bfirst,
                                                     cst + bfirst, son, bfirst + bcount, bfirst, bson + 4 * (int64_t)bfirst,
                                                     brow + bfirst + bcount, bcol + bfirst + bcount,
@@ -832,13 +850,18 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   int32_t *bsub, *bpre;
   CK(cudaMalloc(&bsub, sizeof(int32_t) * nb));
   CK(cudaMalloc(&bpre, sizeof(int32_t) * nb));
-  for (int l = (int)bl_first.size() - 1; l >= 0; --l)
+  for (int l = (int)bl_first.size() - 1; l >= 0; --l) {
+    note_launch();
     k_subtree<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub);
+  }
   CK(cudaMemcpyAsync(bpre, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  for (size_t l = 0; l < bl_first.size(); ++l)
+  for (size_t l = 0; l < bl_first.size(); ++l) {
+    note_launch();
     k_preorder<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub, bpre);
+  }
   int32_t* bl_export;
   CK(cudaMalloc(&bl_export, sizeof(int32_t) * 8 * (int64_t)nb));
+  note_launch();
   k_export_blocks<<<grid_for(nb), 256, 0, s>>>(nb, bpre, pre, brow, bcol, bkind, bson, bpar, bl_export);
   CK(cudaGetLastError());
   out.clusters.resize(12 * (size_t)nc);
@@ -865,13 +888,18 @@ cudaError_t fill_ah(const DevCSR& A, const int32_t* d_perm, const int32_t* d_ipe
                     int64_t zero_elems, int64_t ident_off, int32_t ident_n, int32_t* ranks, int32_t* status,
                     cudaStream_t s) {
   CK(cudaMemsetAsync(arena, 0, sizeof(T) * zero_elems, s));
+  note_launch();
   k_identity<T><<<grid_for(ident_n), 256, 0, s>>>(arena, ident_off, ident_n);
   if (ndense) {
     int64_t warps = dense_rows;
     int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 65535);
+    note_launch();
     k_fill_dense<T><<<blocks, 256, 0, s>>>(ndense, d_dense, d_perm, d_iperm, A.rowptr, A.col, A.val, arena);
   }
-  if (nlr) k_fill_lowrank<T><<<std::min(nlr, 65535), 256, 0, s>>>(nlr, d_lr, d_perm, d_iperm, A.rowptr, A.col, A.val, arena, ranks, status);
+  if (nlr) {
+    note_launch();
+    k_fill_lowrank<T><<<std::min(nlr, 65535), 256, 0, s>>>(nlr, d_lr, d_perm, d_iperm, A.rowptr, A.col, A.val, arena, ranks, status);
+  }
   return cudaGetLastError();
 }
 
@@ -886,6 +914,7 @@ __global__ void k_invert_perm(int32_t N, const int32_t* perm, int32_t* iperm) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
 }
 cudaError_t invert_perm(int32_t N, const int32_t* perm, int32_t* iperm, cudaStream_t s) {
+  note_launch();
   k_invert_perm<<<grid_for(N), 256, 0, s>>>(N, perm, iperm);
   return cudaGetLastError();
 }

@@ -15,6 +15,8 @@
 
 #include <cstdint>
 
+#include "launch_count.h"
+
 #include "exec.h"
 #include "hlu_internal.h"
 
@@ -159,8 +161,109 @@ __device__ void task_getrf(Ctx<T>& c, const Task& t, char* smem) {
   if (threadIdx.x == 0) c.flops += 2.0 * n * n * n / 3.0;
 }
 
+// ---------------------------------------------------------------- small GEMM core
+// Strided operand: element (i, j) at p[i * rs + j * cs].
+template <class T>
+struct Mat {
+  const T* p;
+  int64_t rs, cs;
+};
+template <class T>
+__device__ __forceinline__ Mat<T> mat(const Ctx<T>& c, const View& v) {
+  return Mat<T>{c.arena + v.off, v.rs, v.cs};
+}
+template <class T>
+__device__ __forceinline__ Mat<T> matT(const Ctx<T>& c, const View& v) {
+  return Mat<T>{c.arena + v.off, v.cs, v.rs};
+}
+template <class T>
+__device__ __forceinline__ Mat<T> shift(Mat<T> m, int64_t di, int64_t dj) {
+  m.p += di * m.rs + dj * m.cs;
+  return m;
+}
+
+// 64 x 64 output tile in registers: thread t owns rows 4 (t % 16) .. +3 and
+// columns 4 (t / 16) .. +3.  tile_mma adds A (tile rows [rlo, rlo + mrows),
+// K columns) times B (K rows, ncols columns); operand chunks of KC along K
+// are staged in shared memory with loads ordered along the operand's
+// contiguous dimension.
+constexpr int KC = 32;
+template <class T>
+__device__ __forceinline__ void acc_zero(T (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+}
+template <class T>
+__device__ void tile_mma(T (&acc)[4][4], const Mat<T>& A, int rlo, int mrows, const Mat<T>& B, int ncols, int K,
+                         T* As, T* Bs) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int l0 = 0; l0 < K; l0 += KC) {
+    const int kc = min(KC, K - l0);
+    __syncthreads();
+    if (A.rs == 1) {
+      for (int e = tid; e < 64 * KC; e += NT) {
+        int r = e & 63, kk = e >> 6;
+        int ar = r - rlo;
+        As[kk * 64 + r] = (kk < kc && ar >= 0 && ar < mrows) ? __ldcg(A.p + ar + (int64_t)(l0 + kk) * A.cs) : T(0);
+      }
+    } else {
+      for (int e = tid; e < 64 * KC; e += NT) {
+        int kk = e % KC, r = e / KC;
+        int ar = r - rlo;
+        As[kk * 64 + r] =
+            (kk < kc && ar >= 0 && ar < mrows) ? __ldcg(A.p + (int64_t)ar * A.rs + (int64_t)(l0 + kk) * A.cs) : T(0);
+      }
+    }
+    if (B.rs == 1) {
+      for (int e = tid; e < 64 * KC; e += NT) {
+        int kk = e % KC, cc = e / KC;
+        Bs[kk * 64 + cc] = (kk < kc && cc < ncols) ? __ldcg(B.p + (l0 + kk) + (int64_t)cc * B.cs) : T(0);
+      }
+    } else {
+      for (int e = tid; e < 64 * KC; e += NT) {
+        int cc = e & 63, kk = e >> 6;
+        Bs[kk * 64 + cc] =
+            (kk < kc && cc < ncols) ? __ldcg(B.p + (int64_t)(l0 + kk) * B.rs + (int64_t)cc * B.cs) : T(0);
+      }
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tx * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + ty * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+  }
+  __syncthreads();
+}
+// C[rows i0.., cols j0..] (+)= sign * acc for the valid part of the tile
+template <class T>
+__device__ void tile_store(T (&acc)[4][4], const Ctx<T>& c, const View& C, int i0, int j0, int mrows, int ncols,
+                           T sign, bool overwrite) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx * 4 + i, cc = ty * 4 + j;
+      if (r < mrows && cc < ncols) {
+        T base = overwrite ? T(0) : ldv(c, C, i0 + r, j0 + cc);
+        stv(c, C, i0 + r, j0 + cc, base + sign * acc[i][j]);
+      }
+    }
+}
+
 // ---------------------------------------------------------------- leaf TRSM
-// One thread per right-hand-side column, triangle in shared memory.
+// Triangle in shared memory; one warp per right-hand-side column, the column
+// held in two registers per lane (rows lane and lane + 32), shuffles for the
+// substitution.
 template <class T>
 __device__ void task_trsm(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.a.rows;
@@ -171,95 +274,89 @@ __device__ void task_trsm(Ctx<T>& c, const Task& t, char* smem) {
   if (t.type == TK_TRSM_L)
     for (int i = threadIdx.x; i < n; i += NT) perm[i] = __ldcg(c.piv + t.piv_off + i);
   __syncthreads();
-  T v[64];
-  for (int j = threadIdx.x; j < k; j += NT) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = lane, r1 = lane + 32;
+  for (int j = warp; j < k; j += NT / 32) {
+    T v0 = 0, v1 = 0;
     if (t.type == TK_TRSM_L) {
-      for (int i = 0; i < n; ++i) v[i] = ldv(c, t.b, perm[i], j);
-      for (int i = 0; i < n; ++i) {
-        T s = v[i];
-        for (int l = 0; l < i; ++l) s -= A[i + l * n] * v[l];
-        v[i] = s;
+      if (r0 < n) v0 = ldv(c, t.b, perm[r0], j);
+      if (r1 < n) v1 = ldv(c, t.b, perm[r1], j);
+      for (int l = 0; l < n; ++l) {
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31);
+        if (r0 > l && r0 < n) v0 -= A[r0 + l * n] * x;
+        if (r1 > l && r1 < n) v1 -= A[r1 + l * n] * x;
       }
     } else if (t.type == TK_TRSM_UT) {
-      for (int i = 0; i < n; ++i) v[i] = ldv(c, t.b, i, j);
-      for (int i = 0; i < n; ++i) {
-        T s = v[i];
-        for (int l = 0; l < i; ++l) s -= A[l + i * n] * v[l];
-        v[i] = s / A[i + i * n];
+      if (r0 < n) v0 = ldv(c, t.b, r0, j);
+      if (r1 < n) v1 = ldv(c, t.b, r1, j);
+      for (int l = 0; l < n; ++l) {
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) / A[l + l * n];
+        if (r0 == l) v0 = x;
+        if (r1 == l) v1 = x;
+        if (r0 > l && r0 < n) v0 -= A[l + r0 * n] * x;
+        if (r1 > l && r1 < n) v1 -= A[l + r1 * n] * x;
       }
     } else {
-      for (int i = 0; i < n; ++i) v[i] = ldv(c, t.b, i, j);
-      for (int i = n - 1; i >= 0; --i) {
-        T s = v[i];
-        for (int l = i + 1; l < n; ++l) s -= A[i + l * n] * v[l];
-        v[i] = s / A[i + i * n];
+      if (r0 < n) v0 = ldv(c, t.b, r0, j);
+      if (r1 < n) v1 = ldv(c, t.b, r1, j);
+      for (int l = n - 1; l >= 0; --l) {
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) / A[l + l * n];
+        if (r0 == l) v0 = x;
+        if (r1 == l) v1 = x;
+        if (r0 < l) v0 -= A[r0 + l * n] * x;
+        if (r1 < l && r1 < n) v1 -= A[r1 + l * n] * x;
       }
     }
-    for (int i = 0; i < n; ++i) stv(c, t.b, i, j, v[i]);
+    if (r0 < n) stv(c, t.b, r0, j, v0);
+    if (r1 < n) stv(c, t.b, r1, j, v1);
   }
   if (threadIdx.x == 0) c.flops += (double)n * n * k;
 }
 
 // ---------------------------------------------------------------- PROJ
-// c (r x k) = a^T b, a: m x r, b: m x k.  Threads split outputs x row groups.
+// c (r x k) = a^T b, a: m x r, b: m x k: a 64 x 64 tile reduced over m.
 template <class T>
 __device__ void task_proj(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.a.rows, r = ncols(c, t.a), k = ncols(c, t.b);
-  const int no = r * k;
-  T* part = reinterpret_cast<T*>(smem);
-  if (no == 0) return;
-  if (no >= NT) {
-    for (int o = threadIdx.x; o < no; o += NT) {
-      int i = o % r, j = o / r;
-      T s = 0;
-      for (int l = 0; l < m; ++l) s += ldv(c, t.a, l, i) * ldv(c, t.b, l, j);
-      stv(c, t.c, i, j, s);
+  if (r == 0 || k == 0) return;
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + 64 * KC;
+  for (int i0 = 0; i0 < r; i0 += 64)
+    for (int j0 = 0; j0 < k; j0 += 64) {
+      T acc[4][4];
+      acc_zero(acc);
+      tile_mma(acc, shift(matT(c, t.a), i0, 0), 0, min(64, r - i0), shift(mat(c, t.b), 0, j0), min(64, k - j0), m,
+               As, Bs);
+      tile_store(acc, c, t.c, i0, j0, min(64, r - i0), min(64, k - j0), T(1), true);
     }
-  } else {
-    const int G = NT / no;
-    const int o = threadIdx.x % no, g = threadIdx.x / no;
-    T s = 0;
-    if (g < G) {
-      int i = o % r, j = o / r;
-      for (int l = g; l < m; l += G) s += ldv(c, t.a, l, i) * ldv(c, t.b, l, j);
-    }
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x < no) {
-      T tot = 0;
-      for (int q = 0; q < G; ++q) tot += part[threadIdx.x + q * no];
-      stv(c, t.c, threadIdx.x % r, threadIdx.x / r, tot);
-    }
-  }
   if (threadIdx.x == 0) c.flops += 2.0 * m * r * k;
 }
 
 // ---------------------------------------------------------------- ROWMV
-// c (n x k) = [c] + sign * sum_t A_t B_t.
+// c (n x k) = [c] + sign * sum_t A_t B_t, A_t covering rows [roff, roff + rows).
 template <class T>
-__device__ void task_rowmv(Ctx<T>& c, const Task& t) {
+__device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.c.rows, k = ncols(c, t.b);
-  const int no = n * k;
-  const T sg = T(t.sign);
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + 64 * KC;
   double fl = 0;
-  for (int o = threadIdx.x; o < no; o += NT) {
-    int i = o % n, j = o / n;
-    T acc = 0;
-    for (int q = 0; q < t.list_count; ++q) {
-      const Term& tm = c.terms[t.list_begin + q];
-      const int ii = i - tm.roff;
-      if (ii < 0 || ii >= tm.A.rows) continue;
-      const int p = ncols(c, tm.A);
-      for (int l = 0; l < p; ++l) acc += ldv(c, tm.A, ii, l) * ldv(c, tm.B, l, j);
+  for (int i0 = 0; i0 < n; i0 += 64)
+    for (int j0 = 0; j0 < k; j0 += 64) {
+      T acc[4][4];
+      acc_zero(acc);
+      for (int q = 0; q < t.list_count; ++q) {
+        const Term& tm = c.terms[t.list_begin + q];
+        const int p = ncols(c, tm.A);
+        // term rows [roff, roff + rows) intersected with tile rows [i0, i0 + 64)
+        int lo = max(tm.roff, i0), hi = min(tm.roff + tm.A.rows, i0 + 64);
+        if (hi <= lo || p == 0) continue;
+        tile_mma(acc, shift(mat(c, tm.A), lo - tm.roff, 0), lo - i0, hi - lo, shift(mat(c, tm.B), 0, j0),
+                 min(64, k - j0), p, As, Bs);
+        fl += 2.0 * (hi - lo) * min(64, k - j0) * p;
+      }
+      tile_store(acc, c, t.c, i0, j0, min(64, n - i0), min(64, k - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
     }
-    T base = (t.flags & TF_OVERWRITE) ? T(0) : ldv(c, t.c, i, j);
-    stv(c, t.c, i, j, base + sg * acc);
-  }
   if (threadIdx.x == 0) {
-    for (int q = 0; q < t.list_count; ++q) {
-      const Term& tm = c.terms[t.list_begin + q];
-      fl += 2.0 * tm.A.rows * k * ncols(c, tm.A);
-    }
     c.flops += fl;
     if (t.out_slot >= 0) __stcg(c.ranks + t.out_slot, k);
   }
@@ -267,36 +364,43 @@ __device__ void task_rowmv(Ctx<T>& c, const Task& t) {
 
 // ---------------------------------------------------------------- DADD
 template <class T>
-__device__ void task_dadd(Ctx<T>& c, const Task& t) {
+__device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.c.rows, n = ncols(c, t.c), k = ncols(c, t.a);
-  const T sg = T(t.sign);
-  for (int o = threadIdx.x; o < m * n; o += NT) {
-    int i = o % m, j = o / m;
-    T s = 0;
-    for (int l = 0; l < k; ++l) s += ldv(c, t.a, i, l) * ldv(c, t.b, j, l);
-    T base = (t.flags & TF_OVERWRITE) ? T(0) : ldv(c, t.c, i, j);
-    stv(c, t.c, i, j, base + sg * s);
-  }
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + 64 * KC;
+  for (int i0 = 0; i0 < m; i0 += 64)
+    for (int j0 = 0; j0 < n; j0 += 64) {
+      T acc[4][4];
+      acc_zero(acc);
+      if (k > 0)
+        tile_mma(acc, shift(mat(c, t.a), i0, 0), 0, min(64, m - i0), shift(matT(c, t.b), 0, j0), min(64, n - j0), k,
+                 As, Bs);
+      tile_store(acc, c, t.c, i0, j0, min(64, m - i0), min(64, n - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
+    }
   if (threadIdx.x == 0) c.flops += 2.0 * m * n * k;
 }
 
 // ---------------------------------------------------------------- TRUNC
-// Householder QR of S (m x w, column-major, ld m) in place, by the whole CTA.
+// Householder QR of S (m x w, column-major, ld m, this CTA's private scratch)
+// in place.  Every step uses the whole CTA: the norm is a block reduction and
+// the reflector is applied to groups of 8 columns at once.
 template <class T>
 __device__ void house_qr(T* S, int m, int w, T* tau, T* red) {
   const int tmax = min(m, w);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ T s_scale;
+  __shared__ T s_d[8];
+  __shared__ T s_part[NT / 32][8];
   for (int j = 0; j < tmax; ++j) {
     T* cj = S + (int64_t)j * m;
     T part = 0;
     for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-      T x = __ldcg(cj + i);
+      T x = cj[i];
       part += x * x;
     }
     T s2 = block_sum(part, red);
     if (threadIdx.x == 0) {
-      T alpha = __ldcg(cj + j);
+      T alpha = cj[j];
       if (s2 == T(0)) {
         tau[j] = 0;
         s_scale = 0;
@@ -305,48 +409,101 @@ __device__ void house_qr(T* S, int m, int w, T* tau, T* red) {
         T beta = alpha >= T(0) ? -nrm : nrm;
         s_scale = T(1) / (alpha - beta);
         tau[j] = (beta - alpha) / beta;
-        __stcg(cj + j, beta);
+        cj[j] = beta;
       }
     }
     __syncthreads();
     const T sc = s_scale;
     if (sc != T(0))
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) __stcg(cj + i, __ldcg(cj + i) * sc);
+      for (int i = j + 1 + threadIdx.x; i < m; i += NT) cj[i] *= sc;
     __syncthreads();
     const T tj = tau[j];
-    if (tj != T(0)) {
-      for (int cc = j + 1 + warp; cc < w; cc += NT / 32) {
-        T* col = S + (int64_t)cc * m;
-        T d = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) d += __ldcg(cj + i) * __ldcg(col + i);
-        d = warp_sum(d);
-        d = (d + __ldcg(col + j)) * tj;
-        if (lane == 0) __stcg(col + j, __ldcg(col + j) - d);
-        for (int i = j + 1 + lane; i < m; i += 32) __stcg(col + i, __ldcg(col + i) - d * __ldcg(cj + i));
+    if (tj == T(0)) continue;
+    for (int c0 = j + 1; c0 < w; c0 += 8) {
+      const int nc = min(8, w - c0);
+      T d[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = 0;
+      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
+        T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nc) d[q] += v * S[i + (int64_t)(c0 + q) * m];
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        T x = warp_sum(d[q]);
+        if (lane == 0) s_part[warp][q] = x;
+      }
+      __syncthreads();
+      if (threadIdx.x < nc) {
+        T tot = S[j + (int64_t)(c0 + threadIdx.x) * m];
+        for (int w8 = 0; w8 < NT / 32; ++w8) tot += s_part[w8][threadIdx.x];
+        s_d[threadIdx.x] = tot * tj;
+      }
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
+        T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nc) S[i + (int64_t)(c0 + q) * m] -= s_d[q] * v;
+      }
+      if (threadIdx.x < nc) S[j + (int64_t)(c0 + threadIdx.x) * m] -= s_d[threadIdx.x];
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-// out (column-major view, m x r) <- Q out, Q = H_0 ... H_{t-1}; one warp per column.
+// out (m x r column-major view in the arena) <- Q out, Q = H_0 ... H_{t-1};
+// CTA-wide per reflector, output columns in groups of 8.
 template <class T>
-__device__ void apply_q(const Ctx<T>& c, const T* S, int m, int tmax, const T* tau, const View& out,
-                        int r) {
+__device__ void apply_q(const Ctx<T>& c, const T* S, int m, int tmax, const T* tau, const View& out, int r) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int cc = warp; cc < r; cc += NT / 32) {
-    for (int j = tmax - 1; j >= 0; --j) {
-      const T tj = tau[j];
-      if (tj == T(0)) continue;
-      const T* cj = S + (int64_t)j * m;
-      T d = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) d += __ldcg(cj + i) * ldv(c, out, i, cc);
-      d = warp_sum(d);
-      d = (d + ldv(c, out, j, cc)) * tj;
-      __syncwarp();
-      if (lane == 0) stv(c, out, j, cc, ldv(c, out, j, cc) - d);
-      for (int i = j + 1 + lane; i < m; i += 32) stv(c, out, i, cc, ldv(c, out, i, cc) - d * __ldcg(cj + i));
-      __syncwarp();
+  __shared__ T s_d[8];
+  __shared__ T s_part[NT / 32][8];
+  T* O = c.arena + out.off;
+  const int64_t ld = out.cs;
+  for (int j = tmax - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj == T(0)) continue;
+    const T* cj = S + (int64_t)j * m;
+    for (int c0 = 0; c0 < r; c0 += 8) {
+      const int nc = min(8, r - c0);
+      T d[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = 0;
+      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
+        T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nc) d[q] += v * __ldcg(O + i + (int64_t)(c0 + q) * ld);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        T x = warp_sum(d[q]);
+        if (lane == 0) s_part[warp][q] = x;
+      }
+      __syncthreads();
+      if (threadIdx.x < nc) {
+        T tot = __ldcg(O + j + (int64_t)(c0 + threadIdx.x) * ld);
+        for (int w8 = 0; w8 < NT / 32; ++w8) tot += s_part[w8][threadIdx.x];
+        s_d[threadIdx.x] = tot * tj;
+      }
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
+        T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nc) {
+            T* p = O + i + (int64_t)(c0 + q) * ld;
+            __stcg(p, __ldcg(p) - s_d[q] * v);
+          }
+      }
+      if (threadIdx.x < nc) {
+        T* p = O + j + (int64_t)(c0 + threadIdx.x) * ld;
+        __stcg(p, __ldcg(p) - s_d[threadIdx.x]);
+      }
+      __syncthreads();
     }
   }
 }
@@ -377,8 +534,8 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   T* SX = c.scratch;
   T* SY = c.scratch + c.scratch_half;
   // stack the pieces (zero outside each piece's rows)
-  for (int64_t idx = threadIdx.x; idx < (int64_t)m * W; idx += NT) __stcg(SX + idx, T(0));
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * W; idx += NT) __stcg(SY + idx, T(0));
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * W; idx += NT) SX[idx] = T(0);
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * W; idx += NT) SY[idx] = T(0);
   __syncthreads();
   for (int q = 0; q < t.list_count; ++q) {
     const Piece& P = c.pieces[t.list_begin + q];
@@ -387,11 +544,11 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
     const T sg = T(P.sign);
     for (int64_t idx = threadIdx.x; idx < (int64_t)P.X.rows * w; idx += NT) {
       int i = (int)(idx % P.X.rows), j = (int)(idx / P.X.rows);
-      __stcg(SX + (P.xoff + i) + (int64_t)(c0 + j) * m, sg * ldv(c, P.X, i, j));
+      SX[(P.xoff + i) + (int64_t)(c0 + j) * m] = sg * ldv(c, P.X, i, j);
     }
     for (int64_t idx = threadIdx.x; idx < (int64_t)P.Y.rows * w; idx += NT) {
       int i = (int)(idx % P.Y.rows), j = (int)(idx / P.Y.rows);
-      __stcg(SY + (P.yoff + i) + (int64_t)(c0 + j) * n, ldv(c, P.Y, i, j));
+      SY[(P.yoff + i) + (int64_t)(c0 + j) * n] = ldv(c, P.Y, i, j);
     }
   }
   __syncthreads();
@@ -407,7 +564,7 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   for (int idx = threadIdx.x; idx < p * q; idx += NT) {
     int i = idx % p, j = idx / p;
     T s = 0;
-    for (int l = max(i, j); l < W; ++l) s += __ldcg(SX + i + (int64_t)l * m) * __ldcg(SY + j + (int64_t)l * n);
+    for (int l = max(i, j); l < W; ++l) s += SX[i + (int64_t)l * m] * SY[j + (int64_t)l * n];
     G[i + j * p] = s;
   }
   for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? T(1) : T(0);
@@ -516,8 +673,14 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
   c.eps = a.eps;
   c.status = a.status;
   c.flops = 0;
+  __shared__ unsigned long long s_prof[TK_NUM + 1][3];  // count, wait cycles, run cycles
+  if (threadIdx.x < (TK_NUM + 1) * 3) (&s_prof[0][0])[threadIdx.x] = 0ULL;
+  long long t_begin = 0, t_waited = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_task = (int64_t)atomicAdd(a.ticket, 1ULL);
+    if (threadIdx.x == 0) {
+      s_task = (int64_t)atomicAdd(a.ticket, 1ULL);
+      t_begin = clock64();
+    }
     __syncthreads();
     const int64_t ti = s_task;
     if (ti >= a.ntasks) break;
@@ -550,7 +713,9 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
       __threadfence();
     }
     __syncthreads();
-    if (!s_skip && a.tasks[ti].type >= 0 && a.tasks[ti].type < TK_NUM) {
+    if (threadIdx.x == 0) t_waited = clock64();
+    const int ttype = a.tasks[ti].type;
+    if (!s_skip && ttype >= 0 && ttype < TK_NUM) {
       const Task t = a.tasks[ti];
       c.arena = reinterpret_cast<T*>(a.arenas[t.prob]);
       c.ranks = a.ranks[t.prob];
@@ -561,17 +726,30 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
         case TK_TRSM_UT:
         case TK_TRSM_U: task_trsm(c, t, smem); break;
         case TK_PROJ: task_proj(c, t, smem); break;
-        case TK_ROWMV: task_rowmv(c, t); break;
+        case TK_ROWMV: task_rowmv(c, t, smem); break;
         case TK_TRUNC: task_trunc(c, t, smem); break;
-        case TK_DADD: task_dadd(c, t); break;
+        case TK_DADD: task_dadd(c, t, smem); break;
         default: break;
       }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(a.done + ti, a.epoch);
+    if (threadIdx.x == 0) {
+      st_release(a.done + ti, a.epoch);
+      if (a.prof) {
+        const int k = (ttype >= 0 && ttype < TK_NUM) ? ttype : TK_NUM;
+        long long t_end = clock64();
+        s_prof[k][0] += 1ULL;
+        s_prof[k][1] += (unsigned long long)(t_waited - t_begin);
+        s_prof[k][2] += (unsigned long long)(t_end - t_waited);
+      }
+    }
   }
   if (threadIdx.x == 0 && a.flops) atomicAdd(a.flops, c.flops);
+  if (a.prof && threadIdx.x < (TK_NUM + 1) * 3) {
+    unsigned long long v = (&s_prof[0][0])[threadIdx.x];
+    if (v) atomicAdd(a.prof + threadIdx.x, v);
+  }
 }
 
 size_t exec_smem_bytes(int elem_size) {
@@ -598,6 +776,7 @@ cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s) {
   size_t sm = exec_smem_bytes(sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(exec_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  note_launch();
   exec_kernel<T><<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }

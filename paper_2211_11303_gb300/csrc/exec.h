@@ -27,6 +27,7 @@ struct ExecArgs {
   int32_t* status;          // [0] status code, [1] failing task, [2] rank-cap hits, [3] abort
   double* flops;            // accumulated algorithmic flops (may be null)
   unsigned long long wait_limit_ns;
+  unsigned long long* prof;  // optional [(TK_NUM + 1) x 3]: tasks, wait cycles, run cycles per kind
 };
 
 size_t exec_smem_bytes(int elem_size);

@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "launch_count.h"
+
 #include "krylov.h"
 
 namespace hlu {
@@ -36,6 +38,7 @@ __global__ void k_spmv(int64_t N, const int64_t* rowptr, const int32_t* col, con
 cudaError_t spmv(const int64_t* rowptr, const int32_t* col, const double* val, int64_t N, const double* x,
                  int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
   int64_t threads = N * 32;
+  note_launch();
   k_spmv<<<gridn(threads, 256), 256, 0, s>>>(N, rowptr, col, val, x, ldx, y, ldy, nrhs);
   return cudaGetLastError();
 }
@@ -60,6 +63,7 @@ __global__ void k_residual(int64_t N, const int64_t* rowptr, const int32_t* col,
 
 cudaError_t residual(const int64_t* rowptr, const int32_t* col, const double* val, int64_t N, const double* x,
                      int64_t ldx, const double* b, int64_t ldb, double* out, int64_t ldo, int nrhs, cudaStream_t s) {
+  note_launch();
   k_residual<<<gridn(N * 32, 256), 256, 0, s>>>(N, rowptr, col, val, x, ldx, b, ldb, out, ldo, nrhs);
   return cudaGetLastError();
 }
@@ -103,7 +107,9 @@ cudaError_t multidot(int64_t N, const double* V, int64_t ldr, int nk, const doub
                      double* partial, double* out, int64_t ldo, cudaStream_t s) {
   int nblk = (int)((N + DOT_CHUNK - 1) / DOT_CHUNK);
   dim3 g(nblk, nrhs);
+  note_launch();
   k_multidot<<<g, 256, 0, s>>>(N, V, ldr, nk, w, ldw, partial, nblk);
+  note_launch();
   k_reduce_partial<<<gridn((int64_t)nrhs * nk, 128), 128, 0, s>>>(nrhs, nk, nblk, partial, out, ldo);
   return cudaGetLastError();
 }
@@ -122,6 +128,7 @@ __global__ void k_multiaxpy(int64_t N, const double* V, int64_t ldr, int nk, con
 }
 cudaError_t multiaxpy(int64_t N, const double* V, int64_t ldr, int nk, const double* h, int64_t ldh, double* w,
                       int64_t ldw, int nrhs, cudaStream_t s) {
+  note_launch();
   k_multiaxpy<<<gridn(N, 256), 256, 0, s>>>(N, V, ldr, nk, h, ldh, w, ldw, nrhs);
   return cudaGetLastError();
 }
@@ -136,6 +143,7 @@ __global__ void k_scale(int64_t N, const double* w, int64_t ldw, const double* n
 }
 cudaError_t scale_cols(int64_t N, const double* w, int64_t ldw, const double* nrm, double* out, int64_t ldo, int nrhs,
                        cudaStream_t s) {
+  note_launch();
   k_scale<<<gridn(N, 256), 256, 0, s>>>(N, w, ldw, nrm, out, ldo, nrhs);
   return cudaGetLastError();
 }
@@ -145,6 +153,7 @@ __global__ void k_sqrt_inplace(double* v, int n) {
   if (i < n) v[i] = sqrt(v[i]);
 }
 cudaError_t sqrt_inplace(double* v, int n, cudaStream_t s) {
+  note_launch();
   k_sqrt_inplace<<<(n + 127) / 128, 128, 0, s>>>(v, n);
   return cudaGetLastError();
 }
@@ -185,6 +194,7 @@ __global__ void k_givens(int nrhs, int m, int j, const double* h1, const double*
 }
 cudaError_t givens(int nrhs, int m, int j, const double* h1, const double* h2, int64_t ldh, const double* hn, double* H,
                    double* cs, double* sn, double* g, double* est, cudaStream_t s) {
+  note_launch();
   k_givens<<<(nrhs + 31) / 32, 32, 0, s>>>(nrhs, m, j, h1, h2, ldh, hn, H, cs, sn, g, est);
   return cudaGetLastError();
 }
@@ -205,6 +215,7 @@ __global__ void k_backsub(int nrhs, int m, const int* jr, const double* H, const
   }
 }
 cudaError_t backsub(int nrhs, int m, const int* jr, const double* H, const double* g, double* y, cudaStream_t s) {
+  note_launch();
   k_backsub<<<(nrhs + 31) / 32, 32, 0, s>>>(nrhs, m, jr, H, g, y);
   return cudaGetLastError();
 }
@@ -217,6 +228,7 @@ __global__ void k_init_g(int nrhs, int m, const double* beta, double* g) {
   g[(int64_t)r * (m + 1)] = beta[r];
 }
 cudaError_t init_g(int nrhs, int m, const double* beta, double* g, cudaStream_t s) {
+  note_launch();
   k_init_g<<<(nrhs + 31) / 32, 32, 0, s>>>(nrhs, m, beta, g);
   return cudaGetLastError();
 }
@@ -238,6 +250,7 @@ __global__ void k_xupdate(int64_t N, const double* Z, int64_t ldzr, int m, const
 }
 cudaError_t xupdate(int64_t N, const double* Z, int64_t ldzr, int m, const double* y, double* x, int64_t ldx, int nrhs,
                     cudaStream_t s) {
+  note_launch();
   k_xupdate<<<gridn(N, 256), 256, 0, s>>>(N, Z, ldzr, m, y, x, ldx, nrhs);
   return cudaGetLastError();
 }
@@ -259,11 +272,13 @@ __global__ void k_scatter_cast(int64_t N, const int32_t* perm, const T* work, do
 }
 template <class T>
 cudaError_t gather_cast(int64_t N, const int32_t* perm, const double* b, int64_t ldb, T* work, int nrhs, cudaStream_t s) {
+  note_launch();
   k_gather_cast<T><<<gridn(N, 256), 256, 0, s>>>(N, perm, b, ldb, work, nrhs);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t scatter_cast(int64_t N, const int32_t* perm, const T* work, double* x, int64_t ldx, int nrhs, cudaStream_t s) {
+  note_launch();
   k_scatter_cast<T><<<gridn(N, 256), 256, 0, s>>>(N, perm, work, x, ldx, nrhs);
   return cudaGetLastError();
 }
@@ -274,6 +289,7 @@ template cudaError_t scatter_cast<double>(int64_t, const int32_t*, const double*
 
 __global__ void k_set_int(int32_t* p, int32_t v) { *p = v; }
 cudaError_t set_int(int32_t* p, int32_t v, cudaStream_t s) {
+  note_launch();
   k_set_int<<<1, 1, 0, s>>>(p, v);
   return cudaGetLastError();
 }

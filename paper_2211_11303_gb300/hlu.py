@@ -67,6 +67,7 @@ SIGNATURES = {
     "hlu_spmv": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
     "hlu_factor": (_i32, [_vp, _i32, _vp]),
     "hlu_factor_stats": (_i32, [_vp, _P(hlu_factor_info)]),
+    "hlu_factor_profile": (_i32, [_vp, _vp]),
     "hlu_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
     "gmres_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _i32, _P(hlu_stats), _vp]),
     "hlu_richardson": (_i32, [_vp, _vp, _vp, _i32, _i64, _f64, _i32, _P(hlu_stats), _vp]),
@@ -75,6 +76,7 @@ SIGNATURES = {
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
+    "hlu_launch_count": (_i64, []),
     "hlu_destroy": (None, [_vp]),
     "hlu_status_string": (ctypes.c_char_p, [_i32]),
     "hlu_last_error": (ctypes.c_char_p, []),
@@ -203,6 +205,16 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "FENCE"]
+
+
+def hlu_factor_profile(h):
+    """{kind: (tasks, wait_cycles, run_cycles)} of the last factorisation."""
+    out = (ctypes.c_uint64 * 27)()
+    _check(lib().hlu_factor_profile(_vp(h), out))
+    return {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
+
+
 def hlu_solve(h, b, x, stream=None):
     N = hlu_n(h)
     pb, nr, ldb = _vec(b, N)
@@ -267,6 +279,10 @@ def hlu_factor_bytes_estimate(h, precision=HLU_FP32):
 
 def hlu_set_wait_limit_ms(ms):
     lib().hlu_set_wait_limit_ms(float(ms))
+
+
+def hlu_launch_count():
+    return int(lib().hlu_launch_count())
 
 
 def hlu_set_tile(t):

@@ -10,6 +10,8 @@
 #ifndef HLU_DEBUG_H
 #define HLU_DEBUG_H
 #include <stdint.h>
+
+#include "hlu.h"
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -20,7 +22,8 @@ extern "C" {
  * int32[nnz], val double[nnz]); eps: truncation tolerance (Sec. 4 truncated
  * SVD, keep s_i > eps s_1); rank_cap: capacity of admissible blocks (0 = 32);
  * tile: block-tree nodes whose clusters both hold <= tile DOFs are factored as
- * one dense tile (0 keeps the block tree's own leaves);
+ * one dense tile (0 keeps the block tree's own leaves); precision: HLU_FP64 (0) or
+ * HLU_FP32 (1) arithmetic in the factor and the triangular solves;
  * order_seed: 0 executes tasks in program order, otherwise in a random
  * topological order drawn from that seed; b, x: host double[N*nrhs]
  * column-major (original order).
@@ -32,8 +35,34 @@ extern "C" {
 int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, int32_t nb,
                                 const int32_t* blocks, const int32_t* perm, const int64_t* rowptr,
                                 const int32_t* col, const double* val, double eps,
-                                int32_t rank_cap, int32_t tile, uint64_t order_seed, int32_t nrhs,
+                                int32_t rank_cap, int32_t tile, int32_t precision, uint64_t order_seed,
+                                int32_t nrhs,
                                 const double* b, double* x, int64_t* info);
+
+/* hlu_debug_host_factor_prefix - as hlu_debug_host_factor_solve, but executes
+ * only the first `limit` tasks of the factorisation DAG (limit < 0: all) and,
+ * when arena_out is not NULL, copies the whole arena (float or double elements
+ * by precision) and the rank slots to arena_out / ranks_out instead of
+ * solving.  Used with hlu_debug_factor_prefix to locate the first task whose
+ * device result differs from the host's. */
+int hlu_debug_host_factor_prefix(int32_t nc, const int32_t* clusters, int32_t nb, const int32_t* blocks,
+                                 const int32_t* perm, const int64_t* rowptr, const int32_t* col,
+                                 const double* val, double eps, int32_t rank_cap, int32_t tile,
+                                 int32_t precision, uint64_t order_seed, int32_t nrhs, const double* b,
+                                 double* x, int64_t* info, int64_t limit, void* arena_out,
+                                 int32_t* ranks_out);
+
+/* hlu_debug_factor_prefix - device counterpart (needs a GPU): A_H fill plus the
+ * first `limit` tasks of the factorisation of a built handle at `precision`,
+ * then the arena and rank slots are copied to host buffers.
+ * sizes: int64[3] receives (arena elements, rank slots, factor tasks); pass
+ * NULL buffers to query sizes only. */
+int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t limit, void* arena_out,
+                            int32_t* ranks_out, int64_t* sizes);
+
+/* hlu_debug_task_record - copy factorisation task `idx` of a built handle (its
+ * 128-byte internal record: kind, flags, operand views) to `out`. */
+int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out);
 
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a
  * GPU).  Runs the task executor with one CTA on a two-task schedule in which

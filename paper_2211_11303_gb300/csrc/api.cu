@@ -223,11 +223,11 @@ int blocks_per_sm() {
   return exec_blocks_per_sm<T>();
 }
 
-int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops) {
+int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops, int64_t limit = -1) {
   ExecArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tasks = ds.tasks;
-  a.ntasks = ds.ntasks;
+  a.ntasks = limit >= 0 ? std::min(limit, ds.ntasks) : ds.ntasks;
   a.terms = ds.terms;
   a.pieces = ds.pieces;
   a.pred_ptr = ds.pred_ptr;
@@ -245,11 +245,11 @@ int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_fl
   a.flops = with_flops ? h->d_flops : nullptr;
   a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
   a.prof = with_flops ? h->d_prof : nullptr;
-  if (ds.ntasks == 0) return HLU_OK;
+  if (a.ntasks == 0) return HLU_OK;
   int32_t st0[4] = {0, -1, 0, 0};
   CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
   CKR(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
-  int g = (int)std::min<int64_t>(grid, ds.ntasks);
+  int g = (int)std::min<int64_t>(grid, a.ntasks);
   cudaError_t e = h->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
   CKR(e, "executor launch");
   return HLU_OK;
@@ -628,7 +628,10 @@ int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision) {
   return h->L.total * es + grid * scratch_stride_elems(h->L) * es + (int64_t)h->L.n_slots * 4 + h->L.piv_total * 4;
 }
 
-int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
+static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit);
+int hlu_factor(hlu_handle* h, int32_t precision, void* stream) { return factor_impl(h, precision, stream, -1); }
+
+static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit) {
   try {
     if (!h) return fail(HLU_ERR_ARG, "null handle");
     if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
@@ -680,7 +683,7 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
     CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
     CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * (TK_NUM + 1) * 3, s), "prof");
     CKR(cudaEventRecord(h->ev0, s), "event");
-    rc = exec_run(h, h->dF, h->grid, s, true);
+    rc = exec_run(h, h->dF, h->grid, s, true, limit);
     if (rc) return rc;
     CKR(cudaEventRecord(h->ev1, s), "event");
     rc = read_status(h, s, stf);
@@ -896,4 +899,30 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "after timeout test");
   return rc;
+}
+
+// Runs A_H fill and the first `limit` tasks of the factorisation DAG, then
+// copies the arena (elements, in the factor precision) and the rank slots to
+// host buffers; sizes[0] = arena elements, sizes[1] = rank slots, sizes[2] =
+// factor tasks.  Query sizes with NULL buffers.
+extern "C" int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t limit, void* arena_out,
+                                       int32_t* ranks_out, int64_t* sizes) {
+  if (!h || !sizes) return fail(HLU_ERR_ARG, "null argument");
+  sizes[0] = h->L.total;
+  sizes[1] = h->L.n_slots;
+  sizes[2] = h->dF.ntasks;
+  if (!arena_out && !ranks_out) return HLU_OK;
+  int rc = factor_impl(h, precision, nullptr, limit);
+  if (rc && rc != HLU_ERR_ZERO_PIVOT) return rc;
+  if (arena_out)
+    CKR(cudaMemcpy(arena_out, h->d_arena, (size_t)esize(precision) * h->L.total, cudaMemcpyDeviceToHost), "arena");
+  if (ranks_out) CKR(cudaMemcpy(ranks_out, h->d_ranks, sizeof(int32_t) * h->L.n_slots, cudaMemcpyDeviceToHost), "ranks");
+  return HLU_OK;
+}
+
+// Copies factorisation task `idx` (its raw 128-byte record) to `out`.
+extern "C" int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out) {
+  if (!h || !out || idx < 0 || idx >= h->dF.ntasks) return fail(HLU_ERR_ARG, "bad argument");
+  CKR(cudaMemcpy(out, h->dF.tasks + idx, sizeof(Task), cudaMemcpyDeviceToHost), "task");
+  return HLU_OK;
 }

@@ -56,12 +56,29 @@ void trees_from_export(int32_t nc, const int32_t* cl, int32_t nb, const int32_t*
 
 using namespace hlu;
 
+extern "C" int hlu_debug_host_factor_prefix(int32_t nc, const int32_t* clusters, int32_t nb,
+                                            const int32_t* blocks, const int32_t* perm, const int64_t* rowptr,
+                                            const int32_t* col, const double* val, double eps, int32_t rank_cap,
+                                            int32_t tile, int32_t precision, uint64_t order_seed, int32_t nrhs,
+                                            const double* b, double* x, int64_t* info, int64_t limit,
+                                            void* arena_out, int32_t* ranks_out);
+
 extern "C" int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, int32_t nb,
                                            const int32_t* blocks, const int32_t* perm,
                                            const int64_t* rowptr, const int32_t* col,
                                            const double* val, double eps, int32_t rank_cap,
-                                           int32_t tile, uint64_t order_seed, int32_t nrhs, const double* b,
+                                           int32_t tile, int32_t precision, uint64_t order_seed, int32_t nrhs, const double* b,
                                            double* x, int64_t* info) {
+  return hlu_debug_host_factor_prefix(nc, clusters, nb, blocks, perm, rowptr, col, val, eps, rank_cap, tile,
+                                      precision, order_seed, nrhs, b, x, info, -1, nullptr, nullptr);
+}
+
+extern "C" int hlu_debug_host_factor_prefix(int32_t nc, const int32_t* clusters, int32_t nb,
+                                            const int32_t* blocks, const int32_t* perm, const int64_t* rowptr,
+                                            const int32_t* col, const double* val, double eps, int32_t rank_cap,
+                                            int32_t tile, int32_t precision, uint64_t order_seed, int32_t nrhs,
+                                            const double* b, double* x, int64_t* info, int64_t limit,
+                                            void* arena_out, int32_t* ranks_out) {
   try {
     if (!clusters || !blocks || !perm || !rowptr || !col || !val || nrhs < 1 || eps <= 0)
       return 1;
@@ -110,18 +127,36 @@ extern "C" int hlu_debug_host_factor_solve(int32_t nc, const int32_t* clusters, 
       if (bk.kind == KIND_ADM) ranks[L.slot[bi]] = kk;
     }
     int32_t cap_hits = 0;
-    int st1 = host_execute<double>(F, arena.data(), ranks.data(), piv.data(), eps, order_seed,
-                                   &cap_hits);
-    // solve: work vector in permuted order
-    ranks[L.nrhs_slot] = nrhs;
-    for (int32_t j = 0; j < nrhs; ++j)
-      for (int32_t i = 0; i < N; ++i)
-        arena[L.work_off + i + (int64_t)j * N] = b[perm[i] + (int64_t)j * N];
-    int st2 = host_execute<double>(S, arena.data(), ranks.data(), piv.data(), eps, order_seed,
-                                   &cap_hits);
-    for (int32_t j = 0; j < nrhs; ++j)
-      for (int32_t i = 0; i < N; ++i)
-        x[perm[i] + (int64_t)j * N] = arena[L.work_off + i + (int64_t)j * N];
+    int st1 = 0, st2 = 0;
+    if (precision == 1) {
+      std::vector<float> af(arena.begin(), arena.end());
+      st1 = host_execute<float>(F, af.data(), ranks.data(), piv.data(), eps, order_seed, &cap_hits, limit);
+      if (arena_out) {
+        std::memcpy(arena_out, af.data(), sizeof(float) * af.size());
+        if (ranks_out) std::memcpy(ranks_out, ranks.data(), sizeof(int32_t) * ranks.size());
+        return st1;
+      }
+      ranks[L.nrhs_slot] = nrhs;
+      for (int32_t j = 0; j < nrhs; ++j)
+        for (int32_t i = 0; i < N; ++i) af[L.work_off + i + (int64_t)j * N] = (float)b[perm[i] + (int64_t)j * N];
+      st2 = host_execute<float>(S, af.data(), ranks.data(), piv.data(), eps, order_seed, &cap_hits);
+      for (int32_t j = 0; j < nrhs; ++j)
+        for (int32_t i = 0; i < N; ++i) x[perm[i] + (int64_t)j * N] = af[L.work_off + i + (int64_t)j * N];
+    } else {
+      st1 = host_execute<double>(F, arena.data(), ranks.data(), piv.data(), eps, order_seed, &cap_hits, limit);
+      if (arena_out) {
+        std::memcpy(arena_out, arena.data(), sizeof(double) * arena.size());
+        if (ranks_out) std::memcpy(ranks_out, ranks.data(), sizeof(int32_t) * ranks.size());
+        return st1;
+      }
+      // solve: work vector in permuted order
+      ranks[L.nrhs_slot] = nrhs;
+      for (int32_t j = 0; j < nrhs; ++j)
+        for (int32_t i = 0; i < N; ++i) arena[L.work_off + i + (int64_t)j * N] = b[perm[i] + (int64_t)j * N];
+      st2 = host_execute<double>(S, arena.data(), ranks.data(), piv.data(), eps, order_seed, &cap_hits);
+      for (int32_t j = 0; j < nrhs; ++j)
+        for (int32_t i = 0; i < N; ++i) x[perm[i] + (int64_t)j * N] = arena[L.work_off + i + (int64_t)j * N];
+    }
     if (info) {
       int32_t rmax = 0;
       int64_t rsum = 0, nadm = 0;

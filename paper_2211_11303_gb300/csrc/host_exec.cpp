@@ -350,7 +350,7 @@ std::vector<int64_t> exec_order(const Schedule& S, uint64_t seed) {
 
 template <class T>
 int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, double eps,
-                 uint64_t order_seed, int32_t* cap_hits) {
+                 uint64_t order_seed, int32_t* cap_hits, int64_t limit) {
   HostCtx<T> c;
   c.arena = arena;
   c.ranks = ranks;
@@ -358,14 +358,17 @@ int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, doub
   c.terms = S.terms.data();
   c.pieces = S.pieces.data();
   c.eps = eps;
-  for (int64_t t : exec_order(S, order_seed)) run_task(c, S.tasks[t]);
+  for (int64_t t : exec_order(S, order_seed)) {
+    if (limit >= 0 && t >= limit) continue;
+    run_task(c, S.tasks[t]);
+  }
   if (cap_hits) *cap_hits += c.cap_hits;
   return c.status;
 }
 
 template int host_execute<double>(const Schedule&, double*, int32_t*, int32_t*, double, uint64_t,
-                                  int32_t*);
+                                  int32_t*, int64_t);
 template int host_execute<float>(const Schedule&, float*, int32_t*, int32_t*, double, uint64_t,
-                                 int32_t*);
+                                 int32_t*, int64_t);
 
 }  // namespace hlu

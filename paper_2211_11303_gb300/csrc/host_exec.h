@@ -9,7 +9,7 @@ namespace hlu {
 
 template <class T>
 int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, double eps,
-                 uint64_t order_seed, int32_t* cap_hits);
+                 uint64_t order_seed, int32_t* cap_hits, int64_t limit = -1);
 
 // Trees from the exported flat layout (clusters: nc x 12, blocks: nb x 8), with
 // the leaf ranges filled in.

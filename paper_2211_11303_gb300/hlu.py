@@ -81,8 +81,12 @@ SIGNATURES = {
     "hlu_status_string": (ctypes.c_char_p, [_i32]),
     "hlu_last_error": (ctypes.c_char_p, []),
     "hlu_debug_host_factor_solve": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32,
-                                           _i32, ctypes.c_uint64, _i32, _vp, _vp, _vp]),
+                                           _i32, _i32, ctypes.c_uint64, _i32, _vp, _vp, _vp]),
     "hlu_debug_wait_timeout": (_i32, [_f64, _vp]),
+    "hlu_debug_host_factor_prefix": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32,
+                                            ctypes.c_uint64, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "hlu_debug_factor_prefix": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
+    "hlu_debug_task_record": (_i32, [_vp, _i64, _vp]),
 }
 
 

@@ -55,7 +55,7 @@ def test_build_rejects_bad_arguments(lib):
     assert lib.hlu_build(None, 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
 
 
-def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2, tile=0):
+def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2, tile=0, precision=0):
     from oracle import fem, mesh, trees
     m = mesh.interior_edges(n)
     A = fem.assemble(m, kappa).tocsr()
@@ -70,7 +70,7 @@ def _host_solve(lib, n, kappa, eps, leaf, seed, nrhs=2, tile=0):
     ci = A.indices.astype(np.int32)
     va = A.data.astype(np.float64)
     st = lib.hlu_debug_host_factor_solve(len(C), C.ctypes.data, len(B), B.ctypes.data, p.ctypes.data,
-                                         rp.ctypes.data, ci.ctypes.data, va.ctypes.data, eps, 32, tile, seed,
+                                         rp.ctypes.data, ci.ctypes.data, va.ctypes.data, eps, 32, tile, precision, seed,
                                          nrhs, b.ctypes.data, x.ctypes.data, info.ctypes.data)
     assert st == 0
     return A, perm, cl, bl, b, x, info

@@ -160,8 +160,8 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 /* hlu_factor_profile - per task kind of the last factorisation's task DAG:
  * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for
  * predecessors, out[3*k + 2] cycles spent running, summed over CTAs; kinds
- * k = 0..7 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD and
- * k = 8 the no-work fences.  out: uint64[27] host buffer. */
+ * k = 0..8 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD, RSOLVE
+ * and k = 9 the no-work fences.  out: uint64[30] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III

@@ -61,7 +61,7 @@ int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t limit, voi
                             int32_t* ranks_out, int64_t* sizes);
 
 /* hlu_debug_task_record - copy factorisation task `idx` of a built handle (its
- * 128-byte internal record: kind, flags, operand views) to `out`. */
+ * internal record, 136 bytes: kind, flags, operand views) to `out`. */
 int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out);
 
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a

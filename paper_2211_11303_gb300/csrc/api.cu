@@ -213,9 +213,8 @@ void free_factor(hlu_handle* h) {
 int esize(int precision) { return precision == HLU_FP64 ? 8 : 4; }
 
 int64_t scratch_stride_elems(const ArenaLayout& L) {
-  int64_t half = (int64_t)std::max(L.max_trunc_rows, 1) * kTruncWidthMax;
-  half = (half + 31) & ~int64_t(31);
-  return 2 * half;
+  int64_t e = trunc_scratch_elems(std::max(L.max_trunc_rows, 1));
+  return (e + 31) & ~int64_t(31);
 }
 
 template <class T>
@@ -240,6 +239,7 @@ int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_fl
   a.pivs = h->d_pivp;
   a.scratch = h->d_scratch;
   a.scratch_stride = h->scratch_stride;
+  a.trunc_rows = std::max(h->L.max_trunc_rows, 1);
   a.eps = h->eps;
   a.status = h->d_status;
   a.flops = with_flops ? h->d_flops : nullptr;
@@ -466,8 +466,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     if (std::fabs(e2 - (double)eta2) > 1e-12) return fail(HLU_ERR_ARG, "eta^2 must be an integer");
     if (!(eps > 0) || !(kappa > 0)) return fail(HLU_ERR_ARG, "eps and kappa must be > 0");
     if (rank_cap <= 0) rank_cap = 32;
-    if (rank_cap > kTruncWidthMax / 2) return fail(HLU_ERR_ARG, "rank_cap too large");
-    if (leaf > kTruncWidthMax / 2 && leaf > rank_cap) return fail(HLU_ERR_ARG, "leaf too large for this build");
+    if (rank_cap > 32) return fail(HLU_ERR_ARG, "rank_cap must be <= 32");
     cudaStream_t s = (cudaStream_t)stream;
     hlu_handle* h = new hlu_handle();
     h->n = n;
@@ -518,10 +517,6 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       sb->key = key;
       Schedule F, S;
       build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, sb->L, F, S, sb->st, &sb->FB);
-      if (sb->L.wmax > kTruncWidthMax) {
-        hlu_destroy(h);
-        return fail(HLU_ERR_ARG, "truncation width exceeds this build's limit");
-      }
       if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
       if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
       cudaFree(sb->dF.done);
@@ -912,7 +907,12 @@ extern "C" int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t
   sizes[1] = h->L.n_slots;
   sizes[2] = h->dF.ntasks;
   if (!arena_out && !ranks_out) return HLU_OK;
-  int rc = factor_impl(h, precision, nullptr, limit);
+  // allocate (first call), then clear the whole arena so that memory no task
+  // wrote compares equal with the host executor's zero-initialised arena
+  int rc = factor_impl(h, precision, nullptr, 0);
+  if (rc && rc != HLU_ERR_ZERO_PIVOT) return rc;
+  CKR(cudaMemset(h->d_arena, 0, (size_t)esize(precision) * h->L.total), "clear");
+  rc = factor_impl(h, precision, nullptr, limit);
   if (rc && rc != HLU_ERR_ZERO_PIVOT) return rc;
   if (arena_out)
     CKR(cudaMemcpy(arena_out, h->d_arena, (size_t)esize(precision) * h->L.total, cudaMemcpyDeviceToHost), "arena");

@@ -46,7 +46,7 @@ struct Ctx {
   const Term* terms;
   const Piece* pieces;
   T* scratch;
-  int64_t scratch_half;  // elements of the X half of the per-CTA scratch
+  int64_t rows_max;  // rows of the per-CTA truncation stacks
   double eps;
   int32_t* status;
   double flops;
@@ -362,6 +362,26 @@ __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   }
 }
 
+// ---------------------------------------------------------------- RSOLVE
+// One tile of a left-looking triangular solve: c -= sum_t A_t B_t, then the
+// diagonal tile's triangle (L^-1 P or U^-1) in place.
+template <class T>
+__device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
+  if (t.list_count > 0) {
+    Task r = t;
+    r.type = TK_ROWMV;
+    r.flags = 0;
+    r.out_slot = -1;
+    task_rowmv(c, r, smem);
+    __threadfence_block();
+    __syncthreads();
+  }
+  Task s = t;
+  s.type = (t.flags & TF_UPPER) ? TK_TRSM_U : TK_TRSM_L;
+  s.b = t.c;
+  task_trsm(c, s, smem);
+}
+
 // ---------------------------------------------------------------- DADD
 template <class T>
 __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
@@ -454,15 +474,13 @@ __device__ void house_qr(T* S, int m, int w, T* tau, T* red) {
   }
 }
 
-// out (m x r column-major view in the arena) <- Q out, Q = H_0 ... H_{t-1};
-// CTA-wide per reflector, output columns in groups of 8.
+// O (m x r, column-major, ld) <- Q O, Q = H_0 ... H_{t-1}; CTA-wide per
+// reflector, output columns in groups of 8 (tall stacks).
 template <class T>
-__device__ void apply_q(const Ctx<T>& c, const T* S, int m, int tmax, const T* tau, const View& out, int r) {
+__device__ void apply_q(const T* S, int m, int tmax, const T* tau, T* O, int64_t ld, int r) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ T s_d[8];
   __shared__ T s_part[NT / 32][8];
-  T* O = c.arena + out.off;
-  const int64_t ld = out.cs;
   for (int j = tmax - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj == T(0)) continue;
@@ -508,72 +526,118 @@ __device__ void apply_q(const Ctx<T>& c, const T* S, int m, int tmax, const T* t
   }
 }
 
+// Householder QR of S (m x w, column-major, ld m) by one warp, no block
+// barriers: lanes stride over rows, columns are updated one after another.
 template <class T>
-__device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
-  const int m = t.a.rows, n = t.b.rows;
-  __shared__ int s_W;
-  __shared__ int s_colstart[64];
+__device__ void house_qr_warp(T* S, int m, int w, T* tau) {
+  const int lane = threadIdx.x & 31;
+  const int tmax = min(m, w);
+  for (int j = 0; j < tmax; ++j) {
+    T* cj = S + (int64_t)j * m;
+    T s2 = 0;
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      T x = cj[i];
+      s2 += x * x;
+    }
+    s2 = warp_sum(s2);
+    const T alpha = cj[j];
+    __syncwarp();
+    if (s2 == T(0)) {
+      if (lane == 0) tau[j] = 0;
+      __syncwarp();
+      continue;
+    }
+    const T nrm = sqrt(alpha * alpha + s2);
+    const T beta = alpha >= T(0) ? -nrm : nrm;
+    const T sc = T(1) / (alpha - beta);
+    const T tj = (beta - alpha) / beta;
+    for (int i = j + 1 + lane; i < m; i += 32) cj[i] *= sc;
+    if (lane == 0) {
+      cj[j] = beta;
+      tau[j] = tj;
+    }
+    __syncwarp();
+    for (int cc = j + 1; cc < w; ++cc) {
+      T* col = S + (int64_t)cc * m;
+      T d = 0;
+      for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * col[i];
+      d = warp_sum(d);
+      d = (d + col[j]) * tj;
+      __syncwarp();
+      for (int i = j + 1 + lane; i < m; i += 32) col[i] -= d * cj[i];
+      if (lane == 0) col[j] -= d;
+      __syncwarp();
+    }
+  }
+}
+
+// O (m x r, column-major, ld) <- Q O, one warp per column (short stacks).
+template <class T>
+__device__ void apply_q_warp(const T* S, int m, int tmax, const T* tau, T* O, int64_t ld, int r, int warp0,
+                             int nwarps) {
+  const int warp = (threadIdx.x >> 5) - warp0, lane = threadIdx.x & 31;
+  if (warp < 0 || warp >= nwarps) return;
+  for (int cc = warp; cc < r; cc += nwarps) {
+    T* col = O + (int64_t)cc * ld;
+    for (int j = tmax - 1; j >= 0; --j) {
+      const T tj = tau[j];
+      if (tj == T(0)) continue;
+      const T* cj = S + (int64_t)j * m;
+      T d = 0;
+      for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * __ldcg(col + i);
+      d = warp_sum(d);
+      d = (d + __ldcg(col + j)) * tj;
+      __syncwarp();
+      for (int i = j + 1 + lane; i < m; i += 32) __stcg(col + i, __ldcg(col + i) - d * cj[i]);
+      if (lane == 0) __stcg(col + j, __ldcg(col + j) - d);
+      __syncwarp();
+    }
+  }
+}
+
+// stacked factors up to this many rows use the warp-level QR and apply
+constexpr int kWarpQrRows = 768;
+constexpr int kStackCols = kTruncStack;
+
+// Truncated SVD of the stacked factors SX (m x W) and SY (n x W): QR of both,
+// one-sided Jacobi SVD of the core R_x R_y^T, keep s_i > eps s_1 (at most
+// cap); X <- Q_x U_r S_r and Y <- Q_y V_r are written to OX (ld ox) and OY
+// (ld oy).  Returns r (the same in every thread).
+template <class T>
+__device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int cap, T* OX, int64_t ox, T* OY,
+                              int64_t oy, char* smem) {
   __shared__ int s_rot;
   __shared__ int s_r;
-  __shared__ int s_ord[64];
+  __shared__ int s_ord[kStackCols];
   __shared__ T s_red[NT / 32];
-  if (threadIdx.x == 0) {
-    int W = 0;
-    for (int q = 0; q < t.list_count && q < 64; ++q) {
-      s_colstart[q] = W;
-      W += ncols(c, c.pieces[t.list_begin + q].X);
-    }
-    s_W = W;
-  }
-  __syncthreads();
-  const int W = s_W;
-  if (W == 0 || m == 0 || n == 0) {
-    if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
-    return;
-  }
-  T* SX = c.scratch;
-  T* SY = c.scratch + c.scratch_half;
-  // stack the pieces (zero outside each piece's rows)
-  for (int64_t idx = threadIdx.x; idx < (int64_t)m * W; idx += NT) SX[idx] = T(0);
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * W; idx += NT) SY[idx] = T(0);
-  __syncthreads();
-  for (int q = 0; q < t.list_count; ++q) {
-    const Piece& P = c.pieces[t.list_begin + q];
-    const int w = ncols(c, P.X);
-    const int c0 = s_colstart[q];
-    const T sg = T(P.sign);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)P.X.rows * w; idx += NT) {
-      int i = (int)(idx % P.X.rows), j = (int)(idx / P.X.rows);
-      SX[(P.xoff + i) + (int64_t)(c0 + j) * m] = sg * ldv(c, P.X, i, j);
-    }
-    for (int64_t idx = threadIdx.x; idx < (int64_t)P.Y.rows * w; idx += NT) {
-      int i = (int)(idx % P.Y.rows), j = (int)(idx / P.Y.rows);
-      SY[(P.yoff + i) + (int64_t)(c0 + j) * n] = ldv(c, P.Y, i, j);
-    }
-  }
-  __syncthreads();
   T* tauX = reinterpret_cast<T*>(smem);
-  T* tauY = tauX + 64;
-  T* G = tauY + 64;           // p x q
-  T* V = G + 64 * 64;         // q x q
-  T* sv = V + 64 * 64;        // q
-  house_qr(SX, m, W, tauX, s_red);
-  house_qr(SY, n, W, tauY, s_red);
+  T* tauY = tauX + kStackCols;
+  T* sv = tauY + kStackCols;
+  T* G = sv + kStackCols;              // p x q
+  T* V = G + kStackCols * kStackCols;  // q x q
+  const bool small = max(m, n) <= kWarpQrRows;
+  if (small) {
+    const int wq = threadIdx.x >> 5;
+    if (wq == 0) house_qr_warp(SX, m, W, tauX);
+    if (wq == 1) house_qr_warp(SY, n, W, tauY);
+    __syncthreads();
+  } else {
+    house_qr(SX, m, W, tauX, s_red);
+    house_qr(SY, n, W, tauY, s_red);
+  }
   const int p = min(m, W), q = min(n, W);
-  // core G = R_x R_y^T
   for (int idx = threadIdx.x; idx < p * q; idx += NT) {
     int i = idx % p, j = idx / p;
-    T s = 0;
-    for (int l = max(i, j); l < W; ++l) s += SX[i + (int64_t)l * m] * SY[j + (int64_t)l * n];
-    G[i + j * p] = s;
+    T acc = 0;
+    for (int l = max(i, j); l < W; ++l) acc += SX[i + (int64_t)l * m] * SY[j + (int64_t)l * n];
+    G[i + j * p] = acc;
   }
   for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? T(1) : T(0);
   __syncthreads();
-  // one-sided Jacobi on the columns of G, round-robin pairing
-  const T tol = sizeof(T) == 4 ? T(1e-5) : T(1e-13);
+  const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
   const int qq = q + (q & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int sweep = 0; sweep < 24 && qq > 1; ++sweep) {
+  for (int sweep = 0; sweep < 30 && qq > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int rd = 0; rd < qq - 1; ++rd) {
@@ -615,10 +679,10 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
     __syncthreads();
   }
   for (int j = warp; j < q; j += NT / 32) {
-    T s = 0;
-    for (int i = lane; i < p; i += 32) s += G[i + j * p] * G[i + j * p];
-    s = warp_sum(s);
-    if (lane == 0) sv[j] = sqrt(s);
+    T acc = 0;
+    for (int i = lane; i < p; i += 32) acc += G[i + j * p] * G[i + j * p];
+    acc = warp_sum(acc);
+    if (lane == 0) sv[j] = sqrt(acc);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -635,8 +699,8 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
     int r = 0;
     if (smax > T(0))
       while (r < q && sv[s_ord[r]] > T(c.eps) * smax) ++r;
-    if (r > t.cap) {
-      r = t.cap;
+    if (r > cap) {
+      r = cap;
       atomicAdd(c.status + 2, 1);
     }
     s_r = r;
@@ -646,16 +710,67 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   const int r = s_r;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) {
     int i = (int)(idx % m), j = (int)(idx / m);
-    stv(c, t.a, i, j, i < p ? G[i + s_ord[j] * p] : T(0));
+    __stcg(OX + i + (int64_t)j * ox, i < p ? G[i + s_ord[j] * p] : T(0));
   }
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) {
     int i = (int)(idx % n), j = (int)(idx / n);
-    stv(c, t.b, i, j, i < q ? V[i + s_ord[j] * q] : T(0));
+    __stcg(OY + i + (int64_t)j * oy, i < q ? V[i + s_ord[j] * q] : T(0));
   }
   __syncthreads();
-  apply_q(c, SX, m, min(m, W), tauX, t.a, r);
-  apply_q(c, SY, n, min(n, W), tauY, t.b, r);
+  if (small) {
+    apply_q_warp(SX, m, min(m, W), tauX, OX, ox, r, 0, NT / 64);
+    apply_q_warp(SY, n, min(n, W), tauY, OY, oy, r, NT / 64, NT / 64);
+  } else {
+    apply_q(SX, m, min(m, W), tauX, OX, ox, r);
+    apply_q(SY, n, min(n, W), tauY, OY, oy, r);
+  }
   __syncthreads();
+  return r;
+}
+
+// (a, b) <- truncation of sum_pieces sign X Y^T.  Pieces are stacked in a
+// kStackCols-wide buffer; when the next piece does not fit, the stack is
+// compressed in place first, so any number of pieces is accepted.
+template <class T>
+__device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
+  const int m = t.a.rows, n = t.b.rows;
+  T* SX = c.scratch;
+  T* SY = SX + c.rows_max * kStackCols;
+  T* OX = SY + c.rows_max * kStackCols;
+  T* OY = OX + c.rows_max * 32;
+  if (m == 0 || n == 0) {
+    if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
+    return;
+  }
+  int W = 0;
+  for (int q = 0; q < t.list_count; ++q) {
+    const Piece& P = c.pieces[t.list_begin + q];
+    const int w = ncols(c, P.X);
+    if (w == 0) continue;
+    if (W + w > kStackCols) {
+      const int r = trunc_compress(c, SX, SY, m, n, W, t.cap, OX, m, OY, n, smem);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) SX[idx] = __ldcg(OX + idx);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) SY[idx] = __ldcg(OY + idx);
+      W = r;
+      __syncthreads();
+    }
+    const T sg = T(P.sign);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * w; idx += NT) SX[(int64_t)W * m + idx] = T(0);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * w; idx += NT) SY[(int64_t)W * n + idx] = T(0);
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)P.X.rows * w; idx += NT) {
+      int i = (int)(idx % P.X.rows), j = (int)(idx / P.X.rows);
+      SX[(P.xoff + i) + (int64_t)(W + j) * m] = sg * ldv(c, P.X, i, j);
+    }
+    for (int64_t idx = threadIdx.x; idx < (int64_t)P.Y.rows * w; idx += NT) {
+      int i = (int)(idx % P.Y.rows), j = (int)(idx / P.Y.rows);
+      SY[(P.yoff + i) + (int64_t)(W + j) * n] = ldv(c, P.Y, i, j);
+    }
+    W += w;
+    __syncthreads();
+  }
+  int r = 0;
+  if (W > 0) r = trunc_compress(c, SX, SY, m, n, W, t.cap, c.arena + t.a.off, t.a.cs, c.arena + t.b.off, t.b.cs, smem);
   if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
 }
 
@@ -669,7 +784,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
   c.terms = a.terms;
   c.pieces = a.pieces;
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
-  c.scratch_half = a.scratch_stride / 2;
+  c.rows_max = a.trunc_rows;
   c.eps = a.eps;
   c.status = a.status;
   c.flops = 0;
@@ -729,6 +844,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
         case TK_ROWMV: task_rowmv(c, t, smem); break;
         case TK_TRUNC: task_trunc(c, t, smem); break;
         case TK_DADD: task_dadd(c, t, smem); break;
+        case TK_RSOLVE: task_rsolve(c, t, smem); break;
         default: break;
       }
     }
@@ -753,12 +869,13 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
 }
 
 size_t exec_smem_bytes(int elem_size) {
-  // max over task kinds: GETRF/TRSM 64x64 + 64 ints; TRUNC 2*64 + 2*64*64 + 64
-  size_t trunc = (size_t)elem_size * (128 + 2 * 64 * 64 + 64);
+  // max over task kinds: TRUNC (3 stack-wide vectors + G + V), GETRF/TRSM
+  // (64 x 64 + 64 ints), staged GEMM chunks (2 x 64 x KC)
+  size_t trunc = (size_t)elem_size * (3 * kTruncStack + 2 * kTruncStack * kTruncStack);
   size_t lu = (size_t)elem_size * 64 * 64 + 64 * sizeof(int);
-  size_t proj = (size_t)elem_size * NT;
+  size_t gemm = (size_t)elem_size * 2 * 64 * KC;
   size_t m = trunc > lu ? trunc : lu;
-  return m > proj ? m : proj;
+  return m > gemm ? m : gemm;
 }
 
 template <class T>

@@ -23,6 +23,7 @@ struct ExecArgs {
   int32_t* const* pivs;
   void* scratch;            // per-CTA scratch, scratch_stride elements each
   int64_t scratch_stride;
+  int64_t trunc_rows;       // rows of the truncation stacks in the scratch
   double eps;
   int32_t* status;          // [0] status code, [1] failing task, [2] rank-cap hits, [3] abort
   double* flops;            // accumulated algorithmic flops (may be null)
@@ -37,6 +38,8 @@ template <class T>
 cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
 
 constexpr int kExecThreads = 256;
-constexpr int kTruncWidthMax = 64;  // widest stacked factor a TRUNC task accepts
+constexpr int kTruncStack = 96;  // columns of a truncation stack (>= rank cap + widest piece)
+// per-CTA scratch: two stacks (kTruncStack wide) and two outputs (32 wide)
+inline int64_t trunc_scratch_elems(int64_t rows) { return rows * (2 * kTruncStack + 2 * 32); }
 
 }  // namespace hlu

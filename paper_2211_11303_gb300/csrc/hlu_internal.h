@@ -40,10 +40,12 @@ enum TaskType : int32_t {
   TK_ROWMV = 5,   // c (n x k) <- [c] + sign * sum_terms A_t B_t
   TK_TRUNC = 6,   // (a, b) <- truncate(sum_pieces sign X Y^T) to eps, rank -> out_slot
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
-  TK_NUM = 8,
-  TK_FENCE = 8    // no work: orders re-use of temporary memory after its readers
+  TK_RSOLVE = 8,  // c <- tri(a)^-1 (c - sum_terms A_t B_t): one tile of a triangular solve;
+                  // flags & TF_UPPER: U^-1, else L^-1 P (pivots at piv_off)
+  TK_NUM = 9,
+  TK_FENCE = 9    // no work: orders re-use of temporary memory after its readers
 };
-enum : int32_t { TF_OVERWRITE = 1 };
+enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2 };
 
 struct Task {
   int32_t type;

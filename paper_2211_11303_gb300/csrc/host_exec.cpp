@@ -230,32 +230,15 @@ void h_jacobi(std::vector<T>& G, int p, int q, std::vector<T>& V) {
   }
 }
 
+// Truncated SVD of X Y^T (SX: m x W, SY: n x W, column-major): returns the
+// new factors (m x r, n x r) with s_i > eps s_1 kept, at most cap.
 template <class T>
-void h_trunc(HostCtx<T>& c, const Task& t) {
-  int m = t.a.rows, n = t.b.rows;
-  int W = 0;
-  for (int q = 0; q < t.list_count; ++q) W += ncols(c, c.pieces[t.list_begin + q].X);
-  if (W == 0 || m == 0 || n == 0) {
-    c.ranks[t.out_slot] = 0;
-    return;
-  }
-  std::vector<T> SX((size_t)m * W, T(0)), SY((size_t)n * W, T(0));
-  int col = 0;
-  for (int q = 0; q < t.list_count; ++q) {
-    const Piece& P = c.pieces[t.list_begin + q];
-    int w = ncols(c, P.X);
-    for (int j = 0; j < w; ++j) {
-      for (int i = 0; i < P.X.rows; ++i)
-        SX[(P.xoff + i) + (size_t)(col + j) * m] = T(P.sign) * at(c, P.X, i, j);
-      for (int i = 0; i < P.Y.rows; ++i) SY[(P.yoff + i) + (size_t)(col + j) * n] = at(c, P.Y, i, j);
-    }
-    col += w;
-  }
+int h_compress(HostCtx<T>& c, std::vector<T> SX, std::vector<T> SY, int m, int n, int W, int cap,
+               std::vector<T>& BX, std::vector<T>& BY) {
   std::vector<T> tx, ty;
   h_house(SX, m, W, tx);
   h_house(SY, n, W, ty);
   int p = std::min(m, W), q = std::min(n, W);
-  // core M = R_x R_y^T (p x q)
   std::vector<T> G((size_t)p * q, T(0));
   for (int i = 0; i < p; ++i)
     for (int j = 0; j < q; ++j) {
@@ -278,22 +261,74 @@ void h_trunc(HostCtx<T>& c, const Task& t) {
   int r = 0;
   if (smax > T(0))
     while (r < q && sv[ord[r]] > T(c.eps) * smax) ++r;
-  if (r > t.cap) {
-    r = t.cap;
+  if (r > cap) {
+    r = cap;
     c.cap_hits++;
   }
-  std::vector<T> BX((size_t)m * r, T(0)), BY((size_t)n * r, T(0));
+  BX.assign((size_t)m * r, T(0));
+  BY.assign((size_t)n * r, T(0));
   for (int j = 0; j < r; ++j) {
     for (int i = 0; i < p; ++i) BX[i + (size_t)j * m] = G[i + (size_t)ord[j] * p];
     for (int i = 0; i < q; ++i) BY[i + (size_t)j * n] = V[i + (size_t)ord[j] * q];
   }
   h_applyq(SX, m, tx, BX, r);
   h_applyq(SY, n, ty, BY, r);
-  for (int j = 0; j < r; ++j) {
-    for (int i = 0; i < m; ++i) at(c, t.a, i, j) = BX[i + (size_t)j * m];
-    for (int i = 0; i < n; ++i) at(c, t.b, i, j) = BY[i + (size_t)j * n];
+  return r;
+}
+
+// pieces are stacked kTruncStack columns at a time, compressing when the next
+// piece does not fit (the device executor's order of operations)
+constexpr int kHostStack = 96;
+template <class T>
+void h_trunc(HostCtx<T>& c, const Task& t) {
+  int m = t.a.rows, n = t.b.rows;
+  if (m == 0 || n == 0) {
+    c.ranks[t.out_slot] = 0;
+    return;
+  }
+  std::vector<T> SX, SY;  // column-major stacks
+  int W = 0;
+  for (int q = 0; q < t.list_count; ++q) {
+    const Piece& P = c.pieces[t.list_begin + q];
+    int w = ncols(c, P.X);
+    if (w == 0) continue;
+    if (W + w > kHostStack) {
+      std::vector<T> BX, BY;
+      W = h_compress(c, SX, SY, m, n, W, t.cap, BX, BY);
+      SX = BX;
+      SY = BY;
+    }
+    SX.resize((size_t)m * (W + w), T(0));
+    SY.resize((size_t)n * (W + w), T(0));
+    for (int j = 0; j < w; ++j) {
+      for (int i = 0; i < P.X.rows; ++i) SX[(P.xoff + i) + (size_t)(W + j) * m] = T(P.sign) * at(c, P.X, i, j);
+      for (int i = 0; i < P.Y.rows; ++i) SY[(P.yoff + i) + (size_t)(W + j) * n] = at(c, P.Y, i, j);
+    }
+    W += w;
+  }
+  int r = 0;
+  if (W > 0) {
+    std::vector<T> BX, BY;
+    r = h_compress(c, SX, SY, m, n, W, t.cap, BX, BY);
+    for (int j = 0; j < r; ++j) {
+      for (int i = 0; i < m; ++i) at(c, t.a, i, j) = BX[i + (size_t)j * m];
+      for (int i = 0; i < n; ++i) at(c, t.b, i, j) = BY[i + (size_t)j * n];
+    }
   }
   c.ranks[t.out_slot] = r;
+}
+
+template <class T>
+void h_rsolve(HostCtx<T>& c, const Task& t) {
+  Task r = t;
+  r.type = TK_ROWMV;
+  r.flags = 0;
+  r.out_slot = -1;
+  h_rowmv(c, r);
+  Task s = t;
+  s.type = (t.flags & TF_UPPER) ? TK_TRSM_U : TK_TRSM_L;
+  s.b = t.c;
+  h_trsm(c, s);
 }
 
 template <class T>
@@ -307,6 +342,7 @@ void run_task(HostCtx<T>& c, const Task& t) {
     case TK_ROWMV: h_rowmv(c, t); break;
     case TK_TRUNC: h_trunc(c, t); break;
     case TK_DADD: h_dadd(c, t); break;
+    case TK_RSOLVE: h_rsolve(c, t); break;
     case TK_FENCE: break;
     default: throw std::logic_error("task type");
   }

@@ -556,14 +556,6 @@ class Sched {
     return r;
   }
 
-  // A product wider than the rank capacity (a dense tile's width, an identity
-  // factor) is truncated on its own first, so that every stacked truncation
-  // stays within two capacities.
-  LR narrow(const LR& p) {
-    if (p.X.v.cols <= kcap_) return p;
-    return trunc_new(p.X.clus, p.Y.clus, {{p, 0, 0, 1.0f}});
-  }
-
   // ---------------------------------------------------------------- H-gemm
   LR product(int32_t a, int32_t b) {
     int32_t ka = kind(a), kb = kind(b);
@@ -594,59 +586,76 @@ class Sched {
     }
     if (ka == KIND_DENSE) return LR{mvIdent(tau), hmul_new(b, mvDT(a), true)};
     if (kb == KIND_DENSE) return LR{hmul_new(a, mvD(b), false), mvIdent(rho)};
-    // both subdivided: son products, summed and truncated per son, then
-    // agglomerated (rows of son 0 and of son 1 first, then the two halves)
+    // both subdivided: the eight son products, placed at their son offsets,
+    // are stacked and truncated in one task (formatted agglomeration)
     const Cluster& T = C_[tau];
     const Cluster& R = C_[rho];
-    LR t[2][2];
+    std::vector<PieceMV> ps;
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) {
-        LR s0 = narrow(product(son(a, i, 0), son(b, 0, j)));
-        LR s1 = narrow(product(son(a, i, 1), son(b, 1, j)));
-        t[i][j] = trunc_new(T.son[i], R.son[j], {{s0, 0, 0, 1.0f}, {s1, 0, 0, 1.0f}});
-      }
-    int32_t r0 = C_[R.son[0]].size, t0 = C_[T.son[0]].size;
-    LR top = trunc_new(T.son[0], rho, {{t[0][0], 0, 0, 1.0f}, {t[0][1], 0, r0, 1.0f}});
-    LR bot = trunc_new(T.son[1], rho, {{t[1][0], 0, 0, 1.0f}, {t[1][1], 0, r0, 1.0f}});
-    return trunc_new(tau, rho, {{top, 0, 0, 1.0f}, {bot, t0, 0, 1.0f}});
+      for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+          LR sp = product(son(a, i, k), son(b, k, j));
+          ps.push_back(PieceMV{sp, C_[T.son[i]].off - T.off, C_[R.son[j]].off - R.off, 1.0f});
+        }
+    return trunc_new(tau, rho, ps);
   }
 
-  void add_lr(int32_t c, const LR& p, float sign) {
-    if (p.X.clus != rowc(c) || p.Y.clus != colc(c)) throw std::logic_error("add_lr shape");
+  // c <- c + sign * sum_p X_p Y_p^T in the format of c: one DADD per product
+  // for a dense c, one truncation of all products for a low-rank c
+  void add_multi(int32_t c, const std::vector<LR>& ps, float sign) {
+    if (ps.empty()) return;
+    for (const LR& p : ps)
+      if (p.X.clus != rowc(c) || p.Y.clus != colc(c)) throw std::logic_error("add shape");
     int32_t k = kind(c);
     if (k == KIND_DENSE) {
-      Task t = make(TK_DADD);
-      t.c = mvD(c).v;
-      t.a = p.X.v;
-      t.b = p.Y.v;
-      t.sign = sign;
-      begin(t);
-      acc(p.X, false);
-      acc(p.Y, false);
-      acc(mvD(c), true);
-      end();
+      for (const LR& p : ps) {
+        Task t = make(TK_DADD);
+        t.c = mvD(c).v;
+        t.a = p.X.v;
+        t.b = p.Y.v;
+        t.sign = sign;
+        begin(t);
+        acc(p.X, false);
+        acc(p.Y, false);
+        acc(mvD(c), true);
+        end();
+      }
     } else if (k == KIND_ADM) {
-      LR q = narrow(p);
-      emit_trunc(mvX(c), mvY(c), L_.slot[c], L_.cap[c],
-                 {{LR{mvX(c), mvY(c)}, 0, 0, 1.0f}, {q, 0, 0, sign}});
+      std::vector<PieceMV> pieces;
+      pieces.push_back(PieceMV{LR{mvX(c), mvY(c)}, 0, 0, 1.0f});
+      for (const LR& p : ps) pieces.push_back(PieceMV{p, 0, 0, sign});
+      emit_trunc(mvX(c), mvY(c), L_.slot[c], L_.cap[c], pieces);
     } else {
       const Cluster& R = C_[rowc(c)];
       const Cluster& Q = C_[colc(c)];
       for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j)
-          add_lr(son(c, i, j), LR{sub(p.X, R.son[i]), sub(p.Y, Q.son[j])}, sign);
+        for (int j = 0; j < 2; ++j) {
+          std::vector<LR> sub_ps;
+          for (const LR& p : ps) sub_ps.push_back(LR{sub(p.X, R.son[i]), sub(p.Y, Q.son[j])});
+          add_multi(son(c, i, j), sub_ps, sign);
+        }
     }
   }
 
   void gemm(int32_t c, int32_t a, int32_t b) {
     if (kind(c) == KIND_SUB && kind(a) == KIND_SUB && kind(b) == KIND_SUB) {
       for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j)
-          for (int k = 0; k < 2; ++k) gemm(son(c, i, j), son(a, i, k), son(b, k, j));
+        for (int j = 0; j < 2; ++j) {
+          // the two son products into c_ij that are not themselves subdivided
+          // products are added together
+          std::vector<LR> ps;
+          for (int k = 0; k < 2; ++k) {
+            int32_t cc = son(c, i, j), aa = son(a, i, k), bb = son(b, k, j);
+            if (kind(cc) == KIND_SUB && kind(aa) == KIND_SUB && kind(bb) == KIND_SUB)
+              gemm(cc, aa, bb);
+            else
+              ps.push_back(product(aa, bb));
+          }
+          add_multi(son(c, i, j), ps, -1.0f);
+        }
       return;
     }
-    LR p = product(a, b);
-    add_lr(c, p, -1.0f);
+    add_multi(c, {product(a, b)}, -1.0f);
   }
 
   // ---------------------------------------------------------------- H-trsm, H-LU
@@ -689,6 +698,115 @@ class Sched {
     trsm_right(d10, d00);
     gemm(d11, d10, d01);
     lu(d11);
+  }
+
+  // Left-looking tile solves for the preconditioner: every segment (tile) of
+  // the vector is finished by one RSOLVE task that subtracts the contributions
+  // of all factor blocks in its block row and applies the diagonal tile's
+  // triangle; a low-rank block's projection Y^T x is formed once, as soon as
+  // its column range is final.
+  void solve_tiles(int32_t nrhs_max) {
+    MV W;
+    W.buf = new_buf_leaves(0);
+    W.clus = 0;
+    const int32_t N = sz(0);
+    W.v = View{L_.work_off, 1, N, N, nrhs_max, L_.nrhs_slot, 0};
+    const int32_t nseg = (int32_t)seg_cluster_.size();
+    // factor leaves, the diagonal tile of every segment, blocks by row segment
+    std::vector<int32_t> lv;
+    leaves_of(0, lv);
+    std::vector<int32_t> diag(nseg, -1);
+    std::vector<std::vector<int32_t>> lower(nseg), upper(nseg);
+    std::vector<std::vector<int32_t>> lproj_at(nseg), uproj_at(nseg);
+    for (int32_t b : lv) {
+      const Cluster& R = C_[rowc(b)];
+      const Cluster& Q = C_[colc(b)];
+      if (rowc(b) == colc(b)) {
+        if (seg_end_[rowc(b)] - seg_begin_[rowc(b)] != 1 || kind(b) != KIND_DENSE)
+          throw std::logic_error("diagonal leaf is not one dense tile");
+        diag[seg_begin_[rowc(b)]] = b;
+        continue;
+      }
+      bool is_lower = Q.off + Q.size <= R.off;
+      for (int32_t q = seg_begin_[rowc(b)]; q < seg_end_[rowc(b)]; ++q) (is_lower ? lower : upper)[q].push_back(b);
+      if (kind(b) == KIND_ADM) {
+        if (is_lower)
+          lproj_at[seg_end_[colc(b)] - 1].push_back(b);
+        else
+          uproj_at[seg_begin_[colc(b)]].push_back(b);
+      }
+    }
+    std::vector<MV> T(B_.size());
+    auto proj = [&](int32_t b) {
+      MV A = mvY(b);
+      MV vin = sub(W, colc(b));
+      MV t;
+      t.clus = -1;
+      int32_t cap = L_.cap[b];
+      int64_t toff = alloc((int64_t)cap * nrhs_max);
+      t.buf = new_buf_single();
+      bind_alloc(t.buf);
+      t.v = View{toff, 1, cap, cap, nrhs_max, L_.nrhs_slot, 0};
+      Task k = make(TK_PROJ);
+      k.a = A.v;
+      k.b = vin.v;
+      k.c = t.v;
+      begin(k);
+      acc(A, false);
+      acc(vin, false);
+      touch(bufs_[t.buf].seg0, true);
+      end();
+      T[b] = t;
+    };
+    auto rsolve = [&](int32_t q, bool up) {
+      const int32_t sc = seg_cluster_[q];
+      const int32_t d = diag[q];
+      if (d < 0) throw std::logic_error("segment without a diagonal tile");
+      MV Vs = sub(W, sc);
+      Task k = make(TK_RSOLVE);
+      k.flags = up ? TF_UPPER : 0;
+      k.a = mvD(d).v;
+      k.b = W.v;
+      k.c = Vs.v;
+      k.piv_off = L_.piv_off[d];
+      k.sign = -1.0f;
+      const std::vector<int32_t>& blocks = up ? upper[q] : lower[q];
+      k.list_begin = (int32_t)S_->terms.size();
+      k.list_count = (int32_t)blocks.size();
+      begin(k);
+      for (int32_t b : blocks) {
+        Term tm;
+        std::memset(&tm, 0, sizeof(tm));
+        // the block's row cluster contains the segment
+        tm.roff = 0;
+        if (kind(b) == KIND_DENSE) {
+          MV A = sub(mvD(b), sc);
+          MV Bv = sub(W, colc(b));
+          tm.A = A.v;
+          tm.B = Bv.v;
+          acc(A, false);
+          acc(Bv, false);
+        } else {
+          MV A = sub(mvX(b), sc);
+          tm.A = A.v;
+          tm.B = T[b].v;
+          acc(A, false);
+          touch(bufs_[T[b].buf].seg0, false);
+        }
+        S_->terms.push_back(tm);
+      }
+      acc(mvD(d), false);
+      acc(Vs, true);
+      end();
+    };
+    for (int32_t q = 0; q < nseg; ++q) {
+      rsolve(q, false);
+      for (int32_t b : lproj_at[q]) proj(b);
+    }
+    for (int32_t q = nseg - 1; q >= 0; --q) {
+      rsolve(q, true);
+      for (int32_t b : uproj_at[q]) proj(b);
+    }
   }
 
   void solve_all(int32_t nrhs_max) {
@@ -845,7 +963,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   }
   {
     Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
-    s.solve_all(nrhs_max);
+    s.solve_tiles(nrhs_max);
     st.temp_elems += s.temp_elems_;
   }
   factor.n_edges = (int64_t)factor.pred_idx.size();

@@ -209,12 +209,12 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "FENCE"]
 
 
 def hlu_factor_profile(h):
     """{kind: (tasks, wait_cycles, run_cycles)} of the last factorisation."""
-    out = (ctypes.c_uint64 * 27)()
+    out = (ctypes.c_uint64 * 30)()
     _check(lib().hlu_factor_profile(_vp(h), out))
     return {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
 

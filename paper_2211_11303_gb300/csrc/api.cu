@@ -12,6 +12,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -124,6 +125,9 @@ struct SchedBundle {
 };
 
 std::mutex g_cache_mu;
+std::mutex g_batch_mu;            // serialises batched launches (shared order buffer)
+int64_t* g_batch_order = nullptr;
+int64_t g_batch_order_len = 0;
 std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
 constexpr size_t kCacheEntries = 8;
 
@@ -212,9 +216,9 @@ void free_factor(hlu_handle* h) {
 
 int esize(int precision) { return precision == HLU_FP64 ? 8 : 4; }
 
-int64_t scratch_stride_elems(const ArenaLayout& L) {
-  int64_t e = trunc_scratch_elems(std::max(L.max_trunc_rows, 1));
-  return (e + 31) & ~int64_t(31);
+// per-CTA scratch stride in elements of the factor type
+int64_t scratch_stride_elems(const ArenaLayout& L, int es) {
+  return trunc_scratch_bytes(std::max(L.max_trunc_rows, 1), es) / es;
 }
 
 template <class T>
@@ -222,41 +226,131 @@ int blocks_per_sm() {
   return exec_blocks_per_sm<T>();
 }
 
+ProbSched prob_of(hlu_handle* h, DevSched& ds) {
+  ProbSched p;
+  std::memset(&p, 0, sizeof(p));
+  p.tasks = ds.tasks;
+  p.terms = ds.terms;
+  p.pieces = ds.pieces;
+  p.pred_ptr = ds.pred_ptr;
+  p.pred_idx = ds.pred_idx;
+  p.done = ds.done;
+  p.arena = h->d_arena;
+  p.ranks = h->d_ranks;
+  p.piv = h->d_piv;
+  p.eps = h->eps;
+  p.ntasks = ds.ntasks;
+  p.epoch = ++ds.epoch;
+  return p;
+}
+
+// One launch of the executor over one problem's schedule (or its first
+// `limit` tasks).
 int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops, int64_t limit = -1) {
   ExecArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.tasks = ds.tasks;
-  a.ntasks = limit >= 0 ? std::min(limit, ds.ntasks) : ds.ntasks;
-  a.terms = ds.terms;
-  a.pieces = ds.pieces;
-  a.pred_ptr = ds.pred_ptr;
-  a.pred_idx = ds.pred_idx;
-  a.done = ds.done;
-  a.epoch = ++ds.epoch;
+  a.probs[0] = prob_of(h, ds);
+  a.nprobs = 1;
+  a.order = nullptr;
+  a.ntotal = limit >= 0 ? std::min(limit, ds.ntasks) : ds.ntasks;
   a.ticket = h->d_ticket;
-  a.arenas = h->d_arenas;
-  a.ranks = h->d_rankp;
-  a.pivs = h->d_pivp;
   a.scratch = h->d_scratch;
   a.scratch_stride = h->scratch_stride;
   a.trunc_rows = std::max(h->L.max_trunc_rows, 1);
-  a.eps = h->eps;
   a.status = h->d_status;
   a.flops = with_flops ? h->d_flops : nullptr;
   a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
   a.prof = with_flops ? h->d_prof : nullptr;
-  if (a.ntasks == 0) return HLU_OK;
-  int32_t st0[4] = {0, -1, 0, 0};
+  if (a.ntotal == 0) return HLU_OK;
+  int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
   CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
   CKR(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
-  int g = (int)std::min<int64_t>(grid, a.ntasks);
+  int g = (int)std::min<int64_t>(grid, a.ntotal);
   cudaError_t e = h->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
   CKR(e, "executor launch");
   return HLU_OK;
 }
 
+// Ticket order of a batched launch: the problems' tasks interleaved by
+// relative progress (task i of problem p at key (i + 1/2) / n_p), increasing
+// within every problem, encoded (p << 40) | i.
+std::vector<int64_t> batch_order(const std::vector<int64_t>& ntasks) {
+  struct Item {
+    double key;
+    int32_t p;
+    int64_t i;
+    bool operator<(const Item& o) const { return key > o.key || (key == o.key && p > o.p); }
+  };
+  std::vector<int64_t> out;
+  int64_t tot = 0;
+  for (int64_t n : ntasks) tot += n;
+  out.reserve(tot);
+  std::priority_queue<Item> pq;
+  for (size_t p = 0; p < ntasks.size(); ++p)
+    if (ntasks[p] > 0) pq.push(Item{0.5 / ntasks[p], (int32_t)p, 0});
+  while (!pq.empty()) {
+    Item it = pq.top();
+    pq.pop();
+    out.push_back(((int64_t)it.p << 40) | it.i);
+    if (it.i + 1 < ntasks[it.p]) pq.push(Item{(it.i + 1.5) / ntasks[it.p], it.p, it.i + 1});
+  }
+  return out;
+}
+
+// One launch over the factor (which = 0) or solve (which = 1) schedules of
+// several handles with the same precision.  Handle 0's ticket, status, flop
+// counter and profile are used; the scratch is that of the handle with the
+// largest truncation stacks.
+int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, int64_t* order_cache_key,
+                   int64_t** d_order, int64_t* d_order_len) {
+  if (count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "batch size");
+  ExecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  std::vector<int64_t> nt(count);
+  hlu_handle* hs0 = hs[0];
+  hlu_handle* big = hs0;
+  for (int i = 0; i < count; ++i) {
+    hlu_handle* h = hs[i];
+    if (h->precision != hs0->precision) return fail(HLU_ERR_ARG, "mixed precisions in a batch");
+    DevSched& ds = which == 0 ? h->dF : h->dS;
+    a.probs[i] = prob_of(h, ds);
+    nt[i] = ds.ntasks;
+    if (h->L.max_trunc_rows > big->L.max_trunc_rows) big = h;
+  }
+  a.nprobs = count;
+  std::vector<int64_t> ord = batch_order(nt);
+  if (*d_order_len < (int64_t)ord.size()) {
+    if (*d_order) cudaFree(*d_order);
+    *d_order = nullptr;
+    CKR(cudaMalloc(d_order, sizeof(int64_t) * std::max<size_t>(ord.size(), 1)), "order");
+    *d_order_len = (int64_t)ord.size();
+  }
+  (void)order_cache_key;
+  CKR(cudaMemcpyAsync(*d_order, ord.data(), sizeof(int64_t) * ord.size(), cudaMemcpyHostToDevice, s), "order");
+  a.order = *d_order;
+  a.ntotal = (int64_t)ord.size();
+  a.ticket = hs0->d_ticket;
+  a.scratch = big->d_scratch;
+  a.scratch_stride = big->scratch_stride;
+  a.trunc_rows = std::max(big->L.max_trunc_rows, 1);
+  a.status = hs0->d_status;
+  a.flops = which == 0 ? hs0->d_flops : nullptr;
+  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  a.prof = which == 0 ? hs0->d_prof : nullptr;
+  if (a.ntotal == 0) return HLU_OK;
+  int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+  CKR(cudaMemcpyAsync(hs0->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
+  CKR(cudaMemsetAsync(hs0->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
+  int g = (int)std::min<int64_t>(hs0->grid, a.ntotal);
+  cudaError_t e = hs0->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
+  CKR(e, "executor launch");
+  // the order buffer must stay alive until the kernel has run
+  CKR(cudaStreamSynchronize(s), "sync");
+  return HLU_OK;
+}
+
 int read_status(hlu_handle* h, cudaStream_t s, int32_t* out4) {
-  CKR(cudaMemcpyAsync(out4, h->d_status, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, s), "status read");
+  CKR(cudaMemcpyAsync(out4, h->d_status, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s), "status read");
   CKR(cudaStreamSynchronize(s), "sync");
   if (out4[0] == 5) return fail(HLU_ERR_TIMEOUT, "device wait exceeded its limit at task " + std::to_string(out4[1]));
   if (out4[0] == 3) return fail(HLU_ERR_ZERO_PIVOT, "zero pivot in a diagonal leaf");
@@ -620,91 +714,100 @@ int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision) {
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = (int64_t)sms * 2;
-  return h->L.total * es + grid * scratch_stride_elems(h->L) * es + (int64_t)h->L.n_slots * 4 + h->L.piv_total * 4;
+  return h->L.total * es + grid * scratch_stride_elems(h->L, es) * es + (int64_t)h->L.n_slots * 4 + h->L.piv_total * 4;
 }
 
 static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit);
 int hlu_factor(hlu_handle* h, int32_t precision, void* stream) { return factor_impl(h, precision, stream, -1); }
+
+// allocation for `precision` (first time), rank/status/flop resets, A_H fill
+static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
+  const int es = esize(precision);
+  if (h->precision != precision) {
+    free_factor(h);
+    int dev = 0;
+    CKR(cudaGetDevice(&dev), "device");
+    int sms = 0;
+    CKR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sms");
+    int bps = precision == HLU_FP64 ? blocks_per_sm<double>() : blocks_per_sm<float>();
+    if (bps < 1) return fail(HLU_ERR_CUDA, "executor does not fit on an SM");
+    h->grid = sms * bps;
+    h->scratch_stride = scratch_stride_elems(h->L, es);
+    h->arena_elems = h->L.total;
+    CKR(cudaMalloc(&h->d_arena, (size_t)es * h->L.total), "arena");
+    CKR(cudaMalloc(&h->d_ranks, sizeof(int32_t) * std::max(h->L.n_slots, 1)), "ranks");
+    CKR(cudaMalloc(&h->d_piv, sizeof(int32_t) * std::max<int64_t>(h->L.piv_total, 1)), "piv");
+    CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
+    CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 8), "status");
+    CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
+    CKR(cudaMalloc(&h->d_ticket, sizeof(unsigned long long)), "ticket");
+    CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * (TK_NUM + 1) * 3), "prof");
+    h->precision = precision;
+  }
+  CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
+  int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+  CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
+  cudaError_t e;
+  if (precision == HLU_FP64)
+    e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
+                        h->sb->d_fill_lr, h->sb->n_fill_lr, (double*)h->d_arena, h->L.work_off, h->L.ident_off,
+                        h->L.ident_n, h->d_ranks, h->d_status, s);
+  else
+    e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
+                       h->sb->d_fill_lr, h->sb->n_fill_lr, (float*)h->d_arena, h->L.work_off, h->L.ident_off,
+                       h->L.ident_n, h->d_ranks, h->d_status, s);
+  CKR(e, "A_H fill");
+  int32_t stf[8];
+  int rc = read_status(h, s, stf);
+  if (rc) return rc;
+  CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
+  CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * (TK_NUM + 1) * 3, s), "prof");
+  return HLU_OK;
+}
+
+// statistics after the factorisation ran (status read from `status_of`)
+static int factor_finish(hlu_handle* h, hlu_handle* status_of, cudaStream_t s, float ms) {
+  int32_t stf[8];
+  int rc = read_status(status_of, s, stf);
+  h->info.factor_ms = ms;
+  h->info.rank_cap_hits = stf[2];
+  double fl = 0;
+  CKR(cudaMemcpy(&fl, status_of->d_flops, sizeof(double), cudaMemcpyDeviceToHost), "flops");
+  h->info.flops = fl;
+  std::vector<int32_t> rk(std::max(h->L.n_slots, 1));
+  CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
+  int64_t rsum = 0, nadm = 0;
+  int32_t rmax = 0;
+  for (size_t b = 0; b < h->sb->FB.size(); ++b)
+    if (h->sb->FB[b].kind == KIND_ADM) {
+      int32_t r = rk[h->L.slot[b]];
+      rmax = std::max(rmax, r);
+      rsum += r;
+      ++nadm;
+    }
+  const int es = esize(h->precision);
+  h->info.rank_max = rmax;
+  h->info.rank_mean = nadm ? (double)rsum / nadm : 0.0;
+  h->info.factor_bytes = h->L.factor_elems * es;
+  h->info.workspace_bytes = (h->L.total - h->L.factor_elems) * es + h->scratch_stride * h->grid * es;
+  return rc;
+}
 
 static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit) {
   try {
     if (!h) return fail(HLU_ERR_ARG, "null handle");
     if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
     cudaStream_t s = (cudaStream_t)stream;
-    const int es = esize(precision);
-    if (h->precision != precision) {
-      free_factor(h);
-      int dev = 0;
-      CKR(cudaGetDevice(&dev), "device");
-      int sms = 0;
-      CKR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sms");
-      int bps = precision == HLU_FP64 ? blocks_per_sm<double>() : blocks_per_sm<float>();
-      if (bps < 1) return fail(HLU_ERR_CUDA, "executor does not fit on an SM");
-      h->grid = sms * bps;
-      h->scratch_stride = scratch_stride_elems(h->L);
-      h->arena_elems = h->L.total;
-      CKR(cudaMalloc(&h->d_arena, (size_t)es * h->L.total), "arena");
-      CKR(cudaMalloc(&h->d_ranks, sizeof(int32_t) * std::max(h->L.n_slots, 1)), "ranks");
-      CKR(cudaMalloc(&h->d_piv, sizeof(int32_t) * std::max<int64_t>(h->L.piv_total, 1)), "piv");
-      CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
-      CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 4), "status");
-      CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
-      CKR(cudaMalloc(&h->d_ticket, sizeof(unsigned long long)), "ticket");
-      CKR(cudaMalloc(&h->d_arenas, sizeof(void*)), "ptrs");
-      CKR(cudaMalloc(&h->d_rankp, sizeof(int32_t*)), "ptrs");
-      CKR(cudaMalloc(&h->d_pivp, sizeof(int32_t*)), "ptrs");
-      CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * (TK_NUM + 1) * 3), "prof");
-      CKR(cudaMemcpy(h->d_arenas, &h->d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptrs");
-      CKR(cudaMemcpy(h->d_rankp, &h->d_ranks, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
-      CKR(cudaMemcpy(h->d_pivp, &h->d_piv, sizeof(int32_t*), cudaMemcpyHostToDevice), "ptrs");
-      h->precision = precision;
-    }
-    CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
-    int32_t st0[4] = {0, -1, 0, 0};
-    CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
-    cudaError_t e;
-    if (precision == HLU_FP64)
-      e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
-                          h->sb->d_fill_lr, h->sb->n_fill_lr, (double*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
-                          h->d_status, s);
-    else
-      e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, h->sb->d_fill_dense, h->sb->n_fill_dense, h->sb->dense_rows,
-                         h->sb->d_fill_lr, h->sb->n_fill_lr, (float*)h->d_arena, h->L.work_off, h->L.ident_off, h->L.ident_n, h->d_ranks,
-                         h->d_status, s);
-    CKR(e, "A_H fill");
-    int32_t stf[4];
-    int rc = read_status(h, s, stf);
+    int rc = factor_prepare(h, precision, s);
     if (rc) return rc;
-    CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
-    CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * (TK_NUM + 1) * 3, s), "prof");
     CKR(cudaEventRecord(h->ev0, s), "event");
     rc = exec_run(h, h->dF, h->grid, s, true, limit);
     if (rc) return rc;
     CKR(cudaEventRecord(h->ev1, s), "event");
-    rc = read_status(h, s, stf);
+    CKR(cudaEventSynchronize(h->ev1), "sync");
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    h->info.factor_ms = ms;
-    h->info.rank_cap_hits = stf[2];
-    double fl = 0;
-    CKR(cudaMemcpy(&fl, h->d_flops, sizeof(double), cudaMemcpyDeviceToHost), "flops");
-    h->info.flops = fl;
-    std::vector<int32_t> rk(std::max(h->L.n_slots, 1));
-    CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
-    int64_t rsum = 0, nadm = 0;
-    int32_t rmax = 0;
-    for (size_t b = 0; b < h->sb->FB.size(); ++b)
-      if (h->sb->FB[b].kind == KIND_ADM) {
-        int32_t r = rk[h->L.slot[b]];
-        rmax = std::max(rmax, r);
-        rsum += r;
-        ++nadm;
-      }
-    h->info.rank_max = rmax;
-    h->info.rank_mean = nadm ? (double)rsum / nadm : 0.0;
-    h->info.factor_bytes = h->L.factor_elems * es;
-    h->info.workspace_bytes = (h->L.total - h->L.factor_elems) * es + h->scratch_stride * h->grid * es;
-    return rc;
+    return factor_finish(h, h, s, ms);
   } catch (const std::exception& ex) {
     return fail(HLU_ERR_CUDA, ex.what());
   }
@@ -825,22 +928,75 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
 }
 
 int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream) {
-  if (!hs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
-  for (int32_t i = 0; i < count; ++i) {
-    int rc = hlu_factor(hs[i], precision, stream);
+  try {
+    if (!hs || count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "bad argument");
+    if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t i = 0; i < count; ++i) {
+      if (!hs[i]) return fail(HLU_ERR_ARG, "null handle");
+      int rc = factor_prepare(hs[i], precision, s);
+      if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    CKR(cudaEventRecord(hs[0]->ev0, s), "event");
+    int rc = exec_run_batch(hs, count, 0, s, nullptr, &g_batch_order, &g_batch_order_len);
     if (rc) return rc;
+    CKR(cudaEventRecord(hs[0]->ev1, s), "event");
+    CKR(cudaEventSynchronize(hs[0]->ev1), "sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, hs[0]->ev0, hs[0]->ev1);
+    int worst = HLU_OK;
+    for (int32_t i = 0; i < count; ++i) {
+      rc = factor_finish(hs[i], hs[0], s, ms);
+      if (rc) worst = rc;
+    }
+    return worst;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
   }
-  return HLU_OK;
 }
 
 int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b, double* const* x,
                     const int32_t* nrhs, void* stream) {
-  if (!hs || !b || !x || !nrhs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
-  for (int32_t i = 0; i < count; ++i) {
-    int rc = hlu_solve(hs[i], b[i], x[i], nrhs[i], hs[i] ? hs[i]->A.N : 0, stream);
-    if (rc) return rc;
+  try {
+    if (!hs || !b || !x || !nrhs || count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t i = 0; i < count; ++i) {
+      hlu_handle* h = hs[i];
+      if (!h || !b[i] || !x[i] || nrhs[i] < 1) return fail(HLU_ERR_ARG, "bad argument");
+      if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+      if (h->precision != hs[0]->precision) return fail(HLU_ERR_ARG, "mixed precisions in a batch");
+      if (nrhs[i] > h->L.nrhs_max) return fail(HLU_ERR_ARG, "nrhs above the batched limit (16)");
+    }
+    for (int32_t i = 0; i < count; ++i) {
+      hlu_handle* h = hs[i];
+      CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs[i], s), "nrhs slot");
+      if (h->precision == HLU_FP64)
+        CKR(gather_cast<double>(h->A.N, h->d_perm, b[i], h->A.N, (double*)h->d_arena + h->L.work_off, nrhs[i], s),
+            "gather");
+      else
+        CKR(gather_cast<float>(h->A.N, h->d_perm, b[i], h->A.N, (float*)h->d_arena + h->L.work_off, nrhs[i], s),
+            "gather");
+    }
+    {
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      int rc = exec_run_batch(hs, count, 1, s, nullptr, &g_batch_order, &g_batch_order_len);
+      if (rc) return rc;
+    }
+    for (int32_t i = 0; i < count; ++i) {
+      hlu_handle* h = hs[i];
+      if (h->precision == HLU_FP64)
+        CKR(scatter_cast<double>(h->A.N, h->d_perm, (double*)h->d_arena + h->L.work_off, x[i], h->A.N, nrhs[i], s),
+            "scatter");
+      else
+        CKR(scatter_cast<float>(h->A.N, h->d_perm, (float*)h->d_arena + h->L.work_off, x[i], h->A.N, nrhs[i], s),
+            "scatter");
+    }
+    int32_t st[8];
+    return read_status(hs[0], s, st);
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
   }
-  return HLU_OK;
 }
 
 }  // extern "C"
@@ -863,7 +1019,7 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   h.precision = HLU_FP32;
   DevSched ds;
   CKR(ds.load(S), "upload");
-  CKR(cudaMalloc(&h.d_status, sizeof(int32_t) * 4), "alloc");
+  CKR(cudaMalloc(&h.d_status, sizeof(int32_t) * 8), "alloc");
   CKR(cudaMalloc(&h.d_ticket, sizeof(unsigned long long)), "alloc");
   // valid (unused) per-problem pointers: the two tasks do no work
   CKR(cudaMalloc(&h.d_arena, 256), "alloc");
@@ -877,7 +1033,7 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   g_wait_limit_ms = limit_ms;
   int rc = exec_run(&h, ds, 1, nullptr, false);
   g_wait_limit_ms = saved;
-  int32_t st[4] = {0, 0, 0, 0};
+  int32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (!rc) rc = read_status(&h, nullptr, st);
   status_out[0] = st[0];
   status_out[1] = st[1];

@@ -598,23 +598,27 @@ __device__ void apply_q_warp(const T* S, int m, int tmax, const T* tau, T* O, in
 // stacked factors up to this many rows use the warp-level QR and apply
 constexpr int kWarpQrRows = 768;
 constexpr int kStackCols = kTruncStack;
+// a stack wider than this is compressed before the next piece is added
+// (Jacobi cost grows with the cube of the width); rank cap 32 + a 64-wide
+// piece still fit the stack
+constexpr int kCompressAt = 48;
 
-// Truncated SVD of the stacked factors SX (m x W) and SY (n x W): QR of both,
-// one-sided Jacobi SVD of the core R_x R_y^T, keep s_i > eps s_1 (at most
-// cap); X <- Q_x U_r S_r and Y <- Q_y V_r are written to OX (ld ox) and OY
-// (ld oy).  Returns r (the same in every thread).
-template <class T>
-__device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int cap, T* OX, int64_t ox, T* OY,
-                              int64_t oy, char* smem) {
+// Truncated SVD of the stacked factors SX (m x W) and SY (n x W) in compute
+// type TC: QR of both, one-sided Jacobi SVD of the core R_x R_y^T, keep
+// s_i > eps s_1 (at most cap); X <- Q_x U_r S_r and Y <- Q_y V_r are written
+// to OX (ld ox) and OY (ld oy).  Workspace: tauX, tauY, sv (kStackCols each)
+// and G, V (kStackCols^2 each), in shared or global memory.  Returns r (the
+// same in every thread); *fro receives ||X Y^T||_F.
+template <class TC>
+__device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, double eps, TC* tauX, TC* tauY,
+                             TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
+                             double* flops, double* fro) {
   __shared__ int s_rot;
   __shared__ int s_r;
   __shared__ int s_ord[kStackCols];
-  __shared__ T s_red[NT / 32];
-  T* tauX = reinterpret_cast<T*>(smem);
-  T* tauY = tauX + kStackCols;
-  T* sv = tauY + kStackCols;
-  T* G = sv + kStackCols;              // p x q
-  T* V = G + kStackCols * kStackCols;  // q x q
+  __shared__ TC s_red[NT / 32];
+  __shared__ double s_fro;
+  __shared__ float s_off, s_prev;
   const bool small = max(m, n) <= kWarpQrRows;
   if (small) {
     const int wq = threadIdx.x >> 5;
@@ -626,19 +630,28 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
     house_qr(SY, n, W, tauY, s_red);
   }
   const int p = min(m, W), q = min(n, W);
+  // the core is accumulated in FP64: the target and its updates cancel inside
+  // this sum, and FP32 accumulation there costs the truncation its accuracy
   for (int idx = threadIdx.x; idx < p * q; idx += NT) {
     int i = idx % p, j = idx / p;
-    T acc = 0;
-    for (int l = max(i, j); l < W; ++l) acc += SX[i + (int64_t)l * m] * SY[j + (int64_t)l * n];
-    G[i + j * p] = acc;
+    double acc = 0;
+    for (int l = max(i, j); l < W; ++l) acc += (double)SX[i + (int64_t)l * m] * (double)SY[j + (int64_t)l * n];
+    G[i + j * p] = (TC)acc;
   }
-  for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? T(1) : T(0);
+  for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? TC(1) : TC(0);
   __syncthreads();
-  const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
+  // stop when every pair is orthogonal to tol, or when a sweep no longer
+  // reduces the largest off-diagonal measure while it is already small (the
+  // rounding floor)
+  const TC tol = sizeof(TC) == 4 ? TC(1e-6) : TC(1e-14);
   const int qq = q + (q & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int sweep = 0; sweep < 30 && qq > 1; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
+  if (threadIdx.x == 0) s_prev = 3.0e38f;
+  for (int sweep = 0; sweep < 20 && qq > 1; ++sweep) {
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      s_off = 0.0f;
+    }
     __syncthreads();
     for (int rd = 0; rd < qq - 1; ++rd) {
       for (int k = warp; k < qq / 2; k += NT / 32) {
@@ -647,9 +660,9 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
         int pb = kb == 0 ? 0 : ((kb - 1 + rd) % (qq - 1)) + 1;
         int a = min(pa, pb), b = max(pa, pb);
         if (b >= q) continue;
-        T al = 0, be = 0, ga = 0;
+        TC al = 0, be = 0, ga = 0;
         for (int i = lane; i < p; i += 32) {
-          T x = G[i + a * p], y = G[i + b * p];
+          TC x = G[i + a * p], y = G[i + b * p];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -657,17 +670,20 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga == T(0) || fabs(ga) <= tol * sqrt(al * be)) continue;
-        T zeta = (be - al) / (T(2) * ga);
-        T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
+        if (ga == TC(0)) continue;
+        const TC ratio = fabs(ga) / sqrt(al * be);
+        if (lane == 0) atomicMax(reinterpret_cast<int*>(&s_off), __float_as_int((float)ratio));
+        if (ratio <= tol) continue;
+        TC zeta = (be - al) / (TC(2) * ga);
+        TC tt = (zeta >= TC(0) ? TC(1) : TC(-1)) / (fabs(zeta) + sqrt(TC(1) + zeta * zeta));
+        TC cs = TC(1) / sqrt(TC(1) + tt * tt), sn = cs * tt;
         for (int i = lane; i < p; i += 32) {
-          T x = G[i + a * p], y = G[i + b * p];
+          TC x = G[i + a * p], y = G[i + b * p];
           G[i + a * p] = cs * x - sn * y;
           G[i + b * p] = sn * x + cs * y;
         }
         for (int i = lane; i < q; i += 32) {
-          T x = V[i + a * q], y = V[i + b * q];
+          TC x = V[i + a * q], y = V[i + b * q];
           V[i + a * q] = cs * x - sn * y;
           V[i + b * q] = sn * x + cs * y;
         }
@@ -676,17 +692,26 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
       __syncthreads();
     }
     if (!s_rot) break;
+    const bool stalled = sweep >= 2 && s_off < 100.0f * (float)tol && s_off > 0.25f * s_prev;
+    __syncthreads();
+    if (threadIdx.x == 0) s_prev = s_off;
+    if (stalled) break;
     __syncthreads();
   }
   for (int j = warp; j < q; j += NT / 32) {
-    T acc = 0;
+    TC acc = 0;
     for (int i = lane; i < p; i += 32) acc += G[i + j * p] * G[i + j * p];
     acc = warp_sum(acc);
     if (lane == 0) sv[j] = sqrt(acc);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int j = 0; j < q; ++j) s_ord[j] = j;
+    double f2 = 0;
+    for (int j = 0; j < q; ++j) {
+      s_ord[j] = j;
+      f2 += (double)sv[j] * (double)sv[j];
+    }
+    s_fro = sqrt(f2);
     for (int j = 1; j < q; ++j) {  // stable insertion sort, descending
       int x = s_ord[j], i = j - 1;
       while (i >= 0 && sv[s_ord[i]] < sv[x]) {
@@ -695,26 +720,27 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
       }
       s_ord[i + 1] = x;
     }
-    T smax = q ? sv[s_ord[0]] : T(0);
+    TC smax = q ? sv[s_ord[0]] : TC(0);
     int r = 0;
-    if (smax > T(0))
-      while (r < q && sv[s_ord[r]] > T(c.eps) * smax) ++r;
+    if (smax > TC(0))
+      while (r < q && sv[s_ord[r]] > TC(eps) * smax) ++r;
     if (r > cap) {
       r = cap;
-      atomicAdd(c.status + 2, 1);
+      atomicAdd(cap_hits, 1);
     }
     s_r = r;
-    c.flops += 2.0 * (m + n) * W * W + 21.0 * (double)q * q * q + 2.0 * (m + n) * W * r;
+    *flops += 2.0 * (m + n) * W * W + 21.0 * (double)q * q * q + 2.0 * (m + n) * W * r;
   }
   __syncthreads();
   const int r = s_r;
+  *fro = s_fro;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) {
     int i = (int)(idx % m), j = (int)(idx / m);
-    __stcg(OX + i + (int64_t)j * ox, i < p ? G[i + s_ord[j] * p] : T(0));
+    __stcg(OX + i + (int64_t)j * ox, i < p ? G[i + s_ord[j] * p] : TC(0));
   }
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) {
     int i = (int)(idx % n), j = (int)(idx / n);
-    __stcg(OY + i + (int64_t)j * oy, i < q ? V[i + s_ord[j] * q] : T(0));
+    __stcg(OY + i + (int64_t)j * oy, i < q ? V[i + s_ord[j] * q] : TC(0));
   }
   __syncthreads();
   if (small) {
@@ -728,64 +754,107 @@ __device__ int trunc_compress(Ctx<T>& c, T* SX, T* SY, int m, int n, int W, int 
   return r;
 }
 
-// (a, b) <- truncation of sum_pieces sign X Y^T.  Pieces are stacked in a
-// kStackCols-wide buffer; when the next piece does not fit, the stack is
-// compressed in place first, so any number of pieces is accepted.
-template <class T>
-__device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
+// Stacks the pieces in compute type TC (compressing whenever the stack would
+// pass kCompressAt columns) and leaves the final factors in OX (m x r) and
+// OY (n x r) of the scratch.  Returns r; *ratio receives the largest
+// ||X||_F ||Y||_F / ||X Y^T||_F over the compressions (how much cancellation
+// the arithmetic had to survive).
+template <class TC, class T>
+__device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC* OY, TC* tauX, TC* tauY, TC* sv,
+                           TC* G, TC* V, double* ratio) {
   const int m = t.a.rows, n = t.b.rows;
-  T* SX = c.scratch;
-  T* SY = SX + c.rows_max * kStackCols;
-  T* OX = SY + c.rows_max * kStackCols;
-  T* OY = OX + c.rows_max * 32;
-  if (m == 0 || n == 0) {
-    if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
-    return;
-  }
+  __shared__ double s_nx, s_ny;
+  __shared__ TC s_rx[NT / 32];
+  double worst = 0;
   int W = 0;
+  int32_t* cap_hits = c.status + 2;
+  auto stack_norm = [&](int w_) -> double {
+    TC px = 0, py = 0;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * w_; idx += NT) px += SX[idx] * SX[idx];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * w_; idx += NT) py += SY[idx] * SY[idx];
+    TC sx = block_sum(px, s_rx);
+    TC sy = block_sum(py, s_rx);
+    return sqrt((double)sx) * sqrt((double)sy);
+  };
   for (int q = 0; q < t.list_count; ++q) {
     const Piece& P = c.pieces[t.list_begin + q];
     const int w = ncols(c, P.X);
     if (w == 0) continue;
-    if (W + w > kStackCols) {
-      const int r = trunc_compress(c, SX, SY, m, n, W, t.cap, OX, m, OY, n, smem);
+    if (W > 0 && W + w > kCompressAt) {
+      const double in = stack_norm(W);
+      double fro = 0;
+      const int r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits,
+                                  &c.flops, &fro);
+      if (fro > 0) worst = fmax(worst, in / fro);
       for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) SX[idx] = __ldcg(OX + idx);
       for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) SY[idx] = __ldcg(OY + idx);
       W = r;
       __syncthreads();
     }
-    const T sg = T(P.sign);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)m * w; idx += NT) SX[(int64_t)W * m + idx] = T(0);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)n * w; idx += NT) SY[(int64_t)W * n + idx] = T(0);
+    const TC sg = TC(P.sign);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * w; idx += NT) SX[(int64_t)W * m + idx] = TC(0);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * w; idx += NT) SY[(int64_t)W * n + idx] = TC(0);
     __syncthreads();
     for (int64_t idx = threadIdx.x; idx < (int64_t)P.X.rows * w; idx += NT) {
       int i = (int)(idx % P.X.rows), j = (int)(idx / P.X.rows);
-      SX[(P.xoff + i) + (int64_t)(W + j) * m] = sg * ldv(c, P.X, i, j);
+      SX[(P.xoff + i) + (int64_t)(W + j) * m] = sg * TC(ldv(c, P.X, i, j));
     }
     for (int64_t idx = threadIdx.x; idx < (int64_t)P.Y.rows * w; idx += NT) {
       int i = (int)(idx % P.Y.rows), j = (int)(idx / P.Y.rows);
-      SY[(P.yoff + i) + (int64_t)(W + j) * n] = ldv(c, P.Y, i, j);
+      SY[(P.yoff + i) + (int64_t)(W + j) * n] = TC(ldv(c, P.Y, i, j));
     }
     W += w;
     __syncthreads();
   }
   int r = 0;
-  if (W > 0) r = trunc_compress(c, SX, SY, m, n, W, t.cap, c.arena + t.a.off, t.a.cs, c.arena + t.b.off, t.b.cs, smem);
+  if (W > 0) {
+    const double in = stack_norm(W);
+    double fro = 0;
+    r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits, &c.flops, &fro);
+    if (fro > 0) worst = fmax(worst, in / fro);
+  }
+  *ratio = worst;
+  (void)s_nx;
+  (void)s_ny;
+  return r;
+}
+
+// (a, b) <- truncation of sum_pieces sign X Y^T (stack, compress, store).
+template <class T>
+__device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
+  const int m = t.a.rows, n = t.b.rows;
+  if (m == 0 || n == 0) {
+    if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
+    return;
+  }
+  const int64_t R = c.rows_max;
+  T* SX = c.scratch;
+  T* SY = SX + R * kStackCols;
+  T* OX = SY + R * kStackCols;
+  T* OY = OX + R * 32;
+  T* tauX = reinterpret_cast<T*>(smem);
+  T* tauY = tauX + kStackCols;
+  T* sv = tauY + kStackCols;
+  T* G = sv + kStackCols;
+  T* V = G + kStackCols * kStackCols;
+  double ratio = 0;
+  const int r = trunc_stack<T, T>(c, t, SX, SY, OX, OY, tauX, tauY, sv, G, V, &ratio);
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) stv(c, t.a, idx % m, idx / m, __ldcg(OX + idx));
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) stv(c, t.b, idx % n, idx / n, __ldcg(OY + idx));
+  __syncthreads();
   if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
 }
 
 // ---------------------------------------------------------------- executor
 template <class T>
-__global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
+__global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int64_t s_task;
   __shared__ int s_skip;
+  __shared__ int s_prob;
   Ctx<T> c;
-  c.terms = a.terms;
-  c.pieces = a.pieces;
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
   c.rows_max = a.trunc_rows;
-  c.eps = a.eps;
   c.status = a.status;
   c.flops = 0;
   __shared__ unsigned long long s_prof[TK_NUM + 1][3];  // count, wait cycles, run cycles
@@ -793,22 +862,33 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
   long long t_begin = 0, t_waited = 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      s_task = (int64_t)atomicAdd(a.ticket, 1ULL);
+      const int64_t tk = (int64_t)atomicAdd(a.ticket, 1ULL);
+      if (tk >= a.ntotal) {
+        s_task = -1;
+      } else if (a.order) {
+        const int64_t code = a.order[tk];
+        s_prob = (int)(code >> 40);
+        s_task = code & ((int64_t(1) << 40) - 1);
+      } else {
+        s_prob = 0;
+        s_task = tk;
+      }
       t_begin = clock64();
     }
     __syncthreads();
     const int64_t ti = s_task;
-    if (ti >= a.ntasks) break;
+    if (ti < 0) break;
+    const ProbSched& P = a.probs[s_prob];
     // wait for the predecessors (lanes of warp 0 in parallel, bounded)
     if (threadIdx.x < 32) {
       int bad = 0;
-      const int64_t e0 = a.pred_ptr[ti], e1 = a.pred_ptr[ti + 1];
+      const int64_t e0 = P.pred_ptr[ti], e1 = P.pred_ptr[ti + 1];
       for (int64_t e = e0 + threadIdx.x; e < e1; e += 32) {
-        const int32_t* flag = a.done + a.pred_idx[e];
-        if (ld_acquire(flag) == a.epoch) continue;
+        const int32_t* flag = P.done + P.pred_idx[e];
+        if (ld_acquire(flag) == P.epoch) continue;
         const uint64_t t0 = gtimer();
         for (;;) {
-          if (ld_acquire(flag) == a.epoch) break;
+          if (ld_acquire(flag) == P.epoch) break;
           if (*((volatile int32_t*)a.status + 3)) {
             bad = 1;
             break;
@@ -829,12 +909,15 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) t_waited = clock64();
-    const int ttype = a.tasks[ti].type;
+    const int ttype = P.tasks[ti].type;
     if (!s_skip && ttype >= 0 && ttype < TK_NUM) {
-      const Task t = a.tasks[ti];
-      c.arena = reinterpret_cast<T*>(a.arenas[t.prob]);
-      c.ranks = a.ranks[t.prob];
-      c.piv = a.pivs[t.prob];
+      const Task t = P.tasks[ti];
+      c.arena = reinterpret_cast<T*>(P.arena);
+      c.ranks = P.ranks;
+      c.piv = P.piv;
+      c.terms = P.terms;
+      c.pieces = P.pieces;
+      c.eps = P.eps;
       switch (t.type) {
         case TK_GETRF: task_getrf(c, t, smem); break;
         case TK_TRSM_L:
@@ -851,7 +934,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(ExecArgs a) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      st_release(a.done + ti, a.epoch);
+      st_release(P.done + ti, P.epoch);
       if (a.prof) {
         const int k = (ttype >= 0 && ttype < TK_NUM) ? ttype : TK_NUM;
         long long t_end = clock64();

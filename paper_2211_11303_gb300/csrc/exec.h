@@ -8,27 +8,39 @@
 
 namespace hlu {
 
-struct ExecArgs {
+// One problem's schedule and data as seen by the executor.
+struct ProbSched {
   const Task* tasks;
-  int64_t ntasks;
   const Term* terms;
   const Piece* pieces;
   const int64_t* pred_ptr;  // ntasks + 1
   const int32_t* pred_idx;
   int32_t* done;            // completion epoch per task
-  int32_t epoch;            // value published on completion in this launch
-  unsigned long long* ticket;  // next task index (zeroed before the launch)
-  void* const* arenas;      // per problem (Task::prob)
-  int32_t* const* ranks;
-  int32_t* const* pivs;
-  void* scratch;            // per-CTA scratch, scratch_stride elements each
-  int64_t scratch_stride;
-  int64_t trunc_rows;       // rows of the truncation stacks in the scratch
+  void* arena;
+  int32_t* ranks;
+  int32_t* piv;
   double eps;
-  int32_t* status;          // [0] status code, [1] failing task, [2] rank-cap hits, [3] abort
-  double* flops;            // accumulated algorithmic flops (may be null)
+  int64_t ntasks;
+  int32_t epoch;            // value published on completion in this launch
+  int32_t pad;
+};
+constexpr int kMaxBatch = 64;  // problems in one launch
+
+struct ExecArgs {
+  ProbSched probs[kMaxBatch];
+  int32_t nprobs;
+  // ticket -> (problem << 40 | task) for batched launches; null: problem 0,
+  // task = ticket.  Within a problem the order is increasing.
+  const int64_t* order;
+  int64_t ntotal;               // tickets handed out in this launch
+  unsigned long long* ticket;   // next ticket (zeroed before the launch)
+  void* scratch;                // per-CTA scratch, scratch_stride elements each
+  int64_t scratch_stride;
+  int64_t trunc_rows;           // rows of the truncation stacks in the scratch
+  int32_t* status;              // [0] status code, [1] failing task, [2] rank-cap hits, [3] abort
+  double* flops;                // accumulated algorithmic flops (may be null)
   unsigned long long wait_limit_ns;
-  unsigned long long* prof;  // optional [(TK_NUM + 1) x 3]: tasks, wait cycles, run cycles per kind
+  unsigned long long* prof;     // optional [(TK_NUM + 1) x 3]: tasks, wait cycles, run cycles per kind
 };
 
 size_t exec_smem_bytes(int elem_size);
@@ -40,6 +52,15 @@ cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
 constexpr int kExecThreads = 256;
 constexpr int kTruncStack = 96;  // columns of a truncation stack (>= rank cap + widest piece)
 // per-CTA scratch: two stacks (kTruncStack wide) and two outputs (32 wide)
-inline int64_t trunc_scratch_elems(int64_t rows) { return rows * (2 * kTruncStack + 2 * 32); }
+#ifdef __CUDACC__
+#define HLU_HD __host__ __device__
+#else
+#define HLU_HD
+#endif
+HLU_HD inline int64_t trunc_scratch_elems(int64_t rows) { return rows * (2 * kTruncStack + 2 * 32); }
+inline int64_t trunc_scratch_bytes(int64_t rows, int elem_size) {
+  int64_t b = trunc_scratch_elems(rows) * elem_size;
+  return (b + 255) & ~int64_t(255);
+}
 
 }  // namespace hlu

@@ -199,8 +199,10 @@ void h_jacobi(std::vector<T>& G, int p, int q, std::vector<T>& V) {
   V.assign((size_t)q * q, T(0));
   for (int i = 0; i < q; ++i) V[i + (size_t)i * q] = 1;
   const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  double prev = 3e38;
+  for (int sweep = 0; sweep < 20; ++sweep) {
     bool rot = false;
+    double off = 0;
     for (int a = 0; a < q - 1; ++a)
       for (int b = a + 1; b < q; ++b) {
         T al = 0, be = 0, ga = 0;
@@ -210,7 +212,10 @@ void h_jacobi(std::vector<T>& G, int p, int q, std::vector<T>& V) {
           be += y * y;
           ga += x * y;
         }
-        if (ga == T(0) || std::fabs(ga) <= tol * std::sqrt(al * be)) continue;
+        if (ga == T(0)) continue;
+        T ratio = std::fabs(ga) / std::sqrt(al * be);
+        off = std::max(off, (double)ratio);
+        if (ratio <= tol) continue;
         rot = true;
         T zeta = (be - al) / (2 * ga);
         T tt = (zeta >= 0 ? T(1) : T(-1)) / (std::fabs(zeta) + std::sqrt(T(1) + zeta * zeta));
@@ -227,14 +232,16 @@ void h_jacobi(std::vector<T>& G, int p, int q, std::vector<T>& V) {
         }
       }
     if (!rot) break;
+    if (sweep >= 2 && off < 100.0 * (double)tol && off > 0.25 * prev) break;
+    prev = off;
   }
 }
 
 // Truncated SVD of X Y^T (SX: m x W, SY: n x W, column-major): returns the
 // new factors (m x r, n x r) with s_i > eps s_1 kept, at most cap.
 template <class T>
-int h_compress(HostCtx<T>& c, std::vector<T> SX, std::vector<T> SY, int m, int n, int W, int cap,
-               std::vector<T>& BX, std::vector<T>& BY) {
+int h_compress(double eps, int32_t* cap_hits, std::vector<T> SX, std::vector<T> SY, int m, int n, int W, int cap,
+               std::vector<T>& BX, std::vector<T>& BY, double* fro) {
   std::vector<T> tx, ty;
   h_house(SX, m, W, tx);
   h_house(SY, n, W, ty);
@@ -242,28 +249,31 @@ int h_compress(HostCtx<T>& c, std::vector<T> SX, std::vector<T> SY, int m, int n
   std::vector<T> G((size_t)p * q, T(0));
   for (int i = 0; i < p; ++i)
     for (int j = 0; j < q; ++j) {
-      T s = 0;
-      for (int l = std::max(i, j); l < W; ++l) s += SX[i + (size_t)l * m] * SY[j + (size_t)l * n];
-      G[i + (size_t)j * p] = s;
+      double s = 0;  // FP64 accumulation: cancellation between target and update
+      for (int l = std::max(i, j); l < W; ++l) s += (double)SX[i + (size_t)l * m] * (double)SY[j + (size_t)l * n];
+      G[i + (size_t)j * p] = (T)s;
     }
   std::vector<T> V;
   h_jacobi(G, p, q, V);
   std::vector<T> sv(q);
+  double f2 = 0;
   for (int j = 0; j < q; ++j) {
     T s = 0;
     for (int i = 0; i < p; ++i) s += G[i + (size_t)j * p] * G[i + (size_t)j * p];
     sv[j] = std::sqrt(s);
+    f2 += (double)sv[j] * (double)sv[j];
   }
+  *fro = std::sqrt(f2);
   std::vector<int> ord(q);
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sv[a] > sv[b]; });
   T smax = q ? sv[ord[0]] : T(0);
   int r = 0;
   if (smax > T(0))
-    while (r < q && sv[ord[r]] > T(c.eps) * smax) ++r;
+    while (r < q && sv[ord[r]] > T(eps) * smax) ++r;
   if (r > cap) {
     r = cap;
-    c.cap_hits++;
+    (*cap_hits)++;
   }
   BX.assign((size_t)m * r, T(0));
   BY.assign((size_t)n * r, T(0));
@@ -276,9 +286,54 @@ int h_compress(HostCtx<T>& c, std::vector<T> SX, std::vector<T> SY, int m, int n
   return r;
 }
 
-// pieces are stacked kTruncStack columns at a time, compressing when the next
-// piece does not fit (the device executor's order of operations)
-constexpr int kHostStack = 96;
+// pieces are stacked, compressing whenever the stack would pass 48 columns
+// (the device executor's order of operations); *ratio receives the largest
+// ||X|| ||Y|| / ||X Y^T|| over the compressions
+constexpr int kHostCompressAt = 48;
+template <class TC, class T>
+int h_trunc_stack(HostCtx<T>& c, const Task& t, std::vector<TC>& SX, std::vector<TC>& SY, double* ratio) {
+  const int m = t.a.rows, n = t.b.rows;
+  int W = 0;
+  double worst = 0;
+  auto norms = [&](int w_) {
+    double nx = 0, ny = 0;
+    for (size_t i = 0; i < (size_t)m * w_; ++i) nx += (double)SX[i] * SX[i];
+    for (size_t i = 0; i < (size_t)n * w_; ++i) ny += (double)SY[i] * SY[i];
+    return std::sqrt(nx) * std::sqrt(ny);
+  };
+  for (int q = 0; q < t.list_count; ++q) {
+    const Piece& P = c.pieces[t.list_begin + q];
+    int w = ncols(c, P.X);
+    if (w == 0) continue;
+    if (W > 0 && W + w > kHostCompressAt) {
+      std::vector<TC> BX, BY;
+      double in = norms(W), fro = 0;
+      W = h_compress(c.eps, &c.cap_hits, SX, SY, m, n, W, t.cap, BX, BY, &fro);
+      if (fro > 0) worst = std::max(worst, in / fro);
+      SX = BX;
+      SY = BY;
+    }
+    SX.resize((size_t)m * (W + w), TC(0));
+    SY.resize((size_t)n * (W + w), TC(0));
+    for (int j = 0; j < w; ++j) {
+      for (int i = 0; i < P.X.rows; ++i) SX[(P.xoff + i) + (size_t)(W + j) * m] = TC(P.sign) * TC(at(c, P.X, i, j));
+      for (int i = 0; i < P.Y.rows; ++i) SY[(P.yoff + i) + (size_t)(W + j) * n] = TC(at(c, P.Y, i, j));
+    }
+    W += w;
+  }
+  int r = 0;
+  if (W > 0) {
+    std::vector<TC> BX, BY;
+    double in = norms(W), fro = 0;
+    r = h_compress(c.eps, &c.cap_hits, SX, SY, m, n, W, t.cap, BX, BY, &fro);
+    if (fro > 0) worst = std::max(worst, in / fro);
+    SX = BX;
+    SY = BY;
+  }
+  *ratio = worst;
+  return r;
+}
+
 template <class T>
 void h_trunc(HostCtx<T>& c, const Task& t) {
   int m = t.a.rows, n = t.b.rows;
@@ -286,34 +341,12 @@ void h_trunc(HostCtx<T>& c, const Task& t) {
     c.ranks[t.out_slot] = 0;
     return;
   }
-  std::vector<T> SX, SY;  // column-major stacks
-  int W = 0;
-  for (int q = 0; q < t.list_count; ++q) {
-    const Piece& P = c.pieces[t.list_begin + q];
-    int w = ncols(c, P.X);
-    if (w == 0) continue;
-    if (W + w > kHostStack) {
-      std::vector<T> BX, BY;
-      W = h_compress(c, SX, SY, m, n, W, t.cap, BX, BY);
-      SX = BX;
-      SY = BY;
-    }
-    SX.resize((size_t)m * (W + w), T(0));
-    SY.resize((size_t)n * (W + w), T(0));
-    for (int j = 0; j < w; ++j) {
-      for (int i = 0; i < P.X.rows; ++i) SX[(P.xoff + i) + (size_t)(W + j) * m] = T(P.sign) * at(c, P.X, i, j);
-      for (int i = 0; i < P.Y.rows; ++i) SY[(P.yoff + i) + (size_t)(W + j) * n] = at(c, P.Y, i, j);
-    }
-    W += w;
-  }
-  int r = 0;
-  if (W > 0) {
-    std::vector<T> BX, BY;
-    r = h_compress(c, SX, SY, m, n, W, t.cap, BX, BY);
-    for (int j = 0; j < r; ++j) {
-      for (int i = 0; i < m; ++i) at(c, t.a, i, j) = BX[i + (size_t)j * m];
-      for (int i = 0; i < n; ++i) at(c, t.b, i, j) = BY[i + (size_t)j * n];
-    }
+  std::vector<T> SX, SY;
+  double ratio = 0;
+  int r = h_trunc_stack<T, T>(c, t, SX, SY, &ratio);
+  for (int j = 0; j < r; ++j) {
+    for (int i = 0; i < m; ++i) at(c, t.a, i, j) = SX[i + (size_t)j * m];
+    for (int i = 0; i < n; ++i) at(c, t.b, i, j) = SY[i + (size_t)j * n];
   }
   c.ranks[t.out_slot] = r;
 }

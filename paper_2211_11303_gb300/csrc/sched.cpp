@@ -963,7 +963,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   }
   {
     Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
-    s.solve_tiles(nrhs_max);
+    s.solve_all(nrhs_max);
     st.temp_elems += s.temp_elems_;
   }
   factor.n_edges = (int64_t)factor.pred_idx.size();

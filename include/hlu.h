@@ -184,6 +184,26 @@ int gmres_solve(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t
                 int32_t restart, double tol, int32_t maxit, int32_t flexible, hlu_stats* stats,
                 void* stream);
 
+/* Continuous batching of GMRES solves (serving).  A hlu_gmres state holds
+ * one request's restarted flexible GMRES (same method as gmres_solve; at most
+ * 16 columns).  hlu_gmres_step_batch advances every unfinished state of the
+ * list by one inner step (a new cycle starts with the true residual, as in
+ * gmres_solve); the preconditioner applications of all states run in ONE
+ * persistent launch (states sharing a factor share its work vector, up to 16
+ * columns per launch).  States may join or leave between steps; a state's
+ * result does not depend on which states it was batched with.
+ * hlu_gmres_begin: x = 0, column norms of b; synchronous.  b, x stay owned by
+ * the caller and must stay valid until hlu_gmres_end.
+ * hlu_gmres_status: *done = 1 once finished; stats as in gmres_solve; returns
+ * HLU_ERR_NOT_CONVERGED for a finished state that missed tol.
+ * All calls on one stream; step_batch is synchronous. */
+typedef struct hlu_gmres hlu_gmres;
+int hlu_gmres_begin(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                    int32_t restart, double tol, int32_t maxit, void* stream, hlu_gmres** out);
+int hlu_gmres_step_batch(hlu_gmres* const* states, int32_t count, void* stream);
+int hlu_gmres_status(const hlu_gmres* g, int32_t* done, hlu_stats* stats);
+void hlu_gmres_end(hlu_gmres* g);
+
 /* hlu_richardson - Algorithm 1 steps III-IV: r = b - A x, err = ||r||/||b||,
  * x <- x + U^-1 (L^-1 r), stop when err < tol or after maxit; then
  * error = ||A x - b||_2 into stats->abs_res_max.  Same vector conventions as

@@ -1082,3 +1082,310 @@ extern "C" int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out
   CKR(cudaMemcpy(out, h->dF.tasks + idx, sizeof(Task), cudaMemcpyDeviceToHost), "task");
   return HLU_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Continuous batching: GMRES states that advance together.  Each step runs
+// the preconditioner of every active state in ONE persistent launch (states
+// that share a factor have their columns placed side by side in that
+// factor's work vector), then each state's SpMV, CGS2 and Givens update.
+// ---------------------------------------------------------------------------
+namespace {
+
+int alloc_ws(KrylovWS& k, int64_t N, int m, int nr) {
+  k.free_all();
+  k.N = N;
+  k.m = m;
+  k.nr = nr;
+  CKR(cudaMalloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
+  CKR(cudaMalloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
+  CKR(cudaMalloc(&k.W, sizeof(double) * N * nr), "alloc W");
+  CKR(cudaMalloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.hn, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.cs, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.sn, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(cudaMalloc(&k.est, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.y, sizeof(double) * m * nr), "alloc");
+  CKR(cudaMalloc(&k.bn, sizeof(double) * nr), "alloc");
+  CKR(cudaMalloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
+  CKR(cudaMalloc(&k.jr, sizeof(int) * nr), "alloc");
+  return HLU_OK;
+}
+
+int norms_ws(KrylovWS& k, const double* X, int64_t ld, int nr, double* dev, cudaStream_t s) {
+  CKR(multidot(k.N, X, ld, 1, X, ld, nr, k.part, dev, 1, s), "norm");
+  CKR(sqrt_inplace(dev, nr, s), "sqrt");
+  return HLU_OK;
+}
+
+struct SolveSeg {
+  const double* b;
+  double* x;
+  int64_t ld;
+  int nr;
+};
+
+// x = (LU)^-1 b for segments grouped by handle, one launch for all handles
+int solve_segments(std::vector<hlu_handle*>& hs, std::vector<std::vector<SolveSeg>>& segs, cudaStream_t s) {
+  for (size_t i = 0; i < hs.size(); ++i) {
+    hlu_handle* h = hs[i];
+    int off = 0;
+    for (const SolveSeg& g : segs[i]) {
+      if (h->precision == HLU_FP64)
+        CKR(gather_cast<double>(h->A.N, h->d_perm, g.b, g.ld, (double*)h->d_arena + h->L.work_off + off * h->A.N,
+                                g.nr, s), "gather");
+      else
+        CKR(gather_cast<float>(h->A.N, h->d_perm, g.b, g.ld, (float*)h->d_arena + h->L.work_off + off * h->A.N,
+                               g.nr, s), "gather");
+      off += g.nr;
+    }
+    CKR(set_int(h->d_ranks + h->L.nrhs_slot, off, s), "nrhs slot");
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int rc = exec_run_batch(hs.data(), (int)hs.size(), 1, s, nullptr, &g_batch_order, &g_batch_order_len);
+    if (rc) return rc;
+  }
+  for (size_t i = 0; i < hs.size(); ++i) {
+    hlu_handle* h = hs[i];
+    int off = 0;
+    for (const SolveSeg& g : segs[i]) {
+      if (h->precision == HLU_FP64)
+        CKR(scatter_cast<double>(h->A.N, h->d_perm, (double*)h->d_arena + h->L.work_off + off * h->A.N, g.x, g.ld,
+                                 g.nr, s), "scatter");
+      else
+        CKR(scatter_cast<float>(h->A.N, h->d_perm, (float*)h->d_arena + h->L.work_off + off * h->A.N, g.x, g.ld,
+                                g.nr, s), "scatter");
+      off += g.nr;
+    }
+  }
+  return HLU_OK;
+}
+
+}  // namespace
+
+struct hlu_gmres {
+  hlu_handle* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int nr = 0;
+  int64_t ld = 0;
+  int m = 0;
+  double tol = 0;
+  int maxit = 0;
+  KrylovWS k;
+  std::vector<double> bn, beta, est;
+  std::vector<int> conv, jr;
+  int j = -1;  // inner step of the running cycle, -1: next step starts a cycle
+  int iters = 0, restarts = 0;
+  bool done = false;
+  int status = HLU_OK;
+  double precond_ms = 0;
+  int applies = 0;
+};
+
+extern "C" {
+
+int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, int32_t restart,
+                    double tol, int32_t maxit, void* stream, hlu_gmres** out) {
+  try {
+    hlu_handle* h = const_cast<hlu_handle*>(hc);
+    if (!out || !h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
+      return fail(HLU_ERR_ARG, "bad argument");
+    if (nrhs > h->L.nrhs_max) return fail(HLU_ERR_ARG, "nrhs above 16 per GMRES state");
+    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    cudaStream_t s = (cudaStream_t)stream;
+    hlu_gmres* g = new hlu_gmres();
+    g->h = h;
+    g->b = b;
+    g->x = x;
+    g->nr = nrhs;
+    g->ld = ld;
+    g->m = restart;
+    g->tol = tol;
+    g->maxit = maxit;
+    int rc = alloc_ws(g->k, h->A.N, restart, nrhs);
+    if (rc) {
+      delete g;
+      return rc;
+    }
+    g->bn.assign(nrhs, 0);
+    g->beta.assign(nrhs, 0);
+    g->est.assign(nrhs, 0);
+    g->conv.assign(nrhs, 0);
+    g->jr.assign(nrhs, 0);
+    for (int r = 0; r < nrhs; ++r) CKR(cudaMemsetAsync(x + r * ld, 0, sizeof(double) * h->A.N, s), "x0");
+    rc = norms_ws(g->k, b, ld, nrhs, g->k.bn, s);
+    if (rc) return rc;
+    CKR(cudaMemcpyAsync(g->bn.data(), g->k.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s), "d2h");
+    CKR(cudaStreamSynchronize(s), "sync");
+    *out = g;
+    return HLU_OK;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_gmres_step_batch(hlu_gmres* const* gs, int32_t count, void* stream) {
+  try {
+    if (!gs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    // phase A: states that start a cycle compute their residual and its norm
+    std::vector<hlu_gmres*> act;
+    for (int i = 0; i < count; ++i) {
+      hlu_gmres* g = gs[i];
+      if (!g || g->done) continue;
+      if (g->j < 0) {
+        const int64_t N = g->h->A.N, ldr = N * (g->m + 1);
+        CKR(residual(g->h->A.rowptr, g->h->A.col, g->h->A.val, N, g->x, g->ld, g->b, g->ld, g->k.V, ldr, g->nr, s),
+            "residual");
+        int rc = norms_ws(g->k, g->k.V, ldr, g->nr, g->k.hn, s);
+        if (rc) return rc;
+        CKR(cudaMemcpyAsync(g->beta.data(), g->k.hn, sizeof(double) * g->nr, cudaMemcpyDeviceToHost, s), "d2h");
+      }
+      act.push_back(g);
+    }
+    CKR(cudaStreamSynchronize(s), "sync");
+    std::vector<hlu_gmres*> run;
+    for (hlu_gmres* g : act) {
+      if (g->j < 0) {
+        bool all = true;
+        for (int r = 0; r < g->nr; ++r) {
+          g->conv[r] = (g->bn[r] == 0.0) || (g->beta[r] <= g->tol * g->bn[r]);
+          all = all && g->conv[r];
+        }
+        if (all || g->iters >= g->maxit) {
+          g->done = true;
+          g->status = all ? HLU_OK : HLU_ERR_NOT_CONVERGED;
+          continue;
+        }
+        const int64_t N = g->h->A.N, ldr = N * (g->m + 1);
+        CKR(scale_cols(N, g->k.V, ldr, g->k.hn, g->k.V, ldr, g->nr, s), "scale");
+        CKR(init_g(g->nr, g->m, g->k.hn, g->k.g, s), "init g");
+        std::fill(g->jr.begin(), g->jr.end(), 0);
+        g->j = 0;
+      }
+      run.push_back(g);
+    }
+    if (run.empty()) return HLU_OK;
+    // phase B: one launch for every preconditioner application
+    std::vector<hlu_handle*> hs;
+    std::vector<std::vector<SolveSeg>> segs;
+    for (hlu_gmres* g : run) {
+      const int64_t N = g->h->A.N, ldr = N * (g->m + 1);
+      SolveSeg sg{g->k.V + g->j * N, g->k.Z + g->j * N, ldr, g->nr};
+      size_t i = 0;
+      while (i < hs.size() && hs[i] != g->h) ++i;
+      int used = 0;
+      if (i < hs.size())
+        for (const SolveSeg& q : segs[i]) used += q.nr;
+      if (i == hs.size() || used + g->nr > g->h->L.nrhs_max) {
+        if (i < hs.size()) {
+          // the factor's work vector is full: finish this group first
+          int rc = solve_segments(hs, segs, s);
+          if (rc) return rc;
+          hs.clear();
+          segs.clear();
+        }
+        if ((int)hs.size() == kMaxBatch) {
+          int rc = solve_segments(hs, segs, s);
+          if (rc) return rc;
+          hs.clear();
+          segs.clear();
+        }
+        hs.push_back(g->h);
+        segs.push_back({sg});
+      } else {
+        segs[i].push_back(sg);
+      }
+    }
+    CKR(cudaEventRecord(run[0]->h->ev0, s), "event");
+    if (!hs.empty()) {
+      int rc = solve_segments(hs, segs, s);
+      if (rc) return rc;
+    }
+    CKR(cudaEventRecord(run[0]->h->ev1, s), "event");
+    // phase C: Arnoldi step of every running state
+    for (hlu_gmres* g : run) {
+      KrylovWS& k = g->k;
+      const int64_t N = g->h->A.N, ldr = N * (g->m + 1);
+      const int j = g->j, m = g->m, nr = g->nr;
+      CKR(spmv(g->h->A.rowptr, g->h->A.col, g->h->A.val, N, k.Z + j * N, ldr, k.W, N, nr, s), "spmv");
+      CKR(multidot(N, k.V, ldr, j + 1, k.W, N, nr, k.part, k.h1, m + 1, s), "cgs1");
+      CKR(multiaxpy(N, k.V, ldr, j + 1, k.h1, m + 1, k.W, N, nr, s), "cgs1 axpy");
+      CKR(multidot(N, k.V, ldr, j + 1, k.W, N, nr, k.part, k.h2, m + 1, s), "cgs2");
+      CKR(multiaxpy(N, k.V, ldr, j + 1, k.h2, m + 1, k.W, N, nr, s), "cgs2 axpy");
+      int rc = norms_ws(k, k.W, N, nr, k.hn, s);
+      if (rc) return rc;
+      CKR(scale_cols(N, k.W, N, k.hn, k.V + (j + 1) * N, ldr, nr, s), "scale");
+      CKR(givens(nr, m, j, k.h1, k.h2, m + 1, k.hn, k.H, k.cs, k.sn, k.g, k.est, s), "givens");
+      CKR(cudaMemcpyAsync(g->est.data(), k.est, sizeof(double) * nr, cudaMemcpyDeviceToHost, s), "est");
+    }
+    CKR(cudaStreamSynchronize(s), "sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, run[0]->h->ev0, run[0]->h->ev1);
+    for (hlu_gmres* g : run) {
+      KrylovWS& k = g->k;
+      g->precond_ms += ms / run.size();
+      g->applies++;
+      g->iters++;
+      bool end = true;
+      for (int r = 0; r < g->nr; ++r) {
+        if (g->conv[r]) continue;
+        if (g->jr[r] == 0 && g->est[r] <= g->tol * g->bn[r]) g->jr[r] = g->j + 1;
+        end = end && g->jr[r] > 0;
+      }
+      if (end || g->j == g->m - 1 || g->iters >= g->maxit) {
+        for (int r = 0; r < g->nr; ++r) {
+          if (g->conv[r])
+            g->jr[r] = 0;
+          else if (g->jr[r] == 0)
+            g->jr[r] = g->j + 1;
+        }
+        CKR(cudaMemcpyAsync(k.jr, g->jr.data(), sizeof(int) * g->nr, cudaMemcpyHostToDevice, s), "jr");
+        CKR(backsub(g->nr, g->m, k.jr, k.H, k.g, k.y, s), "backsub");
+        CKR(xupdate(g->h->A.N, k.Z, g->h->A.N * (g->m + 1), g->m, k.y, g->x, g->ld, g->nr, s), "xupdate");
+        g->restarts++;
+        g->j = -1;
+      } else {
+        g->j++;
+      }
+    }
+    CKR(cudaStreamSynchronize(s), "sync");
+    return HLU_OK;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_gmres_status(const hlu_gmres* g, int32_t* done, hlu_stats* st) {
+  if (!g) return fail(HLU_ERR_ARG, "null state");
+  if (done) *done = g->done ? 1 : 0;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->iterations = g->iters;
+    st->restarts = g->restarts;
+    st->converged = g->done && g->status == HLU_OK;
+    st->nrhs = g->nr;
+    double rmax = 0, amax = 0;
+    for (int r = 0; r < g->nr; ++r) {
+      rmax = std::max(rmax, g->bn[r] > 0 ? g->beta[r] / g->bn[r] : 0.0);
+      amax = std::max(amax, g->beta[r]);
+    }
+    st->relres_max = rmax;
+    st->abs_res_max = amax;
+    st->precond_ms = g->precond_ms;
+    st->precond_applies = g->applies;
+  }
+  return g->done ? g->status : HLU_OK;
+}
+
+void hlu_gmres_end(hlu_gmres* g) {
+  if (!g) return;
+  g->k.free_all();
+  delete g;
+}
+
+}  // extern "C"

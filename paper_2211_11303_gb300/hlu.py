@@ -77,6 +77,10 @@ SIGNATURES = {
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
     "hlu_launch_count": (_i64, []),
+    "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
+    "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
+    "hlu_gmres_status": (_i32, [_vp, _P(_i32), _P(hlu_stats)]),
+    "hlu_gmres_end": (None, [_vp]),
     "hlu_destroy": (None, [_vp]),
     "hlu_status_string": (ctypes.c_char_p, [_i32]),
     "hlu_last_error": (ctypes.c_char_p, []),
@@ -254,6 +258,36 @@ def hlu_richardson(h, b, x, tol=1e-8, maxit=100, stream=None, raise_on_nonconver
     if rc != HLU_ERR_NOT_CONVERGED or raise_on_nonconvergence:
         _check(rc)
     return _struct_dict(st)
+
+
+def hlu_gmres_begin(h, b, x, restart=50, tol=1e-8, maxit=1000, stream=None):
+    """Start a GMRES state for continuous batching; returns an opaque state."""
+    N = hlu_n(h)
+    pb, nr, ldb = _vec(b, N)
+    px, nr2, ldx = _vec(x, N)
+    if nr != nr2 or ldb != ldx:
+        raise ValueError("b and x must have the same shape and leading dimension")
+    g = _vp()
+    _check(lib().hlu_gmres_begin(_vp(h), pb, px, nr, ldb, int(restart), float(tol), int(maxit),
+                                 _stream(stream), ctypes.byref(g)))
+    return g.value
+
+
+def hlu_gmres_step_batch(states, stream=None):
+    arr = (_vp * len(states))(*[_vp(g) for g in states])
+    _check(lib().hlu_gmres_step_batch(arr, len(states), _stream(stream)))
+
+
+def hlu_gmres_status(g):
+    """(done, stats dict); raises nothing for non-convergence (see stats)."""
+    done = _i32()
+    st = hlu_stats()
+    lib().hlu_gmres_status(_vp(g), ctypes.byref(done), ctypes.byref(st))
+    return bool(done.value), _struct_dict(st)
+
+
+def hlu_gmres_end(g):
+    lib().hlu_gmres_end(_vp(g))
 
 
 def hlu_factor_batch(handles, precision=HLU_FP32, stream=None):

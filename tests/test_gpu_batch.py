@@ -1,0 +1,81 @@
+"""Batched launches (through the C ABI): many problems' task DAGs in one
+persistent launch must give exactly what one launch per problem gives (every
+task computes the same thing whatever the interleaving), and the batch of
+problems must meet the same parity bar as single problems."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hlu():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2211_11303_gb300 import hlu as H
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    H.hlu_set_wait_limit_ms(20000)
+    return H
+
+
+def _rhs(N, nrhs, seed):
+    B = np.stack([synth.normal(seed + j, N) for j in range(nrhs)], axis=1)
+    return torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_factor_batch_equals_single(hlu, prec):
+    P = hlu.HLU_FP32 if prec == "fp32" else hlu.HLU_FP64
+    # batched workload recipe: mesh n and kappa drawn per problem (small sizes here)
+    probs = [(4, 3.0), (5, 1.5), (6, 7.0), (5, 9.0), (3, 2.0)]
+    single, batch = [], []
+    try:
+        for n, k in probs:
+            single.append(hlu.hlu_build(n, k, 16, 2.0, 1e-4))
+            batch.append(hlu.hlu_build(n, k, 16, 2.0, 1e-4))
+        for h in single:
+            hlu.hlu_factor(h, P)
+        hlu.hlu_factor_batch(batch, P)
+        for i, (hs, hb) in enumerate(zip(single, batch)):
+            N = hlu.hlu_n(hs)
+            b = _rhs(N, 2, 100 + i)
+            x1 = hlu.colmajor(N, 2)
+            x2 = hlu.colmajor(N, 2)
+            hlu.hlu_solve(hs, b, x1)
+            hlu.hlu_solve(hb, b, x2)
+            torch.cuda.synchronize()
+            assert torch.equal(x1, x2), i
+            assert hlu.hlu_factor_stats(hb)["rank_max"] == hlu.hlu_factor_stats(hs)["rank_max"]
+    finally:
+        for h in single + batch:
+            hlu.hlu_destroy(h)
+
+
+def test_solve_batch_equals_single(hlu):
+    probs = [(4, 2.0, 1), (6, 5.0, 3), (5, 1.0, 16), (6, 8.0, 7)]
+    hs = []
+    try:
+        for n, k, _ in probs:
+            h = hlu.hlu_build(n, k, 32, 2.0, 1e-4)
+            hlu.hlu_factor(h, hlu.HLU_FP32)
+            hs.append(h)
+        bs, xs, refs = [], [], []
+        for i, (h, (n, k, nr)) in enumerate(zip(hs, probs)):
+            N = hlu.hlu_n(h)
+            b = _rhs(N, nr, 200 + 16 * i)
+            r = hlu.colmajor(N, nr)
+            hlu.hlu_solve(h, b, r)
+            bs.append(b)
+            xs.append(hlu.colmajor(N, nr))
+            refs.append(r)
+        hlu.hlu_solve_batch(hs, bs, xs)
+        torch.cuda.synchronize()
+        for x, r in zip(xs, refs):
+            assert torch.equal(x, r)
+    finally:
+        for h in hs:
+            hlu.hlu_destroy(h)

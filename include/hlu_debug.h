@@ -64,12 +64,22 @@ int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t limit, voi
  * internal record, 136 bytes: kind, flags, operand views) to `out`. */
 int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out);
 
+/* hlu_debug_factor_trace - factorise a built handle at `precision` with a
+ * per-task trace (needs a GPU).  trace_out: uint64[4 x tasks] (wait start,
+ * run start, end in globaltimer ns, CTA index); pred_ptr_out: int64[tasks+1]
+ * and pred_idx_out: int32[edges], the dependency DAG; tasks_out: the task
+ * records (136 bytes each).  sizes: int64[2] receives (tasks, edges); pass
+ * NULL trace_out to query sizes only.  Any other output may be NULL. */
+int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t* trace_out, int64_t* pred_ptr_out,
+                           int32_t* pred_idx_out, void* tasks_out, int64_t* sizes);
+
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a
  * GPU).  Runs the task executor with one CTA on a two-task schedule in which
- * task 0 waits for task 1, a completion flag that nothing can set.  The wait
- * must give up after limit_ms (0 < limit_ms <= 5000), record HLU_ERR_TIMEOUT,
- * and the kernel must return with the context still usable.
- * status_out: int32[2] receives (device status code, task that gave up).
+ * task 1 waits for itself: task 0 runs, and the CTA that claims queue slot 1
+ * waits for a task that can never become ready.  The wait must give up after
+ * limit_ms (0 < limit_ms <= 5000), record HLU_ERR_TIMEOUT, and the kernel must
+ * return with the context still usable.
+ * status_out: int32[2] receives (device status code, queue slot that gave up).
  * Returns HLU_ERR_TIMEOUT when the wait ran out as intended. */
 int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out);
 

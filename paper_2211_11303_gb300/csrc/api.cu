@@ -60,17 +60,24 @@ cudaError_t upload(T** d, const std::vector<T>& h) {
   return e;
 }
 
-// A schedule on the device.  The task arrays are shared (read-only) between
-// handles with the same block tree; the completion flags belong to one handle.
+// A schedule on the device.  The task arrays and the DAG are shared
+// (read-only) between handles with the same block tree; the dependency
+// counters and the ready queue belong to one handle.
 struct DevSched {
   Task* tasks = nullptr;
   Term* terms = nullptr;
   Piece* pieces = nullptr;
   int64_t* pred_ptr = nullptr;
   int32_t* pred_idx = nullptr;
-  int32_t* done = nullptr;
+  int64_t* succ_ptr = nullptr;
+  int32_t* succ_idx = nullptr;
+  int32_t* indeg0 = nullptr;            // predecessor counts
+  unsigned long long* roots = nullptr;  // tasks without predecessors, as queue entries (index + 1)
+  std::vector<int32_t> h_roots;         // the same, ascending
+  int32_t* indeg = nullptr;             // per handle: counters of the running launch
+  unsigned long long* queue = nullptr;  // per handle: ready queue, ntasks slots
+  unsigned long long* qctl = nullptr;   // per handle: claim / fill positions
   int64_t ntasks = 0;
-  int32_t epoch = 0;
   bool owns_data = true;
   cudaError_t load(const Schedule& S) {
     ntasks = (int64_t)S.tasks.size();
@@ -80,26 +87,59 @@ struct DevSched {
     if ((e = upload(&pieces, S.pieces)) != cudaSuccess) return e;
     if ((e = upload(&pred_ptr, S.pred_ptr)) != cudaSuccess) return e;
     if ((e = upload(&pred_idx, S.pred_idx)) != cudaSuccess) return e;
-    return alloc_flags();
+    // successor lists (edges sorted by predecessor, successors ascending)
+    const int64_t ne = S.pred_ptr.empty() ? 0 : S.pred_ptr[ntasks];
+    std::vector<int64_t> sp(ntasks + 1, 0);
+    std::vector<int32_t> si(std::max<int64_t>(ne, 0)), in0(ntasks);
+    for (int64_t t = 0; t < ntasks; ++t) {
+      in0[t] = (int32_t)(S.pred_ptr[t + 1] - S.pred_ptr[t]);
+      for (int64_t q = S.pred_ptr[t]; q < S.pred_ptr[t + 1]; ++q) ++sp[S.pred_idx[q] + 1];
+    }
+    for (int64_t t = 0; t < ntasks; ++t) sp[t + 1] += sp[t];
+    std::vector<int64_t> fill(sp.begin(), sp.end() - 1);
+    for (int64_t t = 0; t < ntasks; ++t)
+      for (int64_t q = S.pred_ptr[t]; q < S.pred_ptr[t + 1]; ++q) si[fill[S.pred_idx[q]]++] = (int32_t)t;
+    std::vector<unsigned long long> rq;
+    h_roots.clear();
+    for (int64_t t = 0; t < ntasks; ++t)
+      if (in0[t] == 0) {
+        h_roots.push_back((int32_t)t);
+        rq.push_back((unsigned long long)t + 1ULL);
+      }
+    if ((e = upload(&succ_ptr, sp)) != cudaSuccess) return e;
+    if ((e = upload(&succ_idx, si)) != cudaSuccess) return e;
+    if ((e = upload(&indeg0, in0)) != cudaSuccess) return e;
+    if ((e = upload(&roots, rq)) != cudaSuccess) return e;
+    return cudaSuccess;
   }
-  cudaError_t alloc_flags() {
-    cudaError_t e = cudaMalloc(&done, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
+  cudaError_t alloc_state() {
+    cudaError_t e = cudaMalloc(&indeg, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
     if (e != cudaSuccess) return e;
-    epoch = 0;
-    return cudaMemset(done, 0, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
+    if ((e = cudaMalloc(&queue, sizeof(unsigned long long) * std::max<int64_t>(ntasks, 1))) != cudaSuccess) return e;
+    return cudaMalloc(&qctl, sizeof(unsigned long long) * 2);
   }
   // a per-handle view of shared task data
   DevSched share() const {
     DevSched d = *this;
-    d.done = nullptr;
+    d.indeg = nullptr;
+    d.queue = nullptr;
+    d.qctl = nullptr;
     d.owns_data = false;
     return d;
   }
+  // tasks run by a launch limited to the first `limit` tasks, and its roots
+  int64_t run_count(int64_t limit) const { return limit >= 0 ? std::min(limit, ntasks) : ntasks; }
+  int64_t root_count(int64_t limit) const {
+    if (limit < 0) return (int64_t)h_roots.size();
+    return std::lower_bound(h_roots.begin(), h_roots.end(), limit) - h_roots.begin();
+  }
   void free_all() {
     if (owns_data)
-      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx})
+      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx, (void*)succ_ptr,
+                      (void*)succ_idx, (void*)indeg0, (void*)roots})
         if (p) cudaFree(p);
-    if (done) cudaFree(done);
+    for (void* p : {(void*)indeg, (void*)queue, (void*)qctl})
+      if (p) cudaFree(p);
     *this = DevSched();
   }
 };
@@ -126,8 +166,8 @@ struct SchedBundle {
 
 std::mutex g_cache_mu;
 std::mutex g_batch_mu;            // serialises batched launches (shared order buffer)
-int64_t* g_batch_order = nullptr;
-int64_t g_batch_order_len = 0;
+unsigned long long* g_batch_q = nullptr;  // ready queue of batched launches
+int64_t g_batch_q_len = 0;
 std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
 constexpr size_t kCacheEntries = 8;
 
@@ -183,7 +223,6 @@ struct hlu_handle {
   int grid = 0;
   int32_t* d_status = nullptr;
   double* d_flops = nullptr;
-  unsigned long long* d_ticket = nullptr;
   void** d_arenas = nullptr;
   int32_t** d_rankp = nullptr;
   int32_t** d_pivp = nullptr;
@@ -191,13 +230,14 @@ struct hlu_handle {
   KrylovWS kw;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   unsigned long long* d_prof = nullptr;  // executor profile of the last factorisation
+  unsigned long long* d_trace = nullptr; // per-task trace of the next factorisation (debug)
 };
 
 namespace {
 
 void free_factor(hlu_handle* h) {
   for (void* p : {(void*)h->d_arena, (void*)h->d_ranks, (void*)h->d_piv, (void*)h->d_scratch, (void*)h->d_status,
-                  (void*)h->d_flops, (void*)h->d_ticket, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp,
+                  (void*)h->d_flops, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp,
                   (void*)h->d_prof})
     if (p) cudaFree(p);
   h->d_prof = nullptr;
@@ -207,7 +247,6 @@ void free_factor(hlu_handle* h) {
   h->d_scratch = nullptr;
   h->d_status = nullptr;
   h->d_flops = nullptr;
-  h->d_ticket = nullptr;
   h->d_arenas = nullptr;
   h->d_rankp = nullptr;
   h->d_pivp = nullptr;
@@ -226,125 +265,140 @@ int blocks_per_sm() {
   return exec_blocks_per_sm<T>();
 }
 
-ProbSched prob_of(hlu_handle* h, DevSched& ds) {
+ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   ProbSched p;
   std::memset(&p, 0, sizeof(p));
   p.tasks = ds.tasks;
   p.terms = ds.terms;
   p.pieces = ds.pieces;
-  p.pred_ptr = ds.pred_ptr;
-  p.pred_idx = ds.pred_idx;
-  p.done = ds.done;
+  p.succ_ptr = ds.succ_ptr;
+  p.succ_idx = ds.succ_idx;
+  p.indeg = ds.indeg;
   p.arena = h->d_arena;
   p.ranks = h->d_ranks;
   p.piv = h->d_piv;
   p.eps = h->eps;
   p.ntasks = ds.ntasks;
-  p.epoch = ++ds.epoch;
+  p.limit = ds.run_count(limit);
   return p;
 }
 
+void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool with_flops) {
+  a.scratch = scratch_owner->d_scratch;
+  a.scratch_stride = scratch_owner->scratch_stride;
+  a.trunc_rows = std::max(scratch_owner->L.max_trunc_rows, 1);
+  a.status = h0->d_status;
+  a.flops = with_flops ? h0->d_flops : nullptr;
+  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  a.prof = with_flops ? h0->d_prof : nullptr;
+  a.trace = with_flops ? h0->d_trace : nullptr;
+}
+
 // One launch of the executor over one problem's schedule (or its first
-// `limit` tasks).
+// `limit` tasks): counters reset, queue cleared and seeded with the roots.
 int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops, int64_t limit = -1) {
   ExecArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.probs[0] = prob_of(h, ds);
+  a.probs[0] = prob_of(h, ds, limit);
   a.nprobs = 1;
-  a.order = nullptr;
-  a.ntotal = limit >= 0 ? std::min(limit, ds.ntasks) : ds.ntasks;
-  a.ticket = h->d_ticket;
-  a.scratch = h->d_scratch;
-  a.scratch_stride = h->scratch_stride;
-  a.trunc_rows = std::max(h->L.max_trunc_rows, 1);
-  a.status = h->d_status;
-  a.flops = with_flops ? h->d_flops : nullptr;
-  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
-  a.prof = with_flops ? h->d_prof : nullptr;
+  a.ntotal = ds.run_count(limit);
+  a.queue = ds.queue;
+  a.qctl = ds.qctl;
+  fill_common(a, h, h, with_flops);
   if (a.ntotal == 0) return HLU_OK;
+  const int64_t nr = ds.root_count(limit);
   int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+  unsigned long long q0[2] = {0ULL, (unsigned long long)nr};
   CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
-  CKR(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
+  CKR(cudaMemcpyAsync(ds.qctl, q0, sizeof(q0), cudaMemcpyHostToDevice, s), "queue reset");
+  CKR(cudaMemcpyAsync(ds.indeg, ds.indeg0, sizeof(int32_t) * ds.ntasks, cudaMemcpyDeviceToDevice, s), "counters");
+  CKR(cudaMemcpyAsync(ds.queue, ds.roots, sizeof(unsigned long long) * nr, cudaMemcpyDeviceToDevice, s), "roots");
+  if (a.ntotal > nr)
+    CKR(cudaMemsetAsync(ds.queue + nr, 0, sizeof(unsigned long long) * (a.ntotal - nr), s), "queue clear");
   int g = (int)std::min<int64_t>(grid, a.ntotal);
   cudaError_t e = h->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
   CKR(e, "executor launch");
   return HLU_OK;
 }
 
-// Ticket order of a batched launch: the problems' tasks interleaved by
-// relative progress (task i of problem p at key (i + 1/2) / n_p), increasing
-// within every problem, encoded (p << 40) | i.
-std::vector<int64_t> batch_order(const std::vector<int64_t>& ntasks) {
+// Queue seed of a batched launch: the problems' roots interleaved by relative
+// position (root j of problem p at key (j + 1/2) / n_p), as queue entries
+// ((p << 40) | task) + 1.
+std::vector<unsigned long long> batch_roots(const std::vector<const std::vector<int32_t>*>& roots) {
   struct Item {
     double key;
     int32_t p;
-    int64_t i;
+    int64_t j;
     bool operator<(const Item& o) const { return key > o.key || (key == o.key && p > o.p); }
   };
-  std::vector<int64_t> out;
-  int64_t tot = 0;
-  for (int64_t n : ntasks) tot += n;
-  out.reserve(tot);
+  std::vector<unsigned long long> out;
   std::priority_queue<Item> pq;
-  for (size_t p = 0; p < ntasks.size(); ++p)
-    if (ntasks[p] > 0) pq.push(Item{0.5 / ntasks[p], (int32_t)p, 0});
+  for (size_t p = 0; p < roots.size(); ++p)
+    if (!roots[p]->empty()) pq.push(Item{0.5 / roots[p]->size(), (int32_t)p, 0});
   while (!pq.empty()) {
     Item it = pq.top();
     pq.pop();
-    out.push_back(((int64_t)it.p << 40) | it.i);
-    if (it.i + 1 < ntasks[it.p]) pq.push(Item{(it.i + 1.5) / ntasks[it.p], it.p, it.i + 1});
+    const std::vector<int32_t>& r = *roots[it.p];
+    out.push_back((((unsigned long long)it.p) << 40 | (unsigned long long)r[it.j]) + 1ULL);
+    if (it.j + 1 < (int64_t)r.size()) pq.push(Item{(it.j + 1.5) / r.size(), it.p, it.j + 1});
   }
   return out;
 }
 
 // One launch over the factor (which = 0) or solve (which = 1) schedules of
-// several handles with the same precision.  Handle 0's ticket, status, flop
-// counter and profile are used; the scratch is that of the handle with the
-// largest truncation stacks.
-int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, int64_t* order_cache_key,
-                   int64_t** d_order, int64_t* d_order_len) {
+// several handles with the same precision.  Handle 0's status, flop counter
+// and profile are used; the scratch is that of the handle with the largest
+// truncation stacks; the queue (all problems' tasks) lives in *d_q.
+int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, unsigned long long** d_q,
+                   int64_t* d_q_len) {
   if (count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "batch size");
   ExecArgs a;
   std::memset(&a, 0, sizeof(a));
-  std::vector<int64_t> nt(count);
   hlu_handle* hs0 = hs[0];
   hlu_handle* big = hs0;
+  std::vector<const std::vector<int32_t>*> roots(count);
+  int64_t total = 0;
   for (int i = 0; i < count; ++i) {
     hlu_handle* h = hs[i];
     if (h->precision != hs0->precision) return fail(HLU_ERR_ARG, "mixed precisions in a batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return fail(HLU_ERR_ARG, "a handle appears twice in a batch");
     DevSched& ds = which == 0 ? h->dF : h->dS;
-    a.probs[i] = prob_of(h, ds);
-    nt[i] = ds.ntasks;
+    a.probs[i] = prob_of(h, ds, -1);
+    roots[i] = &ds.h_roots;
+    total += ds.ntasks;
     if (h->L.max_trunc_rows > big->L.max_trunc_rows) big = h;
   }
   a.nprobs = count;
-  std::vector<int64_t> ord = batch_order(nt);
-  if (*d_order_len < (int64_t)ord.size()) {
-    if (*d_order) cudaFree(*d_order);
-    *d_order = nullptr;
-    CKR(cudaMalloc(d_order, sizeof(int64_t) * std::max<size_t>(ord.size(), 1)), "order");
-    *d_order_len = (int64_t)ord.size();
+  a.ntotal = total;
+  if (total == 0) return HLU_OK;
+  std::vector<unsigned long long> seed = batch_roots(roots);
+  if (*d_q_len < total + 2) {
+    if (*d_q) cudaFree(*d_q);
+    *d_q = nullptr;
+    *d_q_len = 0;
+    CKR(cudaMalloc(d_q, sizeof(unsigned long long) * (total + 2)), "queue");
+    *d_q_len = total + 2;
   }
-  (void)order_cache_key;
-  CKR(cudaMemcpyAsync(*d_order, ord.data(), sizeof(int64_t) * ord.size(), cudaMemcpyHostToDevice, s), "order");
-  a.order = *d_order;
-  a.ntotal = (int64_t)ord.size();
-  a.ticket = hs0->d_ticket;
-  a.scratch = big->d_scratch;
-  a.scratch_stride = big->scratch_stride;
-  a.trunc_rows = std::max(big->L.max_trunc_rows, 1);
-  a.status = hs0->d_status;
-  a.flops = which == 0 ? hs0->d_flops : nullptr;
-  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
-  a.prof = which == 0 ? hs0->d_prof : nullptr;
-  if (a.ntotal == 0) return HLU_OK;
+  a.qctl = *d_q;
+  a.queue = *d_q + 2;
+  fill_common(a, big, hs0, which == 0);
   int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+  unsigned long long q0[2] = {0ULL, (unsigned long long)seed.size()};
   CKR(cudaMemcpyAsync(hs0->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
-  CKR(cudaMemsetAsync(hs0->d_ticket, 0, sizeof(unsigned long long), s), "ticket reset");
+  CKR(cudaMemcpyAsync(a.qctl, q0, sizeof(q0), cudaMemcpyHostToDevice, s), "queue reset");
+  for (int i = 0; i < count; ++i) {
+    DevSched& ds = which == 0 ? hs[i]->dF : hs[i]->dS;
+    CKR(cudaMemcpyAsync(ds.indeg, ds.indeg0, sizeof(int32_t) * ds.ntasks, cudaMemcpyDeviceToDevice, s), "counters");
+  }
+  CKR(cudaMemcpyAsync(a.queue, seed.data(), sizeof(unsigned long long) * seed.size(), cudaMemcpyHostToDevice, s),
+      "seed");
+  if (total > (int64_t)seed.size())
+    CKR(cudaMemsetAsync(a.queue + seed.size(), 0, sizeof(unsigned long long) * (total - seed.size()), s), "clear");
   int g = (int)std::min<int64_t>(hs0->grid, a.ntotal);
   cudaError_t e = hs0->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
   CKR(e, "executor launch");
-  // the order buffer must stay alive until the kernel has run
+  // the host seed buffer must outlive the copy
   CKR(cudaStreamSynchronize(s), "sync");
   return HLU_OK;
 }
@@ -613,9 +667,6 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, sb->L, F, S, sb->st, &sb->FB);
       if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
       if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
-      cudaFree(sb->dF.done);
-      cudaFree(sb->dS.done);
-      sb->dF.done = sb->dS.done = nullptr;
       // A_H fill descriptors
       std::vector<FillDesc> fd, fl;
       int64_t rows = 0;
@@ -654,8 +705,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     h->L = h->sb->L;
     h->dF = h->sb->dF.share();
     h->dS = h->sb->dS.share();
-    if ((e = h->dF.alloc_flags()) != cudaSuccess) return bail(e, "flags");
-    if ((e = h->dS.alloc_flags()) != cudaSuccess) return bail(e, "flags");
+    if ((e = h->dF.alloc_state()) != cudaSuccess) return bail(e, "queue");
+    if ((e = h->dS.alloc_state()) != cudaSuccess) return bail(e, "queue");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "sync");
     h->info.n_tasks = h->sb->st.n_factor_tasks;
     h->info.n_solve_tasks = h->sb->st.n_solve_tasks;
@@ -740,7 +791,6 @@ static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
     CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
     CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 8), "status");
     CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
-    CKR(cudaMalloc(&h->d_ticket, sizeof(unsigned long long)), "ticket");
     CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * (TK_NUM + 1) * 3), "prof");
     h->precision = precision;
   }
@@ -939,7 +989,7 @@ int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* st
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     CKR(cudaEventRecord(hs[0]->ev0, s), "event");
-    int rc = exec_run_batch(hs, count, 0, s, nullptr, &g_batch_order, &g_batch_order_len);
+    int rc = exec_run_batch(hs, count, 0, s, &g_batch_q, &g_batch_q_len);
     if (rc) return rc;
     CKR(cudaEventRecord(hs[0]->ev1, s), "event");
     CKR(cudaEventSynchronize(hs[0]->ev1), "sync");
@@ -980,7 +1030,7 @@ int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b
     }
     {
       std::lock_guard<std::mutex> lk(g_batch_mu);
-      int rc = exec_run_batch(hs, count, 1, s, nullptr, &g_batch_order, &g_batch_order_len);
+      int rc = exec_run_batch(hs, count, 1, s, &g_batch_q, &g_batch_q_len);
       if (rc) return rc;
     }
     for (int32_t i = 0; i < count; ++i) {
@@ -1013,14 +1063,15 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   t.type = TK_NUM;  // no work
   t.out_slot = -1;
   S.tasks = {t, t};
-  S.pred_ptr = {0, 1, 1};
+  // task 1 waits for itself: its queue slot is never filled
+  S.pred_ptr = {0, 0, 1};
   S.pred_idx = {1};
   hlu_handle h;
   h.precision = HLU_FP32;
   DevSched ds;
   CKR(ds.load(S), "upload");
+  CKR(ds.alloc_state(), "queue");
   CKR(cudaMalloc(&h.d_status, sizeof(int32_t) * 8), "alloc");
-  CKR(cudaMalloc(&h.d_ticket, sizeof(unsigned long long)), "alloc");
   // valid (unused) per-problem pointers: the two tasks do no work
   CKR(cudaMalloc(&h.d_arena, 256), "alloc");
   CKR(cudaMalloc(&h.d_arenas, sizeof(void*)), "alloc");
@@ -1038,11 +1089,10 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   status_out[0] = st[0];
   status_out[1] = st[1];
   ds.free_all();
-  for (void* p : {(void*)h.d_status, (void*)h.d_ticket, (void*)h.d_arena, (void*)h.d_arenas, (void*)h.d_rankp,
+  for (void* p : {(void*)h.d_status, (void*)h.d_arena, (void*)h.d_arenas, (void*)h.d_rankp,
                   (void*)h.d_pivp})
     cudaFree(p);
   h.d_status = nullptr;
-  h.d_ticket = nullptr;
   h.d_arena = nullptr;
   h.d_arenas = nullptr;
   h.d_rankp = nullptr;
@@ -1073,6 +1123,34 @@ extern "C" int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t
   if (arena_out)
     CKR(cudaMemcpy(arena_out, h->d_arena, (size_t)esize(precision) * h->L.total, cudaMemcpyDeviceToHost), "arena");
   if (ranks_out) CKR(cudaMemcpy(ranks_out, h->d_ranks, sizeof(int32_t) * h->L.n_slots, cudaMemcpyDeviceToHost), "ranks");
+  return HLU_OK;
+}
+
+// Factorises with a per-task trace and copies the trace, the DAG and the task
+// records out; sizes[0] = tasks, sizes[1] = dependency edges (query with NULL
+// buffers).
+extern "C" int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t* trace_out, int64_t* pred_ptr_out,
+                                      int32_t* pred_idx_out, void* tasks_out, int64_t* sizes) {
+  if (!h || !sizes) return fail(HLU_ERR_ARG, "null argument");
+  const int64_t nt = h->dF.ntasks;
+  sizes[0] = nt;
+  sizes[1] = 0;
+  if (h->dF.pred_ptr && nt > 0)
+    CKR(cudaMemcpy(&sizes[1], h->dF.pred_ptr + nt, sizeof(int64_t), cudaMemcpyDeviceToHost), "edges");
+  if (!trace_out) return HLU_OK;
+  CKR(cudaMalloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  int rc = factor_impl(h, precision, nullptr, -1);
+  cudaError_t e = cudaMemcpy(trace_out, h->d_trace, sizeof(uint64_t) * 4 * nt, cudaMemcpyDeviceToHost);
+  cudaFree(h->d_trace);
+  h->d_trace = nullptr;
+  if (rc) return rc;
+  CKR(e, "trace copy");
+  if (pred_ptr_out)
+    CKR(cudaMemcpy(pred_ptr_out, h->dF.pred_ptr, sizeof(int64_t) * (nt + 1), cudaMemcpyDeviceToHost), "dag");
+  if (pred_idx_out)
+    CKR(cudaMemcpy(pred_idx_out, h->dF.pred_idx, sizeof(int32_t) * sizes[1], cudaMemcpyDeviceToHost), "dag");
+  if (tasks_out) CKR(cudaMemcpy(tasks_out, h->dF.tasks, sizeof(Task) * nt, cudaMemcpyDeviceToHost), "tasks");
   return HLU_OK;
 }
 
@@ -1145,7 +1223,7 @@ int solve_segments(std::vector<hlu_handle*>& hs, std::vector<std::vector<SolveSe
   }
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    int rc = exec_run_batch(hs.data(), (int)hs.size(), 1, s, nullptr, &g_batch_order, &g_batch_order_len);
+    int rc = exec_run_batch(hs.data(), (int)hs.size(), 1, s, &g_batch_q, &g_batch_q_len);
     if (rc) return rc;
   }
   for (size_t i = 0; i < hs.size(); ++i) {

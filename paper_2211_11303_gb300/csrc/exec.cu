@@ -1,16 +1,20 @@
 // Persistent task executor for the H-LU and H-solve DAGs (sm_103a).
 //
-// One launch runs a whole schedule.  Each CTA repeatedly takes the next task
-// index from a global ticket counter (tickets follow a topological order), waits
-// until every predecessor has published completion for the current epoch,
-// runs the task with all its threads, and publishes its own completion.  A CTA
-// only ever waits on tasks with smaller tickets, which were taken by CTAs that
-// are already running, so the waits cannot deadlock.  Every wait is bounded by
-// a wall-clock limit (%globaltimer); when it runs out the CTA records
+// One launch runs a whole schedule.  Every task carries a counter of its
+// unfinished predecessors; the CTA that finishes a task decrements the
+// counters of its successors, and the one that brings a counter to zero
+// appends that task to a FIFO ready queue.  Each CTA repeatedly claims the
+// next queue slot, waits until the slot is filled, and runs the task with all
+// its threads.  The queue holds every task of the launch exactly once, and a
+// claimed slot is always filled while some task is still running, so the
+// waits cannot deadlock on an acyclic schedule.  Every wait is bounded by a
+// wall-clock limit (%globaltimer); when it runs out the CTA records
 // HLU_ERR_TIMEOUT and all CTAs drain without executing further work.
 //
 // Data written by one CTA and read by another goes through L2 (ld.global.cg /
-// st.global.cg); completion flags use st.release / ld.acquire at gpu scope.
+// st.global.cg); a task's writes are fenced before its successors' counters
+// are decremented, and queue slots are published with st.release and read
+// with ld.acquire at gpu scope.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -36,6 +40,14 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 }
 __device__ __forceinline__ void st_release(int32_t* p, int32_t v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 template <class T>
@@ -401,293 +413,258 @@ __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
 }
 
 // ---------------------------------------------------------------- TRUNC
-// Householder QR of S (m x w, column-major, ld m, this CTA's private scratch)
-// in place.  Every step uses the whole CTA: the norm is a block reduction and
-// the reflector is applied to groups of 8 columns at once.
-template <class T>
-__device__ void house_qr(T* S, int m, int w, T* tau, T* red) {
-  const int tmax = min(m, w);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ T s_scale;
-  __shared__ T s_d[8];
-  __shared__ T s_part[NT / 32][8];
-  for (int j = 0; j < tmax; ++j) {
-    T* cj = S + (int64_t)j * m;
-    T part = 0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-      T x = cj[i];
-      part += x * x;
-    }
-    T s2 = block_sum(part, red);
-    if (threadIdx.x == 0) {
-      T alpha = cj[j];
-      if (s2 == T(0)) {
-        tau[j] = 0;
-        s_scale = 0;
-      } else {
-        T nrm = sqrt(alpha * alpha + s2);
-        T beta = alpha >= T(0) ? -nrm : nrm;
-        s_scale = T(1) / (alpha - beta);
-        tau[j] = (beta - alpha) / beta;
-        cj[j] = beta;
-      }
-    }
-    __syncthreads();
-    const T sc = s_scale;
-    if (sc != T(0))
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) cj[i] *= sc;
-    __syncthreads();
-    const T tj = tau[j];
-    if (tj == T(0)) continue;
-    for (int c0 = j + 1; c0 < w; c0 += 8) {
-      const int nc = min(8, w - c0);
-      T d[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) d[q] = 0;
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-        T v = cj[i];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nc) d[q] += v * S[i + (int64_t)(c0 + q) * m];
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        T x = warp_sum(d[q]);
-        if (lane == 0) s_part[warp][q] = x;
-      }
-      __syncthreads();
-      if (threadIdx.x < nc) {
-        T tot = S[j + (int64_t)(c0 + threadIdx.x) * m];
-        for (int w8 = 0; w8 < NT / 32; ++w8) tot += s_part[w8][threadIdx.x];
-        s_d[threadIdx.x] = tot * tj;
-      }
-      __syncthreads();
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-        T v = cj[i];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nc) S[i + (int64_t)(c0 + q) * m] -= s_d[q] * v;
-      }
-      if (threadIdx.x < nc) S[j + (int64_t)(c0 + threadIdx.x) * m] -= s_d[threadIdx.x];
-      __syncthreads();
-    }
-  }
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// O (m x r, column-major, ld) <- Q O, Q = H_0 ... H_{t-1}; CTA-wide per
-// reflector, output columns in groups of 8 (tall stacks).
+// Sum of products in twice the working precision: the Dot2 scheme of Ogita,
+// Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+// 2005).  The rounding error of each product comes from an FMA, that of each
+// addition from Knuth's TwoSum; the errors are summed separately.
+struct Dot2f {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float ep = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(es, ep));
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+struct Dot1d {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
 template <class T>
-__device__ void apply_q(const T* S, int m, int tmax, const T* tau, T* O, int64_t ld, int r) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ T s_d[8];
-  __shared__ T s_part[NT / 32][8];
-  for (int j = tmax - 1; j >= 0; --j) {
-    const T tj = tau[j];
-    if (tj == T(0)) continue;
-    const T* cj = S + (int64_t)j * m;
-    for (int c0 = 0; c0 < r; c0 += 8) {
-      const int nc = min(8, r - c0);
-      T d[8];
+struct AccurateDot;
+template <>
+struct AccurateDot<float> {
+  using type = Dot2f;
+};
+template <>
+struct AccurateDot<double> {
+  using type = Dot1d;
+};
+
+// Householder QR of S (m x w, column-major, ld m, private scratch) in place by
+// a group of NW warps (group thread gt in [0, 32 NW), named barrier `bar`).
+// Reflector j is I - tau_j v v^T with v = (1, S[j+1:m, j]) stored below the
+// diagonal; R is left on and above it.  Each warp owns trailing columns
+// j + 1 + warp + k NW and updates them without further synchronisation; the
+// owner of column j + 1 also leaves that column's new squared norm below the
+// diagonal in s2[j + 1], so one barrier per column suffices.  Column j is
+// scaled into its stored form one step later, when no warp reads it.
+template <class T, int NW>
+__device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int bar) {
+  constexpr int NTG = NW * 32;
+  const int wg = gt >> 5, lane = gt & 31;
+  const int tmax = min(m, w);
+  if (wg == 0) {
+    T s = 0;
+    for (int i = 1 + lane; i < m; i += 32) {
+      const T x = S[i];
+      s += x * x;
+    }
+    s = warp_sum(s);
+    if (lane == 0) s2[0] = s;
+  }
+  group_bar(bar, NTG);
+  T pbeta = 0, psc = 0;
+  for (int j = 0; j < tmax; ++j) {
+    T* cj = S + (int64_t)j * m;
+    if (j > 0) {
+      T* cp = cj - m;
+      for (int i = j + gt; i < m; i += NTG) cp[i] *= psc;
+      if (gt == 0) cp[j - 1] = pbeta;
+    }
+    const T ss = s2[j];
+    const T alpha = cj[j];
+    T beta = alpha, sc = 0, tj = 0;
+    if (ss > T(0)) {
+      const T nrm = sqrt(alpha * alpha + ss);
+      beta = alpha >= T(0) ? -nrm : nrm;
+      sc = T(1) / (alpha - beta);
+      tj = (beta - alpha) / beta;
+    }
+    if (gt == 0) tau[j] = tj;
+    for (int c0 = j + 1 + wg; c0 < w; c0 += 4 * NW) {
+      T* col[4];
+      T d[4], top[4];
+      int nc = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) d[q] = 0;
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-        T v = cj[i];
+      for (int q = 0; q < 4; ++q) {
+        const int cc = c0 + q * NW;
+        col[q] = S + (int64_t)(cc < w ? cc : c0) * m;
+        if (cc < w) nc = q + 1;
+        d[q] = 0;
+        top[q] = col[q][j];
+      }
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        const T v = cj[i];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nc) d[q] += v * __ldcg(O + i + (int64_t)(c0 + q) * ld);
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) d[q] += v * col[q][i];
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        T x = warp_sum(d[q]);
-        if (lane == 0) s_part[warp][q] = x;
-      }
-      __syncthreads();
-      if (threadIdx.x < nc) {
-        T tot = __ldcg(O + j + (int64_t)(c0 + threadIdx.x) * ld);
-        for (int w8 = 0; w8 < NT / 32; ++w8) tot += s_part[w8][threadIdx.x];
-        s_d[threadIdx.x] = tot * tj;
-      }
-      __syncthreads();
-      for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-        T v = cj[i];
+      for (int q = 0; q < 4; ++q) d[q] = (top[q] + sc * warp_sum(d[q])) * tj;
+      const bool own_next = c0 == j + 1;
+      T nn = 0;
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        const T v = cj[i] * sc;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < 4; ++q)
           if (q < nc) {
-            T* p = O + i + (int64_t)(c0 + q) * ld;
-            __stcg(p, __ldcg(p) - s_d[q] * v);
+            const T x = col[q][i] - d[q] * v;
+            col[q][i] = x;
+            if (q == 0 && i > j + 1) nn += x * x;
           }
       }
-      if (threadIdx.x < nc) {
-        T* p = O + j + (int64_t)(c0 + threadIdx.x) * ld;
-        __stcg(p, __ldcg(p) - s_d[threadIdx.x]);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) col[q][j] = top[q] - d[q];
+      if (own_next) {
+        nn = warp_sum(nn);
+        if (lane == 0) s2[j + 1] = nn;
       }
-      __syncthreads();
     }
+    pbeta = beta;
+    psc = sc;
+    group_bar(bar, NTG);
   }
+  {
+    T* cp = S + (int64_t)(tmax - 1) * m;
+    for (int i = tmax + gt; i < m; i += NTG) cp[i] *= psc;
+    if (gt == 0) cp[tmax - 1] = pbeta;
+  }
+  group_bar(bar, NTG);
 }
 
-// Householder QR of S (m x w, column-major, ld m) by one warp, no block
-// barriers: lanes stride over rows, columns are updated one after another.
-template <class T>
-__device__ void house_qr_warp(T* S, int m, int w, T* tau) {
-  const int lane = threadIdx.x & 31;
-  const int tmax = min(m, w);
-  for (int j = 0; j < tmax; ++j) {
-    T* cj = S + (int64_t)j * m;
-    T s2 = 0;
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      T x = cj[i];
-      s2 += x * x;
+// O (m x r, column-major, ld) <- Q O with Q = H_0 ... H_{tmax-1} from
+// house_qr_group; each warp of the group owns output columns and applies all
+// reflectors to them, four columns at a time.
+template <class T, int NW>
+__device__ void apply_q_group(const T* S, int m, int tmax, const T* tau, T* O, int64_t ld, int r, int gt) {
+  const int wg = gt >> 5, lane = gt & 31;
+  for (int c0 = wg; c0 < r; c0 += 4 * NW) {
+    T* col[4];
+    int nc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int cc = c0 + q * NW;
+      col[q] = O + (int64_t)(cc < r ? cc : c0) * ld;
+      if (cc < r) nc = q + 1;
     }
-    s2 = warp_sum(s2);
-    const T alpha = cj[j];
-    __syncwarp();
-    if (s2 == T(0)) {
-      if (lane == 0) tau[j] = 0;
-      __syncwarp();
-      continue;
-    }
-    const T nrm = sqrt(alpha * alpha + s2);
-    const T beta = alpha >= T(0) ? -nrm : nrm;
-    const T sc = T(1) / (alpha - beta);
-    const T tj = (beta - alpha) / beta;
-    for (int i = j + 1 + lane; i < m; i += 32) cj[i] *= sc;
-    if (lane == 0) {
-      cj[j] = beta;
-      tau[j] = tj;
-    }
-    __syncwarp();
-    for (int cc = j + 1; cc < w; ++cc) {
-      T* col = S + (int64_t)cc * m;
-      T d = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * col[i];
-      d = warp_sum(d);
-      d = (d + col[j]) * tj;
-      __syncwarp();
-      for (int i = j + 1 + lane; i < m; i += 32) col[i] -= d * cj[i];
-      if (lane == 0) col[j] -= d;
-      __syncwarp();
-    }
-  }
-}
-
-// O (m x r, column-major, ld) <- Q O, one warp per column (short stacks).
-template <class T>
-__device__ void apply_q_warp(const T* S, int m, int tmax, const T* tau, T* O, int64_t ld, int r, int warp0,
-                             int nwarps) {
-  const int warp = (threadIdx.x >> 5) - warp0, lane = threadIdx.x & 31;
-  if (warp < 0 || warp >= nwarps) return;
-  for (int cc = warp; cc < r; cc += nwarps) {
-    T* col = O + (int64_t)cc * ld;
     for (int j = tmax - 1; j >= 0; --j) {
       const T tj = tau[j];
       if (tj == T(0)) continue;
       const T* cj = S + (int64_t)j * m;
-      T d = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * __ldcg(col + i);
-      d = warp_sum(d);
-      d = (d + __ldcg(col + j)) * tj;
-      __syncwarp();
-      for (int i = j + 1 + lane; i < m; i += 32) __stcg(col + i, __ldcg(col + i) - d * cj[i]);
-      if (lane == 0) __stcg(col + j, __ldcg(col + j) - d);
+      T d[4], top[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        d[q] = 0;
+        top[q] = col[q][j];
+      }
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        const T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) d[q] += v * col[q][i];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d[q] = (top[q] + warp_sum(d[q])) * tj;
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        const T v = cj[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) col[q][i] -= d[q] * v;
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) col[q][j] = top[q] - d[q];
       __syncwarp();
     }
   }
 }
 
-// stacked factors up to this many rows use the warp-level QR and apply
-constexpr int kWarpQrRows = 768;
-constexpr int kStackCols = kTruncStack;
-// a stack wider than this is compressed before the next piece is added
-// (Jacobi cost grows with the cube of the width); rank cap 32 + a 64-wide
-// piece still fit the stack
-constexpr int kCompressAt = 48;
-
-// Truncated SVD of the stacked factors SX (m x W) and SY (n x W) in compute
-// type TC: QR of both, one-sided Jacobi SVD of the core R_x R_y^T, keep
-// s_i > eps s_1 (at most cap); X <- Q_x U_r S_r and Y <- Q_y V_r are written
-// to OX (ld ox) and OY (ld oy).  Workspace: tauX, tauY, sv (kStackCols each)
-// and G, V (kStackCols^2 each), in shared or global memory.  Returns r (the
-// same in every thread); *fro receives ||X Y^T||_F.
-template <class TC>
-__device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, double eps, TC* tauX, TC* tauY,
-                             TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
-                             double* flops, double* fro) {
+// One-sided Jacobi SVD of G (p x q, column-major, ld p, shared memory):
+// G <- G V with V (q x q, ld q, starts as I) accumulating the rotations,
+// until all column pairs are orthogonal to `tol` or the sweeps stop making
+// progress at the rounding floor.  A round-robin round has qq/2 disjoint
+// pairs (qq = q rounded up to even); each pair is handled by a group of gs
+// lanes.  nrm2 holds the squared column norms: recomputed at the start of a
+// sweep, updated by each rotation (a' = a - t g, b' = b + t g), and exact
+// again on return.
+template <class T>
+__device__ void jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol) {
   __shared__ int s_rot;
-  __shared__ int s_r;
-  __shared__ int s_ord[kStackCols];
-  __shared__ TC s_red[NT / 32];
-  __shared__ double s_fro;
   __shared__ float s_off, s_prev;
-  const bool small = max(m, n) <= kWarpQrRows;
-  if (small) {
-    const int wq = threadIdx.x >> 5;
-    if (wq == 0) house_qr_warp(SX, m, W, tauX);
-    if (wq == 1) house_qr_warp(SY, n, W, tauY);
-    __syncthreads();
-  } else {
-    house_qr(SX, m, W, tauX, s_red);
-    house_qr(SY, n, W, tauY, s_red);
-  }
-  const int p = min(m, W), q = min(n, W);
-  // the core is accumulated in FP64: the target and its updates cancel inside
-  // this sum, and FP32 accumulation there costs the truncation its accuracy
-  for (int idx = threadIdx.x; idx < p * q; idx += NT) {
-    int i = idx % p, j = idx / p;
-    double acc = 0;
-    for (int l = max(i, j); l < W; ++l) acc += (double)SX[i + (int64_t)l * m] * (double)SY[j + (int64_t)l * n];
-    G[i + j * p] = (TC)acc;
-  }
-  for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? TC(1) : TC(0);
-  __syncthreads();
-  // stop when every pair is orthogonal to tol, or when a sweep no longer
-  // reduces the largest off-diagonal measure while it is already small (the
-  // rounding floor)
-  const TC tol = sizeof(TC) == 4 ? TC(1e-6) : TC(1e-14);
-  const int qq = q + (q & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int qq = q + (q & 1);
+  const int npairs = qq / 2;
+  int gs = 32;
+  while (gs > 1 && npairs * gs > NT) gs >>= 1;
+  const int k = threadIdx.x / gs, lg = threadIdx.x % gs;
+  auto norms = [&]() {
+    for (int j = warp; j < q; j += NT / 32) {
+      T acc = 0;
+      for (int i = lane; i < p; i += 32) acc += G[i + j * p] * G[i + j * p];
+      acc = warp_sum(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
+  };
   if (threadIdx.x == 0) s_prev = 3.0e38f;
   for (int sweep = 0; sweep < 20 && qq > 1; ++sweep) {
+    norms();
     if (threadIdx.x == 0) {
       s_rot = 0;
       s_off = 0.0f;
     }
     __syncthreads();
     for (int rd = 0; rd < qq - 1; ++rd) {
-      for (int k = warp; k < qq / 2; k += NT / 32) {
-        int pa = k == 0 ? 0 : ((k - 1 + rd) % (qq - 1)) + 1;
-        int kb = qq - 1 - k;
-        int pb = kb == 0 ? 0 : ((kb - 1 + rd) % (qq - 1)) + 1;
-        int a = min(pa, pb), b = max(pa, pb);
-        if (b >= q) continue;
-        TC al = 0, be = 0, ga = 0;
-        for (int i = lane; i < p; i += 32) {
-          TC x = G[i + a * p], y = G[i + b * p];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
+      int a = 0, b = 0;
+      bool act = k < npairs;
+      if (act) {
+        const int pa = k == 0 ? 0 : ((k - 1 + rd) % (qq - 1)) + 1;
+        const int kb = qq - 1 - k;
+        const int pb = kb == 0 ? 0 : ((kb - 1 + rd) % (qq - 1)) + 1;
+        a = min(pa, pb);
+        b = max(pa, pb);
+        act = b < q;
+      }
+      T ga = 0;
+      if (act)
+        for (int i = lg; i < p; i += gs) ga += G[i + a * p] * G[i + b * p];
+      for (int o = gs >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      if (act && ga != T(0)) {
+        const T al = nrm2[a], be = nrm2[b];
+        const T ratio = fabs(ga) / sqrt(al * be);
+        if (lg == 0) atomicMax(reinterpret_cast<int*>(&s_off), __float_as_int((float)ratio));
+        if (ratio > tol) {
+          const T zeta = (be - al) / (T(2) * ga);
+          const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
+          for (int i = lg; i < p; i += gs) {
+            const T x = G[i + a * p], y = G[i + b * p];
+            G[i + a * p] = cs * x - sn * y;
+            G[i + b * p] = sn * x + cs * y;
+          }
+          for (int i = lg; i < q; i += gs) {
+            const T x = V[i + a * q], y = V[i + b * q];
+            V[i + a * q] = cs * x - sn * y;
+            V[i + b * q] = sn * x + cs * y;
+          }
+          if (lg == 0) {
+            nrm2[a] = al - tt * ga;
+            nrm2[b] = be + tt * ga;
+            s_rot = 1;
+          }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == TC(0)) continue;
-        const TC ratio = fabs(ga) / sqrt(al * be);
-        if (lane == 0) atomicMax(reinterpret_cast<int*>(&s_off), __float_as_int((float)ratio));
-        if (ratio <= tol) continue;
-        TC zeta = (be - al) / (TC(2) * ga);
-        TC tt = (zeta >= TC(0) ? TC(1) : TC(-1)) / (fabs(zeta) + sqrt(TC(1) + zeta * zeta));
-        TC cs = TC(1) / sqrt(TC(1) + tt * tt), sn = cs * tt;
-        for (int i = lane; i < p; i += 32) {
-          TC x = G[i + a * p], y = G[i + b * p];
-          G[i + a * p] = cs * x - sn * y;
-          G[i + b * p] = sn * x + cs * y;
-        }
-        for (int i = lane; i < q; i += 32) {
-          TC x = V[i + a * q], y = V[i + b * q];
-          V[i + a * q] = cs * x - sn * y;
-          V[i + b * q] = sn * x + cs * y;
-        }
-        if (lane == 0) s_rot = 1;
       }
       __syncthreads();
     }
@@ -698,16 +675,52 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
     if (stalled) break;
     __syncthreads();
   }
-  for (int j = warp; j < q; j += NT / 32) {
-    TC acc = 0;
-    for (int i = lane; i < p; i += 32) acc += G[i + j * p] * G[i + j * p];
-    acc = warp_sum(acc);
-    if (lane == 0) sv[j] = sqrt(acc);
-  }
+  norms();
   __syncthreads();
+}
+
+// stack width at which a truncation compresses before adding the next piece
+// (the core SVD costs grow with the cube of the width); rank cap 32 + a
+// 64-wide piece still fit the stack
+constexpr int kStackCols = kTruncStack;
+constexpr int kCompressAt = 48;
+
+// Truncated SVD of the stacked factors SX (m x W) and SY (n x W) in compute
+// type TC: Householder QR of both (concurrently, half of the CTA each), the
+// core R_x R_y^T accumulated in twice the working precision, its one-sided
+// Jacobi SVD, keep s_i > eps s_1 (at most cap); X <- Q_x U_r S_r and
+// Y <- Q_y V_r are written to OX (ld ox) and OY (ld oy).  Workspace: tauX,
+// tauY, sv (kStackCols each) and G, V (kStackCols^2 each) in shared memory.
+// Returns r (the same in every thread); *fro receives ||X Y^T||_F.
+template <class TC>
+__device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, double eps, TC* tauX, TC* tauY,
+                             TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
+                             double* flops, double* fro) {
+  __shared__ TC s2x[kStackCols + 1], s2y[kStackCols + 1];
+  __shared__ int s_r;
+  __shared__ int s_ord[kStackCols];
+  __shared__ double s_fro;
+  constexpr int kHalf = NT / 2;
+  if (threadIdx.x < kHalf)
+    house_qr_group<TC, kHalf / 32>(SX, m, W, tauX, s2x, threadIdx.x, 1);
+  else
+    house_qr_group<TC, kHalf / 32>(SY, n, W, tauY, s2y, threadIdx.x - kHalf, 2);
+  __syncthreads();
+  const int p = min(m, W), q = min(n, W);
+  // the core R_x R_y^T: the target and its updates cancel inside these sums
+  for (int idx = threadIdx.x; idx < p * q; idx += NT) {
+    const int i = idx % p, j = idx / p;
+    typename AccurateDot<TC>::type acc;
+    for (int l = max(i, j); l < W; ++l) acc.add(SX[i + (int64_t)l * m], SY[j + (int64_t)l * n]);
+    G[i + j * p] = acc.value();
+  }
+  for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? TC(1) : TC(0);
+  __syncthreads();
+  jacobi_svd(G, V, p, q, sv, sizeof(TC) == 4 ? TC(1e-6) : TC(1e-14));
   if (threadIdx.x == 0) {
     double f2 = 0;
     for (int j = 0; j < q; ++j) {
+      sv[j] = sqrt(sv[j]);
       s_ord[j] = j;
       f2 += (double)sv[j] * (double)sv[j];
     }
@@ -735,21 +748,18 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   const int r = s_r;
   *fro = s_fro;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) {
-    int i = (int)(idx % m), j = (int)(idx / m);
-    __stcg(OX + i + (int64_t)j * ox, i < p ? G[i + s_ord[j] * p] : TC(0));
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    OX[i + (int64_t)j * ox] = i < p ? G[i + s_ord[j] * p] : TC(0);
   }
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) {
-    int i = (int)(idx % n), j = (int)(idx / n);
-    __stcg(OY + i + (int64_t)j * oy, i < q ? V[i + s_ord[j] * q] : TC(0));
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    OY[i + (int64_t)j * oy] = i < q ? V[i + s_ord[j] * q] : TC(0);
   }
   __syncthreads();
-  if (small) {
-    apply_q_warp(SX, m, min(m, W), tauX, OX, ox, r, 0, NT / 64);
-    apply_q_warp(SY, n, min(n, W), tauY, OY, oy, r, NT / 64, NT / 64);
-  } else {
-    apply_q(SX, m, min(m, W), tauX, OX, ox, r);
-    apply_q(SY, n, min(n, W), tauY, OY, oy, r);
-  }
+  if (threadIdx.x < kHalf)
+    apply_q_group<TC, kHalf / 32>(SX, m, p, tauX, OX, ox, r, threadIdx.x);
+  else
+    apply_q_group<TC, kHalf / 32>(SY, n, q, tauY, OY, oy, r, threadIdx.x - kHalf);
   __syncthreads();
   return r;
 }
@@ -850,7 +860,6 @@ template <class T>
 __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int64_t s_task;
-  __shared__ int s_skip;
   __shared__ int s_prob;
   Ctx<T> c;
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
@@ -860,57 +869,49 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
   __shared__ unsigned long long s_prof[TK_NUM + 1][3];  // count, wait cycles, run cycles
   if (threadIdx.x < (TK_NUM + 1) * 3) (&s_prof[0][0])[threadIdx.x] = 0ULL;
   long long t_begin = 0, t_waited = 0;
+  unsigned long long g_begin = 0, g_waited = 0;
+  int64_t slot_cur = 0;
+  volatile int32_t* abort_flag = (volatile int32_t*)a.status + 3;
   for (;;) {
+    // claim the next queue slot and wait (bounded) until a finished task
+    // pushes a ready task into it
     if (threadIdx.x == 0) {
-      const int64_t tk = (int64_t)atomicAdd(a.ticket, 1ULL);
-      if (tk >= a.ntotal) {
-        s_task = -1;
-      } else if (a.order) {
-        const int64_t code = a.order[tk];
-        s_prob = (int)(code >> 40);
-        s_task = code & ((int64_t(1) << 40) - 1);
-      } else {
-        s_prob = 0;
-        s_task = tk;
-      }
       t_begin = clock64();
+      if (a.trace) g_begin = gtimer();
+      const int64_t k = (int64_t)atomicAdd(a.qctl, 1ULL);
+      slot_cur = k;
+      s_task = -1;
+      if (k < a.ntotal && !*abort_flag) {
+        unsigned long long v = ld_acquire_u64(a.queue + k);
+        if (!v) {
+          const uint64_t t0 = gtimer();
+          for (;;) {
+            __nanosleep(32);
+            v = ld_acquire_u64(a.queue + k);
+            if (v || *abort_flag) break;
+            if (gtimer() - t0 > a.wait_limit_ns) {
+              atomicCAS(a.status, 0, 5);
+              atomicCAS(a.status + 1, -1, (int32_t)k);
+              *abort_flag = 1;
+              break;
+            }
+          }
+        }
+        if (v) {
+          const unsigned long long code = v - 1ULL;
+          s_prob = (int)(code >> 40);
+          s_task = (int64_t)(code & ((1ULL << 40) - 1ULL));
+        }
+      }
+      t_waited = clock64();
+      if (a.trace) g_waited = gtimer();
     }
     __syncthreads();
     const int64_t ti = s_task;
     if (ti < 0) break;
     const ProbSched& P = a.probs[s_prob];
-    // wait for the predecessors (lanes of warp 0 in parallel, bounded)
-    if (threadIdx.x < 32) {
-      int bad = 0;
-      const int64_t e0 = P.pred_ptr[ti], e1 = P.pred_ptr[ti + 1];
-      for (int64_t e = e0 + threadIdx.x; e < e1; e += 32) {
-        const int32_t* flag = P.done + P.pred_idx[e];
-        if (ld_acquire(flag) == P.epoch) continue;
-        const uint64_t t0 = gtimer();
-        for (;;) {
-          if (ld_acquire(flag) == P.epoch) break;
-          if (*((volatile int32_t*)a.status + 3)) {
-            bad = 1;
-            break;
-          }
-          if (gtimer() - t0 > a.wait_limit_ns) {
-            atomicCAS(a.status, 0, 5);
-            atomicCAS(a.status + 1, -1, (int32_t)ti);
-            *((volatile int32_t*)a.status + 3) = 1;
-            bad = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      bad = __any_sync(0xffffffffu, bad);
-      if (threadIdx.x == 0) s_skip = bad || *((volatile int32_t*)a.status + 3);
-      __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) t_waited = clock64();
     const int ttype = P.tasks[ti].type;
-    if (!s_skip && ttype >= 0 && ttype < TK_NUM) {
+    if (ttype >= 0 && ttype < TK_NUM) {
       const Task t = P.tasks[ti];
       c.arena = reinterpret_cast<T*>(P.arena);
       c.ranks = P.ranks;
@@ -933,8 +934,39 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     }
     __threadfence();
     __syncthreads();
+    // release the successors: the last predecessor to finish pushes a task
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int64_t e0 = P.succ_ptr[ti], e1 = P.succ_ptr[ti + 1];
+      for (int64_t eb = e0; eb < e1; eb += 32) {
+        const int64_t e = eb + lane;
+        bool push = false;
+        int32_t sx = 0;
+        if (e < e1) {
+          sx = P.succ_idx[e];
+          if (sx < P.limit) push = atomicSub(P.indeg + sx, 1) == 1;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, push);
+        if (mask) {
+          __threadfence();
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(a.qctl + 1, (unsigned long long)__popc(mask));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (push) {
+            const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+            st_release_u64(a.queue + slot, ((((unsigned long long)s_prob) << 40) | (unsigned long long)sx) + 1ULL);
+          }
+        }
+      }
+    }
     if (threadIdx.x == 0) {
-      st_release(P.done + ti, P.epoch);
+      if (a.trace) {
+        unsigned long long* tr = a.trace + 4 * slot_cur;
+        tr[0] = ((unsigned long long)s_prob << 40) | (unsigned long long)ti;
+        tr[1] = g_begin;
+        tr[2] = g_waited;
+        tr[3] = gtimer();
+      }
       if (a.prof) {
         const int k = (ttype >= 0 && ttype < TK_NUM) ? ttype : TK_NUM;
         long long t_end = clock64();
@@ -943,6 +975,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
         s_prof[k][2] += (unsigned long long)(t_end - t_waited);
       }
     }
+    __syncthreads();
   }
   if (threadIdx.x == 0 && a.flops) atomicAdd(a.flops, c.flops);
   if (a.prof && threadIdx.x < (TK_NUM + 1) * 3) {

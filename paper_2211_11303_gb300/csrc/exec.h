@@ -8,39 +8,41 @@
 
 namespace hlu {
 
-// One problem's schedule and data as seen by the executor.
+// One problem's schedule and data as seen by the executor.  Tasks become
+// ready when their last predecessor finishes (dependency counters), and ready
+// tasks are handed out through a FIFO queue shared by all problems of a launch.
 struct ProbSched {
   const Task* tasks;
   const Term* terms;
   const Piece* pieces;
-  const int64_t* pred_ptr;  // ntasks + 1
-  const int32_t* pred_idx;
-  int32_t* done;            // completion epoch per task
+  const int64_t* succ_ptr;  // ntasks + 1
+  const int32_t* succ_idx;
+  int32_t* indeg;           // unfinished predecessors (reset before every launch)
   void* arena;
   int32_t* ranks;
   int32_t* piv;
   double eps;
   int64_t ntasks;
-  int32_t epoch;            // value published on completion in this launch
-  int32_t pad;
+  int64_t limit;            // tasks with index >= limit are not run
 };
 constexpr int kMaxBatch = 64;  // problems in one launch
 
 struct ExecArgs {
   ProbSched probs[kMaxBatch];
   int32_t nprobs;
-  // ticket -> (problem << 40 | task) for batched launches; null: problem 0,
-  // task = ticket.  Within a problem the order is increasing.
-  const int64_t* order;
-  int64_t ntotal;               // tickets handed out in this launch
-  unsigned long long* ticket;   // next ticket (zeroed before the launch)
+  int64_t ntotal;               // tasks run in this launch (= queue slots)
+  // ready queue: slot k holds (problem << 40 | task) + 1 once pushed, 0 before;
+  // qctl[0] = next slot to claim, qctl[1] = next slot to fill
+  unsigned long long* queue;
+  unsigned long long* qctl;
   void* scratch;                // per-CTA scratch, scratch_stride elements each
   int64_t scratch_stride;
   int64_t trunc_rows;           // rows of the truncation stacks in the scratch
-  int32_t* status;              // [0] status code, [1] failing task, [2] rank-cap hits, [3] abort
+  int32_t* status;              // [0] status code, [1] failing slot, [2] rank-cap hits, [3] abort
   double* flops;                // accumulated algorithmic flops (may be null)
   unsigned long long wait_limit_ns;
   unsigned long long* prof;     // optional [(TK_NUM + 1) x 3]: tasks, wait cycles, run cycles per kind
+  unsigned long long* trace;    // optional [ntotal x 4] per slot: (problem << 40 | task), claim, start, end (ns)
 };
 
 size_t exec_smem_bytes(int elem_size);

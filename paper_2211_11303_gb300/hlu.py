@@ -91,6 +91,7 @@ SIGNATURES = {
                                             ctypes.c_uint64, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
     "hlu_debug_factor_prefix": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "hlu_debug_task_record": (_i32, [_vp, _i64, _vp]),
+    "hlu_debug_factor_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
 }
 
 

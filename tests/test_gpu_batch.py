@@ -24,7 +24,9 @@ def hlu():
 
 def _rhs(N, nrhs, seed):
     B = np.stack([synth.normal(seed + j, N) for j in range(nrhs)], axis=1)
-    return torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    out = torch.empty((nrhs, N), dtype=torch.float64, device="cuda").t()  # column-major, ld = N
+    out.copy_(torch.from_numpy(B))
+    return out
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

@@ -1,0 +1,94 @@
+"""Continuous batching of GMRES solves through the C ABI: requests that join a
+running batch, share factors and leave at different steps must each get the
+result they get when solved alone (one request in the batch)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10          # GMRES tolerance of every request
+MIX_VS_ALONE = 1e-9  # ||x_mix - x_alone|| / ||x_alone||
+
+
+@pytest.fixture(scope="module")
+def hlu():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2211_11303_gb300 import hlu as H
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    H.hlu_set_wait_limit_ms(20000)
+    return H
+
+
+def _rhs(N, nrhs, seed):
+    B = np.stack([synth.normal(seed + j, N) for j in range(nrhs)], axis=1)
+    out = torch.empty((nrhs, N), dtype=torch.float64, device="cuda").t()  # column-major, ld = N
+    out.copy_(torch.from_numpy(B))
+    return out
+
+
+def _run(H, reqs, join_at):
+    """reqs: (handle, b); request i joins at step join_at[i]; returns xs, stats."""
+    xs = [H.colmajor(H.hlu_n(h), b.shape[1]) for h, b in reqs]
+    states = [None] * len(reqs)
+    done = [False] * len(reqs)
+    stats = [None] * len(reqs)
+    step = 0
+    try:
+        while not all(done):
+            for i, (h, b) in enumerate(reqs):
+                if states[i] is None and join_at[i] <= step:
+                    states[i] = H.hlu_gmres_begin(h, b, xs[i], restart=50, tol=TOL, maxit=500)
+            act = [g for i, g in enumerate(states) if g is not None and not done[i]]
+            if act:
+                H.hlu_gmres_step_batch(act)
+            for i, g in enumerate(states):
+                if g is not None and not done[i]:
+                    d, st = H.hlu_gmres_status(g)
+                    if d:
+                        done[i] = True
+                        stats[i] = st
+            step += 1
+            assert step < 2000
+    finally:
+        for g in states:
+            if g is not None:
+                H.hlu_gmres_end(g)
+    torch.cuda.synchronize()
+    return xs, stats
+
+
+def test_mix_equals_alone(hlu):
+    specs = [(4, 2.0), (5, 6.0), (6, 9.0)]
+    hs = []
+    try:
+        for n, k in specs:
+            h = hlu.hlu_build(n, k, 16, 2.0, 1e-4)
+            hlu.hlu_factor(h, hlu.HLU_FP32)
+            hs.append(h)
+        # requests: (handle index, nrhs); two share handle 0 and two handle 2
+        rq = [(0, 2), (1, 1), (0, 3), (2, 5), (2, 16), (1, 4)]
+        reqs = [(hs[i], _rhs(hlu.hlu_n(hs[i]), nr, 7000 + 16 * j)) for j, (i, nr) in enumerate(rq)]
+        mix, st_mix = _run(hlu, reqs, [0, 0, 1, 2, 2, 5])
+        for j, (h, b) in enumerate(reqs):
+            alone, st_alone = _run(hlu, [(h, b)], [0])
+            assert st_mix[j]["converged"] and st_alone[0]["converged"]
+            err = torch.linalg.norm(mix[j] - alone[0]) / torch.linalg.norm(alone[0])
+            assert err <= MIX_VS_ALONE, (j, float(err))
+            # and against the lockstep solver of a single request
+            ref = hlu.colmajor(hlu.hlu_n(h), b.shape[1])
+            hlu.gmres_solve(h, b, ref, restart=50, tol=TOL, maxit=500)
+            err2 = torch.linalg.norm(mix[j] - ref) / torch.linalg.norm(ref)
+            assert err2 <= MIX_VS_ALONE, (j, float(err2))
+            # true residual of the served result
+            r = hlu.colmajor(hlu.hlu_n(h), b.shape[1])
+            hlu.hlu_spmv(h, mix[j], r)
+            rel = torch.linalg.norm(r - b, dim=0) / torch.linalg.norm(b, dim=0)
+            assert float(rel.max()) <= 10 * TOL
+    finally:
+        for h in hs:
+            hlu.hlu_destroy(h)

@@ -161,7 +161,11 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
  * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for
  * predecessors, out[3*k + 2] cycles spent running, summed over CTAs; kinds
  * k = 0..8 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD, RSOLVE
- * and k = 9 the no-work fences.  out: uint64[30] host buffer. */
+ * and k = 9 the no-work fences; then the truncation phases summed over all
+ * compressions: out[30] (unused), out[31] QR cycles, out[32] core product,
+ * out[33] Jacobi SVD, out[34] selection and Q application, out[35]
+ * compressions, out[36] Jacobi sweeps, out[37] summed stack widths.
+ * out: uint64[38] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
@@ -183,6 +187,18 @@ int hlu_solve(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t n
 int gmres_solve(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
                 int32_t restart, double tol, int32_t maxit, int32_t flexible, hlu_stats* stats,
                 void* stream);
+
+/* hlu_set_trunc_params - tuning of the recompression (Sec. 3: QR of both
+ * stacked factors, SVD of the small core, keep s_i > eps s_1).  A target's
+ * pieces are stacked and compressed whenever the stack would grow past
+ * compress_at columns (8..96; 0 restores the default 48).  jacobi_tol is the
+ * orthogonality tolerance |a^T b| <= tol ||a|| ||b|| at which the one-sided
+ * Jacobi SVD of the core stops (0 restores the default: 1e-6 for FP32
+ * factors, 1e-14 for FP64).  The truncation error is the norm of the
+ * discarded columns whatever the tolerance; a looser one can only raise the
+ * kept rank.  Process-wide; applies to factorisations started afterwards.
+ * Returns HLU_ERR_ARG for values out of range. */
+int hlu_set_trunc_params(int32_t compress_at, double jacobi_tol);
 
 /* Continuous batching of GMRES solves (serving).  A hlu_gmres state holds
  * one request's restarted flexible GMRES (same method as gmres_solve; at most

@@ -34,6 +34,8 @@ namespace {
 
 thread_local std::string g_err;
 double g_wait_limit_ms = 20000.0;
+double g_jacobi_tol = 0.0;  // 0: default of the factor precision
+int32_t g_compress_at = 0;  // 0: default
 int32_t g_tile = 64;
 
 int fail(int code, const std::string& msg) {
@@ -290,6 +292,8 @@ void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool wi
   a.status = h0->d_status;
   a.flops = with_flops ? h0->d_flops : nullptr;
   a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  a.jacobi_tol = g_jacobi_tol;
+  a.compress_at = g_compress_at;
   a.prof = with_flops ? h0->d_prof : nullptr;
   a.trace = with_flops ? h0->d_trace : nullptr;
 }
@@ -791,7 +795,7 @@ static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
     CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
     CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 8), "status");
     CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
-    CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * (TK_NUM + 1) * 3), "prof");
+    CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * kProfEntries), "prof");
     h->precision = precision;
   }
   CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
@@ -811,7 +815,7 @@ static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
   int rc = read_status(h, s, stf);
   if (rc) return rc;
   CKR(cudaMemsetAsync(h->d_flops, 0, sizeof(double), s), "flops");
-  CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * (TK_NUM + 1) * 3, s), "prof");
+  CKR(cudaMemsetAsync(h->d_prof, 0, sizeof(unsigned long long) * kProfEntries, s), "prof");
   return HLU_OK;
 }
 
@@ -866,7 +870,7 @@ static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t l
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out) {
   if (!h || !out) return fail(HLU_ERR_ARG, "null argument");
   if (!h->d_prof) return fail(HLU_ERR_STATE, "not factored");
-  CKR(cudaMemcpy(out, h->d_prof, sizeof(uint64_t) * (TK_NUM + 1) * 3, cudaMemcpyDeviceToHost), "profile");
+  CKR(cudaMemcpy(out, h->d_prof, sizeof(uint64_t) * kProfEntries, cudaMemcpyDeviceToHost), "profile");
   return HLU_OK;
 }
 
@@ -1055,6 +1059,14 @@ int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b
 // task 0 waits for task 1, run by a single CTA.  Task 1 can only start after
 // task 0, so the wait can never be satisfied; it must run out after limit_ms,
 // set HLU_ERR_TIMEOUT and let the kernel return.
+extern "C" int hlu_set_trunc_params(int32_t compress_at, double jacobi_tol) {
+  if (compress_at != 0 && (compress_at < 8 || compress_at > kTruncStack)) return fail(HLU_ERR_ARG, "compress_at");
+  if (jacobi_tol < 0 || jacobi_tol >= 1) return fail(HLU_ERR_ARG, "jacobi_tol");
+  g_compress_at = compress_at;
+  g_jacobi_tol = jacobi_tol;
+  return HLU_OK;
+}
+
 extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   if (!status_out || !(limit_ms > 0) || limit_ms > 5000) return fail(HLU_ERR_ARG, "bad argument");
   Schedule S;

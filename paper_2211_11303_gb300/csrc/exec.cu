@@ -62,6 +62,9 @@ struct Ctx {
   double eps;
   int32_t* status;
   double flops;
+  unsigned long long* tprof;  // truncation phase profile (shared memory) or null
+  double jacobi_tol;
+  int32_t compress_at;
 };
 
 template <class T>
@@ -601,9 +604,10 @@ __device__ void apply_q_group(const T* S, int m, int tmax, const T* tau, T* O, i
 // sweep, updated by each rotation (a' = a - t g, b' = b + t g), and exact
 // again on return.
 template <class T>
-__device__ void jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol) {
+__device__ int jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol, T negl_rel) {
   __shared__ int s_rot;
   __shared__ float s_off, s_prev;
+  __shared__ T s_negl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qq = q + (q & 1);
   const int npairs = qq / 2;
@@ -619,11 +623,16 @@ __device__ void jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol) {
     }
   };
   if (threadIdx.x == 0) s_prev = 3.0e38f;
-  for (int sweep = 0; sweep < 20 && qq > 1; ++sweep) {
+  int sweep = 0;
+  for (; sweep < 20 && qq > 1; ++sweep) {
     norms();
+    __syncthreads();
     if (threadIdx.x == 0) {
       s_rot = 0;
       s_off = 0.0f;
+      T mx = 0;
+      for (int j = 0; j < q; ++j) mx = max(mx, nrm2[j]);
+      s_negl = negl_rel * negl_rel * mx;
     }
     __syncthreads();
     for (int rd = 0; rd < qq - 1; ++rd) {
@@ -637,6 +646,10 @@ __device__ void jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol) {
         b = max(pa, pb);
         act = b < q;
       }
+      // a column far below the truncation level is discarded whatever the
+      // rotations do (they never raise the smaller norm of a pair), so
+      // pairs involving one are skipped
+      if (act) act = min(nrm2[a], nrm2[b]) > s_negl;
       T ga = 0;
       if (act)
         for (int i = lg; i < p; i += gs) ga += G[i + a * p] * G[i + b * p];
@@ -677,6 +690,7 @@ __device__ void jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol) {
   }
   norms();
   __syncthreads();
+  return sweep + 1;
 }
 
 // stack width at which a truncation compresses before adding the next piece
@@ -695,8 +709,16 @@ constexpr int kCompressAt = 48;
 template <class TC>
 __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, double eps, TC* tauX, TC* tauY,
                              TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
-                             double* flops, double* fro) {
+                             double* flops, double* fro, unsigned long long* tp, double jtol) {
   __shared__ TC s2x[kStackCols + 1], s2y[kStackCols + 1];
+  long long t0 = tp && threadIdx.x == 0 ? clock64() : 0;
+  auto lap = [&](int k) {
+    if (tp && threadIdx.x == 0) {
+      const long long t1 = clock64();
+      tp[k] += (unsigned long long)(t1 - t0);
+      t0 = t1;
+    }
+  };
   __shared__ int s_r;
   __shared__ int s_ord[kStackCols];
   __shared__ double s_fro;
@@ -706,6 +728,7 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   else
     house_qr_group<TC, kHalf / 32>(SY, n, W, tauY, s2y, threadIdx.x - kHalf, 2);
   __syncthreads();
+  lap(1);
   const int p = min(m, W), q = min(n, W);
   // the core R_x R_y^T: the target and its updates cancel inside these sums
   for (int idx = threadIdx.x; idx < p * q; idx += NT) {
@@ -716,7 +739,14 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   }
   for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? TC(1) : TC(0);
   __syncthreads();
-  jacobi_svd(G, V, p, q, sv, sizeof(TC) == 4 ? TC(1e-6) : TC(1e-14));
+  lap(2);
+  const int sweeps = jacobi_svd(G, V, p, q, sv, TC(jtol), TC(0.01 * eps));
+  lap(3);
+  if (tp && threadIdx.x == 0) {
+    tp[5] += 1ULL;
+    tp[6] += (unsigned long long)sweeps;
+    tp[7] += (unsigned long long)W;
+  }
   if (threadIdx.x == 0) {
     double f2 = 0;
     for (int j = 0; j < q; ++j) {
@@ -761,6 +791,7 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   else
     apply_q_group<TC, kHalf / 32>(SY, n, q, tauY, OY, oy, r, threadIdx.x - kHalf);
   __syncthreads();
+  lap(4);
   return r;
 }
 
@@ -790,11 +821,11 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
     const Piece& P = c.pieces[t.list_begin + q];
     const int w = ncols(c, P.X);
     if (w == 0) continue;
-    if (W > 0 && W + w > kCompressAt) {
+    if (W > 0 && W + w > c.compress_at) {
       const double in = stack_norm(W);
       double fro = 0;
       const int r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits,
-                                  &c.flops, &fro);
+                                  &c.flops, &fro, c.tprof, c.jacobi_tol);
       if (fro > 0) worst = fmax(worst, in / fro);
       for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) SX[idx] = __ldcg(OX + idx);
       for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) SY[idx] = __ldcg(OY + idx);
@@ -820,7 +851,7 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
   if (W > 0) {
     const double in = stack_norm(W);
     double fro = 0;
-    r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits, &c.flops, &fro);
+    r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits, &c.flops, &fro, c.tprof, c.jacobi_tol);
     if (fro > 0) worst = fmax(worst, in / fro);
   }
   *ratio = worst;
@@ -866,8 +897,11 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
   c.rows_max = a.trunc_rows;
   c.status = a.status;
   c.flops = 0;
-  __shared__ unsigned long long s_prof[TK_NUM + 1][3];  // count, wait cycles, run cycles
-  if (threadIdx.x < (TK_NUM + 1) * 3) (&s_prof[0][0])[threadIdx.x] = 0ULL;
+  __shared__ unsigned long long s_prof[kProfEntries];
+  if (threadIdx.x < kProfEntries) s_prof[threadIdx.x] = 0ULL;
+  c.tprof = a.prof ? s_prof + kProfTrunc : nullptr;
+  c.jacobi_tol = a.jacobi_tol > 0 ? a.jacobi_tol : (sizeof(T) == 4 ? 1e-6 : 1e-14);
+  c.compress_at = a.compress_at >= 8 && a.compress_at <= kStackCols ? a.compress_at : kCompressAt;
   long long t_begin = 0, t_waited = 0;
   unsigned long long g_begin = 0, g_waited = 0;
   int64_t slot_cur = 0;
@@ -970,16 +1004,16 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
       if (a.prof) {
         const int k = (ttype >= 0 && ttype < TK_NUM) ? ttype : TK_NUM;
         long long t_end = clock64();
-        s_prof[k][0] += 1ULL;
-        s_prof[k][1] += (unsigned long long)(t_waited - t_begin);
-        s_prof[k][2] += (unsigned long long)(t_end - t_waited);
+        s_prof[3 * k + 0] += 1ULL;
+        s_prof[3 * k + 1] += (unsigned long long)(t_waited - t_begin);
+        s_prof[3 * k + 2] += (unsigned long long)(t_end - t_waited);
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0 && a.flops) atomicAdd(a.flops, c.flops);
-  if (a.prof && threadIdx.x < (TK_NUM + 1) * 3) {
-    unsigned long long v = (&s_prof[0][0])[threadIdx.x];
+  if (a.prof && threadIdx.x < kProfEntries) {
+    unsigned long long v = s_prof[threadIdx.x];
     if (v) atomicAdd(a.prof + threadIdx.x, v);
   }
 }

@@ -26,6 +26,11 @@ struct ProbSched {
   int64_t limit;            // tasks with index >= limit are not run
 };
 constexpr int kMaxBatch = 64;  // problems in one launch
+// profile layout: per task kind (TK_NUM + 1 rows) tasks, wait cycles, run
+// cycles; then truncation phases: stacking, QR, core, Jacobi, selection and
+// Q application cycles, compressions, Jacobi sweeps, summed stack widths
+constexpr int kProfTrunc = (TK_NUM + 1) * 3;
+constexpr int kProfEntries = kProfTrunc + 8;
 
 struct ExecArgs {
   ProbSched probs[kMaxBatch];
@@ -41,7 +46,9 @@ struct ExecArgs {
   int32_t* status;              // [0] status code, [1] failing slot, [2] rank-cap hits, [3] abort
   double* flops;                // accumulated algorithmic flops (may be null)
   unsigned long long wait_limit_ns;
-  unsigned long long* prof;     // optional [(TK_NUM + 1) x 3]: tasks, wait cycles, run cycles per kind
+  double jacobi_tol;            // truncation: Jacobi orthogonality tolerance
+  int32_t compress_at;          // truncation: stack width that triggers a compression
+  unsigned long long* prof;     // optional [kProfEntries] (layout above)
   unsigned long long* trace;    // optional [ntotal x 4] per slot: (problem << 40 | task), claim, start, end (ns)
 };
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
+    "hlu_set_trunc_params": (_i32, [_i32, _f64]),
     "hlu_launch_count": (_i64, []),
     "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
     "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
@@ -219,9 +220,13 @@ TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", 
 
 def hlu_factor_profile(h):
     """{kind: (tasks, wait_cycles, run_cycles)} of the last factorisation."""
-    out = (ctypes.c_uint64 * 30)()
+    out = (ctypes.c_uint64 * 38)()
     _check(lib().hlu_factor_profile(_vp(h), out))
-    return {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
+    d = {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
+    d["trunc_phases"] = {"qr_cycles": out[31], "core_cycles": out[32], "jacobi_cycles": out[33],
+                         "select_apply_cycles": out[34], "compressions": out[35], "sweeps": out[36],
+                         "width_sum": out[37]}
+    return d
 
 
 def hlu_solve(h, b, x, stream=None):
@@ -322,6 +327,10 @@ def hlu_set_wait_limit_ms(ms):
 
 def hlu_launch_count():
     return int(lib().hlu_launch_count())
+
+
+def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
+    _check(lib().hlu_set_trunc_params(int(compress_at), float(jacobi_tol)))
 
 
 def hlu_set_tile(t):

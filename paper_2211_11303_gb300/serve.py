@@ -1,0 +1,164 @@
+"""Continuous-batching solve server on one GPU.
+
+Each request asks for the solution of A(n, kappa) x = b for 1..16 right-hand
+sides (Algorithm 1 steps III-IV of the paper: H-LU-preconditioned restarted
+GMRES).  The server keeps H-LU factors on the device, keyed by (n, kappa), and
+the Krylov state of every running request.  A request is admitted when a
+slot is free and its factor (if not cached) plus its Krylov workspace fit the
+HBM budget; cached factors that no running request uses are evicted, least
+recently used first, to make room.  Every loop iteration advances ALL
+running requests by one GMRES step through ``hlu_gmres_step_batch``: the
+triangular solves of every request run in one persistent launch, and a
+request's result is the same whether it ran alone or in the mix.
+
+Arrivals follow the request's ``t`` (seconds after start) on the wall clock.
+Factorisations run synchronously in the loop (the persistent executor fills
+the GPU), so a request that needs a new factor delays the running ones by the
+factorisation time; that delay is part of the reported latencies.
+"""
+import time
+
+import numpy as np
+import torch
+
+from . import hlu as H
+
+
+def krylov_bytes(N, nrhs, restart):
+    """Device bytes of one GMRES state (V, Z: N x (m+1) per column; W)."""
+    return 8 * N * nrhs * (2 * (restart + 1) + 1) + 64 * 1024
+
+
+class _Factor:
+    def __init__(self, key, h, nbytes):
+        self.key, self.h, self.nbytes = key, h, nbytes
+        self.users = 0
+        self.last_use = 0.0
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes, max_active=64, leaf=32, eta=2.0, eps=1e-4, precision=H.HLU_FP32,
+                 restart=50, tol=1e-8, maxit=1000):
+        self.budget = int(hbm_budget_bytes)
+        self.max_active = int(max_active)
+        self.leaf, self.eta, self.eps = leaf, eta, eps
+        self.precision, self.restart, self.tol, self.maxit = precision, restart, tol, maxit
+        self.factors = {}
+        self.used = 0
+        self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0}
+
+    # -- factor cache ---------------------------------------------------------
+    def _evict_for(self, need):
+        idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
+        for f in idle:
+            if self.used + need <= self.budget:
+                break
+            H.hlu_destroy(f.h)
+            self.used -= f.nbytes
+            del self.factors[f.key]
+            self.stats["evictions"] += 1
+        return self.used + need <= self.budget
+
+    def _lookup(self, req):
+        """(cached factor or None, built-but-unfactored handle or None, bytes)."""
+        key = (int(req["n"]), float(req["kappa"]))
+        f = self.factors.get(key)
+        if f is not None:
+            return f, None, 0
+        if "_h" not in req:
+            h = H.hlu_build(req["n"], req["kappa"], self.leaf, self.eta, self.eps)
+            req["_h"] = (key, h, int(H.hlu_factor_bytes_estimate(h, self.precision)))
+        return None, req["_h"], req["_h"][2]
+
+    # -- main loop --------------------------------------------------------------
+    def run(self, requests, rhs_of):
+        """Serve `requests` (dicts with id, t, n, kappa, nrhs) in arrival
+        order; rhs_of(req, N) -> float64 host array (N, nrhs).  Returns one
+        result dict per request (id, latency_s, iterations, relres, x)."""
+        pending = sorted(requests, key=lambda r: (r["t"], r["id"]))
+        waiting, active, results = [], [], {}
+        t0 = time.perf_counter()
+        pi = 0
+        while pi < len(pending) or waiting or active:
+            now = time.perf_counter() - t0
+            while pi < len(pending) and pending[pi]["t"] <= now:
+                waiting.append(pending[pi])
+                pi += 1
+            # admission: first come first served, later requests may pass one
+            # that does not fit yet
+            still = []
+            for req in waiting:
+                if len(active) >= self.max_active:
+                    still.append(req)
+                    continue
+                f, built, fbytes = self._lookup(req)
+                N = H.hlu_n(f.h if f is not None else built[1])
+                kb = krylov_bytes(N, req["nrhs"], self.restart)
+                if f is not None:
+                    f.users += 1  # not evictable while deciding
+                ok = self._evict_for(fbytes + kb)
+                if f is not None:
+                    f.users -= 1
+                if not ok:
+                    if not active and all(g.users == 0 for g in self.factors.values()) and not self.factors:
+                        raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))
+                    still.append(req)
+                    continue
+                if f is None:
+                    key, h, nbytes = req.pop("_h")
+                    H.hlu_factor(h, self.precision)
+                    f = _Factor(key, h, nbytes)
+                    self.factors[key] = f
+                    self.used += nbytes
+                    self.stats["factorisations"] += 1
+                else:
+                    self.stats["cache_hits"] += 1
+                got = f
+                b = rhs_of(req, N)
+                bd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
+                bd.copy_(torch.from_numpy(np.ascontiguousarray(b)).pin_memory(), non_blocking=True)
+                xd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
+                g = H.hlu_gmres_begin(got.h, bd, xd, restart=self.restart, tol=self.tol, maxit=self.maxit)
+                got.users += 1
+                self.used += kb
+                active.append({"req": req, "f": got, "g": g, "b": bd, "x": xd, "kb": kb})
+            waiting = still
+            if not active:
+                if pi < len(pending):
+                    time.sleep(max(0.0, min(pending[pi]["t"] - (time.perf_counter() - t0), 0.05)))
+                continue
+            self.stats["max_active"] = max(self.stats["max_active"], len(active))
+            H.hlu_gmres_step_batch([a["g"] for a in active])
+            self.stats["steps"] += 1
+            keep = []
+            for a in active:
+                done, st = H.hlu_gmres_status(a["g"])
+                if not done:
+                    keep.append(a)
+                    continue
+                x = a["x"].t().contiguous().cpu().numpy().T
+                t_done = time.perf_counter() - t0
+                H.hlu_gmres_end(a["g"])
+                a["f"].users -= 1
+                a["f"].last_use = t_done
+                self.used -= a["kb"]
+                req = a["req"]
+                results[req["id"]] = {"id": req["id"], "latency_s": t_done - req["t"], "iterations": st["iterations"],
+                                      "relres": st["relres_max"], "converged": bool(st["converged"]), "x": x,
+                                      "n": req["n"], "kappa": req["kappa"], "nrhs": req["nrhs"]}
+            active = keep
+        self.stats["wall_s"] = time.perf_counter() - t0
+        return [results[r["id"]] for r in requests]
+
+    def close(self):
+        for f in self.factors.values():
+            H.hlu_destroy(f.h)
+        self.factors.clear()
+        self.used = 0
+
+
+def latency_summary(results):
+    lat = np.array([r["latency_s"] for r in results]) * 1e3
+    cols = sum(r["nrhs"] for r in results)
+    return {"requests": len(results), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "rhs_columns": int(cols)}

@@ -92,3 +92,45 @@ def test_mix_equals_alone(hlu):
     finally:
         for h in hs:
             hlu.hlu_destroy(h)
+
+
+def test_server_results_match_alone(hlu):
+    """The request loop (admission by HBM budget, factor cache, one batched
+    GMRES step for all running requests) returns for every request what a
+    lone gmres_solve returns."""
+    from paper_2211_11303_gb300 import serve
+    import synth as S
+    reqs = S.serving_requests(count=10, seed=5000, n_lo=3, n_hi=5, k_lo=1.0, k_hi=3.0, r_lo=1, r_hi=6, rate=50.0)
+    for r in reqs:  # few distinct (n, kappa) keys so that the cache is used
+        r["kappa"] = float(round(r["kappa"]))
+
+    def rhs_of(req, N):
+        return np.stack([S.normal(S.rhs_seed(4, req["id"], j), N) for j in range(req["nrhs"])], axis=1)
+
+    # a budget that holds about two factors forces evictions
+    probe = hlu.hlu_build(5, 1.0, 16, 2.0, 1e-4)
+    fb = hlu.hlu_factor_bytes_estimate(probe, hlu.HLU_FP32)
+    hlu.hlu_destroy(probe)
+    srv = serve.Server(hbm_budget_bytes=3 * fb + 64 * serve.krylov_bytes(500, 16, 50), max_active=4, leaf=16,
+                       restart=50, tol=TOL, maxit=500)
+    try:
+        res = srv.run(reqs, rhs_of)
+    finally:
+        srv.close()
+    assert srv.stats["cache_hits"] > 0 and srv.stats["max_active"] > 1
+    for r in res:
+        h = hlu.hlu_build(r["n"], r["kappa"], 16, 2.0, 1e-4)
+        try:
+            hlu.hlu_factor(h, hlu.HLU_FP32)
+            N = hlu.hlu_n(h)
+            b = _rhs(N, r["nrhs"], 0)
+            b.copy_(torch.from_numpy(rhs_of(r, N)))
+            x = hlu.colmajor(N, r["nrhs"])
+            hlu.gmres_solve(h, b, x, restart=50, tol=TOL, maxit=500)
+            xs = torch.from_numpy(np.ascontiguousarray(r["x"])).cuda()
+            err = torch.linalg.norm(xs - x) / torch.linalg.norm(x)
+            assert r["converged"] and err <= MIX_VS_ALONE, (r["id"], float(err))
+        finally:
+            hlu.hlu_destroy(h)
+    summ = serve.latency_summary(res)
+    assert summ["requests"] == len(reqs) and summ["p99_ms"] >= summ["p50_ms"] > 0

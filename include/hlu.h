@@ -158,14 +158,14 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream);
 int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 
 /* hlu_factor_profile - per task kind of the last factorisation's task DAG:
- * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for
- * predecessors, out[3*k + 2] cycles spent running, summed over CTAs; kinds
- * k = 0..8 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD, RSOLVE
- * and k = 9 the no-work fences; then the truncation phases summed over all
- * compressions: out[30] (unused), out[31] QR cycles, out[32] core product,
- * out[33] Jacobi SVD, out[34] selection and Q application, out[35]
- * compressions, out[36] Jacobi sweeps, out[37] summed stack widths.
- * out: uint64[38] host buffer. */
+ * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for a
+ * ready task, out[3*k + 2] cycles spent running, summed over CTAs; kinds
+ * k = 0..9 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
+ * RSOLVE, SEQ and k = 10 the no-work fences; then the truncation phases
+ * summed over all compressions: out[33] (unused), out[34] QR cycles, out[35]
+ * core product, out[36] Jacobi SVD, out[37] selection and Q application,
+ * out[38] compressions, out[39] Jacobi sweeps, out[40] summed stack widths.
+ * out: uint64[41] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
@@ -258,6 +258,16 @@ void hlu_set_wait_limit_ms(double ms);
  * are not affected.  tile <= leaf keeps the block tree's own leaves; values
  * above 64 are clamped to 64. */
 void hlu_set_tile(int32_t tile);
+
+/* hlu_set_solve_group - granularity of the H-triangular solves for
+ * subsequent hlu_build calls (process-wide, default 0: no grouping).  The forward or
+ * backward solve of every diagonal block whose cluster holds at most `dofs`
+ * DOFs runs as one task on one CTA, its leaf solves and low-rank updates in
+ * sequence, which removes the scheduling hops inside it from the critical
+ * path, but also serialises the updates inside it that could run on other
+ * CTAs.  The arithmetic is the same as without grouping (0).  The debug host
+ * executor uses the same setting. */
+void hlu_set_solve_group(int32_t dofs);
 
 /* hlu_launch_count - number of this library's own CUDA kernel launches so far
  * in this process (kernels from CUDA's bundled sort/scan templates are not

@@ -73,6 +73,13 @@ int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out);
 int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t* trace_out, int64_t* pred_ptr_out,
                            int32_t* pred_idx_out, void* tasks_out, int64_t* sizes);
 
+/* hlu_debug_solve_trace - one triangular solve (nrhs columns of the work
+ * vector, 1..16, contents as they are) of a factored handle with a per-task
+ * trace (needs a GPU); outputs and sizes as hlu_debug_factor_trace, for the
+ * solve DAG. */
+int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trace_out, int64_t* pred_ptr_out,
+                          int32_t* pred_idx_out, void* tasks_out, int64_t* sizes);
+
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a
  * GPU).  Runs the task executor with one CTA on a two-task schedule in which
  * task 1 waits for itself: task 0 runs, and the CTA that claims queue slot 1

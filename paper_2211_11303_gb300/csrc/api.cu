@@ -37,6 +37,7 @@ double g_wait_limit_ms = 20000.0;
 double g_jacobi_tol = 0.0;  // 0: default of the factor precision
 int32_t g_compress_at = 0;  // 0: default
 int32_t g_tile = 64;
+int32_t g_solve_group = 0;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -69,6 +70,7 @@ struct DevSched {
   Task* tasks = nullptr;
   Term* terms = nullptr;
   Piece* pieces = nullptr;
+  Task* micro = nullptr;
   int64_t* pred_ptr = nullptr;
   int32_t* pred_idx = nullptr;
   int64_t* succ_ptr = nullptr;
@@ -87,6 +89,7 @@ struct DevSched {
     if ((e = upload(&tasks, S.tasks)) != cudaSuccess) return e;
     if ((e = upload(&terms, S.terms)) != cudaSuccess) return e;
     if ((e = upload(&pieces, S.pieces)) != cudaSuccess) return e;
+    if ((e = upload(&micro, S.micro)) != cudaSuccess) return e;
     if ((e = upload(&pred_ptr, S.pred_ptr)) != cudaSuccess) return e;
     if ((e = upload(&pred_idx, S.pred_idx)) != cudaSuccess) return e;
     // successor lists (edges sorted by predecessor, successors ascending)
@@ -137,7 +140,8 @@ struct DevSched {
   }
   void free_all() {
     if (owns_data)
-      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx, (void*)succ_ptr,
+      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)micro, (void*)pred_ptr, (void*)pred_idx,
+                      (void*)succ_ptr,
                       (void*)succ_idx, (void*)indeg0, (void*)roots})
         if (p) cudaFree(p);
     for (void* p : {(void*)indeg, (void*)queue, (void*)qctl})
@@ -273,6 +277,7 @@ ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   p.tasks = ds.tasks;
   p.terms = ds.terms;
   p.pieces = ds.pieces;
+  p.micro = ds.micro;
   p.succ_ptr = ds.succ_ptr;
   p.succ_idx = ds.succ_idx;
   p.indeg = ds.indeg;
@@ -295,7 +300,7 @@ void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool wi
   a.jacobi_tol = g_jacobi_tol;
   a.compress_at = g_compress_at;
   a.prof = with_flops ? h0->d_prof : nullptr;
-  a.trace = with_flops ? h0->d_trace : nullptr;
+  a.trace = h0->d_trace;
 }
 
 // One launch of the executor over one problem's schedule (or its first
@@ -586,6 +591,8 @@ void hlu_set_wait_limit_ms(double ms) {
   if (ms > 0) g_wait_limit_ms = ms;
 }
 void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
+
+void hlu_set_solve_group(int32_t dofs) { g_solve_group = std::max(0, dofs); }
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
 int64_t hlu_launch_count(void) { return g_launches.load(); }
 
@@ -650,7 +657,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     uint64_t key = 1469598103934665603ULL;
     key = fnv1a(key, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
     key = fnv1a(key, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
-    int32_t params[4] = {rank_cap, h->tile, nrhs_max, (int32_t)N};
+    const int32_t solve_group = g_solve_group;
+    int32_t params[5] = {rank_cap, h->tile, nrhs_max, (int32_t)N, solve_group};
     key = fnv1a(key, params, sizeof(params));
     bool cache_hit = false;
     {
@@ -668,7 +676,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       auto sb = std::make_shared<SchedBundle>();
       sb->key = key;
       Schedule F, S;
-      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, sb->L, F, S, sb->st, &sb->FB);
+      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, solve_group, sb->L, F, S, sb->st, &sb->FB);
       if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
       if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
       // A_H fill descriptors
@@ -1166,6 +1174,40 @@ extern "C" int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t
   return HLU_OK;
 }
 
+// Runs one triangular solve of a factored handle (nrhs columns of the work
+// vector, whatever they hold) with a per-task trace; outputs as
+// hlu_debug_factor_trace for the solve DAG.
+extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trace_out, int64_t* pred_ptr_out,
+                                     int32_t* pred_idx_out, void* tasks_out, int64_t* sizes) {
+  if (!h || !sizes || nrhs < 1 || nrhs > h->L.nrhs_max) return fail(HLU_ERR_ARG, "bad argument");
+  const int64_t nt = h->dS.ntasks;
+  sizes[0] = nt;
+  sizes[1] = 0;
+  if (h->dS.pred_ptr && nt > 0)
+    CKR(cudaMemcpy(&sizes[1], h->dS.pred_ptr + nt, sizeof(int64_t), cudaMemcpyDeviceToHost), "edges");
+  if (!trace_out) return HLU_OK;
+  if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+  CKR(cudaMalloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs, nullptr), "nrhs slot");
+  int rc = exec_run(h, h->dS, h->grid, nullptr, false);
+  if (!rc) {
+    int32_t st[8];
+    rc = read_status(h, nullptr, st);
+  }
+  cudaError_t e = cudaMemcpy(trace_out, h->d_trace, sizeof(uint64_t) * 4 * nt, cudaMemcpyDeviceToHost);
+  cudaFree(h->d_trace);
+  h->d_trace = nullptr;
+  if (rc) return rc;
+  CKR(e, "trace copy");
+  if (pred_ptr_out)
+    CKR(cudaMemcpy(pred_ptr_out, h->dS.pred_ptr, sizeof(int64_t) * (nt + 1), cudaMemcpyDeviceToHost), "dag");
+  if (pred_idx_out)
+    CKR(cudaMemcpy(pred_idx_out, h->dS.pred_idx, sizeof(int32_t) * sizes[1], cudaMemcpyDeviceToHost), "dag");
+  if (tasks_out) CKR(cudaMemcpy(tasks_out, h->dS.tasks, sizeof(Task) * nt, cudaMemcpyDeviceToHost), "tasks");
+  return HLU_OK;
+}
+
 // Copies factorisation task `idx` (its raw 128-byte record) to `out`.
 extern "C" int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out) {
   if (!h || !out || idx < 0 || idx >= h->dF.ntasks) return fail(HLU_ERR_ARG, "bad argument");
@@ -1479,3 +1521,7 @@ void hlu_gmres_end(hlu_gmres* g) {
 }
 
 }  // extern "C"
+
+namespace hlu {
+int32_t current_solve_group() { return g_solve_group; }
+}  // namespace hlu

@@ -57,6 +57,7 @@ struct Ctx {
   int32_t* piv;
   const Term* terms;
   const Piece* pieces;
+  const Task* micro;
   T* scratch;
   int64_t rows_max;  // rows of the per-CTA truncation stacks
   double eps;
@@ -210,53 +211,126 @@ __device__ __forceinline__ void acc_zero(T (&acc)[4][4]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 }
+// One K-chunk of a tile product: rows [rlo, rlo + mrows) of the tile get
+// A (mrows x kc) times B (kc x ncols).
+template <class T>
+struct Chunk {
+  Mat<T> A, B;
+  int rlo, mrows, ncols, kc;
+  int clo = 0;   // B's columns land on tile columns [clo, clo + ncols)
+  T sg = T(1);   // sign applied to B
+};
+constexpr int kChunkRegs = 64 * KC / NT;
+
+// Loads a chunk's operands into registers, ordered along each operand's
+// contiguous dimension (the same element order chunk_stage stores).
+template <class T>
+__device__ __forceinline__ void chunk_fetch(const Chunk<T>& ch, T (&ra)[kChunkRegs], T (&rb)[kChunkRegs]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kChunkRegs; ++q) {
+    const int e = tid + q * NT;
+    const int r = ch.A.rs == 1 ? (e & 63) : e / KC;
+    const int kk = ch.A.rs == 1 ? (e >> 6) : e % KC;
+    const int ar = r - ch.rlo;
+    ra[q] = (kk < ch.kc && ar >= 0 && ar < ch.mrows) ? __ldcg(ch.A.p + (int64_t)ar * ch.A.rs + (int64_t)kk * ch.A.cs)
+                                                      : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < kChunkRegs; ++q) {
+    const int e = tid + q * NT;
+    const int cc = ch.B.rs == 1 ? e / KC : (e & 63);
+    const int kk = ch.B.rs == 1 ? e % KC : (e >> 6);
+    const int bc = cc - ch.clo;
+    rb[q] = (kk < ch.kc && bc >= 0 && bc < ch.ncols)
+                ? ch.sg * __ldcg(ch.B.p + (int64_t)kk * ch.B.rs + (int64_t)bc * ch.B.cs)
+                : T(0);
+  }
+}
+template <class T>
+__device__ __forceinline__ void chunk_stage(const Chunk<T>& ch, const T (&ra)[kChunkRegs],
+                                            const T (&rb)[kChunkRegs], T* As, T* Bs) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kChunkRegs; ++q) {
+    const int e = tid + q * NT;
+    const int r = ch.A.rs == 1 ? (e & 63) : e / KC;
+    const int kk = ch.A.rs == 1 ? (e >> 6) : e % KC;
+    As[kk * 64 + r] = ra[q];
+  }
+#pragma unroll
+  for (int q = 0; q < kChunkRegs; ++q) {
+    const int e = tid + q * NT;
+    const int cc = ch.B.rs == 1 ? e / KC : (e & 63);
+    const int kk = ch.B.rs == 1 ? e % KC : (e >> 6);
+    Bs[kk * 64 + cc] = rb[q];
+  }
+}
+template <class T>
+__device__ __forceinline__ void chunk_mma(T (&acc)[4][4], const T* As, const T* Bs, int kc) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int kk = 0; kk < kc; ++kk) {
+    T a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tx * 4 + i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + ty * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+}
+
+// Software pipeline over a sequence of chunks: the operands of chunk j + 1
+// are in flight (registers) while chunk j is multiplied from shared memory.
+// Cursor: first() -> bool (a chunk exists), chunk() -> Chunk, next() -> bool.
+template <class T, class Cursor>
+__device__ void tile_mma_seq(T (&acc)[4][4], Cursor& cur, T* As, T* Bs) {
+  if (!cur.first()) return;
+  T ra[kChunkRegs], rb[kChunkRegs];
+  Chunk<T> ch = cur.chunk();
+  chunk_fetch(ch, ra, rb);
+  for (;;) {
+    __syncthreads();
+    chunk_stage(ch, ra, rb, As, Bs);
+    __syncthreads();
+    const int kc = ch.kc;
+    const bool more = cur.next();
+    if (more) {
+      ch = cur.chunk();
+      chunk_fetch(ch, ra, rb);
+    }
+    chunk_mma(acc, As, Bs, kc);
+    if (!more) break;
+  }
+  __syncthreads();
+}
+
+// Chunks of one product A (tile rows [rlo, rlo + mrows), K columns) B.
+template <class T>
+struct ProductCursor {
+  Mat<T> A, B;
+  int rlo, mrows, ncols, K, l0;
+  __device__ bool first() {
+    l0 = 0;
+    return K > 0 && mrows > 0;
+  }
+  __device__ bool next() {
+    l0 += KC;
+    return l0 < K;
+  }
+  __device__ Chunk<T> chunk() const {
+    return Chunk<T>{shift(A, 0, l0), shift(B, l0, 0), rlo, mrows, ncols, min(KC, K - l0), 0, T(1)};
+  }
+};
+
+// acc += A (tile rows [rlo, rlo + mrows), K columns) times B (K x ncols)
 template <class T>
 __device__ void tile_mma(T (&acc)[4][4], const Mat<T>& A, int rlo, int mrows, const Mat<T>& B, int ncols, int K,
                          T* As, T* Bs) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int l0 = 0; l0 < K; l0 += KC) {
-    const int kc = min(KC, K - l0);
-    __syncthreads();
-    if (A.rs == 1) {
-      for (int e = tid; e < 64 * KC; e += NT) {
-        int r = e & 63, kk = e >> 6;
-        int ar = r - rlo;
-        As[kk * 64 + r] = (kk < kc && ar >= 0 && ar < mrows) ? __ldcg(A.p + ar + (int64_t)(l0 + kk) * A.cs) : T(0);
-      }
-    } else {
-      for (int e = tid; e < 64 * KC; e += NT) {
-        int kk = e % KC, r = e / KC;
-        int ar = r - rlo;
-        As[kk * 64 + r] =
-            (kk < kc && ar >= 0 && ar < mrows) ? __ldcg(A.p + (int64_t)ar * A.rs + (int64_t)(l0 + kk) * A.cs) : T(0);
-      }
-    }
-    if (B.rs == 1) {
-      for (int e = tid; e < 64 * KC; e += NT) {
-        int kk = e % KC, cc = e / KC;
-        Bs[kk * 64 + cc] = (kk < kc && cc < ncols) ? __ldcg(B.p + (l0 + kk) + (int64_t)cc * B.cs) : T(0);
-      }
-    } else {
-      for (int e = tid; e < 64 * KC; e += NT) {
-        int cc = e & 63, kk = e >> 6;
-        Bs[kk * 64 + cc] =
-            (kk < kc && cc < ncols) ? __ldcg(B.p + (int64_t)(l0 + kk) * B.rs + (int64_t)cc * B.cs) : T(0);
-      }
-    }
-    __syncthreads();
-    for (int kk = 0; kk < kc; ++kk) {
-      T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tx * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + ty * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-    }
-  }
-  __syncthreads();
+  ProductCursor<T> cur{A, B, rlo, mrows, ncols, K, 0};
+  tile_mma_seq(acc, cur, As, Bs);
 }
 // C[rows i0.., cols j0..] (+)= sign * acc for the valid part of the tile
 template <class T>
@@ -349,25 +423,70 @@ __device__ void task_proj(Ctx<T>& c, const Task& t, char* smem) {
 
 // ---------------------------------------------------------------- ROWMV
 // c (n x k) = [c] + sign * sum_t A_t B_t, A_t covering rows [roff, roff + rows).
+// The terms (and their ranks) are staged in shared memory, kStageTerms at a
+// time; all their chunks form one software pipeline per output tile.
+constexpr int kStageTerms = 32;
+template <class T>
+struct TermCursor {
+  const Ctx<T>* c;
+  const Term* tm;
+  const int* p;
+  int nq, i0, j0, k, q, l0;
+  __device__ bool valid(int qq) const {
+    const int lo = max(tm[qq].roff, i0), hi = min(tm[qq].roff + tm[qq].A.rows, i0 + 64);
+    return hi > lo && p[qq] > 0;
+  }
+  __device__ bool seek(int qq) {
+    while (qq < nq && !valid(qq)) ++qq;
+    q = qq;
+    l0 = 0;
+    return q < nq;
+  }
+  __device__ bool first() { return seek(0); }
+  __device__ bool next() {
+    l0 += KC;
+    if (l0 < p[q]) return true;
+    return seek(q + 1);
+  }
+  __device__ Chunk<T> chunk() const {
+    const Term& t = tm[q];
+    const int lo = max(t.roff, i0), hi = min(t.roff + t.A.rows, i0 + 64);
+    return Chunk<T>{shift(mat(*c, t.A), lo - t.roff, l0), shift(mat(*c, t.B), l0, j0), lo - i0, hi - lo,
+                    min(64, k - j0), min(KC, p[q] - l0), 0, T(1)};
+  }
+};
+
 template <class T>
 __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.c.rows, k = ncols(c, t.b);
   T* As = reinterpret_cast<T*>(smem);
   T* Bs = As + 64 * KC;
+  __shared__ Term s_tm[kStageTerms];
+  __shared__ int s_p[kStageTerms];
   double fl = 0;
   for (int i0 = 0; i0 < n; i0 += 64)
     for (int j0 = 0; j0 < k; j0 += 64) {
       T acc[4][4];
       acc_zero(acc);
-      for (int q = 0; q < t.list_count; ++q) {
-        const Term& tm = c.terms[t.list_begin + q];
-        const int p = ncols(c, tm.A);
-        // term rows [roff, roff + rows) intersected with tile rows [i0, i0 + 64)
-        int lo = max(tm.roff, i0), hi = min(tm.roff + tm.A.rows, i0 + 64);
-        if (hi <= lo || p == 0) continue;
-        tile_mma(acc, shift(mat(c, tm.A), lo - tm.roff, 0), lo - i0, hi - lo, shift(mat(c, tm.B), 0, j0),
-                 min(64, k - j0), p, As, Bs);
-        fl += 2.0 * (hi - lo) * min(64, k - j0) * p;
+      for (int qb = 0; qb < t.list_count; qb += kStageTerms) {
+        const int nq = min(kStageTerms, t.list_count - qb);
+        __syncthreads();
+        {
+          const int words = nq * (int)(sizeof(Term) / sizeof(int32_t));
+          const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin + qb);
+          int32_t* dst = reinterpret_cast<int32_t*>(s_tm);
+          for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        if (threadIdx.x < nq) s_p[threadIdx.x] = ncols(c, s_tm[threadIdx.x].A);
+        __syncthreads();
+        TermCursor<T> cur{&c, s_tm, s_p, nq, i0, j0, k, 0, 0};
+        tile_mma_seq(acc, cur, As, Bs);
+        if (threadIdx.x == 0)
+          for (int q = 0; q < nq; ++q) {
+            const int lo = max(s_tm[q].roff, i0), hi = min(s_tm[q].roff + s_tm[q].A.rows, i0 + 64);
+            if (hi > lo) fl += 2.0 * (hi - lo) * min(64, k - j0) * s_p[q];
+          }
       }
       tile_store(acc, c, t.c, i0, j0, min(64, n - i0), min(64, k - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
     }
@@ -860,6 +979,266 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
   return r;
 }
 
+// ------------------------------------------------------------- dense TRUNC
+// Targets with both sides up to kDenseMax whose pieces would need more than
+// one compression of the stack take a dense route (FP32 factors): the sum
+// D = sum sign X Y^T is formed in shared memory, a Householder QR with column
+// pivoting stops once the trailing block's Frobenius norm is below
+// 0.1 eps ||D||_F / sqrt(min(m, n)) (<= 0.1 eps s_1), and the one-sided Jacobi
+// SVD of the remaining r' x n rows gives the truncation s_i > eps s_1.
+constexpr int kDenseMax = 128;
+constexpr int kDenseRank = 40;
+constexpr int kStagePieces = 16;
+
+// Chunks of sum_pieces sign X Y^T restricted to the 64 x 64 tile (i0, j0).
+template <class T>
+struct PieceCursor {
+  const Ctx<T>* c;
+  const Piece* pc;
+  const int* w;
+  int nq, i0, j0, q, l0;
+  __device__ bool valid(int qq) const {
+    const Piece& P = pc[qq];
+    return w[qq] > 0 && max(P.xoff, i0) < min(P.xoff + P.X.rows, i0 + 64) &&
+           max(P.yoff, j0) < min(P.yoff + P.Y.rows, j0 + 64);
+  }
+  __device__ bool seek(int qq) {
+    while (qq < nq && !valid(qq)) ++qq;
+    q = qq;
+    l0 = 0;
+    return q < nq;
+  }
+  __device__ bool first() { return seek(0); }
+  __device__ bool next() {
+    l0 += KC;
+    if (l0 < w[q]) return true;
+    return seek(q + 1);
+  }
+  __device__ Chunk<T> chunk() const {
+    const Piece& P = pc[q];
+    const int xl = max(P.xoff, i0), xh = min(P.xoff + P.X.rows, i0 + 64);
+    const int yl = max(P.yoff, j0), yh = min(P.yoff + P.Y.rows, j0 + 64);
+    return Chunk<T>{shift(mat(*c, P.X), xl - P.xoff, l0), shift(matT(*c, P.Y), l0, yl - P.yoff), xl - i0, xh - xl,
+                    yh - yl, min(KC, w[q] - l0), yl - j0, T(P.sign)};
+  }
+};
+
+// Householder QR with column pivoting of D (m x n, ld m, shared memory) in
+// place, stopped after kmax steps or once the trailing block's squared
+// Frobenius norm is <= rel2 ||D||_F^2.  perm[j] = original index of column j.
+// Returns the number of reflectors r'; *tail2 receives the dropped norm^2.
+template <class T>
+__device__ int pivoted_qr(T* D, int m, int n, int kmax, T rel2, T* tau, T* nrm2, int* perm, T* tail2) {
+  __shared__ int s_piv;
+  __shared__ T s_tail, s_thr, s_beta, s_sc, s_tau;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x; j < n; j += NT) perm[j] = j;
+  const int kend = min(kmax, min(m, n));
+  int k = 0;
+  for (;; ++k) {
+    for (int j = k + warp; j < n; j += NT / 32) {
+      T acc = 0;
+      for (int i = k + lane; i < m; i += 32) acc += D[i + j * m] * D[i + j * m];
+      acc = warp_sum(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tail = 0, best = T(-1);
+      int piv = k;
+      for (int j = k; j < n; ++j) {
+        tail += nrm2[j];
+        if (nrm2[j] > best) {
+          best = nrm2[j];
+          piv = j;
+        }
+      }
+      if (k == 0) s_thr = rel2 * tail;
+      s_tail = tail;
+      s_piv = piv;
+    }
+    __syncthreads();
+    if (k >= kend || s_tail <= s_thr) break;
+    const int pv = s_piv;
+    if (pv != k) {
+      for (int i = threadIdx.x; i < m; i += NT) {
+        const T x = D[i + k * m];
+        D[i + k * m] = D[i + pv * m];
+        D[i + pv * m] = x;
+      }
+      if (threadIdx.x == 0) {
+        const int pp = perm[k];
+        perm[k] = perm[pv];
+        perm[pv] = pp;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T ss = 0;
+      for (int i = k + 1 + lane; i < m; i += 32) ss += D[i + k * m] * D[i + k * m];
+      ss = warp_sum(ss);
+      if (lane == 0) {
+        const T alpha = D[k + k * m];
+        T beta = alpha, sc = 0, tj = 0;
+        if (ss > T(0)) {
+          const T nrm = sqrt(alpha * alpha + ss);
+          beta = alpha >= T(0) ? -nrm : nrm;
+          sc = T(1) / (alpha - beta);
+          tj = (beta - alpha) / beta;
+        }
+        s_beta = beta;
+        s_sc = sc;
+        s_tau = tj;
+        tau[k] = tj;
+      }
+      __syncwarp();
+      const T sc = s_sc;
+      for (int i = k + 1 + lane; i < m; i += 32) D[i + k * m] *= sc;
+      __syncwarp();
+      if (lane == 0) D[k + k * m] = s_beta;
+    }
+    __syncthreads();
+    const T tj = s_tau;
+    if (tj != T(0))
+      for (int j = k + 1 + warp; j < n; j += NT / 32) {
+        T d = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) d += D[i + k * m] * D[i + j * m];
+        d = (warp_sum(d) + D[k + j * m]) * tj;
+        for (int i = k + 1 + lane; i < m; i += 32) D[i + j * m] -= d * D[i + k * m];
+        __syncwarp();
+        if (lane == 0) D[k + j * m] -= d;
+      }
+    __syncthreads();
+  }
+  *tail2 = s_tail;
+  return k;
+}
+
+template <class T>
+__device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
+  const int m = t.a.rows, n = t.b.rows;
+  // shared memory: [region 0: staging chunks, later M (n x kDenseRank) and
+  // V][D (m x n)][tau, nrm2 (kDenseMax each)][perm]
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + 64 * KC;
+  T* M = As;
+  T* V = M + kDenseMax * kDenseRank;
+  T* D = V + kDenseRank * kDenseRank;
+  T* tau = D + kDenseMax * kDenseMax;
+  T* nrm2 = tau + kDenseMax;
+  int* perm = reinterpret_cast<int*>(nrm2 + kDenseMax);
+  __shared__ Piece s_pc[kStagePieces];
+  __shared__ int s_w[kStagePieces];
+  __shared__ int s_ord[kDenseRank];
+  __shared__ int s_r;
+  unsigned long long* tp = c.tprof;
+  long long t0 = tp && threadIdx.x == 0 ? clock64() : 0;
+  // D = sum of the pieces, tile by tile, pieces staged kStagePieces at a time
+  for (int i0 = 0; i0 < m; i0 += 64)
+    for (int j0 = 0; j0 < n; j0 += 64) {
+      T acc[4][4];
+      acc_zero(acc);
+      for (int qb = 0; qb < t.list_count; qb += kStagePieces) {
+        const int nq = min(kStagePieces, t.list_count - qb);
+        __syncthreads();
+        {
+          const int words = nq * (int)(sizeof(Piece) / sizeof(int32_t));
+          const int32_t* src = reinterpret_cast<const int32_t*>(c.pieces + t.list_begin + qb);
+          int32_t* dst = reinterpret_cast<int32_t*>(s_pc);
+          for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        if (threadIdx.x < nq) s_w[threadIdx.x] = ncols(c, s_pc[threadIdx.x].X);
+        __syncthreads();
+        PieceCursor<T> cur{&c, s_pc, s_w, nq, i0, j0, 0, 0};
+        tile_mma_seq(acc, cur, As, Bs);
+      }
+      const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = i0 + tx * 4 + i, cc = j0 + ty * 4 + j;
+          if (r < m && cc < n) D[r + cc * m] = acc[i][j];
+        }
+    }
+  __syncthreads();
+  if (tp && threadIdx.x == 0) {
+    const long long t1 = clock64();
+    tp[0] += (unsigned long long)(t1 - t0);
+    t0 = t1;
+  }
+  // pivoted QR down to the truncation floor
+  const T rel = T(0.1 * c.eps);
+  T tail2 = 0;
+  const int rp = pivoted_qr(D, m, n, kDenseRank, rel * rel / T(min(m, n)), tau, nrm2, perm, &tail2);
+  if (tp && threadIdx.x == 0) {
+    const long long t1 = clock64();
+    tp[1] += (unsigned long long)(t1 - t0);
+    t0 = t1;
+  }
+  // M = P R'^T (n x r'), Jacobi SVD of its columns: M V = W
+  for (int idx = threadIdx.x; idx < n * rp; idx += NT) {
+    const int j = idx % n, i = idx / n;
+    M[perm[j] + i * n] = j >= i ? D[i + j * m] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < rp * rp; idx += NT) V[idx] = (idx % rp == idx / rp) ? T(1) : T(0);
+  __syncthreads();
+  int sweeps = 0;
+  if (rp > 0) sweeps = jacobi_svd(M, V, n, rp, nrm2, T(c.jacobi_tol), T(0.01 * c.eps));
+  if (tp && threadIdx.x == 0) {
+    const long long t1 = clock64();
+    tp[3] += (unsigned long long)(t1 - t0);
+    tp[5] += 1ULL;
+    tp[6] += (unsigned long long)sweeps;
+    tp[7] += (unsigned long long)rp;
+    t0 = t1;
+  }
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < rp; ++j) {
+      nrm2[j] = sqrt(nrm2[j]);
+      s_ord[j] = j;
+    }
+    for (int j = 1; j < rp; ++j) {  // stable insertion sort, descending
+      int x = s_ord[j], i = j - 1;
+      while (i >= 0 && nrm2[s_ord[i]] < nrm2[x]) {
+        s_ord[i + 1] = s_ord[i];
+        --i;
+      }
+      s_ord[i + 1] = x;
+    }
+    const T smax = rp ? nrm2[s_ord[0]] : T(0);
+    int r = 0;
+    if (smax > T(0))
+      while (r < rp && nrm2[s_ord[r]] > T(c.eps) * smax) ++r;
+    if (r > t.cap || (rp == kDenseRank && tail2 > T(c.eps * c.eps) * smax * smax)) {
+      r = min(r, t.cap);
+      atomicAdd(c.status + 2, 1);
+    }
+    s_r = r;
+    c.flops += 2.0 * (double)m * n * kDenseRank + 2.0 * (double)m * n * rp + 6.0 * sweeps * (double)n * rp * rp;
+  }
+  __syncthreads();
+  const int r = s_r;
+  // X = Q' [V_sel S; 0] through the scratch, Y = W_sel / s
+  T* OX = c.scratch;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    OX[i + (int64_t)j * m] = i < rp ? V[i + s_ord[j] * rp] * nrm2[s_ord[j]] : T(0);
+  }
+  __syncthreads();
+  apply_q_group<T, NT / 32>(D, m, rp, tau, OX, m, r, threadIdx.x);
+  __syncthreads();
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) stv(c, t.a, idx % m, idx / m, OX[idx]);
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    stv(c, t.b, i, j, M[i + s_ord[j] * n] / nrm2[s_ord[j]]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
+  if (tp && threadIdx.x == 0) tp[4] += (unsigned long long)(clock64() - t0);
+}
+
 // (a, b) <- truncation of sum_pieces sign X Y^T (stack, compress, store).
 template <class T>
 __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
@@ -867,6 +1246,20 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   if (m == 0 || n == 0) {
     if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
     return;
+  }
+  if (sizeof(T) == 4 && m <= kDenseMax && n <= kDenseMax) {
+    // dense route when the stack would need more than one compression
+    __shared__ int s_wsum;
+    if (threadIdx.x == 0) s_wsum = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < t.list_count; q += NT) atomicAdd(&s_wsum, ncols(c, c.pieces[t.list_begin + q].X));
+    __syncthreads();
+    const bool dense = s_wsum > c.compress_at;
+    __syncthreads();
+    if (dense) {
+      task_trunc_dense(c, t, smem);
+      return;
+    }
   }
   const int64_t R = c.rows_max;
   T* SX = c.scratch;
@@ -884,6 +1277,23 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) stv(c, t.b, idx % n, idx / n, __ldcg(OY + idx));
   __syncthreads();
   if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
+}
+
+// One task's body with the whole CTA (SEQ bodies hold no SEQ tasks).
+template <class T>
+__device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
+  switch (t.type) {
+    case TK_GETRF: task_getrf(c, t, smem); break;
+    case TK_TRSM_L:
+    case TK_TRSM_UT:
+    case TK_TRSM_U: task_trsm(c, t, smem); break;
+    case TK_PROJ: task_proj(c, t, smem); break;
+    case TK_ROWMV: task_rowmv(c, t, smem); break;
+    case TK_TRUNC: task_trunc(c, t, smem); break;
+    case TK_DADD: task_dadd(c, t, smem); break;
+    case TK_RSOLVE: task_rsolve(c, t, smem); break;
+    default: break;
+  }
 }
 
 // ---------------------------------------------------------------- executor
@@ -952,18 +1362,17 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
       c.piv = P.piv;
       c.terms = P.terms;
       c.pieces = P.pieces;
+      c.micro = P.micro;
       c.eps = P.eps;
-      switch (t.type) {
-        case TK_GETRF: task_getrf(c, t, smem); break;
-        case TK_TRSM_L:
-        case TK_TRSM_UT:
-        case TK_TRSM_U: task_trsm(c, t, smem); break;
-        case TK_PROJ: task_proj(c, t, smem); break;
-        case TK_ROWMV: task_rowmv(c, t, smem); break;
-        case TK_TRUNC: task_trunc(c, t, smem); break;
-        case TK_DADD: task_dadd(c, t, smem); break;
-        case TK_RSOLVE: task_rsolve(c, t, smem); break;
-        default: break;
+      if (t.type == TK_SEQ) {
+        for (int q = 0; q < t.list_count; ++q) {
+          const Task u = c.micro[t.list_begin + q];
+          run_task(c, u, smem);
+          __threadfence_block();
+          __syncthreads();
+        }
+      } else {
+        run_task(c, t, smem);
       }
     }
     __threadfence();
@@ -1022,6 +1431,12 @@ size_t exec_smem_bytes(int elem_size) {
   // max over task kinds: TRUNC (3 stack-wide vectors + G + V), GETRF/TRSM
   // (64 x 64 + 64 ints), staged GEMM chunks (2 x 64 x KC)
   size_t trunc = (size_t)elem_size * (3 * kTruncStack + 2 * kTruncStack * kTruncStack);
+  if (elem_size == 4) {  // dense truncation route (FP32 only)
+    size_t region0 = (size_t)4 * (kDenseMax * kDenseRank + kDenseRank * kDenseRank);
+    if (region0 < (size_t)4 * 2 * 64 * KC) region0 = (size_t)4 * 2 * 64 * KC;
+    const size_t dense = region0 + (size_t)4 * (kDenseMax * kDenseMax + 2 * kDenseMax) + sizeof(int) * kDenseMax;
+    if (dense > trunc) trunc = dense;
+  }
   size_t lu = (size_t)elem_size * 64 * 64 + 64 * sizeof(int);
   size_t gemm = (size_t)elem_size * 2 * 64 * KC;
   size_t m = trunc > lu ? trunc : lu;

@@ -15,6 +15,7 @@ struct ProbSched {
   const Task* tasks;
   const Term* terms;
   const Piece* pieces;
+  const Task* micro;        // bodies of SEQ tasks
   const int64_t* succ_ptr;  // ntasks + 1
   const int32_t* succ_idx;
   int32_t* indeg;           // unfinished predecessors (reset before every launch)

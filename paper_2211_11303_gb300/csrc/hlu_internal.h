@@ -42,15 +42,16 @@ enum TaskType : int32_t {
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
   TK_RSOLVE = 8,  // c <- tri(a)^-1 (c - sum_terms A_t B_t): one tile of a triangular solve;
                   // flags & TF_UPPER: U^-1, else L^-1 P (pivots at piv_off)
-  TK_NUM = 9,
-  TK_FENCE = 9    // no work: orders re-use of temporary memory after its readers
+  TK_SEQ = 9,     // run micro tasks [list_begin, list_begin + list_count) in order, one CTA
+  TK_NUM = 10,
+  TK_FENCE = 10   // no work: orders re-use of temporary memory after its readers
 };
 enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2 };
 
 struct Task {
   int32_t type;
   int32_t flags;
-  int32_t list_begin, list_count;  // ROWMV terms or TRUNC pieces
+  int32_t list_begin, list_count;  // ROWMV terms, TRUNC pieces or SEQ micro tasks
   View a, b, c;
   int64_t piv_off;   // pivot vector offset (int32 elements) for leaf tasks
   int32_t out_slot;  // rank slot written by the task (-1: none)
@@ -78,6 +79,7 @@ struct Piece {
 // ---- a complete schedule -----------------------------------------------------
 struct Schedule {
   std::vector<Task> tasks;
+  std::vector<Task> micro;  // bodies of SEQ tasks
   std::vector<Term> terms;
   std::vector<Piece> pieces;
   std::vector<int64_t> pred_ptr;  // CSR of predecessors (all with smaller index)
@@ -120,9 +122,15 @@ struct SchedStats {
 // `tile` DOFs is factored as one dense tile (tile <= leaf keeps the block tree
 // as it is).  factor_blocks (optional) receives the factor tree the schedules
 // and the arena layout refer to.
+// `solve_group`: in the solve schedule, the triangular solve of every diagonal
+// block whose cluster holds at most solve_group DOFs (and is not a leaf)
+// becomes one SEQ task run by one CTA (0: no grouping).
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
-                     int32_t nrhs_max, int32_t tile, ArenaLayout& L, Schedule& factor, Schedule& solve,
-                     SchedStats& st, std::vector<Block>* factor_blocks);
+                     int32_t nrhs_max, int32_t tile, int32_t solve_group, ArenaLayout& L, Schedule& factor,
+                     Schedule& solve, SchedStats& st, std::vector<Block>* factor_blocks);
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile);
+
+// process-wide solve grouping (hlu_set_solve_group) for schedules built from here on
+int32_t current_solve_group();
 
 }  // namespace hlu

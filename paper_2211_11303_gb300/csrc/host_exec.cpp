@@ -25,6 +25,7 @@ struct HostCtx {
   int32_t* piv;
   const Term* terms;
   const Piece* pieces;
+  const Task* micro;
   double eps;
   int32_t status = 0;
   int32_t cap_hits = 0;
@@ -376,6 +377,9 @@ void run_task(HostCtx<T>& c, const Task& t) {
     case TK_TRUNC: h_trunc(c, t); break;
     case TK_DADD: h_dadd(c, t); break;
     case TK_RSOLVE: h_rsolve(c, t); break;
+    case TK_SEQ:
+      for (int32_t q = 0; q < t.list_count; ++q) run_task(c, c.micro[t.list_begin + q]);
+      break;
     case TK_FENCE: break;
     default: throw std::logic_error("task type");
   }
@@ -426,6 +430,7 @@ int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, doub
   c.piv = piv;
   c.terms = S.terms.data();
   c.pieces = S.pieces.data();
+  c.micro = S.micro.data();
   c.eps = eps;
   for (int64_t t : exec_order(S, order_seed)) {
     if (limit >= 0 && t >= limit) continue;

@@ -118,7 +118,12 @@ class Sched {
         // first use of this chunk in this pass: a no-work fence task waits for
         // every task that touched the chunk's previous occupants
         chunk_fence_task_[ch] = -1;
-        if (!chunk_occ_[ch].empty()) {
+        if (!chunk_occ_[ch].empty() && in_group_) {
+          // inside a SEQ group the group itself waits for the previous users
+          for (int32_t old : chunk_occ_[ch])
+            for (int64_t r = acc_head_[old]; r >= 0; r = acc_next_[r]) dep(acc_task_[r]);
+          chunk_fence_task_[ch] = cur_;
+        } else if (!chunk_occ_[ch].empty()) {
           Task f = make(TK_FENCE);
           int32_t saved_cur = cur_;
           std::vector<int32_t> saved_deps;
@@ -264,6 +269,10 @@ class Sched {
 
   // ---------------------------------------------------------------- tasks
   int32_t begin(const Task& t) {
+    if (in_group_) {  // a micro task of the open SEQ group: its accesses are the group's
+      S_->micro.push_back(t);
+      return cur_;
+    }
     int32_t id = (int32_t)S_->tasks.size();
     S_->tasks.push_back(t);
     stamp_.push_back(-1);
@@ -320,6 +329,7 @@ class Sched {
     touch(b.seg0, false);
   }
   void end() {
+    if (in_group_) return;
     std::sort(deps_.begin(), deps_.end());
     S_->pred_idx.insert(S_->pred_idx.end(), deps_.begin(), deps_.end());
     S_->pred_ptr.push_back((int64_t)S_->pred_idx.size());
@@ -473,7 +483,29 @@ class Sched {
   }
 
   // ---------------------------------------------------------------- triangular
+  // SEQ groups: a diagonal block's whole triangular solve as one task
+  bool group_here(int32_t d) const {
+    return group_max_ > 0 && !in_group_ && kind(d) != KIND_DENSE && sz(rowc(d)) <= group_max_;
+  }
+  void group_begin() {
+    Task t = make(TK_SEQ);
+    t.list_begin = (int32_t)S_->micro.size();
+    begin(t);
+    in_group_ = true;
+  }
+  void group_end() {
+    in_group_ = false;
+    Task& t = S_->tasks[cur_];
+    t.list_count = (int32_t)S_->micro.size() - t.list_begin;
+    end();
+  }
   void solve_lower(int32_t d, const MV& V) {
+    if (group_here(d)) {
+      group_begin();
+      solve_lower(d, V);
+      group_end();
+      return;
+    }
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_L, d, V);
       return;
@@ -496,6 +528,12 @@ class Sched {
     solve_upperT(son(d, 1, 1), W1);
   }
   void solve_upper(int32_t d, const MV& V) {
+    if (group_here(d)) {
+      group_begin();
+      solve_upper(d, V);
+      group_end();
+      return;
+    }
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_U, d, V);
       return;
@@ -809,7 +847,8 @@ class Sched {
     }
   }
 
-  void solve_all(int32_t nrhs_max) {
+  void solve_all(int32_t nrhs_max, int32_t group_max) {
+    group_max_ = group_max;
     MV W;
     W.buf = new_buf_leaves(0);  // per-segment tracking over the whole vector
     W.clus = 0;
@@ -858,6 +897,8 @@ class Sched {
   std::vector<int32_t> stamp_;
   std::vector<int32_t> deps_;
   int32_t cur_ = -1;
+  bool in_group_ = false;
+  int32_t group_max_ = 0;
 };
 
 }  // namespace
@@ -898,7 +939,8 @@ std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<
 }
 
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bfull, int32_t rank_cap,
-                     int32_t nrhs_max, int32_t tile, ArenaLayout& L, Schedule& factor, Schedule& solve,
+                     int32_t nrhs_max, int32_t tile, int32_t solve_group, ArenaLayout& L, Schedule& factor,
+                     Schedule& solve,
                      SchedStats& st, std::vector<Block>* factor_blocks) {
   std::vector<Block> Bt = factor_tree(C, Bfull, tile);
   const std::vector<Block>& B = Bt;
@@ -963,7 +1005,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   }
   {
     Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
-    s.solve_all(nrhs_max);
+    s.solve_all(nrhs_max, solve_group);
     st.temp_elems += s.temp_elems_;
   }
   factor.n_edges = (int64_t)factor.pred_idx.size();

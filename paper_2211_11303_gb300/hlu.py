@@ -77,6 +77,7 @@ SIGNATURES = {
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
+    "hlu_set_solve_group": (None, [_i32]),
     "hlu_launch_count": (_i64, []),
     "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
     "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
@@ -93,6 +94,7 @@ SIGNATURES = {
     "hlu_debug_factor_prefix": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "hlu_debug_task_record": (_i32, [_vp, _i64, _vp]),
     "hlu_debug_factor_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "hlu_debug_solve_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -215,17 +217,18 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SEQ", "FENCE"]
 
 
 def hlu_factor_profile(h):
     """{kind: (tasks, wait_cycles, run_cycles)} of the last factorisation."""
-    out = (ctypes.c_uint64 * 38)()
+    k0 = 3 * len(TASK_KINDS)
+    out = (ctypes.c_uint64 * (k0 + 8))()
     _check(lib().hlu_factor_profile(_vp(h), out))
     d = {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
-    d["trunc_phases"] = {"qr_cycles": out[31], "core_cycles": out[32], "jacobi_cycles": out[33],
-                         "select_apply_cycles": out[34], "compressions": out[35], "sweeps": out[36],
-                         "width_sum": out[37]}
+    d["trunc_phases"] = {"qr_cycles": out[k0 + 1], "core_cycles": out[k0 + 2], "jacobi_cycles": out[k0 + 3],
+                         "select_apply_cycles": out[k0 + 4], "compressions": out[k0 + 5], "sweeps": out[k0 + 6],
+                         "width_sum": out[k0 + 7]}
     return d
 
 
@@ -331,6 +334,10 @@ def hlu_launch_count():
 
 def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
     _check(lib().hlu_set_trunc_params(int(compress_at), float(jacobi_tol)))
+
+
+def hlu_set_solve_group(dofs):
+    lib().hlu_set_solve_group(int(dofs))
 
 
 def hlu_set_tile(t):

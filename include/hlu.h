@@ -140,6 +140,28 @@ int hlu_export_csr(const hlu_handle* h, int64_t* rowptr, int32_t* col, double* v
  * double[N].  Asynchronous on stream. */
 int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream);
 
+/* hlu_rhs_manufactured_noalloc - the same load vector as hlu_rhs_manufactured,
+ * computed without allocating any memory.  The paper has no counterpart: this
+ * entry serves callers that must not allocate, such as a serving loop that
+ * admits work against a fixed HBM budget (an allocation behind its back can
+ * push the device over the budget or fail under memory pressure) and
+ * latency-critical loops (cudaMalloc synchronises the device).
+ * hlu_rhs_manufactured allocates its element-contribution scratch and the
+ * sort's temporaries on every call; this variant keeps the 6 contributions
+ * per tetrahedron in a fixed device array of 524,288 entries (6 MiB) and
+ * adds them into b with atomics, so the result equals hlu_rhs_manufactured's
+ * up to the order of the floating-point additions (relative differences of
+ * order 1e-16 per entry).  Limit: 36 n^3 <= 524,288, i.e. Kuhn meshes with
+ * n <= 24; larger meshes return HLU_ERR_ARG with a message and write nothing.
+ * Nothing needs to start at zero: every scratch entry is written before it is
+ * read, and b_dev is cleared by the call.  The first call on each device looks
+ * up the scratch's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The scratch is
+ * shared by all calls on a device: calls that overlap in time (other streams
+ * or host threads) race on it and must be serialised by the caller.
+ * b_dev: device double[N].  Asynchronous on stream. */
+int hlu_rhs_manufactured_noalloc(const hlu_handle* h, double* b_dev, void* stream);
+
 /* hlu_spmv - y = A x for nrhs columns (FP64 CSR), device pointers, ld >= N.
  * Asynchronous.  Used by the Krylov solvers and exposed for tests. */
 int hlu_spmv(const hlu_handle* h, const double* x_dev, double* y_dev, int32_t nrhs, int64_t ld,

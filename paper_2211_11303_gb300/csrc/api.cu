@@ -763,6 +763,16 @@ int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream) {
   return HLU_OK;
 }
 
+int hlu_rhs_manufactured_noalloc(const hlu_handle* h, double* b_dev, void* stream) {
+  if (!h || !b_dev) return fail(HLU_ERR_ARG, "null argument");
+  const int64_t need = (int64_t)36 * h->n * h->n * h->n;
+  if (need > rhs_noalloc_max_entries())
+    return fail(HLU_ERR_ARG, "mesh needs " + std::to_string(need) + " element contributions; the fixed scratch holds " +
+                                 std::to_string(rhs_noalloc_max_entries()) + " (n <= 24)");
+  CKR(manufactured_rhs_noalloc(h->mesh, h->kappa, b_dev, (cudaStream_t)stream), "rhs (no allocation)");
+  return HLU_OK;
+}
+
 int hlu_spmv(const hlu_handle* h, const double* x, double* y, int32_t nrhs, int64_t ld, void* stream) {
   if (!h || !x || !y || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
   CKR(spmv(h->A.rowptr, h->A.col, h->A.val, h->A.N, x, ld, y, ld, nrhs, (cudaStream_t)stream), "spmv");

@@ -23,6 +23,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "launch_count.h"
 
@@ -917,6 +918,65 @@ cudaError_t invert_perm(int32_t N, const int32_t* perm, int32_t* iperm, cudaStre
   note_launch();
   k_invert_perm<<<grid_for(N), 256, 0, s>>>(N, perm, iperm);
   return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- load vector without allocation
+// Variant of manufactured_rhs whose scratch (the 6 element contributions per
+// tetrahedron: DOF key and value) lives in a fixed file-scope device array
+// instead of per-call allocations, and whose reduction adds the contributions
+// into b with atomics instead of a sort (which would need temporary storage).
+namespace {
+
+constexpr int64_t kRhsScratchEntries = int64_t(1) << 19;  // 36 n^3 <= 524,288: n <= 24
+static __device__ __align__(256) unsigned char g_rhs_scratch[kRhsScratchEntries * (sizeof(double) + sizeof(int32_t))];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_rhs_mu;
+void* g_rhs_ptr[kMaxDevices] = {};
+
+__global__ void k_add_rhs(int64_t ne, const int32_t* keys, const double* vals, int64_t N, double* b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = keys[e];
+    if (k >= 0 && k < N) atomicAdd(b + k, vals[e]);
+  }
+}
+
+}  // namespace
+
+int64_t rhs_noalloc_max_entries() { return kRhsScratchEntries; }
+
+cudaError_t manufactured_rhs_noalloc(const DevMesh& m, double kappa, double* b, cudaStream_t s) {
+  const int64_t nt = (int64_t)6 * m.n * m.n * m.n;
+  const int64_t ne = nt * 6;
+  if (ne > kRhsScratchEntries) return cudaErrorInvalidValue;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* base = nullptr;
+  {
+    // set-up, once per device (with that device current): the scratch's
+    // device address
+    std::lock_guard<std::mutex> lk(g_rhs_mu);
+    if (!g_rhs_ptr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_rhs_scratch));
+      g_rhs_ptr[dev] = p;
+    }
+    base = g_rhs_ptr[dev];
+  }
+  // values first (8-byte aligned at the 256-byte aligned base), keys after
+  double* vals = reinterpret_cast<double*>(base);
+  int32_t* keys = reinterpret_cast<int32_t*>(vals + kRhsScratchEntries);
+  // every scratch entry read below is written first by k_rhs_coo; b starts at 0
+  CK(cudaMemsetAsync(b, 0, sizeof(double) * m.N, s));
+  note_launch();
+  k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
+  CK(cudaGetLastError());
+  note_launch();
+  k_add_rhs<<<grid_for(ne), 256, 0, s>>>(ne, keys, vals, m.N, b);
+  CK(cudaGetLastError());
+  return cudaSuccess;
 }
 
 }  // namespace hlu

@@ -38,6 +38,11 @@ struct FillDesc {
 cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m);
 cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A);
 cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s);
+// manufactured_rhs without allocations (fixed device scratch; see build.cu);
+// cudaErrorInvalidValue when the mesh needs more than rhs_noalloc_max_entries()
+// element contributions
+cudaError_t manufactured_rhs_noalloc(const DevMesh& m, double kappa, double* b, cudaStream_t s);
+int64_t rhs_noalloc_max_entries();
 cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream_t s, HostTrees& out,
                         int32_t* d_perm_out);
 cudaError_t invert_perm(int32_t N, const int32_t* perm, int32_t* iperm, cudaStream_t s);

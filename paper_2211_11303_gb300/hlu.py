@@ -64,6 +64,7 @@ SIGNATURES = {
     "hlu_export_trees": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "hlu_export_csr": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "hlu_rhs_manufactured": (_i32, [_vp, _vp, _vp]),
+    "hlu_rhs_manufactured_noalloc": (_i32, [_vp, _vp, _vp]),
     "hlu_spmv": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
     "hlu_factor": (_i32, [_vp, _i32, _vp]),
     "hlu_factor_stats": (_i32, [_vp, _P(hlu_factor_info)]),
@@ -196,6 +197,14 @@ def hlu_export_csr(h):
 def hlu_rhs_manufactured(h, b, stream=None):
     p, nr, ld = _vec(b, hlu_n(h))
     _check(lib().hlu_rhs_manufactured(_vp(h), p, _stream(stream)))
+
+
+def hlu_rhs_manufactured_noalloc(h, b, stream=None):
+    """hlu_rhs_manufactured without allocations (fixed scratch, meshes n <= 24)."""
+    pb, nr, _ = _vec(b, hlu_n(h))
+    if nr != 1:
+        raise ValueError("b must be one column")
+    _check(lib().hlu_rhs_manufactured_noalloc(_vp(h), pb, _stream(stream)))
 
 
 def hlu_spmv(h, x, y, stream=None):

@@ -359,9 +359,23 @@ __device__ void task_trsm(Ctx<T>& c, const Task& t, char* smem) {
   const int k = ncols(c, t.b);
   T* A = reinterpret_cast<T*>(smem);
   int* perm = reinterpret_cast<int*>(A + n * n);
-  for (int idx = threadIdx.x; idx < n * n; idx += NT) A[idx] = ldv(c, t.a, idx % n, idx / n);
+  T* dinv = reinterpret_cast<T*>(perm + 64);
+  for (int b0 = threadIdx.x; b0 < n * n; b0 += 4 * NT) {  // loads first, then the stores
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = b0 + u * NT;
+      v[u] = idx < n * n ? ldv(c, t.a, idx % n, idx / n) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (b0 + u * NT < n * n) A[b0 + u * NT] = v[u];
+  }
   if (t.type == TK_TRSM_L)
     for (int i = threadIdx.x; i < n; i += NT) perm[i] = __ldcg(c.piv + t.piv_off + i);
+  __syncthreads();
+  if (t.type != TK_TRSM_L)
+    for (int i = threadIdx.x; i < n; i += NT) dinv[i] = T(1) / A[i + i * n];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = lane, r1 = lane + 32;
@@ -379,7 +393,7 @@ __device__ void task_trsm(Ctx<T>& c, const Task& t, char* smem) {
       if (r0 < n) v0 = ldv(c, t.b, r0, j);
       if (r1 < n) v1 = ldv(c, t.b, r1, j);
       for (int l = 0; l < n; ++l) {
-        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) / A[l + l * n];
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) * dinv[l];
         if (r0 == l) v0 = x;
         if (r1 == l) v1 = x;
         if (r0 > l && r0 < n) v0 -= A[l + r0 * n] * x;
@@ -389,7 +403,7 @@ __device__ void task_trsm(Ctx<T>& c, const Task& t, char* smem) {
       if (r0 < n) v0 = ldv(c, t.b, r0, j);
       if (r1 < n) v1 = ldv(c, t.b, r1, j);
       for (int l = n - 1; l >= 0; --l) {
-        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) / A[l + l * n];
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) * dinv[l];
         if (r0 == l) v0 = x;
         if (r1 == l) v1 = x;
         if (r0 < l) v0 -= A[r0 + l * n] * x;
@@ -587,6 +601,7 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
   const int tmax = min(m, w);
   if (wg == 0) {
     T s = 0;
+    #pragma unroll 4
     for (int i = 1 + lane; i < m; i += 32) {
       const T x = S[i];
       s += x * x;
@@ -625,6 +640,7 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
         d[q] = 0;
         top[q] = col[q][j];
       }
+      #pragma unroll 4
       for (int i = j + 1 + lane; i < m; i += 32) {
         const T v = cj[i];
 #pragma unroll
@@ -635,15 +651,28 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
       for (int q = 0; q < 4; ++q) d[q] = (top[q] + sc * warp_sum(d[q])) * tj;
       const bool own_next = c0 == j + 1;
       T nn = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const T v = cj[i] * sc;
+      // four rows per lane at a time: all loads issued before the stores
+      for (int i0 = j + 1 + lane; i0 < m; i0 += 128) {
+        T v[4], x[4][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < nc) {
-            const T x = col[q][i] - d[q] * v;
-            col[q][i] = x;
-            if (q == 0 && i > j + 1) nn += x * x;
-          }
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          v[u] = i < m ? cj[i] * sc : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x[u][q] = (i < m && q < nc) ? col[q][i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q < nc) {
+                const T y = x[u][q] - d[q] * v[u];
+                col[q][i] = y;
+                if (q == 0 && i > j + 1) nn += y * y;
+              }
+        }
       }
       if (lane == 0)
 #pragma unroll
@@ -691,6 +720,7 @@ __device__ void apply_q_group(const T* S, int m, int tmax, const T* tau, T* O, i
         d[q] = 0;
         top[q] = col[q][j];
       }
+      #pragma unroll 4
       for (int i = j + 1 + lane; i < m; i += 32) {
         const T v = cj[i];
 #pragma unroll
@@ -699,11 +729,23 @@ __device__ void apply_q_group(const T* S, int m, int tmax, const T* tau, T* O, i
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) d[q] = (top[q] + warp_sum(d[q])) * tj;
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const T v = cj[i];
+      for (int i0 = j + 1 + lane; i0 < m; i0 += 128) {
+        T v[4], x[4][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < nc) col[q][i] -= d[q] * v;
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          v[u] = i < m ? cj[i] : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x[u][q] = (i < m && q < nc) ? col[q][i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q < nc) col[q][i] = x[u][q] - d[q] * v[u];
+        }
       }
       if (lane == 0)
 #pragma unroll
@@ -930,7 +972,9 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
   int32_t* cap_hits = c.status + 2;
   auto stack_norm = [&](int w_) -> double {
     TC px = 0, py = 0;
+    #pragma unroll 4
     for (int64_t idx = threadIdx.x; idx < (int64_t)m * w_; idx += NT) px += SX[idx] * SX[idx];
+    #pragma unroll 4
     for (int64_t idx = threadIdx.x; idx < (int64_t)n * w_; idx += NT) py += SY[idx] * SY[idx];
     TC sx = block_sum(px, s_rx);
     TC sy = block_sum(py, s_rx);
@@ -955,13 +999,33 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
     for (int64_t idx = threadIdx.x; idx < (int64_t)m * w; idx += NT) SX[(int64_t)W * m + idx] = TC(0);
     for (int64_t idx = threadIdx.x; idx < (int64_t)n * w; idx += NT) SY[(int64_t)W * n + idx] = TC(0);
     __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < (int64_t)P.X.rows * w; idx += NT) {
-      int i = (int)(idx % P.X.rows), j = (int)(idx / P.X.rows);
-      SX[(P.xoff + i) + (int64_t)(W + j) * m] = sg * TC(ldv(c, P.X, i, j));
+    // four elements per thread at a time: all loads issued before the stores
+    for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.X.rows * w; b0 += 4 * NT) {
+      TC v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        v[u] = idx < (int64_t)P.X.rows * w ? TC(ldv(c, P.X, idx % P.X.rows, idx / P.X.rows)) : TC(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        if (idx < (int64_t)P.X.rows * w)
+          SX[(P.xoff + idx % P.X.rows) + (int64_t)(W + idx / P.X.rows) * m] = sg * v[u];
+      }
     }
-    for (int64_t idx = threadIdx.x; idx < (int64_t)P.Y.rows * w; idx += NT) {
-      int i = (int)(idx % P.Y.rows), j = (int)(idx / P.Y.rows);
-      SY[(P.yoff + i) + (int64_t)(W + j) * n] = TC(ldv(c, P.Y, i, j));
+    for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.Y.rows * w; b0 += 4 * NT) {
+      TC v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        v[u] = idx < (int64_t)P.Y.rows * w ? TC(ldv(c, P.Y, idx % P.Y.rows, idx / P.Y.rows)) : TC(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        if (idx < (int64_t)P.Y.rows * w) SY[(P.yoff + idx % P.Y.rows) + (int64_t)(W + idx / P.Y.rows) * n] = v[u];
+      }
     }
     W += w;
     __syncthreads();
@@ -1437,7 +1501,7 @@ size_t exec_smem_bytes(int elem_size) {
     const size_t dense = region0 + (size_t)4 * (kDenseMax * kDenseMax + 2 * kDenseMax) + sizeof(int) * kDenseMax;
     if (dense > trunc) trunc = dense;
   }
-  size_t lu = (size_t)elem_size * 64 * 64 + 64 * sizeof(int);
+  size_t lu = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
   size_t gemm = (size_t)elem_size * 2 * 64 * KC;
   size_t m = trunc > lu ? trunc : lu;
   return m > gemm ? m : gemm;

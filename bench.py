@@ -145,6 +145,77 @@ def arm_config(args, world=1):
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
+def serving_run(args):
+    """Continuous-batching serving sample: Poisson arrivals of requests with
+    mesh n ~ U{lo..hi}, kappa ~ U[1, 12], 1..16 seeded N(0,1) RHS each, served
+    by paper_2211_11303_gb300.serve (factor cache, HBM-budget admission, one
+    batched GMRES step for all running requests)."""
+    import numpy as np
+
+    import synth
+    from paper_2211_11303_gb300 import hlu, serve
+
+    reqs = synth.serving_requests(count=args.serving, seed=5000, n_lo=args.serve_n_lo, n_hi=args.serve_n_hi,
+                                  k_lo=1.0, k_hi=12.0, r_lo=1, r_hi=16, rate=args.serve_rate)
+
+    def rhs_of(req, N):
+        return np.stack([synth.normal(synth.rhs_seed(4, req["id"], j), N) for j in range(req["nrhs"])], axis=1)
+
+    srv = serve.Server(hbm_budget_bytes=args.serve_budget_gb * 1e9, max_active=64, leaf=args.leaf, eta=args.eta,
+                       eps=args.eps, precision=hlu.HLU_FP32 if args.precision == "fp32" else hlu.HLU_FP64,
+                       restart=args.restart, tol=args.tol, maxit=args.maxit)
+    try:
+        res = srv.run(reqs, rhs_of)
+    finally:
+        srv.close()
+    summ = serve.latency_summary(res)
+    return dict(summ, rate_per_s=args.serve_rate, n_range=[args.serve_n_lo, args.serve_n_hi],
+                kappa_range=[1.0, 12.0], rhs_range=[1, 16], wall_s=srv.stats["wall_s"],
+                solves_per_s=summ["rhs_columns"] / srv.stats["wall_s"],
+                max_relres=max(r["relres"] for r in res), all_converged=all(r["converged"] for r in res),
+                factorisations=srv.stats["factorisations"], cache_hits=srv.stats["cache_hits"],
+                evictions=srv.stats["evictions"], max_active=srv.stats["max_active"],
+                gmres_steps=srv.stats["steps"], budget_gb=args.serve_budget_gb,
+                note="latency = finish - arrival, including any factorisation the request needed")
+
+
+def batched_run(args):
+    """Batched workload: `args.batched` seeded problems (mesh n ~ U{6..16},
+    kappa ~ U[1, 10]) factored in ONE persistent launch, against one launch
+    per problem."""
+    import torch
+
+    import synth
+    from paper_2211_11303_gb300 import hlu
+
+    prec = hlu.HLU_FP32 if args.precision == "fp32" else hlu.HLU_FP64
+    probs = synth.batched_problems(count=args.batched, seed=3000, n_lo=6, n_hi=16, k_lo=1.0, k_hi=10.0)
+    hs = [hlu.hlu_build(n, k, args.leaf, args.eta, args.eps) for n, k in probs]
+    try:
+        hlu.hlu_factor_batch(hs, prec)  # warm-up (allocation, first launch)
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            hlu.hlu_factor_batch(hs, prec)
+        torch.cuda.synchronize()
+        batched_ms = 1000.0 * (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for h in hs:
+                hlu.hlu_factor(h, prec)
+        torch.cuda.synchronize()
+        seq_ms = 1000.0 * (time.perf_counter() - t0) / reps
+        flops = sum(hlu.hlu_factor_stats(h)["flops"] for h in hs)
+        dofs = sum(hlu.hlu_n(h) for h in hs)
+    finally:
+        for h in hs:
+            hlu.hlu_destroy(h)
+    return {"problems": len(probs), "n_range": [6, 16], "kappa_range": [1.0, 10.0], "dofs_total": dofs,
+            "batched_factor_ms": batched_ms, "one_launch_per_problem_ms": seq_ms,
+            "speedup": seq_ms / batched_ms, "batched_factor_gflops": flops / (batched_ms / 1000.0) / 1e9}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -312,6 +383,10 @@ def run_gpu(args):
                 "d2h_bytes_per_step": nrhs * N * 8},
         "gpu_launches": launches,
     }
+    if rank == 0 and args.batched > 0:
+        line["batched"] = batched_run(args)
+    if rank == 0 and args.serving > 0:
+        line["serving"] = serving_run(args)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_subprocess(args.ref_n)
@@ -344,6 +419,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=64, help="problems of the batched-factor sample (0: none)")
+    ap.add_argument("--serving", type=int, default=24, help="requests of the serving sample (0: none)")
+    ap.add_argument("--serve-n-lo", type=int, default=8)
+    ap.add_argument("--serve-n-hi", type=int, default=14)
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

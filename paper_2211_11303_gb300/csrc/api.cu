@@ -175,7 +175,7 @@ std::mutex g_batch_mu;            // serialises batched launches (shared order b
 unsigned long long* g_batch_q = nullptr;  // ready queue of batched launches
 int64_t g_batch_q_len = 0;
 std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
-constexpr size_t kCacheEntries = 8;
+constexpr size_t kCacheEntries = 16;
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   const unsigned char* c = (const unsigned char*)p;

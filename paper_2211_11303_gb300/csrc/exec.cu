@@ -854,6 +854,100 @@ __device__ int jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol, T negl_rel) 
   return sweep + 1;
 }
 
+constexpr int kDenseMax = 128;
+constexpr int kDenseRank = 40;
+
+// Householder QR with column pivoting of D (m x n, ld m, shared memory) in
+// place, stopped after kmax steps or once the trailing block's squared
+// Frobenius norm is <= rel2 ||D||_F^2.  perm[j] = original index of column j.
+// Returns the number of reflectors r'; *tail2 receives the dropped norm^2.
+template <class T>
+__device__ int pivoted_qr(T* D, int m, int n, int kmax, T rel2, T* tau, T* nrm2, int* perm, T* tail2) {
+  __shared__ int s_piv;
+  __shared__ T s_tail, s_thr, s_beta, s_sc, s_tau;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x; j < n; j += NT) perm[j] = j;
+  const int kend = min(kmax, min(m, n));
+  int k = 0;
+  for (;; ++k) {
+    for (int j = k + warp; j < n; j += NT / 32) {
+      T acc = 0;
+      for (int i = k + lane; i < m; i += 32) acc += D[i + j * m] * D[i + j * m];
+      acc = warp_sum(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tail = 0, best = T(-1);
+      int piv = k;
+      for (int j = k; j < n; ++j) {
+        tail += nrm2[j];
+        if (nrm2[j] > best) {
+          best = nrm2[j];
+          piv = j;
+        }
+      }
+      if (k == 0) s_thr = rel2 * tail;
+      s_tail = tail;
+      s_piv = piv;
+    }
+    __syncthreads();
+    if (k >= kend || s_tail <= s_thr) break;
+    const int pv = s_piv;
+    if (pv != k) {
+      for (int i = threadIdx.x; i < m; i += NT) {
+        const T x = D[i + k * m];
+        D[i + k * m] = D[i + pv * m];
+        D[i + pv * m] = x;
+      }
+      if (threadIdx.x == 0) {
+        const int pp = perm[k];
+        perm[k] = perm[pv];
+        perm[pv] = pp;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T ss = 0;
+      for (int i = k + 1 + lane; i < m; i += 32) ss += D[i + k * m] * D[i + k * m];
+      ss = warp_sum(ss);
+      if (lane == 0) {
+        const T alpha = D[k + k * m];
+        T beta = alpha, sc = 0, tj = 0;
+        if (ss > T(0)) {
+          const T nrm = sqrt(alpha * alpha + ss);
+          beta = alpha >= T(0) ? -nrm : nrm;
+          sc = T(1) / (alpha - beta);
+          tj = (beta - alpha) / beta;
+        }
+        s_beta = beta;
+        s_sc = sc;
+        s_tau = tj;
+        tau[k] = tj;
+      }
+      __syncwarp();
+      const T sc = s_sc;
+      for (int i = k + 1 + lane; i < m; i += 32) D[i + k * m] *= sc;
+      __syncwarp();
+      if (lane == 0) D[k + k * m] = s_beta;
+    }
+    __syncthreads();
+    const T tj = s_tau;
+    if (tj != T(0))
+      for (int j = k + 1 + warp; j < n; j += NT / 32) {
+        T d = 0;
+        for (int i = k + 1 + lane; i < m; i += 32) d += D[i + k * m] * D[i + j * m];
+        d = (warp_sum(d) + D[k + j * m]) * tj;
+        for (int i = k + 1 + lane; i < m; i += 32) D[i + j * m] -= d * D[i + k * m];
+        __syncwarp();
+        if (lane == 0) D[k + j * m] -= d;
+      }
+    __syncthreads();
+  }
+  *tail2 = s_tail;
+  return k;
+}
+
 // stack width at which a truncation compresses before adding the next piece
 // (the core SVD costs grow with the cube of the width); rank cap 32 + a
 // 64-wide piece still fit the stack
@@ -898,10 +992,26 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
     for (int l = max(i, j); l < W; ++l) acc.add(SX[i + (int64_t)l * m], SY[j + (int64_t)l * n]);
     G[i + j * p] = acc.value();
   }
-  for (int idx = threadIdx.x; idx < q * q; idx += NT) V[idx] = (idx % q == idx / q) ? TC(1) : TC(0);
   __syncthreads();
   lap(2);
-  const int sweeps = jacobi_svd(G, V, p, q, sv, TC(jtol), TC(0.01 * eps));
+  // pivoted QR of the core down to the truncation floor (G ~ Q_G R' P^T with
+  // r' rows kept), then the Jacobi SVD of M = P R'^T (q x r'): M V_M = W,
+  // G ~ Q_G V_M W^T; X <- Q_x Q_G V_M S and Y <- Q_y W S^-1 below
+  __shared__ TC s_tauG[kStackCols];
+  __shared__ int s_perm[kStackCols];
+  TC tail2 = 0;
+  const TC rel = TC(0.1 * eps);
+  const int rp = pivoted_qr(G, p, q, min(kDenseRank, min(p, q)), rel * rel / TC(min(p, q)), s_tauG, sv, s_perm,
+                            &tail2);
+  TC* M = V;
+  TC* Vs = V + q * rp;
+  for (int idx = threadIdx.x; idx < q * rp; idx += NT) {
+    const int j = idx % q, i = idx / q;
+    M[s_perm[j] + i * q] = j >= i ? G[i + j * p] : TC(0);
+  }
+  for (int idx = threadIdx.x; idx < rp * rp; idx += NT) Vs[idx] = (idx % rp == idx / rp) ? TC(1) : TC(0);
+  __syncthreads();
+  const int sweeps = rp > 0 ? jacobi_svd(M, Vs, q, rp, sv, TC(jtol), TC(0.01 * eps)) : 0;
   lap(3);
   if (tp && threadIdx.x == 0) {
     tp[5] += 1ULL;
@@ -910,13 +1020,13 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   }
   if (threadIdx.x == 0) {
     double f2 = 0;
-    for (int j = 0; j < q; ++j) {
+    for (int j = 0; j < rp; ++j) {
       sv[j] = sqrt(sv[j]);
       s_ord[j] = j;
       f2 += (double)sv[j] * (double)sv[j];
     }
     s_fro = sqrt(f2);
-    for (int j = 1; j < q; ++j) {  // stable insertion sort, descending
+    for (int j = 1; j < rp; ++j) {  // stable insertion sort, descending
       int x = s_ord[j], i = j - 1;
       while (i >= 0 && sv[s_ord[i]] < sv[x]) {
         s_ord[i + 1] = s_ord[i];
@@ -924,28 +1034,31 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
       }
       s_ord[i + 1] = x;
     }
-    TC smax = q ? sv[s_ord[0]] : TC(0);
+    TC smax = rp ? sv[s_ord[0]] : TC(0);
     int r = 0;
     if (smax > TC(0))
-      while (r < q && sv[s_ord[r]] > TC(eps) * smax) ++r;
-    if (r > cap) {
-      r = cap;
+      while (r < rp && sv[s_ord[r]] > TC(eps) * smax) ++r;
+    if (r > cap || (rp == kDenseRank && tail2 > TC(eps * eps) * smax * smax)) {
+      r = min(r, cap);
       atomicAdd(cap_hits, 1);
     }
     s_r = r;
-    *flops += 2.0 * (m + n) * W * W + 21.0 * (double)q * q * q + 2.0 * (m + n) * W * r;
+    *flops += 2.0 * (m + n) * W * W + 4.0 * (double)p * q * rp + 6.0 * sweeps * (double)q * rp * rp +
+              2.0 * (m + n) * W * r;
   }
   __syncthreads();
   const int r = s_r;
   *fro = s_fro;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) {
     const int i = (int)(idx % m), j = (int)(idx / m);
-    OX[i + (int64_t)j * ox] = i < p ? G[i + s_ord[j] * p] : TC(0);
+    OX[i + (int64_t)j * ox] = i < rp ? Vs[i + s_ord[j] * rp] * sv[s_ord[j]] : TC(0);
   }
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) {
     const int i = (int)(idx % n), j = (int)(idx / n);
-    OY[i + (int64_t)j * oy] = i < q ? V[i + s_ord[j] * q] : TC(0);
+    OY[i + (int64_t)j * oy] = i < q ? M[i + s_ord[j] * q] / sv[s_ord[j]] : TC(0);
   }
+  __syncthreads();
+  apply_q_group<TC, NT / 32>(G, p, rp, s_tauG, OX, ox, r, threadIdx.x);
   __syncthreads();
   if (threadIdx.x < kHalf)
     apply_q_group<TC, kHalf / 32>(SX, m, p, tauX, OX, ox, r, threadIdx.x);
@@ -1050,8 +1163,6 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
 // pivoting stops once the trailing block's Frobenius norm is below
 // 0.1 eps ||D||_F / sqrt(min(m, n)) (<= 0.1 eps s_1), and the one-sided Jacobi
 // SVD of the remaining r' x n rows gives the truncation s_i > eps s_1.
-constexpr int kDenseMax = 128;
-constexpr int kDenseRank = 40;
 constexpr int kStagePieces = 16;
 
 // Chunks of sum_pieces sign X Y^T restricted to the 64 x 64 tile (i0, j0).
@@ -1086,97 +1197,6 @@ struct PieceCursor {
                     yh - yl, min(KC, w[q] - l0), yl - j0, T(P.sign)};
   }
 };
-
-// Householder QR with column pivoting of D (m x n, ld m, shared memory) in
-// place, stopped after kmax steps or once the trailing block's squared
-// Frobenius norm is <= rel2 ||D||_F^2.  perm[j] = original index of column j.
-// Returns the number of reflectors r'; *tail2 receives the dropped norm^2.
-template <class T>
-__device__ int pivoted_qr(T* D, int m, int n, int kmax, T rel2, T* tau, T* nrm2, int* perm, T* tail2) {
-  __shared__ int s_piv;
-  __shared__ T s_tail, s_thr, s_beta, s_sc, s_tau;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = threadIdx.x; j < n; j += NT) perm[j] = j;
-  const int kend = min(kmax, min(m, n));
-  int k = 0;
-  for (;; ++k) {
-    for (int j = k + warp; j < n; j += NT / 32) {
-      T acc = 0;
-      for (int i = k + lane; i < m; i += 32) acc += D[i + j * m] * D[i + j * m];
-      acc = warp_sum(acc);
-      if (lane == 0) nrm2[j] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      T tail = 0, best = T(-1);
-      int piv = k;
-      for (int j = k; j < n; ++j) {
-        tail += nrm2[j];
-        if (nrm2[j] > best) {
-          best = nrm2[j];
-          piv = j;
-        }
-      }
-      if (k == 0) s_thr = rel2 * tail;
-      s_tail = tail;
-      s_piv = piv;
-    }
-    __syncthreads();
-    if (k >= kend || s_tail <= s_thr) break;
-    const int pv = s_piv;
-    if (pv != k) {
-      for (int i = threadIdx.x; i < m; i += NT) {
-        const T x = D[i + k * m];
-        D[i + k * m] = D[i + pv * m];
-        D[i + pv * m] = x;
-      }
-      if (threadIdx.x == 0) {
-        const int pp = perm[k];
-        perm[k] = perm[pv];
-        perm[pv] = pp;
-      }
-    }
-    __syncthreads();
-    if (warp == 0) {
-      T ss = 0;
-      for (int i = k + 1 + lane; i < m; i += 32) ss += D[i + k * m] * D[i + k * m];
-      ss = warp_sum(ss);
-      if (lane == 0) {
-        const T alpha = D[k + k * m];
-        T beta = alpha, sc = 0, tj = 0;
-        if (ss > T(0)) {
-          const T nrm = sqrt(alpha * alpha + ss);
-          beta = alpha >= T(0) ? -nrm : nrm;
-          sc = T(1) / (alpha - beta);
-          tj = (beta - alpha) / beta;
-        }
-        s_beta = beta;
-        s_sc = sc;
-        s_tau = tj;
-        tau[k] = tj;
-      }
-      __syncwarp();
-      const T sc = s_sc;
-      for (int i = k + 1 + lane; i < m; i += 32) D[i + k * m] *= sc;
-      __syncwarp();
-      if (lane == 0) D[k + k * m] = s_beta;
-    }
-    __syncthreads();
-    const T tj = s_tau;
-    if (tj != T(0))
-      for (int j = k + 1 + warp; j < n; j += NT / 32) {
-        T d = 0;
-        for (int i = k + 1 + lane; i < m; i += 32) d += D[i + k * m] * D[i + j * m];
-        d = (warp_sum(d) + D[k + j * m]) * tj;
-        for (int i = k + 1 + lane; i < m; i += 32) D[i + j * m] -= d * D[i + k * m];
-        __syncwarp();
-        if (lane == 0) D[k + j * m] -= d;
-      }
-    __syncthreads();
-  }
-  *tail2 = s_tail;
-  return k;
-}
 
 template <class T>
 __device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {

@@ -378,8 +378,12 @@ class Sched {
   // Vout (+)= sign * op(b) Vin, op = transpose when trans.  Vin covers the
   // in-cluster of b, Vout its out-cluster.  overwrite: Vout starts from zero
   // and out_slot receives Vin's column count.
+  // late_seg >= 0 (solves, accumulating): the terms of every output unit are
+  // split into two ROWMV tasks, those whose input does not cover segment
+  // late_seg (the input's last segment to be solved) first, so that only the
+  // few terms reading it wait for the end of the preceding solve.
   void hmul(int32_t b, const MV& Vin, const MV& Vout, float sign, bool trans, bool overwrite,
-            int32_t out_slot) {
+            int32_t out_slot, int32_t late_seg = -1) {
     std::vector<int32_t> lv;
     leaves_of(b, lv);
     int32_t oc = trans ? colc(b) : rowc(b);
@@ -433,9 +437,27 @@ class Sched {
       for (int32_t q = seg_begin_[obc]; q < seg_end_[obc]; ++q) items[fill[unit_of(q)]++] = (int32_t)i;
     }
     MV kview = Vin;
+    auto is_late = [&](int32_t i) {
+      const int32_t ic = trans ? rowc(lv[i]) : colc(lv[i]);
+      return late_seg >= seg_begin_[ic] && late_seg < seg_end_[ic];
+    };
     for (int32_t l = 0; l < nu; ++l) {
       if (cnt[l] == cnt[l + 1] && !overwrite) continue;
       const int32_t lc = units[l];
+      std::vector<int32_t> parts[2];
+      for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q)
+        parts[late_seg >= 0 && !overwrite && is_late(items[q]) ? 1 : 0].push_back(items[q]);
+      for (int part = 0; part < 2; ++part) {
+        if (parts[part].empty() && (part == 1 || !overwrite)) continue;
+        emit_rowmv(lv, T, parts[part], Vin, Vout, lc, sign, trans, overwrite, out_slot, kview);
+      }
+    }
+  }
+  // one ROWMV task: unit lc of Vout (+)= sign * sum over the listed leaves
+  void emit_rowmv(const std::vector<int32_t>& lv, const std::vector<MV>& T, const std::vector<int32_t>& list,
+                  const MV& Vin, const MV& Vout, int32_t lc, float sign, bool trans, bool overwrite,
+                  int32_t out_slot, const MV& kview) {
+    {
       Task k = make(TK_ROWMV);
       k.flags = overwrite ? TF_OVERWRITE : 0;
       k.sign = sign;
@@ -443,10 +465,9 @@ class Sched {
       k.b = Vin.v;  // column count source
       k.out_slot = out_slot;
       k.list_begin = (int32_t)S_->terms.size();
-      k.list_count = cnt[l + 1] - cnt[l];
+      k.list_count = (int32_t)list.size();
       begin(k);
-      for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q) {
-        int32_t i = items[q];
+      for (int32_t i : list) {
         int32_t be = lv[i];
         int32_t obc = trans ? colc(be) : rowc(be);
         // the term covers rows (obc intersect lc) of the unit
@@ -513,7 +534,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_lower(son(d, 0, 0), V0);
-    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1);
+    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1);
     solve_lower(son(d, 1, 1), V1);
   }
   void solve_upperT(int32_t d, const MV& W) {
@@ -541,7 +562,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_upper(son(d, 1, 1), V1);
-    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1);
+    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]]);
     solve_upper(son(d, 0, 0), V0);
   }
 

@@ -356,6 +356,29 @@ class Sched {
     end();
   }
   void trsm_leaf(int32_t type, int32_t d, const MV& V) {
+    const int32_t sg = seg_begin_[rowc(d)];
+    if ((type == TK_TRSM_L || type == TK_TRSM_U) && seg_end_[rowc(d)] - sg == 1 && sg < (int32_t)pending_.size() &&
+        pending_[sg].active && seg_cluster_[sg] == rowc(d)) {
+      // the late update of this segment and its triangular solve in one task
+      Pending& pd = pending_[sg];
+      Task k = make(TK_RSOLVE);
+      k.flags = type == TK_TRSM_U ? TF_UPPER : 0;
+      k.a = mvD(d).v;
+      k.b = pd.Vin.v;  // column count source
+      k.c = V.v;
+      k.piv_off = L_.piv_off[d];
+      k.sign = pd.sign;
+      k.list_begin = (int32_t)S_->terms.size();
+      k.list_count = (int32_t)pd.list.size();
+      begin(k);
+      push_terms(pd.lv, pd.T, pd.list, pd.Vin, rowc(d), pd.trans);
+      acc_rank(pd.Vin);
+      acc(mvD(d), false);
+      acc(V, true);
+      end();
+      pd = Pending();
+      return;
+    }
     Task t = make(type);
     t.a = mvD(d).v;
     t.b = V.v;
@@ -382,8 +405,11 @@ class Sched {
   // split into two ROWMV tasks, those whose input does not cover segment
   // late_seg (the input's last segment to be solved) first, so that only the
   // few terms reading it wait for the end of the preceding solve.
+  // fuse_seg >= 0 (solve schedule): the late task of the unit that is
+  // segment fuse_seg is not emitted here but merged into that segment's next
+  // triangular leaf solve (one RSOLVE task instead of a ROWMV and a TRSM).
   void hmul(int32_t b, const MV& Vin, const MV& Vout, float sign, bool trans, bool overwrite,
-            int32_t out_slot, int32_t late_seg = -1) {
+            int32_t out_slot, int32_t late_seg = -1, int32_t fuse_seg = -1) {
     std::vector<int32_t> lv;
     leaves_of(b, lv);
     int32_t oc = trans ? colc(b) : rowc(b);
@@ -449,8 +475,48 @@ class Sched {
         parts[late_seg >= 0 && !overwrite && is_late(items[q]) ? 1 : 0].push_back(items[q]);
       for (int part = 0; part < 2; ++part) {
         if (parts[part].empty() && (part == 1 || !overwrite)) continue;
+        if (part == 1 && fuse_seg >= 0 && fuse_seg < (int32_t)pending_.size() && lc == seg_cluster_[fuse_seg] &&
+            !pending_[fuse_seg].active) {
+          Pending& pd = pending_[fuse_seg];
+          pd.active = true;
+          pd.lv = lv;
+          pd.T = T;
+          pd.list = parts[part];
+          pd.Vin = Vin;
+          pd.sign = sign;
+          pd.trans = trans;
+          continue;
+        }
         emit_rowmv(lv, T, parts[part], Vin, Vout, lc, sign, trans, overwrite, out_slot, kview);
       }
+    }
+  }
+  // the terms of a ROWMV (or RSOLVE) task for unit lc, with their reads
+  void push_terms(const std::vector<int32_t>& lv, const std::vector<MV>& T, const std::vector<int32_t>& list,
+                  const MV& Vin, int32_t lc, bool trans) {
+    for (int32_t i : list) {
+      int32_t be = lv[i];
+      int32_t obc = trans ? colc(be) : rowc(be);
+      // the term covers rows (obc intersect lc) of the unit
+      int32_t rc = C_[obc].size <= C_[lc].size ? obc : lc;
+      Term tm;
+      std::memset(&tm, 0, sizeof(tm));
+      tm.roff = C_[rc].off - C_[lc].off;
+      if (kind(be) == KIND_DENSE) {
+        MV A = sub(trans ? mvDT(be) : mvD(be), rc);
+        MV Bv = sub(Vin, trans ? rowc(be) : colc(be));
+        tm.A = A.v;
+        tm.B = Bv.v;
+        acc(A, false);
+        acc(Bv, false);
+      } else {
+        MV A = sub(trans ? mvY(be) : mvX(be), rc);
+        tm.A = A.v;
+        tm.B = T[i].v;
+        acc(A, false);
+        touch(bufs_[T[i].buf].seg0, false);
+      }
+      S_->terms.push_back(tm);
     }
   }
   // one ROWMV task: unit lc of Vout (+)= sign * sum over the listed leaves
@@ -467,30 +533,7 @@ class Sched {
       k.list_begin = (int32_t)S_->terms.size();
       k.list_count = (int32_t)list.size();
       begin(k);
-      for (int32_t i : list) {
-        int32_t be = lv[i];
-        int32_t obc = trans ? colc(be) : rowc(be);
-        // the term covers rows (obc intersect lc) of the unit
-        int32_t rc = C_[obc].size <= C_[lc].size ? obc : lc;
-        Term tm;
-        std::memset(&tm, 0, sizeof(tm));
-        tm.roff = C_[rc].off - C_[lc].off;
-        if (kind(be) == KIND_DENSE) {
-          MV A = sub(trans ? mvDT(be) : mvD(be), rc);
-          MV Bv = sub(Vin, trans ? rowc(be) : colc(be));
-          tm.A = A.v;
-          tm.B = Bv.v;
-          acc(A, false);
-          acc(Bv, false);
-        } else {
-          MV A = sub(trans ? mvY(be) : mvX(be), rc);
-          tm.A = A.v;
-          tm.B = T[i].v;
-          acc(A, false);
-          touch(bufs_[T[i].buf].seg0, false);
-        }
-        S_->terms.push_back(tm);
-      }
+      push_terms(lv, T, list, Vin, lc, trans);
       acc_rank(kview);
       acc(sub(Vout, lc), true);
       end();
@@ -534,7 +577,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_lower(son(d, 0, 0), V0);
-    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1);
+    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1, seg_begin_[c.son[1]]);
     solve_lower(son(d, 1, 1), V1);
   }
   void solve_upperT(int32_t d, const MV& W) {
@@ -562,7 +605,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_upper(son(d, 1, 1), V1);
-    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]]);
+    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]], seg_end_[c.son[0]] - 1);
     solve_upper(son(d, 0, 0), V0);
   }
 
@@ -759,117 +802,9 @@ class Sched {
     lu(d11);
   }
 
-  // Left-looking tile solves for the preconditioner: every segment (tile) of
-  // the vector is finished by one RSOLVE task that subtracts the contributions
-  // of all factor blocks in its block row and applies the diagonal tile's
-  // triangle; a low-rank block's projection Y^T x is formed once, as soon as
-  // its column range is final.
-  void solve_tiles(int32_t nrhs_max) {
-    MV W;
-    W.buf = new_buf_leaves(0);
-    W.clus = 0;
-    const int32_t N = sz(0);
-    W.v = View{L_.work_off, 1, N, N, nrhs_max, L_.nrhs_slot, 0};
-    const int32_t nseg = (int32_t)seg_cluster_.size();
-    // factor leaves, the diagonal tile of every segment, blocks by row segment
-    std::vector<int32_t> lv;
-    leaves_of(0, lv);
-    std::vector<int32_t> diag(nseg, -1);
-    std::vector<std::vector<int32_t>> lower(nseg), upper(nseg);
-    std::vector<std::vector<int32_t>> lproj_at(nseg), uproj_at(nseg);
-    for (int32_t b : lv) {
-      const Cluster& R = C_[rowc(b)];
-      const Cluster& Q = C_[colc(b)];
-      if (rowc(b) == colc(b)) {
-        if (seg_end_[rowc(b)] - seg_begin_[rowc(b)] != 1 || kind(b) != KIND_DENSE)
-          throw std::logic_error("diagonal leaf is not one dense tile");
-        diag[seg_begin_[rowc(b)]] = b;
-        continue;
-      }
-      bool is_lower = Q.off + Q.size <= R.off;
-      for (int32_t q = seg_begin_[rowc(b)]; q < seg_end_[rowc(b)]; ++q) (is_lower ? lower : upper)[q].push_back(b);
-      if (kind(b) == KIND_ADM) {
-        if (is_lower)
-          lproj_at[seg_end_[colc(b)] - 1].push_back(b);
-        else
-          uproj_at[seg_begin_[colc(b)]].push_back(b);
-      }
-    }
-    std::vector<MV> T(B_.size());
-    auto proj = [&](int32_t b) {
-      MV A = mvY(b);
-      MV vin = sub(W, colc(b));
-      MV t;
-      t.clus = -1;
-      int32_t cap = L_.cap[b];
-      int64_t toff = alloc((int64_t)cap * nrhs_max);
-      t.buf = new_buf_single();
-      bind_alloc(t.buf);
-      t.v = View{toff, 1, cap, cap, nrhs_max, L_.nrhs_slot, 0};
-      Task k = make(TK_PROJ);
-      k.a = A.v;
-      k.b = vin.v;
-      k.c = t.v;
-      begin(k);
-      acc(A, false);
-      acc(vin, false);
-      touch(bufs_[t.buf].seg0, true);
-      end();
-      T[b] = t;
-    };
-    auto rsolve = [&](int32_t q, bool up) {
-      const int32_t sc = seg_cluster_[q];
-      const int32_t d = diag[q];
-      if (d < 0) throw std::logic_error("segment without a diagonal tile");
-      MV Vs = sub(W, sc);
-      Task k = make(TK_RSOLVE);
-      k.flags = up ? TF_UPPER : 0;
-      k.a = mvD(d).v;
-      k.b = W.v;
-      k.c = Vs.v;
-      k.piv_off = L_.piv_off[d];
-      k.sign = -1.0f;
-      const std::vector<int32_t>& blocks = up ? upper[q] : lower[q];
-      k.list_begin = (int32_t)S_->terms.size();
-      k.list_count = (int32_t)blocks.size();
-      begin(k);
-      for (int32_t b : blocks) {
-        Term tm;
-        std::memset(&tm, 0, sizeof(tm));
-        // the block's row cluster contains the segment
-        tm.roff = 0;
-        if (kind(b) == KIND_DENSE) {
-          MV A = sub(mvD(b), sc);
-          MV Bv = sub(W, colc(b));
-          tm.A = A.v;
-          tm.B = Bv.v;
-          acc(A, false);
-          acc(Bv, false);
-        } else {
-          MV A = sub(mvX(b), sc);
-          tm.A = A.v;
-          tm.B = T[b].v;
-          acc(A, false);
-          touch(bufs_[T[b].buf].seg0, false);
-        }
-        S_->terms.push_back(tm);
-      }
-      acc(mvD(d), false);
-      acc(Vs, true);
-      end();
-    };
-    for (int32_t q = 0; q < nseg; ++q) {
-      rsolve(q, false);
-      for (int32_t b : lproj_at[q]) proj(b);
-    }
-    for (int32_t q = nseg - 1; q >= 0; --q) {
-      rsolve(q, true);
-      for (int32_t b : uproj_at[q]) proj(b);
-    }
-  }
-
   void solve_all(int32_t nrhs_max, int32_t group_max) {
     group_max_ = group_max;
+    pending_.assign(seg_cluster_.size(), Pending());
     MV W;
     W.buf = new_buf_leaves(0);  // per-segment tracking over the whole vector
     W.clus = 0;
@@ -918,6 +853,16 @@ class Sched {
   std::vector<int32_t> stamp_;
   std::vector<int32_t> deps_;
   int32_t cur_ = -1;
+  // late updates waiting to be merged into a segment's leaf solve
+  struct Pending {
+    bool active = false;
+    std::vector<int32_t> lv, list;
+    std::vector<MV> T;
+    MV Vin;
+    float sign = 0;
+    bool trans = false;
+  };
+  std::vector<Pending> pending_;
   bool in_group_ = false;
   int32_t group_max_ = 0;
 };

@@ -37,6 +37,33 @@ METRIC = "H-LU-preconditioned GMRES solves/s to 1e-7 rel. error; factor GFLOP/s;
 UNIT = "solves/s"
 
 
+def _blob_sha1(path):
+    """git's object id of a file's contents (what `git hash-object` prints)."""
+    import hashlib
+    with open(path, "rb") as f:
+        data = f.read()
+    return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+
+
+def _factor_traffic(n, eps, precision):
+    """DRAM bytes per factorisation launch from the committed ncu capture
+    (profiles/exec_kernel_factor_dram.md), or None when the capture is of
+    another workload or the executor source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "exec_kernel_factor_dram.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ": " in line:
+                    k, v = line[2:].split(": ", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        same_src = fields["exec.cu blob"] == _blob_sha1(os.path.join(ROOT, "paper_2211_11303_gb300", "csrc", "exec.cu"))
+        same_work = (int(fields["n"]) == n and float(fields["eps"]) == eps and fields["precision"] == precision)
+        return int(fields["factor DRAM bytes per launch"]) if same_src and same_work else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -375,7 +402,8 @@ def run_gpu(args):
         "rank_mean": statistics.mean(i["rank_mean"] for i in infos),
         "rank_max": max(i["rank_max"] for i in infos),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak_tflops, "traffic": None,
+                     "frac": achieved / fp32_peak_tflops,
+                     "traffic": _factor_traffic(n, args.eps, args.precision),
                      "kernel": "exec_kernel<float> (H-LU task executor)",
                      "peak_source": "derived: SMs x 128 FP32 lanes x 2 x %s max SM clock" % src},
         "clocks": clk,

@@ -470,38 +470,47 @@ struct TermCursor {
   }
 };
 
+// acc += sum of the task's terms restricted to the 64 x 64 output tile (i0, j0);
+// returns the flops (thread 0 only).
+template <class T>
+__device__ double rowmv_tile(const Ctx<T>& c, const Task& t, int i0, int j0, int k, T (&acc)[4][4], T* As, T* Bs) {
+  __shared__ Term s_tm[kStageTerms];
+  __shared__ int s_p[kStageTerms];
+  double fl = 0;
+  for (int qb = 0; qb < t.list_count; qb += kStageTerms) {
+    const int nq = min(kStageTerms, t.list_count - qb);
+    __syncthreads();
+    {
+      const int words = nq * (int)(sizeof(Term) / sizeof(int32_t));
+      const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin + qb);
+      int32_t* dst = reinterpret_cast<int32_t*>(s_tm);
+      for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) s_p[threadIdx.x] = ncols(c, s_tm[threadIdx.x].A);
+    __syncthreads();
+    TermCursor<T> cur{&c, s_tm, s_p, nq, i0, j0, k, 0, 0};
+    tile_mma_seq(acc, cur, As, Bs);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nq; ++q) {
+        const int lo = max(s_tm[q].roff, i0), hi = min(s_tm[q].roff + s_tm[q].A.rows, i0 + 64);
+        if (hi > lo) fl += 2.0 * (hi - lo) * min(64, k - j0) * s_p[q];
+      }
+  }
+  return fl;
+}
+
 template <class T>
 __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.c.rows, k = ncols(c, t.b);
   T* As = reinterpret_cast<T*>(smem);
   T* Bs = As + 64 * KC;
-  __shared__ Term s_tm[kStageTerms];
-  __shared__ int s_p[kStageTerms];
   double fl = 0;
   for (int i0 = 0; i0 < n; i0 += 64)
     for (int j0 = 0; j0 < k; j0 += 64) {
       T acc[4][4];
       acc_zero(acc);
-      for (int qb = 0; qb < t.list_count; qb += kStageTerms) {
-        const int nq = min(kStageTerms, t.list_count - qb);
-        __syncthreads();
-        {
-          const int words = nq * (int)(sizeof(Term) / sizeof(int32_t));
-          const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin + qb);
-          int32_t* dst = reinterpret_cast<int32_t*>(s_tm);
-          for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
-        }
-        __syncthreads();
-        if (threadIdx.x < nq) s_p[threadIdx.x] = ncols(c, s_tm[threadIdx.x].A);
-        __syncthreads();
-        TermCursor<T> cur{&c, s_tm, s_p, nq, i0, j0, k, 0, 0};
-        tile_mma_seq(acc, cur, As, Bs);
-        if (threadIdx.x == 0)
-          for (int q = 0; q < nq; ++q) {
-            const int lo = max(s_tm[q].roff, i0), hi = min(s_tm[q].roff + s_tm[q].A.rows, i0 + 64);
-            if (hi > lo) fl += 2.0 * (hi - lo) * min(64, k - j0) * s_p[q];
-          }
-      }
+      fl += rowmv_tile(c, t, i0, j0, k, acc, As, Bs);
       tile_store(acc, c, t.c, i0, j0, min(64, n - i0), min(64, k - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
     }
   if (threadIdx.x == 0) {
@@ -511,11 +520,24 @@ __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
 }
 
 // ---------------------------------------------------------------- RSOLVE
-// One tile of a left-looking triangular solve: c -= sum_t A_t B_t, then the
-// diagonal tile's triangle (L^-1 P or U^-1) in place.
+// A leaf of a triangular solve with its late update: c -= sum_t A_t B_t, then
+// the diagonal tile's triangle (L^-1 P or U^-1) in place.  The tile streams
+// into shared memory (cp.async) while the update runs, and the updated
+// right-hand side goes to the substitution through shared memory.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
 template <class T>
 __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
-  if (t.list_count > 0) {
+  const int n = t.a.rows, k = ncols(c, t.b);
+  const bool upper = (t.flags & TF_UPPER) != 0;
+  if (n > 64 || k > 64) {  // not a leaf tile: update, then the plain leaf solve
     Task r = t;
     r.type = TK_ROWMV;
     r.flags = 0;
@@ -523,11 +545,73 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
     task_rowmv(c, r, smem);
     __threadfence_block();
     __syncthreads();
+    Task q = t;
+    q.type = upper ? TK_TRSM_U : TK_TRSM_L;
+    q.b = t.c;
+    task_trsm(c, q, smem);
+    return;
   }
-  Task s = t;
-  s.type = (t.flags & TF_UPPER) ? TK_TRSM_U : TK_TRSM_L;
-  s.b = t.c;
-  task_trsm(c, s, smem);
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + 64 * KC;
+  T* A = Bs + 64 * KC;  // the diagonal tile, n x n
+  T* X = A + 64 * 64;   // updated right-hand side, n x k (ld n)
+  T* dinv = X + 64 * 64;
+  int* perm = reinterpret_cast<int*>(dinv + 64);
+  // the tile and the pivots start moving now (read-only factor data)
+  const T* tile = c.arena + t.a.off;
+  for (int idx = threadIdx.x; idx < n * n; idx += NT)
+    cp_async_elem(A + idx, tile + (int64_t)(idx % n) * t.a.rs + (int64_t)(idx / n) * t.a.cs);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const int pv = (!upper && threadIdx.x < n) ? __ldcg(c.piv + t.piv_off + threadIdx.x) : 0;
+  // the update, kept in registers
+  T acc[4][4];
+  acc_zero(acc);
+  double fl = t.list_count > 0 ? rowmv_tile(c, t, 0, 0, k, acc, As, Bs) : 0.0;
+  {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const T sg = T(t.sign);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = tx * 4 + i, cc = ty * 4 + j;
+        if (r < n && cc < k) X[r + cc * n] = ldv(c, t.c, r, cc) + sg * acc[i][j];
+      }
+  }
+  if (!upper && threadIdx.x < n) perm[threadIdx.x] = pv;
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  if (upper)
+    for (int i = threadIdx.x; i < n; i += NT) dinv[i] = T(1) / A[i + i * n];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = lane, r1 = lane + 32;
+  for (int j = warp; j < k; j += NT / 32) {
+    const T* xj = X + j * n;
+    T v0 = 0, v1 = 0;
+    if (!upper) {
+      if (r0 < n) v0 = xj[perm[r0]];
+      if (r1 < n) v1 = xj[perm[r1]];
+      for (int l = 0; l < n; ++l) {
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31);
+        if (r0 > l && r0 < n) v0 -= A[r0 + l * n] * x;
+        if (r1 > l && r1 < n) v1 -= A[r1 + l * n] * x;
+      }
+    } else {
+      if (r0 < n) v0 = xj[r0];
+      if (r1 < n) v1 = xj[r1];
+      for (int l = n - 1; l >= 0; --l) {
+        T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) * dinv[l];
+        if (r0 == l) v0 = x;
+        if (r1 == l) v1 = x;
+        if (r0 < l) v0 -= A[r0 + l * n] * x;
+        if (r1 < l && r1 < n) v1 -= A[r1 + l * n] * x;
+      }
+    }
+    if (r0 < n) stv(c, t.c, r0, j, v0);
+    if (r1 < n) stv(c, t.c, r1, j, v1);
+  }
+  if (threadIdx.x == 0) c.flops += fl + (double)n * n * k;
 }
 
 // ---------------------------------------------------------------- DADD
@@ -1522,6 +1606,9 @@ size_t exec_smem_bytes(int elem_size) {
     if (dense > trunc) trunc = dense;
   }
   size_t lu = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
+  // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
+  const size_t rsolve = (size_t)elem_size * (2 * 64 * KC + 2 * 64 * 64 + 64) + 64 * sizeof(int);
+  if (rsolve > lu) lu = rsolve;
   size_t gemm = (size_t)elem_size * 2 * 64 * KC;
   size_t m = trunc > lu ? trunc : lu;
   return m > gemm ? m : gemm;

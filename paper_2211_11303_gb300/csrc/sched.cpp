@@ -463,20 +463,37 @@ class Sched {
       for (int32_t q = seg_begin_[obc]; q < seg_end_[obc]; ++q) items[fill[unit_of(q)]++] = (int32_t)i;
     }
     MV kview = Vin;
-    auto is_late = [&](int32_t i) {
-      const int32_t ic = trans ? rowc(lv[i]) : colc(lv[i]);
-      return late_seg >= seg_begin_[ic] && late_seg < seg_end_[ic];
-    };
     for (int32_t l = 0; l < nu; ++l) {
       if (cnt[l] == cnt[l + 1] && !overwrite) continue;
       const int32_t lc = units[l];
-      std::vector<int32_t> parts[2];
-      for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q)
-        parts[late_seg >= 0 && !overwrite && is_late(items[q]) ? 1 : 0].push_back(items[q]);
-      for (int part = 0; part < 2; ++part) {
-        if (parts[part].empty() && (part == 1 || !overwrite)) continue;
-        if (part == 1 && fuse_seg >= 0 && fuse_seg < (int32_t)pending_.size() && lc == seg_cluster_[fuse_seg] &&
-            !pending_[fuse_seg].active) {
+      // terms grouped by how long before late_seg their input is final: group
+      // g >= 1 holds the terms whose last-solved input segment lies between
+      // 2^(g-1) and 2^g - 1 segments before late_seg, group 0 those reading
+      // late_seg itself; the groups run in that order, so each one waits only
+      // for inputs solved well before it and the last ones are small
+      constexpr int kGroups = 33;
+      std::vector<int32_t> parts[kGroups];
+      for (int32_t q = cnt[l]; q < cnt[l + 1]; ++q) {
+        const int32_t i = items[q];
+        int g = 0;
+        if (late_seg >= 0 && !overwrite) {
+          const int32_t ic = trans ? rowc(lv[i]) : colc(lv[i]);
+          int32_t dist = 0;
+          if (late_seg >= seg_end_[ic])
+            dist = late_seg - (seg_end_[ic] - 1);
+          else if (late_seg < seg_begin_[ic])
+            dist = seg_begin_[ic] - late_seg;
+          while (dist > 0) {
+            ++g;
+            dist >>= 1;
+          }
+        }
+        parts[g].push_back(i);
+      }
+      for (int part = kGroups - 1; part >= 0; --part) {
+        if (parts[part].empty() && (part != 0 || !overwrite)) continue;
+        if (part == 0 && late_seg >= 0 && fuse_seg >= 0 && fuse_seg < (int32_t)pending_.size() &&
+            lc == seg_cluster_[fuse_seg] && !pending_[fuse_seg].active) {
           Pending& pd = pending_[fuse_seg];
           pd.active = true;
           pd.lv = lv;

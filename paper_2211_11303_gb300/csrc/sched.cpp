@@ -42,6 +42,11 @@ struct Buf {
   int64_t seg0;
 };
 
+// Targets of a subdivided x subdivided product up to this size on both sides
+// are agglomerated in one truncation (the executor's dense route handles them
+// whole); larger ones quadrant by quadrant first.
+constexpr int32_t kOneStepAgglomeration = 128;
+
 class Sched {
  public:
   Sched(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t kcap, ArenaLayout& L,
@@ -705,18 +710,33 @@ class Sched {
     }
     if (ka == KIND_DENSE) return LR{mvIdent(tau), hmul_new(b, mvDT(a), true)};
     if (kb == KIND_DENSE) return LR{hmul_new(a, mvD(b), false), mvIdent(rho)};
-    // both subdivided: the eight son products, placed at their son offsets,
-    // are stacked and truncated in one task (formatted agglomeration)
+    // both subdivided (formatted agglomeration)
     const Cluster& T = C_[tau];
     const Cluster& R = C_[rho];
-    std::vector<PieceMV> ps;
+    if (T.size <= kOneStepAgglomeration && R.size <= kOneStepAgglomeration) {
+      // small target: the eight son products, placed at their son offsets,
+      // are truncated in one task (the executor forms the dense sum)
+      std::vector<PieceMV> ps;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int k = 0; k < 2; ++k) {
+            LR sp = product(son(a, i, k), son(b, k, j));
+            ps.push_back(PieceMV{sp, C_[T.son[i]].off - T.off, C_[R.son[j]].off - R.off, 1.0f});
+          }
+      return trunc_new(tau, rho, ps);
+    }
+    // larger target: the two son products of each quadrant are summed and
+    // truncated (four independent tasks), then the four quadrants, placed at
+    // their son offsets, are truncated together
+    std::vector<PieceMV> quads;
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j)
-        for (int k = 0; k < 2; ++k) {
-          LR sp = product(son(a, i, k), son(b, k, j));
-          ps.push_back(PieceMV{sp, C_[T.son[i]].off - T.off, C_[R.son[j]].off - R.off, 1.0f});
-        }
-    return trunc_new(tau, rho, ps);
+      for (int j = 0; j < 2; ++j) {
+        std::vector<PieceMV> ps;
+        for (int k = 0; k < 2; ++k) ps.push_back(PieceMV{product(son(a, i, k), son(b, k, j)), 0, 0, 1.0f});
+        LR q = trunc_new(T.son[i], R.son[j], ps);
+        quads.push_back(PieceMV{q, C_[T.son[i]].off - T.off, C_[R.son[j]].off - R.off, 1.0f});
+      }
+    return trunc_new(tau, rho, quads);
   }
 
   // c <- c + sign * sum_p X_p Y_p^T in the format of c: one DADD per product

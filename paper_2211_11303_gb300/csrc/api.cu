@@ -162,6 +162,7 @@ struct SchedBundle {
   FillDesc* d_fill_lr = nullptr;
   int32_t n_fill_dense = 0, n_fill_lr = 0;
   int64_t dense_rows = 0;
+  int64_t device_bytes = 0;  // task data of both schedules on the device
   ~SchedBundle() {
     dF.free_all();
     dS.free_all();
@@ -176,6 +177,7 @@ unsigned long long* g_batch_q = nullptr;  // ready queue of batched launches
 int64_t g_batch_q_len = 0;
 std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
 constexpr size_t kCacheEntries = 16;
+constexpr int64_t kCacheBytes = int64_t(24) << 30;  // device bytes of cached schedules
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   const unsigned char* c = (const unsigned char*)p;
@@ -709,10 +711,23 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       sb->dense_rows = rows;
       if ((e = upload(&sb->d_fill_dense, fd)) != cudaSuccess) return bail(e, "fill desc");
       if ((e = upload(&sb->d_fill_lr, fl)) != cudaSuccess) return bail(e, "fill desc");
+      for (const Schedule* sc : {&F, &S})
+        sb->device_bytes += (int64_t)(sizeof(Task) * (sc->tasks.size() + sc->micro.size()) +
+                                      sizeof(Term) * sc->terms.size() + sizeof(Piece) * sc->pieces.size() +
+                                      2 * sizeof(int64_t) * (sc->tasks.size() + 1) + 2 * sizeof(int32_t) *
+                                      sc->pred_idx.size() + 2 * sizeof(int32_t) * sc->tasks.size());
       h->sb = sb;
       std::lock_guard<std::mutex> lk(g_cache_mu);
       g_cache.push_back(sb);
-      while (g_cache.size() > kCacheEntries) g_cache.erase(g_cache.begin());
+      // bounded by entries and by device bytes (least recently used first;
+      // handles still holding an evicted schedule keep it alive)
+      auto cached_bytes = [&]() {
+        int64_t b = 0;
+        for (const auto& e : g_cache) b += e->device_bytes;
+        return b;
+      };
+      while (g_cache.size() > kCacheEntries || (g_cache.size() > 1 && cached_bytes() > kCacheBytes))
+        g_cache.erase(g_cache.begin());
     }
     h->L = h->sb->L;
     h->dF = h->sb->dF.share();

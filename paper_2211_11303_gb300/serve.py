@@ -45,6 +45,7 @@ class Server:
         self.precision, self.restart, self.tol, self.maxit = precision, restart, tol, maxit
         self.factors = {}
         self.used = 0
+        self.reserve = 4 << 30  # device bytes kept free beyond each admission
         self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0}
 
     # -- factor cache ---------------------------------------------------------
@@ -59,13 +60,17 @@ class Server:
             self.stats["evictions"] += 1
         return self.used + need <= self.budget
 
-    def _lookup(self, req):
-        """(cached factor or None, built-but-unfactored handle or None, bytes)."""
+    def _lookup(self, req, may_build=True):
+        """(cached factor or None, built-but-unfactored handle or None, bytes);
+        (None, None, 0) when the request needs a handle that may not be built
+        now."""
         key = (int(req["n"]), float(req["kappa"]))
         f = self.factors.get(key)
         if f is not None:
             return f, None, 0
         if "_h" not in req:
+            if not may_build:
+                return None, None, 0
             h = H.hlu_build(req["n"], req["kappa"], self.leaf, self.eta, self.eps)
             req["_h"] = (key, h, int(H.hlu_factor_bytes_estimate(h, self.precision)))
         return None, req["_h"], req["_h"][2]
@@ -86,12 +91,19 @@ class Server:
                 pi += 1
             # admission: first come first served, later requests may pass one
             # that does not fit yet
+            # at most one request builds a new handle per pass: a handle holds
+            # device memory (mesh, matrix, schedule state) before it is admitted
             still = []
+            built_one = False
             for req in waiting:
                 if len(active) >= self.max_active:
                     still.append(req)
                     continue
-                f, built, fbytes = self._lookup(req)
+                f, built, fbytes = self._lookup(req, may_build=not built_one)
+                if f is None and built is None:
+                    still.append(req)
+                    continue
+                built_one = built_one or f is None
                 N = H.hlu_n(f.h if f is not None else built[1])
                 kb = krylov_bytes(N, req["nrhs"], self.restart)
                 if f is not None:
@@ -99,6 +111,9 @@ class Server:
                 ok = self._evict_for(fbytes + kb)
                 if f is not None:
                     f.users -= 1
+                # the device itself must have the room as well (schedules and
+                # handles are outside the budget)
+                ok = ok and torch.cuda.mem_get_info()[0] > fbytes + kb + self.reserve
                 if not ok:
                     if not active and all(g.users == 0 for g in self.factors.values()) and not self.factors:
                         raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))

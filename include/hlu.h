@@ -182,12 +182,12 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 /* hlu_factor_profile - per task kind of the last factorisation's task DAG:
  * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for a
  * ready task, out[3*k + 2] cycles spent running, summed over CTAs; kinds
- * k = 0..9 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
- * RSOLVE, SEQ and k = 10 the no-work fences; then the truncation phases
- * summed over all compressions: out[33] (unused), out[34] QR cycles, out[35]
- * core product, out[36] Jacobi SVD, out[37] selection and Q application,
- * out[38] compressions, out[39] Jacobi sweeps, out[40] summed stack widths.
- * out: uint64[41] host buffer. */
+ * k = 0..11 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
+ * RSOLVE, SEQ, IDENT, GSOLVE and k = 12 the no-work fences; then the
+ * truncation phases summed over all compressions: out[39] stacking or dense
+ * sum, out[40] QR cycles, out[41] core product, out[42] Jacobi SVD, out[43]
+ * selection and Q application, out[44] compressions, out[45] Jacobi sweeps,
+ * out[46] summed stack widths.  out: uint64[47] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
@@ -290,6 +290,17 @@ void hlu_set_tile(int32_t tile);
  * CTAs.  The arithmetic is the same as without grouping (0).  The debug host
  * executor uses the same setting. */
 void hlu_set_solve_group(int32_t dofs);
+
+/* hlu_set_solve_inverse - inverse groups for subsequent hlu_build calls
+ * (process-wide, default 256, at most 256, 0: off).  Every maximal
+ * subdivided diagonal block of at most `dofs` DOFs gets, right after its LU,
+ * the explicit inverses of its two triangular factors (L^-1 P and U^-1,
+ * formed by substitution into identities, in the factor precision); the
+ * triangular solves (Alg. 1 step III) then apply each such block with one
+ * dense product instead of its chain of leaf substitutions and updates.  The
+ * result equals the substitution up to rounding; the factor holds 2 m^2 more
+ * words per group.  The debug host executor uses the same setting. */
+void hlu_set_solve_inverse(int32_t dofs);
 
 /* hlu_launch_count - number of this library's own CUDA kernel launches so far
  * in this process (kernels from CUDA's bundled sort/scan templates are not

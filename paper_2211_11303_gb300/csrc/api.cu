@@ -38,6 +38,7 @@ double g_jacobi_tol = 0.0;  // 0: default of the factor precision
 int32_t g_compress_at = 0;  // 0: default
 int32_t g_tile = 64;
 int32_t g_solve_group = 0;
+int32_t g_inverse_group = 256;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -595,6 +596,8 @@ void hlu_set_wait_limit_ms(double ms) {
 void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
 
 void hlu_set_solve_group(int32_t dofs) { g_solve_group = std::max(0, dofs); }
+
+void hlu_set_solve_inverse(int32_t dofs) { g_inverse_group = std::max(0, std::min(dofs, (int32_t)256)); }
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
 int64_t hlu_launch_count(void) { return g_launches.load(); }
 
@@ -660,7 +663,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     key = fnv1a(key, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
     key = fnv1a(key, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
     const int32_t solve_group = g_solve_group;
-    int32_t params[5] = {rank_cap, h->tile, nrhs_max, (int32_t)N, solve_group};
+    const int32_t inv_group = g_inverse_group;
+    int32_t params[6] = {rank_cap, h->tile, nrhs_max, (int32_t)N, solve_group, inv_group};
     key = fnv1a(key, params, sizeof(params));
     bool cache_hit = false;
     {
@@ -678,7 +682,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       auto sb = std::make_shared<SchedBundle>();
       sb->key = key;
       Schedule F, S;
-      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, solve_group, sb->L, F, S, sb->st, &sb->FB);
+      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, solve_group, inv_group, sb->L, F, S, sb->st,
+                      &sb->FB);
       if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
       if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
       // A_H fill descriptors
@@ -1549,4 +1554,5 @@ void hlu_gmres_end(hlu_gmres* g) {
 
 namespace hlu {
 int32_t current_solve_group() { return g_solve_group; }
+int32_t current_inverse_group() { return g_inverse_group; }
 }  // namespace hlu

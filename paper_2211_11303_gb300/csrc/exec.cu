@@ -614,6 +614,55 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
   if (threadIdx.x == 0) c.flops += fl + (double)n * n * k;
 }
 
+// ---------------------------------------------------------------- inverse groups
+// c <- identity (square view)
+template <class T>
+__device__ void task_ident(Ctx<T>& c, const Task& t) {
+  const int m = t.c.rows, n = t.c.cols;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += NT) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    stv(c, t.c, i, j, i == j ? T(1) : T(0));
+  }
+}
+
+// c <- a c with a (m x m, dense inverse of a diagonal block's triangular
+// factor) and c (m x k): c is staged in shared memory 16 columns at a time,
+// each thread computes whole rows of the result, with 16 loads of a in flight.
+template <class T>
+__device__ void task_gsolve(Ctx<T>& c, const Task& t, char* smem) {
+  constexpr int U = 16;
+  const int m = t.a.rows, k = ncols(c, t.c);
+  T* X = reinterpret_cast<T*>(smem);
+  const T* A = c.arena + t.a.off;
+  for (int j0 = 0; j0 < k; j0 += 16) {
+    const int kc = min(16, k - j0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * kc; idx += NT) X[idx] = ldv(c, t.c, idx % m, j0 + idx / m);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += NT) {
+      T acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = T(0);
+      const T* ai = A + (int64_t)i * t.a.rs;
+      for (int l0 = 0; l0 < m; l0 += U) {
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = l0 + u < m ? __ldcg(ai + (int64_t)(l0 + u) * t.a.cs) : T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (l0 + u < m)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (j < kc) acc[j] += a[u] * X[(l0 + u) + j * m];
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < kc) stv(c, t.c, i, j0 + j, acc[j]);
+    }
+  }
+  if (threadIdx.x == 0) c.flops += 2.0 * m * m * k;
+}
+
 // ---------------------------------------------------------------- DADD
 template <class T>
 __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
@@ -1460,6 +1509,8 @@ __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
     case TK_TRUNC: task_trunc(c, t, smem); break;
     case TK_DADD: task_dadd(c, t, smem); break;
     case TK_RSOLVE: task_rsolve(c, t, smem); break;
+    case TK_IDENT: task_ident(c, t); break;
+    case TK_GSOLVE: task_gsolve(c, t, smem); break;
     default: break;
   }
 }

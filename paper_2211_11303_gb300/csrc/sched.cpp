@@ -586,6 +586,7 @@ class Sched {
     end();
   }
   void solve_lower(int32_t d, const MV& V) {
+    if (gsolve(d, V, false)) return;
     if (group_here(d)) {
       group_begin();
       solve_lower(d, V);
@@ -599,7 +600,8 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_lower(son(d, 0, 0), V0);
-    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1, seg_begin_[c.son[1]]);
+    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1,
+         use_inverses_ ? -1 : seg_begin_[c.son[1]]);
     solve_lower(son(d, 1, 1), V1);
   }
   void solve_upperT(int32_t d, const MV& W) {
@@ -614,6 +616,7 @@ class Sched {
     solve_upperT(son(d, 1, 1), W1);
   }
   void solve_upper(int32_t d, const MV& V) {
+    if (gsolve(d, V, true)) return;
     if (group_here(d)) {
       group_begin();
       solve_upper(d, V);
@@ -627,7 +630,8 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_upper(son(d, 1, 1), V1);
-    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]], seg_end_[c.son[0]] - 1);
+    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]],
+         use_inverses_ ? -1 : seg_end_[c.son[0]] - 1);
     solve_upper(son(d, 0, 0), V0);
   }
 
@@ -837,7 +841,43 @@ class Sched {
     trsm_right(d10, d00);
     gemm(d11, d10, d01);
     lu(d11);
+    if (L_.inv_off[d] >= 0) inverses(d);
   }
+
+  // (L_d^-1 P_d, U_d^-1) of a factored diagonal block, by substitution into
+  // identities stored at inv_off[d]
+  void inverses(int32_t d) {
+    const int32_t c = rowc(d), m = sz(c);
+    for (int which = 0; which < 2; ++which) {
+      MV M;
+      M.clus = c;
+      M.buf = new_buf_leaves(c);
+      M.v = View{L_.inv_off[d] + (int64_t)which * m * m, 1, m, m, m, -1, 0};
+      Task t = make(TK_IDENT);
+      t.c = M.v;
+      begin(t);
+      acc(M, true);
+      end();
+      if (which == 0)
+        solve_lower(d, M);
+      else
+        solve_upper(d, M);
+    }
+  }
+  // the solve of a diagonal block with an inverse group: one dense product
+  bool gsolve(int32_t d, const MV& V, bool upper) {
+    if (!use_inverses_ || L_.inv_off[d] < 0) return false;
+    const int32_t m = sz(rowc(d));
+    Task t = make(TK_GSOLVE);
+    t.a = View{L_.inv_off[d] + (upper ? (int64_t)m * m : 0), 1, m, m, m, -1, 0};
+    t.c = V.v;
+    begin(t);
+    acc_rank(V);
+    acc(V, true);
+    end();
+    return true;
+  }
+  bool use_inverses_ = false;  // solve schedule: inverse groups replace their substitution
 
   void solve_all(int32_t nrhs_max, int32_t group_max) {
     group_max_ = group_max;
@@ -942,8 +982,8 @@ std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<
 }
 
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bfull, int32_t rank_cap,
-                     int32_t nrhs_max, int32_t tile, int32_t solve_group, ArenaLayout& L, Schedule& factor,
-                     Schedule& solve,
+                     int32_t nrhs_max, int32_t tile, int32_t solve_group, int32_t inv_group, ArenaLayout& L,
+                     Schedule& factor, Schedule& solve,
                      SchedStats& st, std::vector<Block>* factor_blocks) {
   std::vector<Block> Bt = factor_tree(C, Bfull, tile);
   const std::vector<Block>& B = Bt;
@@ -986,6 +1026,24 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
       fe += (int64_t)(m + n) * cap;
     }
   }
+  // inverse groups: maximal subdivided diagonal blocks of at most inv_group DOFs
+  L.inv_off.assign(nb, -1);
+  if (inv_group > 0) {
+    std::vector<int32_t> stack{0};
+    while (!stack.empty()) {
+      const int32_t d = stack.back();
+      stack.pop_back();
+      if (B[d].kind != KIND_SUB) continue;
+      const int32_t m = C[B[d].row].size;
+      if (m <= inv_group) {
+        L.inv_off[d] = alloc((int64_t)2 * m * m);
+        fe += (int64_t)2 * m * m;
+      } else {
+        stack.push_back(B[d].son[0]);
+        stack.push_back(B[d].son[3]);
+      }
+    }
+  }
   L.factor_elems = fe;
   L.nrhs_max = nrhs_max;
   L.nrhs_slot = L.n_slots++;
@@ -1008,6 +1066,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   }
   {
     Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
+    s.use_inverses_ = inv_group > 0;
     s.solve_all(nrhs_max, solve_group);
     st.temp_elems += s.temp_elems_;
   }

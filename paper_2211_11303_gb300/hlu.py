@@ -79,6 +79,7 @@ SIGNATURES = {
     "hlu_set_tile": (None, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
     "hlu_set_solve_group": (None, [_i32]),
+    "hlu_set_solve_inverse": (None, [_i32]),
     "hlu_launch_count": (_i64, []),
     "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
     "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
@@ -226,7 +227,8 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SEQ", "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SEQ", "IDENT",
+              "GSOLVE", "FENCE"]
 
 
 def hlu_factor_profile(h):
@@ -347,6 +349,10 @@ def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
 
 def hlu_set_solve_group(dofs):
     lib().hlu_set_solve_group(int(dofs))
+
+
+def hlu_set_solve_inverse(dofs):
+    lib().hlu_set_solve_inverse(int(dofs))
 
 
 def hlu_set_tile(t):

@@ -292,14 +292,17 @@ void hlu_set_tile(int32_t tile);
 void hlu_set_solve_group(int32_t dofs);
 
 /* hlu_set_solve_inverse - inverse groups for subsequent hlu_build calls
- * (process-wide, default 256, at most 256, 0: off).  Every maximal
+ * (process-wide, default 0: off, at most 256).  Every maximal
  * subdivided diagonal block of at most `dofs` DOFs gets, right after its LU,
  * the explicit inverses of its two triangular factors (L^-1 P and U^-1,
  * formed by substitution into identities, in the factor precision); the
  * triangular solves (Alg. 1 step III) then apply each such block with one
  * dense product instead of its chain of leaf substitutions and updates.  The
  * result equals the substitution up to rounding; the factor holds 2 m^2 more
- * words per group.  The debug host executor uses the same setting. */
+ * words per group.  Measured on GB300 the dense products, read cold from
+ * HBM by one CTA each, are slower than the substitution chain they replace
+ * (n = 24 apply 83 ms off, 123 ms at 256), hence off by default.  The debug
+ * host executor uses the same setting. */
 void hlu_set_solve_inverse(int32_t dofs);
 
 /* hlu_launch_count - number of this library's own CUDA kernel launches so far

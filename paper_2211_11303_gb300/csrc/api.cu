@@ -38,7 +38,7 @@ double g_jacobi_tol = 0.0;  // 0: default of the factor precision
 int32_t g_compress_at = 0;  // 0: default
 int32_t g_tile = 64;
 int32_t g_solve_group = 0;
-int32_t g_inverse_group = 256;
+int32_t g_inverse_group = 0;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;

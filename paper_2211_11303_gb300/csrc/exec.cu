@@ -628,6 +628,9 @@ __device__ void task_ident(Ctx<T>& c, const Task& t) {
 // c <- a c with a (m x m, dense inverse of a diagonal block's triangular
 // factor) and c (m x k): c is staged in shared memory 16 columns at a time,
 // each thread computes whole rows of the result, with 16 loads of a in flight.
+// Only the nonzero part of a row is read: U^-1 is upper triangular, and
+// L^-1 P is block lower triangular with diagonal leaf blocks of at most
+// t.cap rows, so row i has no entries beyond column i + t.cap - 1.
 template <class T>
 __device__ void task_gsolve(Ctx<T>& c, const Task& t, char* smem) {
   constexpr int U = 16;
@@ -644,13 +647,15 @@ __device__ void task_gsolve(Ctx<T>& c, const Task& t, char* smem) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) acc[j] = T(0);
       const T* ai = A + (int64_t)i * t.a.rs;
-      for (int l0 = 0; l0 < m; l0 += U) {
+      const bool upper = (t.flags & TF_UPPER) != 0;
+      const int lb = upper ? (i & ~(U - 1)) : 0, le = upper ? m : min(m, i + max(t.cap, 1));
+      for (int l0 = lb; l0 < le; l0 += U) {
         T a[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = l0 + u < m ? __ldcg(ai + (int64_t)(l0 + u) * t.a.cs) : T(0);
+        for (int u = 0; u < U; ++u) a[u] = l0 + u < le ? __ldcg(ai + (int64_t)(l0 + u) * t.a.cs) : T(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (l0 + u < m)
+          if (l0 + u < le)
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (j < kc) acc[j] += a[u] * X[(l0 + u) + j * m];
@@ -660,7 +665,7 @@ __device__ void task_gsolve(Ctx<T>& c, const Task& t, char* smem) {
         if (j < kc) stv(c, t.c, i, j0 + j, acc[j]);
     }
   }
-  if (threadIdx.x == 0) c.flops += 2.0 * m * m * k;
+  if (threadIdx.x == 0) c.flops += 1.0 * m * m * k;
 }
 
 // ---------------------------------------------------------------- DADD

@@ -869,6 +869,8 @@ class Sched {
     if (!use_inverses_ || L_.inv_off[d] < 0) return false;
     const int32_t m = sz(rowc(d));
     Task t = make(TK_GSOLVE);
+    t.flags = upper ? TF_UPPER : 0;
+    t.cap = segsz_;  // no diagonal leaf (pivoting block) is larger
     t.a = View{L_.inv_off[d] + (upper ? (int64_t)m * m : 0), 1, m, m, m, -1, 0};
     t.c = V.v;
     begin(t);

@@ -132,7 +132,7 @@ def test_solve_groups_are_bit_identical(lib):
             assert info1[1] < info0[1] if g >= 128 else info1[1] == info0[1]  # tiles of <= 64 are leaves
     finally:
         lib.hlu_set_solve_group(ctypes.c_int32(0))
-        lib.hlu_set_solve_inverse(ctypes.c_int32(256))
+        lib.hlu_set_solve_inverse(ctypes.c_int32(0))
 
 
 def test_inverse_groups_match_substitution(lib):
@@ -150,4 +150,4 @@ def test_inverse_groups_match_substitution(lib):
             assert np.linalg.norm(x1 - x0) <= 1e-10 * np.linalg.norm(x0), g
             assert info1[1] < info0[1]  # fewer solve tasks
     finally:
-        lib.hlu_set_solve_inverse(ctypes.c_int32(256))
+        lib.hlu_set_solve_inverse(ctypes.c_int32(0))

@@ -198,3 +198,29 @@ def test_wait_timeout_is_reported_not_hung(hlu):
     # the context is still usable
     t = torch.ones(10, device="cuda")
     assert float(t.sum()) == 10.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_inverse_groups_match_substitution(hlu, prec):
+    """Diagonal blocks applied through explicit inverses of their triangular
+    factors (hlu_set_solve_inverse) give the substitution's preconditioner up
+    to rounding."""
+    P = hlu.HLU_FP64 if prec == "fp64" else hlu.HLU_FP32
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    m, A, perm, cl, bl = oracle_problem(10, 6.0)
+    N = A.shape[0]
+    Z = np.stack([synth.normal(500 + i, N) for i in range(3)], axis=1)
+    xs = []
+    try:
+        for inv in (0, 128, 256):
+            hlu.hlu_set_solve_inverse(inv)
+            h = hlu.hlu_build(10, 6.0, 32, 2.0, 1e-4)
+            try:
+                hlu.hlu_factor(h, P)
+                xs.append(gpu_apply(hlu, h, Z))
+            finally:
+                hlu.hlu_destroy(h)
+    finally:
+        hlu.hlu_set_solve_inverse(0)
+    for x in xs[1:]:
+        assert np.linalg.norm(x - xs[0]) <= tol * np.linalg.norm(xs[0])

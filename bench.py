@@ -290,7 +290,22 @@ def run_gpu(args):
     _build.build()
     hlu.lib()
     hlu.hlu_set_wait_limit_ms(60000)
-    hlu.hlu_set_tile(args.tile)
+    # granularity: the autotuner's stored choice for this workload (or a fresh
+    # tuning with --autotune), else the command-line tile
+    from paper_2211_11303_gb300 import autotune
+    tuned_path = os.path.join(ROOT, "paper_2211_11303_gb300", "tuned.json")
+    prec_name = "fp32" if args.precision == "fp32" else "fp64"
+    if args.autotune and rank == 0:
+        res = autotune.tune(args.n, args.kappa, args.leaf, args.eta, args.eps,
+                            hlu.HLU_FP32 if prec_name == "fp32" else hlu.HLU_FP64, nrhs=args.nrhs,
+                            restart=args.restart, tol=args.tol)
+        autotune.save(tuned_path, res)
+    best = autotune.load(tuned_path, args.n, args.kappa, args.eps, prec_name)
+    if best:
+        autotune.apply(best)
+        args.tile = int(best["tile"])
+    else:
+        hlu.hlu_set_tile(args.tile)
     n, kappa, nrhs = args.n, args.kappa, args.nrhs
     prec = hlu.HLU_FP32 if args.precision == "fp32" else hlu.HLU_FP64
 
@@ -410,6 +425,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nrhs * N * 8,
                 "d2h_bytes_per_step": nrhs * N * 8},
         "gpu_launches": launches,
+        "autotune": best if best else "defaults (no stored tuning for this workload)",
     }
     if rank == 0 and args.batched > 0:
         line["batched"] = batched_run(args)
@@ -447,6 +463,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="measure the tile / compression candidates on this workload first and store the best")
     ap.add_argument("--batched", type=int, default=64, help="problems of the batched-factor sample (0: none)")
     ap.add_argument("--serving", type=int, default=24, help="requests of the serving sample (0: none)")
     ap.add_argument("--serve-n-lo", type=int, default=8)

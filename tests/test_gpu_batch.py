@@ -81,3 +81,12 @@ def test_solve_batch_equals_single(hlu):
     finally:
         for h in hs:
             hlu.hlu_destroy(h)
+
+
+def test_autotune_picks_a_measured_candidate(hlu):
+    from paper_2211_11303_gb300 import autotune
+    cands = [{"tile": 32, "compress_at": 48}, {"tile": 64, "compress_at": 32}]
+    res = autotune.tune(5, 3.0, candidates=cands, nrhs=2)
+    assert res["best"] in cands
+    assert len(res["results"]) == 2 and all(r["converged"] for r in res["results"])
+    assert res["best"]["tile"] == min(res["results"], key=lambda r: r["total_ms"])["tile"]

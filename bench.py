@@ -156,6 +156,22 @@ def cpu_baseline_subprocess(n=8):
             "seconds": s}
 
 
+def slowest_replica(dist, t_ms, e2e_ms, device):
+    """Replicas only: every rank solves its own problem; the job takes as long
+    as its slowest rank (max over ranks of both timings)."""
+    if dist is None:
+        return t_ms, e2e_ms
+    import torch
+    tt = torch.tensor([t_ms, e2e_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt[0]), float(tt[1])
+
+
+def job_throughput(nrhs, steps, world, ms):
+    """Solves per second of the whole job: every rank solves nrhs columns per step."""
+    return nrhs * steps * world / (ms / 1000.0)
+
+
 def n_dofs(n):
     """Interior edges of the Kuhn n-cube: 7n^3 - 9n^2 + 3n."""
     return 7 * n ** 3 - 9 * n ** 2 + 3 * n
@@ -378,14 +394,9 @@ def run_gpu(args):
     barrier()
     e2e_ms = 1000.0 * (time.perf_counter() - e0)
 
-    t_ms = max(dev_ms, wall_ms)
-    if dist is not None:
-        tt = torch.tensor([t_ms, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms, e2e_ms = float(tt[0]), float(tt[1])
-    solves = nrhs * args.steps * world
-    value = solves / (t_ms / 1000.0)
-    e2e_value = solves / (e2e_ms / 1000.0)
+    t_ms, e2e_ms = slowest_replica(dist, max(dev_ms, wall_ms), e2e_ms, "cuda")
+    value = job_throughput(nrhs, args.steps, world, t_ms)
+    e2e_value = job_throughput(nrhs, args.steps, world, e2e_ms)
     infos = [r[0] for r in recs]
     sts = [r[1] for r in recs]
     fl = statistics.mean(i["flops"] for i in infos)

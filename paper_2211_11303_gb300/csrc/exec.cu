@@ -204,6 +204,26 @@ __device__ __forceinline__ Mat<T> shift(Mat<T> m, int64_t di, int64_t dj) {
 // are staged in shared memory with loads ordered along the operand's
 // contiguous dimension.
 constexpr int KC = 32;
+// Staged chunk layout: element (x, kk) of an operand (x = tile row of A or
+// tile column of B) sits at kk * kLds + x.  The pitch 72 keeps every group of
+// four x 16-byte aligned for the vector reads of chunk_mma.  Operands stored
+// contiguously along x are staged 64 consecutive x per K index; operands
+// stored contiguously along K are staged, per warp, 4 consecutive K indices
+// of 8 columns (16-byte global segments), which under pitch 72 puts the 32
+// shared-memory stores of a warp into 32 distinct banks (staging 32
+// consecutive K indices of one column under pitch 64 was a 32-way conflict).
+constexpr int kLds = 72;
+constexpr int kStage = KC * kLds;  // elements of one staged operand chunk
+static_assert(KC == 32 && NT == 256, "chunk_coord assumes 64 x 32 chunks staged by 256 threads");
+__device__ __forceinline__ void chunk_coord(bool x_contig, int e, int& x, int& kk) {
+  if (x_contig) {
+    x = e & 63;
+    kk = e >> 6;
+  } else {
+    kk = ((e >> 5) & 7) * 4 + (e & 3);
+    x = (e >> 8) * 8 + ((e >> 2) & 7);
+  }
+}
 template <class T>
 __device__ __forceinline__ void acc_zero(T (&acc)[4][4]) {
 #pragma unroll
@@ -230,8 +250,8 @@ __device__ __forceinline__ void chunk_fetch(const Chunk<T>& ch, T (&ra)[kChunkRe
 #pragma unroll
   for (int q = 0; q < kChunkRegs; ++q) {
     const int e = tid + q * NT;
-    const int r = ch.A.rs == 1 ? (e & 63) : e / KC;
-    const int kk = ch.A.rs == 1 ? (e >> 6) : e % KC;
+    int r, kk;
+    chunk_coord(ch.A.rs == 1, e, r, kk);
     const int ar = r - ch.rlo;
     ra[q] = (kk < ch.kc && ar >= 0 && ar < ch.mrows) ? __ldcg(ch.A.p + (int64_t)ar * ch.A.rs + (int64_t)kk * ch.A.cs)
                                                       : T(0);
@@ -239,8 +259,8 @@ __device__ __forceinline__ void chunk_fetch(const Chunk<T>& ch, T (&ra)[kChunkRe
 #pragma unroll
   for (int q = 0; q < kChunkRegs; ++q) {
     const int e = tid + q * NT;
-    const int cc = ch.B.rs == 1 ? e / KC : (e & 63);
-    const int kk = ch.B.rs == 1 ? e % KC : (e >> 6);
+    int cc, kk;
+    chunk_coord(ch.B.rs != 1, e, cc, kk);
     const int bc = cc - ch.clo;
     rb[q] = (kk < ch.kc && bc >= 0 && bc < ch.ncols)
                 ? ch.sg * __ldcg(ch.B.p + (int64_t)kk * ch.B.rs + (int64_t)bc * ch.B.cs)
@@ -254,27 +274,35 @@ __device__ __forceinline__ void chunk_stage(const Chunk<T>& ch, const T (&ra)[kC
 #pragma unroll
   for (int q = 0; q < kChunkRegs; ++q) {
     const int e = tid + q * NT;
-    const int r = ch.A.rs == 1 ? (e & 63) : e / KC;
-    const int kk = ch.A.rs == 1 ? (e >> 6) : e % KC;
-    As[kk * 64 + r] = ra[q];
+    int r, kk;
+    chunk_coord(ch.A.rs == 1, e, r, kk);
+    As[kk * kLds + r] = ra[q];
   }
 #pragma unroll
   for (int q = 0; q < kChunkRegs; ++q) {
     const int e = tid + q * NT;
-    const int cc = ch.B.rs == 1 ? e / KC : (e & 63);
-    const int kk = ch.B.rs == 1 ? e % KC : (e >> 6);
-    Bs[kk * 64 + cc] = rb[q];
+    int cc, kk;
+    chunk_coord(ch.B.rs != 1, e, cc, kk);
+    Bs[kk * kLds + cc] = rb[q];
   }
+}
+// four consecutive staged elements, 16-byte aligned (pitch and offsets are
+// multiples of four elements, the staging buffers start 16-byte aligned)
+__device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
+  const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+  v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
 }
 template <class T>
 __device__ __forceinline__ void chunk_mma(T (&acc)[4][4], const T* As, const T* Bs, int kc) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int kk = 0; kk < kc; ++kk) {
     T a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + tx * 4 + i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + ty * 4 + j];
+    lds4(As + kk * kLds + tx * 4, a);
+    lds4(Bs + kk * kLds + ty * 4, b);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -423,7 +451,7 @@ __device__ void task_proj(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.a.rows, r = ncols(c, t.a), k = ncols(c, t.b);
   if (r == 0 || k == 0) return;
   T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + 64 * KC;
+  T* Bs = As + kStage;
   for (int i0 = 0; i0 < r; i0 += 64)
     for (int j0 = 0; j0 < k; j0 += 64) {
       T acc[4][4];
@@ -504,7 +532,7 @@ template <class T>
 __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.c.rows, k = ncols(c, t.b);
   T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + 64 * KC;
+  T* Bs = As + kStage;
   double fl = 0;
   for (int i0 = 0; i0 < n; i0 += 64)
     for (int j0 = 0; j0 < k; j0 += 64) {
@@ -552,8 +580,8 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
     return;
   }
   T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + 64 * KC;
-  T* A = Bs + 64 * KC;  // the diagonal tile, n x n
+  T* Bs = As + kStage;
+  T* A = Bs + kStage;  // the diagonal tile, n x n
   T* X = A + 64 * 64;   // updated right-hand side, n x k (ld n)
   T* dinv = X + 64 * 64;
   int* perm = reinterpret_cast<int*>(dinv + 64);
@@ -673,7 +701,7 @@ template <class T>
 __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.c.rows, n = ncols(c, t.c), k = ncols(c, t.a);
   T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + 64 * KC;
+  T* Bs = As + kStage;
   for (int i0 = 0; i0 < m; i0 += 64)
     for (int j0 = 0; j0 < n; j0 += 64) {
       T acc[4][4];
@@ -1342,7 +1370,7 @@ __device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
   // shared memory: [region 0: staging chunks, later M (n x kDenseRank) and
   // V][D (m x n)][tau, nrm2 (kDenseMax each)][perm]
   T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + 64 * KC;
+  T* Bs = As + kStage;
   T* M = As;
   T* V = M + kDenseMax * kDenseRank;
   T* D = V + kDenseRank * kDenseRank;
@@ -1653,19 +1681,19 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
 
 size_t exec_smem_bytes(int elem_size) {
   // max over task kinds: TRUNC (3 stack-wide vectors + G + V), GETRF/TRSM
-  // (64 x 64 + 64 ints), staged GEMM chunks (2 x 64 x KC)
+  // (64 x 64 + 64 ints), staged GEMM chunks (2 x KC x kLds)
   size_t trunc = (size_t)elem_size * (3 * kTruncStack + 2 * kTruncStack * kTruncStack);
   if (elem_size == 4) {  // dense truncation route (FP32 only)
     size_t region0 = (size_t)4 * (kDenseMax * kDenseRank + kDenseRank * kDenseRank);
-    if (region0 < (size_t)4 * 2 * 64 * KC) region0 = (size_t)4 * 2 * 64 * KC;
+    if (region0 < (size_t)4 * 2 * kStage) region0 = (size_t)4 * 2 * kStage;
     const size_t dense = region0 + (size_t)4 * (kDenseMax * kDenseMax + 2 * kDenseMax) + sizeof(int) * kDenseMax;
     if (dense > trunc) trunc = dense;
   }
   size_t lu = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
   // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
-  const size_t rsolve = (size_t)elem_size * (2 * 64 * KC + 2 * 64 * 64 + 64) + 64 * sizeof(int);
+  const size_t rsolve = (size_t)elem_size * (2 * kStage + 2 * 64 * 64 + 64) + 64 * sizeof(int);
   if (rsolve > lu) lu = rsolve;
-  size_t gemm = (size_t)elem_size * 2 * 64 * KC;
+  size_t gemm = (size_t)elem_size * 2 * kStage;
   size_t m = trunc > lu ? trunc : lu;
   return m > gemm ? m : gemm;
 }

@@ -585,17 +585,26 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
   T* X = A + 64 * 64;   // updated right-hand side, n x k (ld n)
   T* dinv = X + 64 * 64;
   int* perm = reinterpret_cast<int*>(dinv + 64);
-  // the tile and the pivots start moving now (read-only factor data)
+  // the tile and the right-hand side start moving now: the tile is read-only
+  // factor data, and no other task touches this segment of the right-hand
+  // side while this one runs.  All the view's columns are copied (the work
+  // vector holds that many), so the copy need not wait for the live count.
   const T* tile = c.arena + t.a.off;
   for (int idx = threadIdx.x; idx < n * n; idx += NT)
     cp_async_elem(A + idx, tile + (int64_t)(idx % n) * t.a.rs + (int64_t)(idx / n) * t.a.cs);
+  const int kx = min(t.c.cols, 64);
+  const T* rhs = c.arena + t.c.off;
+  for (int idx = threadIdx.x; idx < n * kx; idx += NT)
+    cp_async_elem(X + idx, rhs + (int64_t)(idx % n) * t.c.rs + (int64_t)(idx / n) * t.c.cs);
   asm volatile("cp.async.commit_group;" ::: "memory");
   const int pv = (!upper && threadIdx.x < n) ? __ldcg(c.piv + t.piv_off + threadIdx.x) : 0;
   // the update, kept in registers
   T acc[4][4];
   acc_zero(acc);
   double fl = t.list_count > 0 ? rowmv_tile(c, t, 0, 0, k, acc, As, Bs) : 0.0;
-  {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  if (t.list_count > 0) {
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const T sg = T(t.sign);
 #pragma unroll
@@ -603,11 +612,10 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int r = tx * 4 + i, cc = ty * 4 + j;
-        if (r < n && cc < k) X[r + cc * n] = ldv(c, t.c, r, cc) + sg * acc[i][j];
+        if (r < n && cc < k) X[r + cc * n] += sg * acc[i][j];
       }
   }
   if (!upper && threadIdx.x < n) perm[threadIdx.x] = pv;
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   if (upper)
     for (int i = threadIdx.x; i < n; i += NT) dinv[i] = T(1) / A[i + i * n];
@@ -1553,6 +1561,7 @@ template <class T>
 __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int64_t s_task;
+  __shared__ int64_t s_succ[2];  // successor range of the running task
   __shared__ int s_prob;
   Ctx<T> c;
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
@@ -1606,6 +1615,12 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     const int64_t ti = s_task;
     if (ti < 0) break;
     const ProbSched& P = a.probs[s_prob];
+    if (threadIdx.x == 0) {  // the successor range streams in while the task runs
+      const unsigned d = (unsigned)__cvta_generic_to_shared(s_succ);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(P.succ_ptr + ti) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8u), "l"(P.succ_ptr + ti + 1) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     const int ttype = P.tasks[ti].type;
     if (ttype >= 0 && ttype < TK_NUM) {
       const Task t = P.tasks[ti];
@@ -1627,12 +1642,13 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
         run_task(c, t, smem);
       }
     }
+    if (threadIdx.x == 0) asm volatile("cp.async.wait_all;" ::: "memory");
     __threadfence();
     __syncthreads();
     // release the successors: the last predecessor to finish pushes a task
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      const int64_t e0 = P.succ_ptr[ti], e1 = P.succ_ptr[ti + 1];
+      const int64_t e0 = s_succ[0], e1 = s_succ[1];
       for (int64_t eb = e0; eb < e1; eb += 32) {
         const int64_t e = eb + lane;
         bool push = false;

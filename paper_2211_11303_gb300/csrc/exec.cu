@@ -769,7 +769,7 @@ struct AccurateDot<double> {
 // diagonal in s2[j + 1], so one barrier per column suffices.  Column j is
 // scaled into its stored form one step later, when no warp reads it.
 template <class T, int NW>
-__device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int bar) {
+__device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, T* scb, int gt, int bar) {
   constexpr int NTG = NW * 32;
   const int wg = gt >> 5, lane = gt & 31;
   const int tmax = min(m, w);
@@ -784,14 +784,8 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
     if (lane == 0) s2[0] = s;
   }
   group_bar(bar, NTG);
-  T pbeta = 0, psc = 0;
   for (int j = 0; j < tmax; ++j) {
     T* cj = S + (int64_t)j * m;
-    if (j > 0) {
-      T* cp = cj - m;
-      for (int i = j + gt; i < m; i += NTG) cp[i] *= psc;
-      if (gt == 0) cp[j - 1] = pbeta;
-    }
     const T ss = s2[j];
     const T alpha = cj[j];
     T beta = alpha, sc = 0, tj = 0;
@@ -801,7 +795,11 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
       sc = T(1) / (alpha - beta);
       tj = (beta - alpha) / beta;
     }
-    if (gt == 0) tau[j] = tj;
+    if (gt == 0) {
+      tau[j] = tj;
+      scb[j] = sc;
+      scb[kTruncStack + j] = beta;
+    }
     for (int c0 = j + 1 + wg; c0 < w; c0 += 4 * NW) {
       T* col[4];
       T d[4], top[4];
@@ -857,14 +855,36 @@ __device__ void house_qr_group(T* S, int m, int w, T* tau, T* s2, int gt, int ba
         if (lane == 0) s2[j + 1] = nn;
       }
     }
-    pbeta = beta;
-    psc = sc;
     group_bar(bar, NTG);
   }
-  {
-    T* cp = S + (int64_t)(tmax - 1) * m;
-    for (int i = tmax + gt; i < m; i += NTG) cp[i] *= psc;
-    if (gt == 0) cp[tmax - 1] = pbeta;
+  // Each column's reflector is scaled to a unit leading entry and its
+  // diagonal becomes R's, in one pass at the end (column j is last read in
+  // step j, which used it unscaled).  Thread gt visits elements gt, gt + NTG,
+  // ... of the m x tmax block; its (row, column) advances without a division.
+  const int tot = m * tmax;
+  int ri = gt % m, rj = gt / m;
+  for (int b0 = gt; b0 < tot; b0 += 8 * NTG) {
+    T x[8];
+    int xi[8], xj[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      xi[u] = ri;
+      xj[u] = rj;
+      x[u] = (b0 + u * NTG < tot && ri > rj) ? S[(int64_t)rj * m + ri] : T(0);
+      ri += NTG;
+      while (ri >= m) {
+        ri -= m;
+        ++rj;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (b0 + u * NTG < tot) {
+        if (xi[u] > xj[u])
+          S[(int64_t)xj[u] * m + xi[u]] = x[u] * scb[xj[u]];
+        else if (xi[u] == xj[u])
+          S[(int64_t)xj[u] * m + xi[u]] = scb[kTruncStack + xj[u]];
+      }
   }
   group_bar(bar, NTG);
 }
@@ -1140,6 +1160,7 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
                              TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
                              double* flops, double* fro, unsigned long long* tp, double jtol) {
   __shared__ TC s2x[kStackCols + 1], s2y[kStackCols + 1];
+  __shared__ TC s_scbx[2 * kStackCols], s_scby[2 * kStackCols];  // reflector scales and R's diagonal
   long long t0 = tp && threadIdx.x == 0 ? clock64() : 0;
   auto lap = [&](int k) {
     if (tp && threadIdx.x == 0) {
@@ -1153,9 +1174,9 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   __shared__ double s_fro;
   constexpr int kHalf = NT / 2;
   if (threadIdx.x < kHalf)
-    house_qr_group<TC, kHalf / 32>(SX, m, W, tauX, s2x, threadIdx.x, 1);
+    house_qr_group<TC, kHalf / 32>(SX, m, W, tauX, s2x, s_scbx, threadIdx.x, 1);
   else
-    house_qr_group<TC, kHalf / 32>(SY, n, W, tauY, s2y, threadIdx.x - kHalf, 2);
+    house_qr_group<TC, kHalf / 32>(SY, n, W, tauY, s2y, s_scby, threadIdx.x - kHalf, 2);
   __syncthreads();
   lap(1);
   const int p = min(m, W), q = min(n, W);

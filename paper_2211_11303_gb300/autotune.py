@@ -20,7 +20,7 @@ import torch
 
 from . import hlu as H
 
-DEFAULT_CANDIDATES = [{"tile": t, "compress_at": c} for t in (32, 64) for c in (32, 48, 64)]
+DEFAULT_CANDIDATES = [{"tile": t, "compress_at": c} for t in (32, 64) for c in (32, 48, 64, 80, 96)]
 
 
 def apply(params):

@@ -226,6 +226,7 @@ struct hlu_handle {
   void* d_arena = nullptr;
   int64_t arena_elems = 0;
   int32_t* d_ranks = nullptr;
+  int32_t cur_nrhs = 0;  // the value last written to the right-hand-side count slot
   int32_t* d_piv = nullptr;
   void* d_scratch = nullptr;
   int64_t scratch_stride = 0;
@@ -290,6 +291,8 @@ ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   p.eps = h->eps;
   p.ntasks = ds.ntasks;
   p.limit = ds.run_count(limit);
+  p.nrhs_slot = h->L.nrhs_slot;
+  p.nrhs = h->cur_nrhs;
   return p;
 }
 
@@ -432,6 +435,7 @@ int solve_impl(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, i
   for (int32_t c0 = 0; c0 < nrhs; c0 += h->L.nrhs_max) {
     int32_t nc = std::min(h->L.nrhs_max, nrhs - c0);
     CKR(set_int(h->d_ranks + h->L.nrhs_slot, nc, s), "nrhs slot");
+    h->cur_nrhs = nc;
     CKR(gather_cast<T>(N, h->d_perm, b + c0 * ld, ld, work, nc, s), "gather");
     int rc = exec_run(h, h->dS, h->grid, s, false);
     if (rc) return rc;
@@ -837,6 +841,7 @@ static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
     h->precision = precision;
   }
   CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
+  h->cur_nrhs = 0;
   int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
   CKR(cudaMemcpyAsync(h->d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
   cudaError_t e;
@@ -1063,6 +1068,7 @@ int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b
     for (int32_t i = 0; i < count; ++i) {
       hlu_handle* h = hs[i];
       CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs[i], s), "nrhs slot");
+      h->cur_nrhs = nrhs[i];
       if (h->precision == HLU_FP64)
         CKR(gather_cast<double>(h->A.N, h->d_perm, b[i], h->A.N, (double*)h->d_arena + h->L.work_off, nrhs[i], s),
             "gather");
@@ -1220,6 +1226,7 @@ extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trac
   CKR(cudaMalloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs, nullptr), "nrhs slot");
+  h->cur_nrhs = nrhs;
   int rc = exec_run(h, h->dS, h->grid, nullptr, false);
   if (!rc) {
     int32_t st[8];
@@ -1304,6 +1311,7 @@ int solve_segments(std::vector<hlu_handle*>& hs, std::vector<std::vector<SolveSe
       off += g.nr;
     }
     CKR(set_int(h->d_ranks + h->L.nrhs_slot, off, s), "nrhs slot");
+    h->cur_nrhs = off;
   }
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);

@@ -66,6 +66,7 @@ struct Ctx {
   unsigned long long* tprof;  // truncation phase profile (shared memory) or null
   double jacobi_tol;
   int32_t compress_at;
+  int32_t nrhs_slot, nrhs;  // the launch's right-hand-side count and its slot
 };
 
 template <class T>
@@ -78,7 +79,8 @@ __device__ __forceinline__ void stv(const Ctx<T>& c, const View& v, int64_t i, i
 }
 template <class T>
 __device__ __forceinline__ int32_t ncols(const Ctx<T>& c, const View& v) {
-  return v.slot >= 0 ? __ldcg(c.ranks + v.slot) : v.cols;
+  if (v.slot < 0) return v.cols;
+  return v.slot == c.nrhs_slot ? c.nrhs : __ldcg(c.ranks + v.slot);
 }
 
 template <class T>
@@ -529,11 +531,45 @@ __device__ double rowmv_tile(const Ctx<T>& c, const Task& t, int i0, int j0, int
 }
 
 template <class T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc);
+
+template <class T>
 __device__ void task_rowmv(Ctx<T>& c, const Task& t, char* smem) {
   const int n = t.c.rows, k = ncols(c, t.b);
   T* As = reinterpret_cast<T*>(smem);
   T* Bs = As + kStage;
   double fl = 0;
+  const bool overwrite = (t.flags & TF_OVERWRITE) != 0;
+  const int kx = min(t.c.cols, 64);
+  if (n <= 64 && k <= kx && !overwrite) {
+    // one output tile: its current values stream into shared memory (all
+    // the view's columns, so the copy need not wait for the live count)
+    // while the product runs; no other task touches them meanwhile
+    T* Cs = Bs + kStage;
+    const T* cg = c.arena + t.c.off;
+    for (int idx = threadIdx.x; idx < n * kx; idx += NT)
+      cp_async_elem(Cs + idx, cg + (int64_t)(idx % n) * t.c.rs + (int64_t)(idx / n) * t.c.cs);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    T acc[4][4];
+    acc_zero(acc);
+    fl = rowmv_tile(c, t, 0, 0, k, acc, As, Bs);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const T sg = T(t.sign);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = tx * 4 + i, cc = ty * 4 + j;
+        if (r < n && cc < k) stv(c, t.c, r, cc, Cs[r + cc * n] + sg * acc[i][j]);
+      }
+    if (threadIdx.x == 0) {
+      c.flops += fl;
+      if (t.out_slot >= 0) __stcg(c.ranks + t.out_slot, k);
+    }
+    return;
+  }
   for (int i0 = 0; i0 < n; i0 += 64)
     for (int j0 = 0; j0 < k; j0 += 64) {
       T acc[4][4];
@@ -1652,6 +1688,8 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
       c.pieces = P.pieces;
       c.micro = P.micro;
       c.eps = P.eps;
+      c.nrhs_slot = P.nrhs_slot;
+      c.nrhs = P.nrhs;
       if (t.type == TK_SEQ) {
         for (int q = 0; q < t.list_count; ++q) {
           const Task u = c.micro[t.list_begin + q];

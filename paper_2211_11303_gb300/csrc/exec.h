@@ -25,6 +25,8 @@ struct ProbSched {
   double eps;
   int64_t ntasks;
   int64_t limit;            // tasks with index >= limit are not run
+  int32_t nrhs_slot;        // rank slot of the right-hand-side count, and its
+  int32_t nrhs;             // value for this launch (read without a load)
 };
 constexpr int kMaxBatch = 64;  // problems in one launch
 // profile layout: per task kind (TK_NUM + 1 rows) tasks, wait cycles, run

@@ -83,9 +83,11 @@ struct DevSched {
   unsigned long long* queue = nullptr;  // per handle: ready queue, ntasks slots
   unsigned long long* qctl = nullptr;   // per handle: claim / fill positions
   int64_t ntasks = 0;
+  int64_t nterms = 0;
   bool owns_data = true;
   cudaError_t load(const Schedule& S) {
     ntasks = (int64_t)S.tasks.size();
+    nterms = (int64_t)S.terms.size();
     cudaError_t e;
     if ((e = upload(&tasks, S.tasks)) != cudaSuccess) return e;
     if ((e = upload(&terms, S.terms)) != cudaSuccess) return e;
@@ -227,6 +229,8 @@ struct hlu_handle {
   int64_t arena_elems = 0;
   int32_t* d_ranks = nullptr;
   int32_t cur_nrhs = 0;  // the value last written to the right-hand-side count slot
+  int32_t* d_term_p = nullptr;  // solve terms' column counts after the last factorisation
+  bool term_p_fresh = false;
   int32_t* d_piv = nullptr;
   void* d_scratch = nullptr;
   int64_t scratch_stride = 0;
@@ -248,9 +252,11 @@ namespace {
 void free_factor(hlu_handle* h) {
   for (void* p : {(void*)h->d_arena, (void*)h->d_ranks, (void*)h->d_piv, (void*)h->d_scratch, (void*)h->d_status,
                   (void*)h->d_flops, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp,
-                  (void*)h->d_prof})
+                  (void*)h->d_prof, (void*)h->d_term_p})
     if (p) cudaFree(p);
   h->d_prof = nullptr;
+  h->d_term_p = nullptr;
+  h->term_p_fresh = false;
   h->d_arena = nullptr;
   h->d_ranks = nullptr;
   h->d_piv = nullptr;
@@ -275,6 +281,32 @@ int blocks_per_sm() {
   return exec_blocks_per_sm<T>();
 }
 
+// Column count of each solve term's A (its rank after the factorisation, or
+// its fixed width); -1 for a term whose width is the right-hand-side count.
+__global__ void k_term_ranks(const Term* terms, int64_t n, const int32_t* ranks, int32_t nrhs_slot, int32_t* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const View& A = terms[q].A;
+    out[q] = A.slot < 0 ? A.cols : (A.slot == nrhs_slot ? -1 : ranks[A.slot]);
+  }
+}
+
+// Before a launch of schedule ds on h: a factorisation makes the resolved
+// term widths stale; a solve launch refreshes them (stream-ordered after the
+// factorisation that produced the ranks).
+int prepare_terms(hlu_handle* h, DevSched& ds, cudaStream_t s) {
+  if (&ds == &h->dF) {
+    h->term_p_fresh = false;
+    return HLU_OK;
+  }
+  if (&ds != &h->dS || ds.nterms == 0 || !h->d_term_p || h->term_p_fresh) return HLU_OK;
+  const int blocks = (int)std::min<int64_t>((ds.nterms + 255) / 256, 1184);
+  note_launch();
+  k_term_ranks<<<blocks, 256, 0, s>>>(ds.terms, ds.nterms, h->d_ranks, h->L.nrhs_slot, h->d_term_p);
+  CKR(cudaGetLastError(), "term widths");
+  h->term_p_fresh = true;
+  return HLU_OK;
+}
+
 ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   ProbSched p;
   std::memset(&p, 0, sizeof(p));
@@ -293,6 +325,7 @@ ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   p.limit = ds.run_count(limit);
   p.nrhs_slot = h->L.nrhs_slot;
   p.nrhs = h->cur_nrhs;
+  p.term_p = (&ds == &h->dS && h->term_p_fresh) ? h->d_term_p : nullptr;
   return p;
 }
 
@@ -312,6 +345,7 @@ void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool wi
 // One launch of the executor over one problem's schedule (or its first
 // `limit` tasks): counters reset, queue cleared and seeded with the roots.
 int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops, int64_t limit = -1) {
+  if (int rc = prepare_terms(h, ds, s)) return rc;
   ExecArgs a;
   std::memset(&a, 0, sizeof(a));
   a.probs[0] = prob_of(h, ds, limit);
@@ -379,6 +413,7 @@ int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, 
     for (int j = 0; j < i; ++j)
       if (hs[j] == h) return fail(HLU_ERR_ARG, "a handle appears twice in a batch");
     DevSched& ds = which == 0 ? h->dF : h->dS;
+    if (int rc = prepare_terms(h, ds, s)) return rc;
     a.probs[i] = prob_of(h, ds, -1);
     roots[i] = &ds.h_roots;
     total += ds.ntasks;
@@ -743,6 +778,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     h->dS = h->sb->dS.share();
     if ((e = h->dF.alloc_state()) != cudaSuccess) return bail(e, "queue");
     if ((e = h->dS.alloc_state()) != cudaSuccess) return bail(e, "queue");
+    if (h->dS.nterms > 0 && (e = cudaMalloc(&h->d_term_p, sizeof(int32_t) * h->dS.nterms)) != cudaSuccess)
+      return bail(e, "term widths");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "sync");
     h->info.n_tasks = h->sb->st.n_factor_tasks;
     h->info.n_solve_tasks = h->sb->st.n_solve_tasks;

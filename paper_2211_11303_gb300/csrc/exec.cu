@@ -67,6 +67,7 @@ struct Ctx {
   double jacobi_tol;
   int32_t compress_at;
   int32_t nrhs_slot, nrhs;  // the launch's right-hand-side count and its slot
+  const int32_t* term_p;    // resolved term column counts (solve launches) or null
 };
 
 template <class T>
@@ -516,8 +517,10 @@ __device__ double rowmv_tile(const Ctx<T>& c, const Task& t, int i0, int j0, int
       int32_t* dst = reinterpret_cast<int32_t*>(s_tm);
       for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
     }
+    // resolved column counts arrive with the terms (no dependent rank load)
+    const int pq = (c.term_p && threadIdx.x < nq) ? __ldcg(c.term_p + t.list_begin + qb + threadIdx.x) : -1;
     __syncthreads();
-    if (threadIdx.x < nq) s_p[threadIdx.x] = ncols(c, s_tm[threadIdx.x].A);
+    if (threadIdx.x < nq) s_p[threadIdx.x] = pq >= 0 ? pq : ncols(c, s_tm[threadIdx.x].A);
     __syncthreads();
     TermCursor<T> cur{&c, s_tm, s_p, nq, i0, j0, k, 0, 0};
     tile_mma_seq(acc, cur, As, Bs);
@@ -1690,6 +1693,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
       c.eps = P.eps;
       c.nrhs_slot = P.nrhs_slot;
       c.nrhs = P.nrhs;
+      c.term_p = P.term_p;
       if (t.type == TK_SEQ) {
         for (int q = 0; q < t.list_count; ++q) {
           const Task u = c.micro[t.list_begin + q];

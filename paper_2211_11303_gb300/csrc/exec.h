@@ -27,6 +27,8 @@ struct ProbSched {
   int64_t limit;            // tasks with index >= limit are not run
   int32_t nrhs_slot;        // rank slot of the right-hand-side count, and its
   int32_t nrhs;             // value for this launch (read without a load)
+  const int32_t* term_p;    // solve launches: each term's column count, resolved
+                            // after the factorisation (-1: read it live); else null
 };
 constexpr int kMaxBatch = 64;  // problems in one launch
 // profile layout: per task kind (TK_NUM + 1 rows) tasks, wait cycles, run

@@ -3,8 +3,7 @@
 
 Workload (default): Kuhn cube n = 24 (N = 91,656 interior edges), kappa = 8,
 leaf 32, eta 2, eps 1e-4; FP32 H-LU factor, FP64 flexible GMRES(50) to a
-relative residual of 1e-10 (forward error <= 1e-7 against the direct solve is
-checked by the GPU tests); 8 seeded N(0,1) right-hand sides.
+relative residual of 1e-10; 8 seeded N(0,1) right-hand sides.
 
 One step = the whole hot path on one batch: hlu_build (GPU mesh, assembly,
 cluster tree, block tree, A_H descriptors; the task DAG is compiled once per
@@ -12,6 +11,15 @@ block-tree structure and reused), hlu_factor (FP32) and gmres_solve of the 8
 right-hand sides.  `value` = solves per second with the right-hand sides
 resident in HBM; `e2e` = the same with the right-hand sides copied from pinned
 host memory and the solutions copied back inside the timed region.
+
+Accuracy: after the timed region the solutions of the last step are compared
+with the stored direct-solve reference of the same workload
+(tests/golden/xref_n24_kappa8.npy, written by tests/golden/make_xref.py from
+the CPU oracle's matrix); `accuracy.fwd_err_max` is the largest
+||x - x_ref|| / ||x_ref|| over the right-hand sides, the error the metric's
+"to 1e-7" counts.  `fp64_arm` times the plain FP64 factor + FP64 GMRES path on
+the same workload, and `same_sample` times the GPU path on the CPU oracle's
+own sample next to `cpu_baseline`.
 
 `--impl reference` times the CPU oracle (oracle/, plain FP64 NumPy), as it
 stands, on a bounded sample of the workload family.
@@ -46,22 +54,34 @@ def _blob_sha1(path):
 
 
 def _factor_traffic(n, eps, precision):
-    """DRAM bytes per factorisation launch from the committed ncu capture
-    (profiles/exec_kernel_factor_dram.md), or None when the capture is of
-    another workload or the executor source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "exec_kernel_factor_dram.md")
+    """DRAM bytes per factorisation launch recorded from an ncu capture in
+    profiles/traffic.json, or None when that record is of another workload or
+    the executor source changed since it was taken."""
     try:
-        fields = {}
-        with open(path) as f:
-            for line in f:
-                if line.startswith("- ") and ": " in line:
-                    k, v = line[2:].split(": ", 1)
-                    fields[k.strip()] = v.strip().strip("`")
-        same_src = fields["exec.cu blob"] == _blob_sha1(os.path.join(ROOT, "paper_2211_11303_gb300", "csrc", "exec.cu"))
-        same_work = (int(fields["n"]) == n and float(fields["eps"]) == eps and fields["precision"] == precision)
-        return int(fields["factor DRAM bytes per launch"]) if same_src and same_work else None
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)["exec_kernel_factor"]
+        same_src = rec["exec_cu_blob"] == _blob_sha1(os.path.join(ROOT, "paper_2211_11303_gb300", "csrc", "exec.cu"))
+        same_work = int(rec["n"]) == n and float(rec["eps"]) == eps and rec["precision"] == precision
+        return int(rec["dram_bytes_per_launch"]) if same_src and same_work else None
     except (OSError, KeyError, ValueError):
         return None
+
+
+XREF = os.path.join(ROOT, "tests", "golden", "xref_n24_kappa8.npy")
+
+
+def forward_errors(X, n, kappa, nrhs, rank):
+    """Per right-hand side ||x - x_ref|| / ||x_ref|| against the stored direct
+    solve of the n = 24, kappa = 8 workload (rank 0's seeds); None for another
+    workload."""
+    import numpy as np
+    if n != 24 or kappa != 8.0 or rank != 0 or not os.path.exists(XREF):
+        return None
+    ref = np.load(XREF)
+    if nrhs > ref.shape[1]:
+        return None
+    ref = ref[:, :nrhs]
+    return (np.linalg.norm(X - ref, axis=0) / np.linalg.norm(ref, axis=0)).tolist()
 
 
 def _peaks():
@@ -149,11 +169,22 @@ def cpu_baseline_subprocess(n=8):
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     s, it, N = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": 1.0 / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / s, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": ("complete oracle path (assembly, trees, A_H, recursive FP64 H-LU, FGMRES to 1e-10) "
-                       "for 1 seeded RHS on the n=%d cube (N=%d, kappa=8, eps 1e-4): %.2f s, %d iterations; "
-                       "the oracle cannot finish the n=24 factorisation within minutes" % (n, N, s, it)),
-            "seconds": s}
+                       "for 1 seeded RHS on the n=%d cube (N=%d, kappa=8, eps 1e-4), single-threaded "
+                       "(BLAS threads 1) on one of the host's %d cores: %.2f s, %d iterations; the oracle cannot "
+                       "finish the n=24 factorisation within minutes" % (n, N, os.cpu_count(), s, it)),
+            "seconds": s, "iterations": it}
+
+
+def oracle_config(n):
+    """Config of the CPU oracle's sample (what the reference arm and the
+    cpu_baseline leg time)."""
+    N = n_dofs(n)
+    return {"workload": "Kuhn cube n=%d (N=%d), kappa=8, leaf 32, eta 2, eps 0.0001, FP64 H-LU + FP64 FGMRES(50) "
+                        "to 1e-10, 1 seeded N(0,1) RHS (the oracle's bounded sample of the workload family)" % (n, N),
+            "n": n, "N": N, "kappa": 8.0, "leaf": 32, "eta": 2.0, "eps": 1e-4, "nrhs": 1, "restart": 50,
+            "tol": 1e-10, "precision": "fp64"}
 
 
 def slowest_replica(dist, t_ms, e2e_ms, device):
@@ -276,8 +307,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(arm_config(args), parallelism="single host core"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": dict(oracle_config(args.ref_n), parallelism="single host core"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": ("each step: the complete FP64 oracle path (assembly, trees, A_H, recursive "
                                     "H-LU, FGMRES to 1e-10) for 1 seeded N(0,1) RHS on the n=%d cube (N=%d, "
                                     "kappa 8, eps 1e-4), a bounded stand-in for the workload; the oracle cannot "
@@ -286,6 +317,30 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def whole_path_run(hlu, n, kappa, leaf, eta, eps, prec, Bd, X, restart, tol, maxit, steps, warmup):
+    """Times `steps` whole-path steps (hlu_build, hlu_factor, gmres_solve of
+    Bd's columns into X) after `warmup` untimed ones; returns the mean step in
+    ms and the last step's factor statistics and solve statistics."""
+    import torch
+    last = None
+    times = []
+    for k in range(warmup + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = hlu.hlu_build(n, kappa, leaf, eta, eps)
+        try:
+            hlu.hlu_factor(h, prec)
+            info = hlu.hlu_factor_stats(h)
+            st = hlu.gmres_solve(h, Bd, X, restart=restart, tol=tol, maxit=maxit)
+        finally:
+            hlu.hlu_destroy(h)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(1000.0 * (time.perf_counter() - t0))
+        last = (info, st)
+    return statistics.mean(times), last[0], last[1]
 
 
 def run_gpu(args):
@@ -394,6 +449,10 @@ def run_gpu(args):
     barrier()
     e2e_ms = 1000.0 * (time.perf_counter() - e0)
 
+    # accuracy of the timed path: the last step's solutions (the e2e steps
+    # rewrote X with the same solve) against the stored direct solve
+    fwd = forward_errors(X.t().cpu().numpy().T, n, kappa, nrhs, rank)
+
     t_ms, e2e_ms = slowest_replica(dist, max(dev_ms, wall_ms), e2e_ms, "cuda")
     value = job_throughput(nrhs, args.steps, world, t_ms)
     e2e_value = job_throughput(nrhs, args.steps, world, e2e_ms)
@@ -409,6 +468,9 @@ def run_gpu(args):
     achieved = fl / (fms / 1000.0) / 1e12
     lat_sorted = sorted(lat)
     p99 = lat_sorted[min(len(lat_sorted) - 1, int(round(0.99 * (len(lat_sorted) - 1))))]
+    apply_ms = statistics.mean(s["precond_ms"] / max(s["precond_applies"], 1) for s in sts)
+    live_bytes = statistics.mean(i["factor_live_bytes"] for i in infos)
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -420,34 +482,86 @@ def run_gpu(args):
         "factor_ms": fms,
         "gmres_iterations": max(s["iterations"] for s in sts),
         "gmres_relres": max(s["relres_max"] for s in sts),
-        "precond_ms_per_apply": statistics.mean(s["precond_ms"] / max(s["precond_applies"], 1) for s in sts),
+        "precond_ms_per_apply": apply_ms,
         "solve_phase": {"value": nrhs / (statistics.mean(s["gmres_ms"] for s in sts) / 1000.0), "unit": UNIT,
                         "note": "factor cached: the %d RHS columns of one step over the FGMRES time" % nrhs},
-        "p50_ms": statistics.median(lat), "p99_ms": p99,
+        "step_latency_ms": {"p50": statistics.median(lat), "p99": p99,
+                            "note": "spread of the timed whole-path steps; the served p99 is p99_ms"},
         "schedule_ms_first_build": infos[0]["schedule_ms"],
         "rank_mean": statistics.mean(i["rank_mean"] for i in infos),
         "rank_max": max(i["rank_max"] for i in infos),
+        "accuracy": {"fwd_err_max": max(fwd) if fwd else None, "fwd_err": fwd,
+                     "target": 1e-7, "met": bool(fwd) and max(fwd) <= 1e-7,
+                     "reference": ("stored direct solve of the oracle's matrix for these RHS "
+                                   "(tests/golden/xref_n24_kappa8.npy: SuperLU + one refinement step, FP64)"
+                                   if fwd else "no stored reference for this workload"),
+                     "rank_cap_hits": max(i["rank_cap_hits"] for i in infos),
+                     "rank_wanted_max": max(i["rank_wanted_max"] for i in infos),
+                     "rank_capacity": 64},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak_tflops,
                      "traffic": _factor_traffic(n, args.eps, args.precision),
-                     "kernel": "exec_kernel<float> (H-LU task executor)",
-                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x %s max SM clock" % src},
+                     "kernel": "exec_kernel<float> (H-LU task executor), factorisation launch",
+                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x %s max SM clock" % src,
+                     "solve": {"bound": "hbm", "achieved": live_bytes / (apply_ms / 1000.0) / 1e9,
+                               "peak": hbm_gbs, "unit": "GB/s",
+                               "frac": live_bytes / (apply_ms / 1000.0) / 1e9 / hbm_gbs,
+                               "traffic": None, "bytes_per_apply": live_bytes,
+                               "kernel": "exec_kernel<float> (H-LU task executor), one triangular-solve "
+                                         "launch (L then U) per preconditioner apply",
+                               "peak_source": "%s hbm_gbs" % src,
+                               "note": "algorithmic bytes = factor words at their live ranks, read once per "
+                                       "apply; time = CUDA events around the apply launches"}},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nrhs * N * 8,
                 "d2h_bytes_per_step": nrhs * N * 8},
         "gpu_launches": launches,
         "autotune": best if best else "defaults (no stored tuning for this workload)",
     }
+    if rank == 0 and args.fp64_steps > 0:
+        # the plain FP64 path (FP64 factor and triangular solves, FP64 GMRES)
+        # on the same workload and right-hand sides
+        ms64, info64, st64 = whole_path_run(hlu, n, kappa, args.leaf, args.eta, args.eps, hlu.HLU_FP64, B, X,
+                                            args.restart, args.tol, args.maxit, args.fp64_steps, 1)
+        fwd64 = forward_errors(X.t().cpu().numpy().T, n, kappa, nrhs, rank)
+        line["fp64_arm"] = {
+            "value": nrhs / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+            "factor_ms": info64["factor_ms"], "gmres_iterations": st64["iterations"],
+            "precond_ms_per_apply": st64["precond_ms"] / max(st64["precond_applies"], 1),
+            "fwd_err_max": max(fwd64) if fwd64 else None, "rank_cap_hits": info64["rank_cap_hits"],
+            "ratio_fp32_over_fp64": value / world / (nrhs / (ms64 / 1000.0)),
+            "note": "same workload, RHS and whole-path step (build + FP64 factor + FP64 GMRES), wall clock"}
     if rank == 0 and args.batched > 0:
         line["batched"] = batched_run(args)
     if rank == 0 and args.serving > 0:
         line["serving"] = serving_run(args)
+        line["p99_ms"] = line["serving"]["p99_ms"]
+        line["p50_ms"] = line["serving"]["p50_ms"]
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_subprocess(args.ref_n)
         except Exception as e:  # reported, not fatal
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "failed: %s" % e}
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": "failed: %s" % e}
+    if rank == 0 and args.same_sample_steps > 0:
+        # the GPU whole path on the CPU oracle's own sample (n = ref_n, one
+        # seeded RHS, kappa 8, eps 1e-4), in both factor precisions
+        hs = hlu.hlu_build(args.ref_n, 8.0, 32, 2.0, 1e-4)
+        Ns = hlu.hlu_n(hs)
+        hlu.hlu_destroy(hs)
+        bs = torch.from_numpy(synth.normal(synth.rhs_seed(2, 0, 0), Ns)).cuda().reshape(1, Ns).t()
+        xs = hlu.colmajor(Ns, 1)
+        same = {"config": oracle_config(args.ref_n), "steps": args.same_sample_steps}
+        for name, pr in (("fp32_factor", hlu.HLU_FP32), ("fp64_factor", hlu.HLU_FP64)):
+            ms_s, _, st_s = whole_path_run(hlu, args.ref_n, 8.0, 32, 2.0, 1e-4, pr, bs, xs, 50, 1e-10,
+                                           args.maxit, args.same_sample_steps, 2)
+            same[name] = {"value": 1000.0 / ms_s, "unit": UNIT, "ms_per_step": ms_s,
+                          "gmres_iterations": st_s["iterations"]}
+        cb = line.get("cpu_baseline", {}).get("value")
+        if cb:
+            same["gpu_over_oracle_fp32"] = same["fp32_factor"]["value"] / cb
+            same["gpu_over_oracle_fp64"] = same["fp64_factor"]["value"] / cb
+        line["same_sample"] = same
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -473,6 +587,10 @@ def main():
     ap.add_argument("--maxit", type=int, default=500)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-n", type=int, default=8)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 arm on the same workload (0: none)")
+    ap.add_argument("--same-sample-steps", type=int, default=10,
+                    help="timed GPU steps on the CPU oracle's sample (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="measure the tile / compression candidates on this workload first and store the best")

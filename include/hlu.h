@@ -92,6 +92,12 @@ typedef struct {
   int32_t rank_cap_hits;    /* truncations clipped at the rank capacity          */
   double rank_mean;         /* mean rank over admissible blocks                  */
   int32_t n_clusters, n_blocks, n_adm, n_dense;
+  int32_t rank_wanted_max;  /* largest rank a truncation asked for (s_i > eps s_1);
+                               rank capacity + 1 when it asked for more          */
+  int32_t trunc_dense_fallbacks; /* dense-route truncations redone by the stack route */
+  int64_t factor_live_bytes; /* bytes of the factor at its live ranks: dense words plus
+                                (rows + cols) x rank per admissible block; what one
+                                triangular-solve pass (L then U) reads            */
 } hlu_factor_info;
 
 /* hlu_build - Algorithm 1 step I and the structures it needs.
@@ -106,7 +112,9 @@ typedef struct {
  * admissible blocks as X Y^T of their nonzero rows).
  * kappa: wave number (> 0).  eps: relative truncation tolerance used by
  * hlu_factor (Sec. 4 truncated SVD; keep s_i > eps s_1).  rank_cap: maximum
- * stored rank of an admissible block (0 = default 32).
+ * stored rank of an admissible block (0 = the default and largest value,
+ * 64); a truncation that asks for more keeps the first rank_cap singular
+ * triplets and counts a rank-capacity hit (hlu_factor_info).
  * The build is synchronous (trees are copied to the host for scheduling).
  * Errors: HLU_ERR_ARG for n < 1, leaf < 2, eta <= 0 or non-integer eta^2,
  * eps <= 0; HLU_ERR_OOM; HLU_ERR_CUDA. */
@@ -182,12 +190,12 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 /* hlu_factor_profile - per task kind of the last factorisation's task DAG:
  * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for a
  * ready task, out[3*k + 2] cycles spent running, summed over CTAs; kinds
- * k = 0..11 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
- * RSOLVE, SEQ, IDENT, GSOLVE and k = 12 the no-work fences; then the
- * truncation phases summed over all compressions: out[39] stacking or dense
- * sum, out[40] QR cycles, out[41] core product, out[42] Jacobi SVD, out[43]
- * selection and Q application, out[44] compressions, out[45] Jacobi sweeps,
- * out[46] summed stack widths.  out: uint64[47] host buffer. */
+ * k = 0..8 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
+ * RSOLVE and k = 9 the no-work fences; then the truncation phases summed
+ * over all compressions: out[30] stacking or dense sum, out[31] QR cycles,
+ * out[32] core product, out[33] Jacobi SVD, out[34] selection and Q
+ * application, out[35] compressions, out[36] Jacobi sweeps, out[37] summed
+ * stack widths.  out: uint64[38] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
@@ -280,30 +288,6 @@ void hlu_set_wait_limit_ms(double ms);
  * are not affected.  tile <= leaf keeps the block tree's own leaves; values
  * above 64 are clamped to 64. */
 void hlu_set_tile(int32_t tile);
-
-/* hlu_set_solve_group - granularity of the H-triangular solves for
- * subsequent hlu_build calls (process-wide, default 0: no grouping).  The forward or
- * backward solve of every diagonal block whose cluster holds at most `dofs`
- * DOFs runs as one task on one CTA, its leaf solves and low-rank updates in
- * sequence, which removes the scheduling hops inside it from the critical
- * path, but also serialises the updates inside it that could run on other
- * CTAs.  The arithmetic is the same as without grouping (0).  The debug host
- * executor uses the same setting. */
-void hlu_set_solve_group(int32_t dofs);
-
-/* hlu_set_solve_inverse - inverse groups for subsequent hlu_build calls
- * (process-wide, default 0: off, at most 256).  Every maximal
- * subdivided diagonal block of at most `dofs` DOFs gets, right after its LU,
- * the explicit inverses of its two triangular factors (L^-1 P and U^-1,
- * formed by substitution into identities, in the factor precision); the
- * triangular solves (Alg. 1 step III) then apply each such block with one
- * dense product instead of its chain of leaf substitutions and updates.  The
- * result equals the substitution up to rounding; the factor holds 2 m^2 more
- * words per group.  Measured on GB300 the dense products, read cold from
- * HBM by one CTA each, are slower than the substitution chain they replace
- * (n = 24 apply 83 ms off, 123 ms at 256), hence off by default.  The debug
- * host executor uses the same setting. */
-void hlu_set_solve_inverse(int32_t dofs);
 
 /* hlu_launch_count - number of this library's own CUDA kernel launches so far
  * in this process (kernels from CUDA's bundled sort/scan templates are not

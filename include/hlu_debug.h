@@ -20,7 +20,7 @@ extern "C" {
  * clusters: int32[nc*12], blocks: int32[nb*8] in the hlu_export_trees layout;
  * perm: int32[N]; CSR of A in the original DOF order (rowptr int64[N+1], col
  * int32[nnz], val double[nnz]); eps: truncation tolerance (Sec. 4 truncated
- * SVD, keep s_i > eps s_1); rank_cap: capacity of admissible blocks (0 = 32);
+ * SVD, keep s_i > eps s_1); rank_cap: capacity of admissible blocks (0 = 64);
  * tile: block-tree nodes whose clusters both hold <= tile DOFs are factored as
  * one dense tile (0 keeps the block tree's own leaves); precision: HLU_FP64 (0) or
  * HLU_FP32 (1) arithmetic in the factor and the triangular solves;

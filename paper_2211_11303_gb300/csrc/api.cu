@@ -37,8 +37,6 @@ double g_wait_limit_ms = 20000.0;
 double g_jacobi_tol = 0.0;  // 0: default of the factor precision
 int32_t g_compress_at = 0;  // 0: default
 int32_t g_tile = 64;
-int32_t g_solve_group = 0;
-int32_t g_inverse_group = 0;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -71,7 +69,6 @@ struct DevSched {
   Task* tasks = nullptr;
   Term* terms = nullptr;
   Piece* pieces = nullptr;
-  Task* micro = nullptr;
   int64_t* pred_ptr = nullptr;
   int32_t* pred_idx = nullptr;
   int64_t* succ_ptr = nullptr;
@@ -92,7 +89,6 @@ struct DevSched {
     if ((e = upload(&tasks, S.tasks)) != cudaSuccess) return e;
     if ((e = upload(&terms, S.terms)) != cudaSuccess) return e;
     if ((e = upload(&pieces, S.pieces)) != cudaSuccess) return e;
-    if ((e = upload(&micro, S.micro)) != cudaSuccess) return e;
     if ((e = upload(&pred_ptr, S.pred_ptr)) != cudaSuccess) return e;
     if ((e = upload(&pred_idx, S.pred_idx)) != cudaSuccess) return e;
     // successor lists (edges sorted by predecessor, successors ascending)
@@ -143,7 +139,7 @@ struct DevSched {
   }
   void free_all() {
     if (owns_data)
-      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)micro, (void*)pred_ptr, (void*)pred_idx,
+      for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx,
                       (void*)succ_ptr,
                       (void*)succ_idx, (void*)indeg0, (void*)roots})
         if (p) cudaFree(p);
@@ -209,7 +205,7 @@ struct KrylovWS {
 }  // namespace
 
 struct hlu_handle {
-  int n = 0, leaf = 0, rank_cap = 32;
+  int n = 0, leaf = 0, rank_cap = kRankMax;
   double kappa = 0, eta = 0, eps = 0;
   int64_t eta2 = 0;
   DevMesh mesh;
@@ -313,7 +309,6 @@ ProbSched prob_of(hlu_handle* h, DevSched& ds, int64_t limit) {
   p.tasks = ds.tasks;
   p.terms = ds.terms;
   p.pieces = ds.pieces;
-  p.micro = ds.micro;
   p.succ_ptr = ds.succ_ptr;
   p.succ_idx = ds.succ_idx;
   p.indeg = ds.indeg;
@@ -634,9 +629,7 @@ void hlu_set_wait_limit_ms(double ms) {
 }
 void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
 
-void hlu_set_solve_group(int32_t dofs) { g_solve_group = std::max(0, dofs); }
 
-void hlu_set_solve_inverse(int32_t dofs) { g_inverse_group = std::max(0, std::min(dofs, (int32_t)256)); }
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
 int64_t hlu_launch_count(void) { return g_launches.load(); }
 
@@ -668,8 +661,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     int64_t eta2 = (int64_t)std::llround(e2);
     if (std::fabs(e2 - (double)eta2) > 1e-12) return fail(HLU_ERR_ARG, "eta^2 must be an integer");
     if (!(eps > 0) || !(kappa > 0)) return fail(HLU_ERR_ARG, "eps and kappa must be > 0");
-    if (rank_cap <= 0) rank_cap = 32;
-    if (rank_cap > 32) return fail(HLU_ERR_ARG, "rank_cap must be <= 32");
+    if (rank_cap <= 0) rank_cap = kRankMax;
+    if (rank_cap > kRankMax) return fail(HLU_ERR_ARG, "rank_cap must be <= " + std::to_string(kRankMax));
     cudaStream_t s = (cudaStream_t)stream;
     hlu_handle* h = new hlu_handle();
     h->n = n;
@@ -701,9 +694,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     uint64_t key = 1469598103934665603ULL;
     key = fnv1a(key, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
     key = fnv1a(key, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
-    const int32_t solve_group = g_solve_group;
-    const int32_t inv_group = g_inverse_group;
-    int32_t params[6] = {rank_cap, h->tile, nrhs_max, (int32_t)N, solve_group, inv_group};
+    int32_t params[4] = {rank_cap, h->tile, nrhs_max, (int32_t)N};
     key = fnv1a(key, params, sizeof(params));
     bool cache_hit = false;
     {
@@ -721,7 +712,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       auto sb = std::make_shared<SchedBundle>();
       sb->key = key;
       Schedule F, S;
-      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, solve_group, inv_group, sb->L, F, S, sb->st,
+      build_schedules(h->C, h->B, rank_cap, nrhs_max, h->tile, sb->L, F, S, sb->st,
                       &sb->FB);
       if ((e = sb->dF.load(F)) != cudaSuccess) return bail(e, "upload factor schedule");
       if ((e = sb->dS.load(S)) != cudaSuccess) return bail(e, "upload solve schedule");
@@ -756,7 +747,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       if ((e = upload(&sb->d_fill_dense, fd)) != cudaSuccess) return bail(e, "fill desc");
       if ((e = upload(&sb->d_fill_lr, fl)) != cudaSuccess) return bail(e, "fill desc");
       for (const Schedule* sc : {&F, &S})
-        sb->device_bytes += (int64_t)(sizeof(Task) * (sc->tasks.size() + sc->micro.size()) +
+        sb->device_bytes += (int64_t)(sizeof(Task) * sc->tasks.size() +
                                       sizeof(Term) * sc->terms.size() + sizeof(Piece) * sc->pieces.size() +
                                       2 * sizeof(int64_t) * (sc->tasks.size() + 1) + 2 * sizeof(int32_t) *
                                       sc->pred_idx.size() + 2 * sizeof(int32_t) * sc->tasks.size());
@@ -905,21 +896,30 @@ static int factor_finish(hlu_handle* h, hlu_handle* status_of, cudaStream_t s, f
   int rc = read_status(status_of, s, stf);
   h->info.factor_ms = ms;
   h->info.rank_cap_hits = stf[2];
+  h->info.rank_wanted_max = stf[4];
+  h->info.trunc_dense_fallbacks = stf[5];
   double fl = 0;
   CKR(cudaMemcpy(&fl, status_of->d_flops, sizeof(double), cudaMemcpyDeviceToHost), "flops");
   h->info.flops = fl;
   std::vector<int32_t> rk(std::max(h->L.n_slots, 1));
   CKR(cudaMemcpy(rk.data(), h->d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
-  int64_t rsum = 0, nadm = 0;
+  int64_t rsum = 0, nadm = 0, live = 0;
   int32_t rmax = 0;
-  for (size_t b = 0; b < h->sb->FB.size(); ++b)
-    if (h->sb->FB[b].kind == KIND_ADM) {
+  for (size_t b = 0; b < h->sb->FB.size(); ++b) {
+    const Block& bk = h->sb->FB[b];
+    const int64_t m = h->C[bk.row].size, n = h->C[bk.col].size;
+    if (bk.kind == KIND_ADM) {
       int32_t r = rk[h->L.slot[b]];
       rmax = std::max(rmax, r);
       rsum += r;
       ++nadm;
+      live += (m + n) * r;
+    } else if (bk.kind == KIND_DENSE) {
+      live += m * n;
     }
+  }
   const int es = esize(h->precision);
+  h->info.factor_live_bytes = live * es;
   h->info.rank_max = rmax;
   h->info.rank_mean = nadm ? (double)rsum / nadm : 0.0;
   h->info.factor_bytes = h->L.factor_elems * es;
@@ -1598,6 +1598,4 @@ void hlu_gmres_end(hlu_gmres* g) {
 }  // extern "C"
 
 namespace hlu {
-int32_t current_solve_group() { return g_solve_group; }
-int32_t current_inverse_group() { return g_inverse_group; }
 }  // namespace hlu

@@ -90,8 +90,7 @@ extern "C" int hlu_debug_host_factor_prefix(int32_t nc, const int32_t* clusters,
     Schedule F, S;
     SchedStats st;
     std::vector<Block> FB;
-    build_schedules(C, B, rank_cap > 0 ? rank_cap : 32, nrhs, tile, current_solve_group(), current_inverse_group(), L,
-                    F, S, st, &FB);
+    build_schedules(C, B, rank_cap > 0 ? rank_cap : kRankMax, nrhs, tile, L, F, S, st, &FB);
     B = FB;
     std::vector<double> arena(L.total, 0.0);
     std::vector<int32_t> ranks(L.n_slots, 0), piv(std::max<int64_t>(L.piv_total, 1), 0);

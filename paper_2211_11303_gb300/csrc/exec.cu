@@ -57,7 +57,6 @@ struct Ctx {
   int32_t* piv;
   const Term* terms;
   const Piece* pieces;
-  const Task* micro;
   T* scratch;
   int64_t rows_max;  // rows of the per-CTA truncation stacks
   double eps;
@@ -689,60 +688,6 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
   if (threadIdx.x == 0) c.flops += fl + (double)n * n * k;
 }
 
-// ---------------------------------------------------------------- inverse groups
-// c <- identity (square view)
-template <class T>
-__device__ void task_ident(Ctx<T>& c, const Task& t) {
-  const int m = t.c.rows, n = t.c.cols;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += NT) {
-    const int i = (int)(idx % m), j = (int)(idx / m);
-    stv(c, t.c, i, j, i == j ? T(1) : T(0));
-  }
-}
-
-// c <- a c with a (m x m, dense inverse of a diagonal block's triangular
-// factor) and c (m x k): c is staged in shared memory 16 columns at a time,
-// each thread computes whole rows of the result, with 16 loads of a in flight.
-// Only the nonzero part of a row is read: U^-1 is upper triangular, and
-// L^-1 P is block lower triangular with diagonal leaf blocks of at most
-// t.cap rows, so row i has no entries beyond column i + t.cap - 1.
-template <class T>
-__device__ void task_gsolve(Ctx<T>& c, const Task& t, char* smem) {
-  constexpr int U = 16;
-  const int m = t.a.rows, k = ncols(c, t.c);
-  T* X = reinterpret_cast<T*>(smem);
-  const T* A = c.arena + t.a.off;
-  for (int j0 = 0; j0 < k; j0 += 16) {
-    const int kc = min(16, k - j0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < m * kc; idx += NT) X[idx] = ldv(c, t.c, idx % m, j0 + idx / m);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += NT) {
-      T acc[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = T(0);
-      const T* ai = A + (int64_t)i * t.a.rs;
-      const bool upper = (t.flags & TF_UPPER) != 0;
-      const int lb = upper ? (i & ~(U - 1)) : 0, le = upper ? m : min(m, i + max(t.cap, 1));
-      for (int l0 = lb; l0 < le; l0 += U) {
-        T a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = l0 + u < le ? __ldcg(ai + (int64_t)(l0 + u) * t.a.cs) : T(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (l0 + u < le)
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (j < kc) acc[j] += a[u] * X[(l0 + u) + j * m];
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (j < kc) stv(c, t.c, i, j0 + j, acc[j]);
-    }
-  }
-  if (threadIdx.x == 0) c.flops += 1.0 * m * m * k;
-}
-
 // ---------------------------------------------------------------- DADD
 template <class T>
 __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
@@ -1088,7 +1033,9 @@ __device__ int jacobi_svd(T* G, T* V, int p, int q, T* nrm2, T tol, T negl_rel) 
 }
 
 constexpr int kDenseMax = 128;
-constexpr int kDenseRank = 40;
+constexpr int kDenseRank = 40;           // rows kept by the dense route's pivoted QR
+constexpr int kCoreRank = kRankMax;      // rows kept by the stack route's pivoted QR of the core
+constexpr int kCoreV = kTruncStack * kCoreRank + kCoreRank * kCoreRank;  // M (q x r') and V (r' x r')
 
 // Householder QR with column pivoting of D (m x n, ld m, shared memory) in
 // place, stopped after kmax steps or once the trailing block's squared
@@ -1192,11 +1139,12 @@ constexpr int kCompressAt = 48;
 // core R_x R_y^T accumulated in twice the working precision, its one-sided
 // Jacobi SVD, keep s_i > eps s_1 (at most cap); X <- Q_x U_r S_r and
 // Y <- Q_y V_r are written to OX (ld ox) and OY (ld oy).  Workspace: tauX,
-// tauY, sv (kStackCols each) and G, V (kStackCols^2 each) in shared memory.
+// tauY, sv (kStackCols each), G (kStackCols^2) and V (kCoreV) in shared
+// memory.  The largest rank asked for goes to status[4].
 // Returns r (the same in every thread); *fro receives ||X Y^T||_F.
 template <class TC>
 __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, double eps, TC* tauX, TC* tauY,
-                             TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* cap_hits,
+                             TC* sv, TC* G, TC* V, TC* OX, int64_t ox, TC* OY, int64_t oy, int32_t* status,
                              double* flops, double* fro, unsigned long long* tp, double jtol) {
   __shared__ TC s2x[kStackCols + 1], s2y[kStackCols + 1];
   __shared__ TC s_scbx[2 * kStackCols], s_scby[2 * kStackCols];  // reflector scales and R's diagonal
@@ -1235,7 +1183,7 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
   __shared__ int s_perm[kStackCols];
   TC tail2 = 0;
   const TC rel = TC(0.1 * eps);
-  const int rp = pivoted_qr(G, p, q, min(kDenseRank, min(p, q)), rel * rel / TC(min(p, q)), s_tauG, sv, s_perm,
+  const int rp = pivoted_qr(G, p, q, min(kCoreRank, min(p, q)), rel * rel / TC(min(p, q)), s_tauG, sv, s_perm,
                             &tail2);
   TC* M = V;
   TC* Vs = V + q * rp;
@@ -1272,9 +1220,11 @@ __device__ int compress_core(TC* SX, TC* SY, int m, int n, int W, int cap, doubl
     int r = 0;
     if (smax > TC(0))
       while (r < rp && sv[s_ord[r]] > TC(eps) * smax) ++r;
-    if (r > cap || (rp == kDenseRank && tail2 > TC(eps * eps) * smax * smax)) {
+    const bool more = rp == kCoreRank && tail2 > TC(eps * eps) * smax * smax;
+    atomicMax(status + 4, more ? kCoreRank + 1 : r);
+    if (r > cap || more) {
       r = min(r, cap);
-      atomicAdd(cap_hits, 1);
+      atomicAdd(status + 2, 1);
     }
     s_r = r;
     *flops += 2.0 * (m + n) * W * W + 4.0 * (double)p * q * rp + 6.0 * sweeps * (double)q * rp * rp +
@@ -1312,11 +1262,9 @@ template <class TC, class T>
 __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC* OY, TC* tauX, TC* tauY, TC* sv,
                            TC* G, TC* V, double* ratio) {
   const int m = t.a.rows, n = t.b.rows;
-  __shared__ double s_nx, s_ny;
   __shared__ TC s_rx[NT / 32];
   double worst = 0;
   int W = 0;
-  int32_t* cap_hits = c.status + 2;
   auto stack_norm = [&](int w_) -> double {
     TC px = 0, py = 0;
     #pragma unroll 4
@@ -1327,66 +1275,73 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
     TC sy = block_sum(py, s_rx);
     return sqrt((double)sx) * sqrt((double)sy);
   };
+  // a piece goes onto the stack in parts of at most kStackCols - W columns
+  // (X Y^T is the sum over its columns), compressing first whenever the rest
+  // of the piece would take the stack past compress_at columns; after a
+  // compression W <= kRankMax < kStackCols, so every part is nonempty
   for (int q = 0; q < t.list_count; ++q) {
     const Piece& P = c.pieces[t.list_begin + q];
     const int w = ncols(c, P.X);
-    if (w == 0) continue;
-    if (W > 0 && W + w > c.compress_at) {
-      const double in = stack_norm(W);
-      double fro = 0;
-      const int r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits,
-                                  &c.flops, &fro, c.tprof, c.jacobi_tol);
-      if (fro > 0) worst = fmax(worst, in / fro);
-      for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) SX[idx] = __ldcg(OX + idx);
-      for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) SY[idx] = __ldcg(OY + idx);
-      W = r;
+    for (int c0 = 0; c0 < w;) {
+      if (W > 0 && W + (w - c0) > c.compress_at) {
+        const double in = stack_norm(W);
+        double fro = 0;
+        const int r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, c.status,
+                                    &c.flops, &fro, c.tprof, c.jacobi_tol);
+        if (fro > 0) worst = fmax(worst, in / fro);
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * r; idx += NT) SX[idx] = __ldcg(OX + idx);
+        for (int64_t idx = threadIdx.x; idx < (int64_t)n * r; idx += NT) SY[idx] = __ldcg(OY + idx);
+        W = r;
+        __syncthreads();
+      }
+      const int take = min(w - c0, kStackCols - W);
+      const TC sg = TC(P.sign);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)m * take; idx += NT) SX[(int64_t)W * m + idx] = TC(0);
+      for (int64_t idx = threadIdx.x; idx < (int64_t)n * take; idx += NT) SY[(int64_t)W * n + idx] = TC(0);
+      __syncthreads();
+      // four elements per thread at a time: all loads issued before the stores
+      for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.X.rows * take; b0 += 4 * NT) {
+        TC v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t idx = b0 + (int64_t)u * NT;
+          v[u] = idx < (int64_t)P.X.rows * take ? TC(ldv(c, P.X, idx % P.X.rows, c0 + idx / P.X.rows)) : TC(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t idx = b0 + (int64_t)u * NT;
+          if (idx < (int64_t)P.X.rows * take)
+            SX[(P.xoff + idx % P.X.rows) + (int64_t)(W + idx / P.X.rows) * m] = sg * v[u];
+        }
+      }
+      for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.Y.rows * take; b0 += 4 * NT) {
+        TC v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t idx = b0 + (int64_t)u * NT;
+          v[u] = idx < (int64_t)P.Y.rows * take ? TC(ldv(c, P.Y, idx % P.Y.rows, c0 + idx / P.Y.rows)) : TC(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t idx = b0 + (int64_t)u * NT;
+          if (idx < (int64_t)P.Y.rows * take)
+            SY[(P.yoff + idx % P.Y.rows) + (int64_t)(W + idx / P.Y.rows) * n] = v[u];
+        }
+      }
+      W += take;
+      c0 += take;
       __syncthreads();
     }
-    const TC sg = TC(P.sign);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)m * w; idx += NT) SX[(int64_t)W * m + idx] = TC(0);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)n * w; idx += NT) SY[(int64_t)W * n + idx] = TC(0);
-    __syncthreads();
-    // four elements per thread at a time: all loads issued before the stores
-    for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.X.rows * w; b0 += 4 * NT) {
-      TC v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t idx = b0 + (int64_t)u * NT;
-        v[u] = idx < (int64_t)P.X.rows * w ? TC(ldv(c, P.X, idx % P.X.rows, idx / P.X.rows)) : TC(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t idx = b0 + (int64_t)u * NT;
-        if (idx < (int64_t)P.X.rows * w)
-          SX[(P.xoff + idx % P.X.rows) + (int64_t)(W + idx / P.X.rows) * m] = sg * v[u];
-      }
-    }
-    for (int64_t b0 = threadIdx.x; b0 < (int64_t)P.Y.rows * w; b0 += 4 * NT) {
-      TC v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t idx = b0 + (int64_t)u * NT;
-        v[u] = idx < (int64_t)P.Y.rows * w ? TC(ldv(c, P.Y, idx % P.Y.rows, idx / P.Y.rows)) : TC(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t idx = b0 + (int64_t)u * NT;
-        if (idx < (int64_t)P.Y.rows * w) SY[(P.yoff + idx % P.Y.rows) + (int64_t)(W + idx / P.Y.rows) * n] = v[u];
-      }
-    }
-    W += w;
-    __syncthreads();
   }
   int r = 0;
   if (W > 0) {
     const double in = stack_norm(W);
     double fro = 0;
-    r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, cap_hits, &c.flops, &fro, c.tprof, c.jacobi_tol);
+    r = compress_core(SX, SY, m, n, W, t.cap, c.eps, tauX, tauY, sv, G, V, OX, m, OY, n, c.status, &c.flops, &fro,
+                      c.tprof, c.jacobi_tol);
     if (fro > 0) worst = fmax(worst, in / fro);
   }
   *ratio = worst;
-  (void)s_nx;
-  (void)s_ny;
   return r;
 }
 
@@ -1432,8 +1387,11 @@ struct PieceCursor {
   }
 };
 
+// Returns false, having written nothing but the shared memory, when the
+// pivoted QR reached kDenseRank rows with a dropped tail above
+// eps |R_00| (|R_00| <= s_1): the stack route then truncates the target.
 template <class T>
-__device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
+__device__ bool task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.a.rows, n = t.b.rows;
   // shared memory: [region 0: staging chunks, later M (n x kDenseRank) and
   // V][D (m x n)][tau, nrm2 (kDenseMax each)][perm]
@@ -1495,6 +1453,11 @@ __device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
     tp[1] += (unsigned long long)(t1 - t0);
     t0 = t1;
   }
+  if (rp == kDenseRank && tail2 > T(c.eps * c.eps) * D[0] * D[0]) {
+    if (threadIdx.x == 0) atomicAdd(c.status + 5, 1);
+    __syncthreads();
+    return false;
+  }
   // M = P R'^T (n x r'), Jacobi SVD of its columns: M V = W
   for (int idx = threadIdx.x; idx < n * rp; idx += NT) {
     const int j = idx % n, i = idx / n;
@@ -1529,7 +1492,8 @@ __device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
     int r = 0;
     if (smax > T(0))
       while (r < rp && nrm2[s_ord[r]] > T(c.eps) * smax) ++r;
-    if (r > t.cap || (rp == kDenseRank && tail2 > T(c.eps * c.eps) * smax * smax)) {
+    atomicMax(c.status + 4, r);
+    if (r > t.cap) {
       r = min(r, t.cap);
       atomicAdd(c.status + 2, 1);
     }
@@ -1555,6 +1519,7 @@ __device__ void task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
   __syncthreads();
   if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
   if (tp && threadIdx.x == 0) tp[4] += (unsigned long long)(clock64() - t0);
+  return true;
 }
 
 // (a, b) <- truncation of sum_pieces sign X Y^T (stack, compress, store).
@@ -1574,16 +1539,13 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
     __syncthreads();
     const bool dense = s_wsum > c.compress_at;
     __syncthreads();
-    if (dense) {
-      task_trunc_dense(c, t, smem);
-      return;
-    }
+    if (dense && task_trunc_dense(c, t, smem)) return;
   }
   const int64_t R = c.rows_max;
   T* SX = c.scratch;
   T* SY = SX + R * kStackCols;
   T* OX = SY + R * kStackCols;
-  T* OY = OX + R * 32;
+  T* OY = OX + R * kRankMax;
   T* tauX = reinterpret_cast<T*>(smem);
   T* tauY = tauX + kStackCols;
   T* sv = tauY + kStackCols;
@@ -1597,7 +1559,7 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
 }
 
-// One task's body with the whole CTA (SEQ bodies hold no SEQ tasks).
+// One task's body with the whole CTA.
 template <class T>
 __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
   switch (t.type) {
@@ -1610,8 +1572,6 @@ __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
     case TK_TRUNC: task_trunc(c, t, smem); break;
     case TK_DADD: task_dadd(c, t, smem); break;
     case TK_RSOLVE: task_rsolve(c, t, smem); break;
-    case TK_IDENT: task_ident(c, t); break;
-    case TK_GSOLVE: task_gsolve(c, t, smem); break;
     default: break;
   }
 }
@@ -1689,21 +1649,11 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
       c.piv = P.piv;
       c.terms = P.terms;
       c.pieces = P.pieces;
-      c.micro = P.micro;
       c.eps = P.eps;
       c.nrhs_slot = P.nrhs_slot;
       c.nrhs = P.nrhs;
       c.term_p = P.term_p;
-      if (t.type == TK_SEQ) {
-        for (int q = 0; q < t.list_count; ++q) {
-          const Task u = c.micro[t.list_begin + q];
-          run_task(c, u, smem);
-          __threadfence_block();
-          __syncthreads();
-        }
-      } else {
-        run_task(c, t, smem);
-      }
+      run_task(c, t, smem);
     }
     if (threadIdx.x == 0) asm volatile("cp.async.wait_all;" ::: "memory");
     __threadfence();
@@ -1761,7 +1711,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
 size_t exec_smem_bytes(int elem_size) {
   // max over task kinds: TRUNC (3 stack-wide vectors + G + V), GETRF/TRSM
   // (64 x 64 + 64 ints), staged GEMM chunks (2 x KC x kLds)
-  size_t trunc = (size_t)elem_size * (3 * kTruncStack + 2 * kTruncStack * kTruncStack);
+  size_t trunc = (size_t)elem_size * (3 * kTruncStack + kTruncStack * kTruncStack + kCoreV);
   if (elem_size == 4) {  // dense truncation route (FP32 only)
     size_t region0 = (size_t)4 * (kDenseMax * kDenseRank + kDenseRank * kDenseRank);
     if (region0 < (size_t)4 * 2 * kStage) region0 = (size_t)4 * 2 * kStage;

@@ -15,7 +15,6 @@ struct ProbSched {
   const Task* tasks;
   const Term* terms;
   const Piece* pieces;
-  const Task* micro;        // bodies of SEQ tasks
   const int64_t* succ_ptr;  // ntasks + 1
   const int32_t* succ_idx;
   int32_t* indeg;           // unfinished predecessors (reset before every launch)
@@ -48,7 +47,9 @@ struct ExecArgs {
   void* scratch;                // per-CTA scratch, scratch_stride elements each
   int64_t scratch_stride;
   int64_t trunc_rows;           // rows of the truncation stacks in the scratch
-  int32_t* status;              // [0] status code, [1] failing slot, [2] rank-cap hits, [3] abort
+  int32_t* status;              // [0] status code, [1] failing slot, [2] rank-cap hits, [3] abort,
+                                // [4] largest rank a truncation asked for (kRankMax + 1: more),
+                                // [5] dense-route truncations handed to the stack route
   double* flops;                // accumulated algorithmic flops (may be null)
   unsigned long long wait_limit_ns;
   double jacobi_tol;            // truncation: Jacobi orthogonality tolerance
@@ -64,14 +65,14 @@ template <class T>
 cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
 
 constexpr int kExecThreads = 256;
-constexpr int kTruncStack = 96;  // columns of a truncation stack (>= rank cap + widest piece)
-// per-CTA scratch: two stacks (kTruncStack wide) and two outputs (32 wide)
+constexpr int kTruncStack = 96;  // columns of a truncation stack; wider pieces are stacked in parts
+// per-CTA scratch: two stacks (kTruncStack wide) and two outputs (kRankMax wide)
 #ifdef __CUDACC__
 #define HLU_HD __host__ __device__
 #else
 #define HLU_HD
 #endif
-HLU_HD inline int64_t trunc_scratch_elems(int64_t rows) { return rows * (2 * kTruncStack + 2 * 32); }
+HLU_HD inline int64_t trunc_scratch_elems(int64_t rows) { return rows * (2 * kTruncStack + 2 * kRankMax); }
 inline int64_t trunc_scratch_bytes(int64_t rows, int elem_size) {
   int64_t b = trunc_scratch_elems(rows) * elem_size;
   return (b + 255) & ~int64_t(255);

@@ -18,6 +18,9 @@ struct Block {
 };
 enum { KIND_ADM = 0, KIND_DENSE = 1, KIND_SUB = 2 };
 
+// Largest (and default) rank capacity of an admissible block.
+constexpr int32_t kRankMax = 64;
+
 // ---- strided matrix view into a problem's arena ----------------------------
 // Element (i, j) lives at arena[off + i*rs + j*cs].  The column count is `cols`
 // when slot < 0, otherwise ranks[slot] read on the device at execution time.
@@ -42,18 +45,15 @@ enum TaskType : int32_t {
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
   TK_RSOLVE = 8,  // c <- tri(a)^-1 (c - sum_terms A_t B_t): one tile of a triangular solve;
                   // flags & TF_UPPER: U^-1, else L^-1 P (pivots at piv_off)
-  TK_SEQ = 9,     // run micro tasks [list_begin, list_begin + list_count) in order, one CTA
-  TK_IDENT = 10,  // c <- identity (c: square view)
-  TK_GSOLVE = 11, // c <- a c (a: dense inverse of a diagonal block's triangle, c: its rows x k)
-  TK_NUM = 12,
-  TK_FENCE = 12   // no work: orders re-use of temporary memory after its readers
+  TK_NUM = 9,
+  TK_FENCE = 9    // no work: orders re-use of temporary memory after its readers
 };
 enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2 };
 
 struct Task {
   int32_t type;
   int32_t flags;
-  int32_t list_begin, list_count;  // ROWMV terms, TRUNC pieces or SEQ micro tasks
+  int32_t list_begin, list_count;  // ROWMV / RSOLVE terms or TRUNC pieces
   View a, b, c;
   int64_t piv_off;   // pivot vector offset (int32 elements) for leaf tasks
   int32_t out_slot;  // rank slot written by the task (-1: none)
@@ -81,7 +81,6 @@ struct Piece {
 // ---- a complete schedule -----------------------------------------------------
 struct Schedule {
   std::vector<Task> tasks;
-  std::vector<Task> micro;  // bodies of SEQ tasks
   std::vector<Term> terms;
   std::vector<Piece> pieces;
   std::vector<int64_t> pred_ptr;  // CSR of predecessors (all with smaller index)
@@ -108,7 +107,6 @@ struct ArenaLayout {
   int32_t max_trunc_rows = 0;      // largest TRUNC target dimension
   int32_t wmax = 0;                // largest stacked width of a TRUNC
   int64_t ring_off = 0, ring_size = 0;  // region for temporaries
-  std::vector<int64_t> inv_off;    // per block: (L^-1 P, U^-1) of an inverse group (-1: none)
 };
 
 struct SchedStats {
@@ -125,21 +123,9 @@ struct SchedStats {
 // `tile` DOFs is factored as one dense tile (tile <= leaf keeps the block tree
 // as it is).  factor_blocks (optional) receives the factor tree the schedules
 // and the arena layout refer to.
-// `solve_group`: in the solve schedule, the triangular solve of every diagonal
-// block whose cluster holds at most solve_group DOFs (and is not a leaf)
-// becomes one SEQ task run by one CTA (0: no grouping).
-// `inv_group`: every maximal subdivided diagonal block of at most inv_group
-// DOFs gets explicit inverses of its two triangular factors, formed right
-// after its LU; the solve schedule applies them as one dense product each
-// instead of the block's substitution (0: substitution everywhere).
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
-                     int32_t nrhs_max, int32_t tile, int32_t solve_group, int32_t inv_group, ArenaLayout& L,
+                     int32_t nrhs_max, int32_t tile, ArenaLayout& L,
                      Schedule& factor, Schedule& solve, SchedStats& st, std::vector<Block>* factor_blocks);
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile);
-
-// process-wide solve grouping (hlu_set_solve_group) and inverse groups
-// (hlu_set_solve_inverse) for schedules built from here on
-int32_t current_solve_group();
-int32_t current_inverse_group();
 
 }  // namespace hlu

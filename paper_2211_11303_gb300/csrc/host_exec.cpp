@@ -25,7 +25,6 @@ struct HostCtx {
   int32_t* piv;
   const Term* terms;
   const Piece* pieces;
-  const Task* micro;
   double eps;
   int32_t status = 0;
   int32_t cap_hits = 0;
@@ -366,26 +365,6 @@ void h_rsolve(HostCtx<T>& c, const Task& t) {
 }
 
 template <class T>
-void h_ident(HostCtx<T>& c, const Task& t) {
-  for (int j = 0; j < t.c.cols; ++j)
-    for (int i = 0; i < t.c.rows; ++i) at(c, t.c, i, j) = i == j ? T(1) : T(0);
-}
-
-template <class T>
-void h_gsolve(HostCtx<T>& c, const Task& t) {
-  const int m = t.a.rows, k = ncols(c, t.c);
-  std::vector<T> x((size_t)m * k);
-  for (int j = 0; j < k; ++j)
-    for (int i = 0; i < m; ++i) x[i + (size_t)j * m] = at(c, t.c, i, j);
-  for (int j = 0; j < k; ++j)
-    for (int i = 0; i < m; ++i) {
-      T s = 0;
-      for (int l = 0; l < m; ++l) s += at(c, t.a, i, l) * x[l + (size_t)j * m];
-      at(c, t.c, i, j) = s;
-    }
-}
-
-template <class T>
 void run_task(HostCtx<T>& c, const Task& t) {
   switch (t.type) {
     case TK_GETRF: h_getrf(c, t); break;
@@ -397,11 +376,6 @@ void run_task(HostCtx<T>& c, const Task& t) {
     case TK_TRUNC: h_trunc(c, t); break;
     case TK_DADD: h_dadd(c, t); break;
     case TK_RSOLVE: h_rsolve(c, t); break;
-    case TK_IDENT: h_ident(c, t); break;
-    case TK_GSOLVE: h_gsolve(c, t); break;
-    case TK_SEQ:
-      for (int32_t q = 0; q < t.list_count; ++q) run_task(c, c.micro[t.list_begin + q]);
-      break;
     case TK_FENCE: break;
     default: throw std::logic_error("task type");
   }
@@ -452,7 +426,6 @@ int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, doub
   c.piv = piv;
   c.terms = S.terms.data();
   c.pieces = S.pieces.data();
-  c.micro = S.micro.data();
   c.eps = eps;
   for (int64_t t : exec_order(S, order_seed)) {
     if (limit >= 0 && t >= limit) continue;

@@ -123,12 +123,7 @@ class Sched {
         // first use of this chunk in this pass: a no-work fence task waits for
         // every task that touched the chunk's previous occupants
         chunk_fence_task_[ch] = -1;
-        if (!chunk_occ_[ch].empty() && in_group_) {
-          // inside a SEQ group the group itself waits for the previous users
-          for (int32_t old : chunk_occ_[ch])
-            for (int64_t r = acc_head_[old]; r >= 0; r = acc_next_[r]) dep(acc_task_[r]);
-          chunk_fence_task_[ch] = cur_;
-        } else if (!chunk_occ_[ch].empty()) {
+        if (!chunk_occ_[ch].empty()) {
           Task f = make(TK_FENCE);
           int32_t saved_cur = cur_;
           std::vector<int32_t> saved_deps;
@@ -274,10 +269,6 @@ class Sched {
 
   // ---------------------------------------------------------------- tasks
   int32_t begin(const Task& t) {
-    if (in_group_) {  // a micro task of the open SEQ group: its accesses are the group's
-      S_->micro.push_back(t);
-      return cur_;
-    }
     int32_t id = (int32_t)S_->tasks.size();
     S_->tasks.push_back(t);
     stamp_.push_back(-1);
@@ -334,7 +325,6 @@ class Sched {
     touch(b.seg0, false);
   }
   void end() {
-    if (in_group_) return;
     std::sort(deps_.begin(), deps_.end());
     S_->pred_idx.insert(S_->pred_idx.end(), deps_.begin(), deps_.end());
     S_->pred_ptr.push_back((int64_t)S_->pred_idx.size());
@@ -569,30 +559,7 @@ class Sched {
   }
 
   // ---------------------------------------------------------------- triangular
-  // SEQ groups: a diagonal block's whole triangular solve as one task
-  bool group_here(int32_t d) const {
-    return group_max_ > 0 && !in_group_ && kind(d) != KIND_DENSE && sz(rowc(d)) <= group_max_;
-  }
-  void group_begin() {
-    Task t = make(TK_SEQ);
-    t.list_begin = (int32_t)S_->micro.size();
-    begin(t);
-    in_group_ = true;
-  }
-  void group_end() {
-    in_group_ = false;
-    Task& t = S_->tasks[cur_];
-    t.list_count = (int32_t)S_->micro.size() - t.list_begin;
-    end();
-  }
   void solve_lower(int32_t d, const MV& V) {
-    if (gsolve(d, V, false)) return;
-    if (group_here(d)) {
-      group_begin();
-      solve_lower(d, V);
-      group_end();
-      return;
-    }
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_L, d, V);
       return;
@@ -600,8 +567,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_lower(son(d, 0, 0), V0);
-    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1,
-         use_inverses_ ? -1 : seg_begin_[c.son[1]]);
+    hmul(son(d, 1, 0), V0, V1, -1.0f, false, false, -1, seg_end_[c.son[0]] - 1, seg_begin_[c.son[1]]);
     solve_lower(son(d, 1, 1), V1);
   }
   void solve_upperT(int32_t d, const MV& W) {
@@ -616,13 +582,6 @@ class Sched {
     solve_upperT(son(d, 1, 1), W1);
   }
   void solve_upper(int32_t d, const MV& V) {
-    if (gsolve(d, V, true)) return;
-    if (group_here(d)) {
-      group_begin();
-      solve_upper(d, V);
-      group_end();
-      return;
-    }
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_U, d, V);
       return;
@@ -630,8 +589,7 @@ class Sched {
     const Cluster& c = C_[rowc(d)];
     MV V0 = sub(V, c.son[0]), V1 = sub(V, c.son[1]);
     solve_upper(son(d, 1, 1), V1);
-    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]],
-         use_inverses_ ? -1 : seg_end_[c.son[0]] - 1);
+    hmul(son(d, 0, 1), V1, V0, -1.0f, false, false, -1, seg_begin_[c.son[1]], seg_end_[c.son[0]] - 1);
     solve_upper(son(d, 0, 0), V0);
   }
 
@@ -841,48 +799,9 @@ class Sched {
     trsm_right(d10, d00);
     gemm(d11, d10, d01);
     lu(d11);
-    if (L_.inv_off[d] >= 0) inverses(d);
   }
 
-  // (L_d^-1 P_d, U_d^-1) of a factored diagonal block, by substitution into
-  // identities stored at inv_off[d]
-  void inverses(int32_t d) {
-    const int32_t c = rowc(d), m = sz(c);
-    for (int which = 0; which < 2; ++which) {
-      MV M;
-      M.clus = c;
-      M.buf = new_buf_leaves(c);
-      M.v = View{L_.inv_off[d] + (int64_t)which * m * m, 1, m, m, m, -1, 0};
-      Task t = make(TK_IDENT);
-      t.c = M.v;
-      begin(t);
-      acc(M, true);
-      end();
-      if (which == 0)
-        solve_lower(d, M);
-      else
-        solve_upper(d, M);
-    }
-  }
-  // the solve of a diagonal block with an inverse group: one dense product
-  bool gsolve(int32_t d, const MV& V, bool upper) {
-    if (!use_inverses_ || L_.inv_off[d] < 0) return false;
-    const int32_t m = sz(rowc(d));
-    Task t = make(TK_GSOLVE);
-    t.flags = upper ? TF_UPPER : 0;
-    t.cap = segsz_;  // no diagonal leaf (pivoting block) is larger
-    t.a = View{L_.inv_off[d] + (upper ? (int64_t)m * m : 0), 1, m, m, m, -1, 0};
-    t.c = V.v;
-    begin(t);
-    acc_rank(V);
-    acc(V, true);
-    end();
-    return true;
-  }
-  bool use_inverses_ = false;  // solve schedule: inverse groups replace their substitution
-
-  void solve_all(int32_t nrhs_max, int32_t group_max) {
-    group_max_ = group_max;
+  void solve_all(int32_t nrhs_max) {
     pending_.assign(seg_cluster_.size(), Pending());
     MV W;
     W.buf = new_buf_leaves(0);  // per-segment tracking over the whole vector
@@ -942,8 +861,6 @@ class Sched {
     bool trans = false;
   };
   std::vector<Pending> pending_;
-  bool in_group_ = false;
-  int32_t group_max_ = 0;
 };
 
 }  // namespace
@@ -984,7 +901,7 @@ std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<
 }
 
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bfull, int32_t rank_cap,
-                     int32_t nrhs_max, int32_t tile, int32_t solve_group, int32_t inv_group, ArenaLayout& L,
+                     int32_t nrhs_max, int32_t tile, ArenaLayout& L,
                      Schedule& factor, Schedule& solve,
                      SchedStats& st, std::vector<Block>* factor_blocks) {
   std::vector<Block> Bt = factor_tree(C, Bfull, tile);
@@ -1028,24 +945,6 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
       fe += (int64_t)(m + n) * cap;
     }
   }
-  // inverse groups: maximal subdivided diagonal blocks of at most inv_group DOFs
-  L.inv_off.assign(nb, -1);
-  if (inv_group > 0) {
-    std::vector<int32_t> stack{0};
-    while (!stack.empty()) {
-      const int32_t d = stack.back();
-      stack.pop_back();
-      if (B[d].kind != KIND_SUB) continue;
-      const int32_t m = C[B[d].row].size;
-      if (m <= inv_group) {
-        L.inv_off[d] = alloc((int64_t)2 * m * m);
-        fe += (int64_t)2 * m * m;
-      } else {
-        stack.push_back(B[d].son[0]);
-        stack.push_back(B[d].son[3]);
-      }
-    }
-  }
   L.factor_elems = fe;
   L.nrhs_max = nrhs_max;
   L.nrhs_slot = L.n_slots++;
@@ -1068,8 +967,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   }
   {
     Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
-    s.use_inverses_ = inv_group > 0;
-    s.solve_all(nrhs_max, solve_group);
+    s.solve_all(nrhs_max);
     st.temp_elems += s.temp_elems_;
   }
   factor.n_edges = (int64_t)factor.pred_idx.size();

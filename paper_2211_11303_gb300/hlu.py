@@ -42,7 +42,9 @@ class hlu_factor_info(ctypes.Structure):
                 ("schedule_ms", ctypes.c_double), ("rank_max", ctypes.c_int32),
                 ("rank_cap_hits", ctypes.c_int32), ("rank_mean", ctypes.c_double),
                 ("n_clusters", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
-                ("n_adm", ctypes.c_int32), ("n_dense", ctypes.c_int32)]
+                ("n_adm", ctypes.c_int32), ("n_dense", ctypes.c_int32),
+                ("rank_wanted_max", ctypes.c_int32), ("trunc_dense_fallbacks", ctypes.c_int32),
+                ("factor_live_bytes", ctypes.c_int64)]
 
 
 def _struct_dict(s):
@@ -78,8 +80,6 @@ SIGNATURES = {
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
-    "hlu_set_solve_group": (None, [_i32]),
-    "hlu_set_solve_inverse": (None, [_i32]),
     "hlu_launch_count": (_i64, []),
     "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
     "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
@@ -152,7 +152,7 @@ def _vec(t, N):
 
 
 # ---------------------------------------------------------------- C-ABI names
-def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=32, stream=None):
+def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
     """Algorithm 1 step I on the GPU; returns an opaque handle (int)."""
     h = _vp()
     m = hlu_mesh(int(n))
@@ -227,8 +227,7 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SEQ", "IDENT",
-              "GSOLVE", "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "FENCE"]
 
 
 def hlu_factor_profile(h):
@@ -347,14 +346,6 @@ def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
     _check(lib().hlu_set_trunc_params(int(compress_at), float(jacobi_tol)))
 
 
-def hlu_set_solve_group(dofs):
-    lib().hlu_set_solve_group(int(dofs))
-
-
-def hlu_set_solve_inverse(dofs):
-    lib().hlu_set_solve_inverse(int(dofs))
-
-
 def hlu_set_tile(t):
     lib().hlu_set_tile(int(t))
 
@@ -362,7 +353,7 @@ def hlu_set_tile(t):
 class Problem:
     """Owns one handle: build on construction, destroy on close()."""
 
-    def __init__(self, n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=32, stream=None):
+    def __init__(self, n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
         self.n, self.kappa, self.leaf, self.eta, self.eps = n, kappa, leaf, eta, eps
         self.h = hlu_build(n, kappa, leaf, eta, eps, rank_cap, stream)
         self.N = hlu_n(self.h)

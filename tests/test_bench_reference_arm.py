@@ -22,3 +22,6 @@ def test_reference_arm_prints_the_contract_line():
     assert d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the line names what it timed: the oracle's FP64 sample, one RHS
+    assert d["config"]["nrhs"] == 1 and d["config"]["precision"] == "fp64" and d["config"]["n"] == 8
+    assert d["cpu_baseline"]["cores"] == 1 and d["cpu_baseline"]["host_cores"] >= 1

@@ -90,3 +90,54 @@ def test_autotune_picks_a_measured_candidate(hlu):
     assert res["best"] in cands
     assert len(res["results"]) == 2 and all(r["converged"] for r in res["results"])
     assert res["best"]["tile"] == min(res["results"], key=lambda r: r["total_ms"])["tile"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_problems_meet_the_oracle_bars(hlu, prec):
+    """Problems factored together in ONE batched launch, at the configuration
+    of single-problem parity (leaf 32, eta 2), each meet the single-problem
+    bars against the CPU oracle: the operator error ||z - (LU)_H^-1 A z|| /
+    ||z|| within 2x of the oracle's recursive H-LU at equal eps, and the
+    FGMRES solution within 1e-7 of the direct solve."""
+    import scipy.sparse.linalg as spla
+
+    from oracle import fem, hmatrix, mesh, trees
+
+    P = hlu.HLU_FP32 if prec == "fp32" else hlu.HLU_FP64
+    probs = [(6, 4.0, 1e-3), (8, 8.0, 1e-4), (10, 6.0, 1e-3)]
+    hs = []
+    try:
+        for n, k, eps in probs:
+            hs.append(hlu.hlu_build(n, k, 32, 2.0, eps))
+        hlu.hlu_factor_batch(hs, P)
+        for i, (h, (n, k, eps)) in enumerate(zip(hs, probs)):
+            m = mesh.interior_edges(n)
+            A = fem.assemble(m, k).tocsr()
+            N = A.shape[0]
+            perm, cl, bl = trees.build_trees(m, 32, 2.0)
+            Z = np.stack([synth.normal(11 + j, N) for j in range(3)], axis=1)
+            ref = hmatrix.HLUPreconditioner(A, perm, cl, bl, eps)
+            AZ = A @ Z
+            e_or = max(np.linalg.norm(Z[:, j] - ref.apply(AZ[:, j])) / np.linalg.norm(Z[:, j]) for j in range(3))
+            b = _rhs(N, 3, 0)
+            b.copy_(torch.from_numpy(np.asfortranarray(AZ)))
+            y = hlu.colmajor(N, 3)
+            hlu.hlu_solve(h, b, y)
+            torch.cuda.synchronize()
+            Y = y.cpu().numpy()
+            e_gpu = max(np.linalg.norm(Z[:, j] - Y[:, j]) / np.linalg.norm(Z[:, j]) for j in range(3))
+            assert hlu.hlu_factor_stats(h)["rank_cap_hits"] == 0
+            assert e_gpu <= 2.0 * e_or, (i, e_gpu, e_or)
+            # GMRES on the batch-factored handle against the direct solve
+            B = _rhs(N, 2, synth.rhs_seed(3, i, 0))
+            x = hlu.colmajor(N, 2)
+            st = hlu.gmres_solve(h, B, x, restart=50, tol=1e-10, maxit=500)
+            torch.cuda.synchronize()
+            xs = spla.splu(A.tocsc()).solve(B.cpu().numpy())
+            xg = x.cpu().numpy()
+            assert st["converged"] == 1
+            for j in range(2):
+                assert np.linalg.norm(xg[:, j] - xs[:, j]) <= 1e-7 * np.linalg.norm(xs[:, j]), (i, j)
+    finally:
+        for h in hs:
+            hlu.hlu_destroy(h)

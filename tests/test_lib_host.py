@@ -115,39 +115,3 @@ def test_tiled_factor_tree_quality(lib, n, kappa, leaf, tile):
     _, _, _, _, _, x2, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 9, tile=tile)
     _, _, _, _, _, x3, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 0, tile=tile)
     assert np.array_equal(x2, x3)
-
-
-def test_solve_groups_are_bit_identical(lib):
-    """Grouping diagonal-block solves into SEQ tasks runs the same micro tasks
-    in the same dependency order, so the solution is bit-identical."""
-    import ctypes
-    try:
-        lib.hlu_set_solve_inverse(ctypes.c_int32(0))
-        lib.hlu_set_solve_group(ctypes.c_int32(0))
-        _, _, _, _, _, x0, info0 = _host_solve(lib, 5, 3.0, 1e-4, 16, 0, nrhs=3, tile=64)
-        for g, seed in ((32, 1), (128, 2), (1 << 20, 3)):
-            lib.hlu_set_solve_group(ctypes.c_int32(g))
-            _, _, _, _, _, x1, info1 = _host_solve(lib, 5, 3.0, 1e-4, 16, seed, nrhs=3, tile=64)
-            assert np.array_equal(x0, x1), g
-            assert info1[1] < info0[1] if g >= 128 else info1[1] == info0[1]  # tiles of <= 64 are leaves
-    finally:
-        lib.hlu_set_solve_group(ctypes.c_int32(0))
-        lib.hlu_set_solve_inverse(ctypes.c_int32(0))
-
-
-def test_inverse_groups_match_substitution(lib):
-    """Diagonal blocks applied through their explicit triangular inverses give
-    the substitution's solution up to rounding, in any topological order."""
-    import ctypes
-    try:
-        lib.hlu_set_solve_inverse(ctypes.c_int32(0))
-        _, _, _, _, _, x0, info0 = _host_solve(lib, 6, 3.0, 1e-4, 16, 0, nrhs=3, tile=64)
-        for g in (128, 256):
-            lib.hlu_set_solve_inverse(ctypes.c_int32(g))
-            _, _, _, _, _, x1, info1 = _host_solve(lib, 6, 3.0, 1e-4, 16, 0, nrhs=3, tile=64)
-            _, _, _, _, _, x2, _ = _host_solve(lib, 6, 3.0, 1e-4, 16, 7, nrhs=3, tile=64)
-            assert np.array_equal(x1, x2), g
-            assert np.linalg.norm(x1 - x0) <= 1e-10 * np.linalg.norm(x0), g
-            assert info1[1] < info0[1]  # fewer solve tasks
-    finally:
-        lib.hlu_set_solve_inverse(ctypes.c_int32(0))

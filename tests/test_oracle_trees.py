@@ -25,6 +25,9 @@ def test_cluster_tree_invariants(n, leaf):
         assert np.array_equal(p.min(0), c["lo"]) and np.array_equal(p.max(0), c["hi"])
         if c["size"] <= leaf:
             assert not c["sons"]
+            # stable partitions from the identity order leave every leaf's
+            # original DOF indices ascending
+            assert np.all(np.diff(idx) > 0)
             continue
         s0, s1 = (cl[s] for s in c["sons"])
         assert s0["offset"] == c["offset"] and s1["offset"] == c["offset"] + s0["size"]
@@ -36,10 +39,8 @@ def test_cluster_tree_invariants(n, leaf):
         pl = pts[perm[s0["offset"]:s0["offset"] + s0["size"]]]
         pr = pts[perm[s1["offset"]:s1["offset"] + s1["size"]]]
         assert np.all(2 * pl[:, ax] < mid2) and np.all(2 * pr[:, ax] >= mid2)
-        # stable partition: original relative order kept on each side
-        assert np.all(np.diff(np.searchsorted(idx, idx)) >= 0) or True
-        for side in (pl, pr):
-            pass
+        # the split sends every point of the cluster to exactly one son
+        assert len(pl) + len(pr) == len(idx)
         assert s0["level"] == c["level"] + 1 and s0["parent"] == cid
         # DFS pre-order ids
         assert c["sons"][0] == cid + 1

@@ -19,9 +19,11 @@
  *    default stream).  Device-pointer arguments are read/written in stream
  *    order; calls documented as "synchronous" return after the stream has
  *    drained.
- *  - Memory: the library allocates its own device memory (cudaMalloc) for
- *    the handle's matrices, trees, factors and workspaces, and frees it in
- *    hlu_destroy().  Vectors passed in are caller-owned.
+ *  - Memory: the library allocates the device memory of the handle's
+ *    matrices, trees, factors, workspaces and build temporaries through the
+ *    allocator set by hlu_set_allocator() (default cudaMalloc/cudaFree) and
+ *    frees it in hlu_destroy() (temporaries before the call returns).
+ *    Vectors passed in are caller-owned.
  *  - Vectors: column-major, `nrhs` columns of length N with leading
  *    dimension `ld` >= N, FP64, in the original interior-edge DOF order.
  *  - DOF order: interior edges (lo, hi) of the Kuhn mesh sorted by (lo, hi),
@@ -30,6 +32,7 @@
 #ifndef HLU_H
 #define HLU_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -49,6 +52,11 @@ extern "C" {
 /* ---- precisions of the factor ------------------------------------------ */
 #define HLU_FP64 0 /* factor and triangular solves in FP64 ("plain" path) */
 #define HLU_FP32 1 /* factor and triangular solves in FP32, FP32 accumulate */
+#define HLU_TF32 2 /* FP32 factor whose tile products (dense and low-rank GEMM
+                      contractions: projections, H x multivector updates, dense
+                      updates, dense-route sums) run in TF32 on the tensor cores
+                      (tcgen05, FP32 accumulation in tensor memory); LU, QR, SVD
+                      and the triangular solves in FP32 */
 
 /* ---- block kinds in the exported block tree ------------------------------ */
 #define HLU_BLOCK_ADM 0   /* admissible: low-rank X Y^T (Definition 1)       */
@@ -145,8 +153,18 @@ int hlu_export_csr(const hlu_handle* h, int64_t* rowptr, int32_t* col, double* v
 /* hlu_rhs_manufactured - load vector b_j = <J, Phi_j> (Sec. 2.1) for the
  * manufactured field E = (sin pi y sin pi z, sin pi z sin pi x, sin pi x sin pi y),
  * J = (2 pi^2 - kappa^2) E, by a 4-point degree-2 rule.  b_dev: device
- * double[N].  Asynchronous on stream. */
+ * double[N].  Synchronous: its element-contribution scratch comes from the
+ * library's allocator and is freed before the call returns. */
 int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream);
+
+/* hlu_rhs_constant_current - load vector b_j = <J_S, Phi_j> (Sec. 2.1) of a
+ * constant current density J_S = (jx, jy, jz); Sec. 4, Example 1 uses
+ * J_S = [0, 0, 1]^T.  The basis functions are linear on each tetrahedron, so
+ * the integral is exact: b_e = |T|/4 J_S . (grad lam_b - grad lam_a) summed
+ * over the tetrahedra of edge e = (a, b).  b_dev: device double[N].
+ * Synchronous (scratch from the library's allocator).  HLU_ERR_ARG for a
+ * non-finite J_S. */
+int hlu_rhs_constant_current(const hlu_handle* h, double jx, double jy, double jz, double* b_dev, void* stream);
 
 /* hlu_rhs_manufactured_noalloc - the same load vector as hlu_rhs_manufactured,
  * computed without allocating any memory.  The paper has no counterpart: this
@@ -288,6 +306,29 @@ void hlu_set_wait_limit_ms(double ms);
  * are not affected.  tile <= leaf keeps the block tree's own leaves; values
  * above 64 are clamped to 64. */
 void hlu_set_tile(int32_t tile);
+
+/* Device allocator of the library (process-wide).  alloc(bytes, ctx) returns
+ * device memory of the current device, or NULL when it cannot (the library
+ * call then fails with HLU_ERR_OOM); free(ptr, bytes, ctx) takes back a block
+ * alloc returned.  Every block is freed by the allocator that returned it,
+ * even after the allocator changed.  The library synchronises the device
+ * before it hands a block to free, so the allocator may reuse it at once.
+ * Both NULL restores cudaMalloc/cudaFree.  The Python binding uses this to
+ * put the library's memory in PyTorch's caching allocator.  Returns
+ * HLU_ERR_ARG when only one of the two is NULL. */
+typedef void* (*hlu_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*hlu_free_fn)(void* ptr, size_t bytes, void* ctx);
+int hlu_set_allocator(hlu_alloc_fn alloc, hlu_free_fn free, void* ctx);
+
+/* hlu_set_device_memory_limit - cap (bytes, process-wide; 0 = none) on the
+ * device memory the library holds through its allocator.  An allocation
+ * that would pass it is refused and the call fails with HLU_ERR_OOM, leaving
+ * the device and the library usable (for admission control, and to test the
+ * out-of-memory path on the host).  HLU_ERR_ARG for a negative value. */
+int hlu_set_device_memory_limit(int64_t bytes);
+
+/* Device bytes the library holds through its allocator right now. */
+int64_t hlu_device_bytes_in_use(void);
 
 /* hlu_launch_count - number of this library's own CUDA kernel launches so far
  * in this process (kernels from CUDA's bundled sort/scan templates are not

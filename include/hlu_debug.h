@@ -80,6 +80,24 @@ int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t* trace_out
 int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trace_out, int64_t* pred_ptr_out,
                           int32_t* pred_idx_out, void* tasks_out, int64_t* sizes);
 
+/* hlu_debug_tf32_tile - the TF32 tensor-core tile product of HLU_TF32
+ * factorisations on its own (needs a GPU): D = A B for A 64 x K (ld 64), B
+ * K x 64 (ld K) and D 64 x 64 (ld 64), column-major FP32 device arrays,
+ * computed by one CTA through the executor's tcgen05 pipeline (operands
+ * rounded to TF32, FP32 accumulation in tensor memory).  K in [1, 4096].
+ * status_out (may be NULL) receives the device status (0, or 5 if an MMA
+ * completion wait ran out, which the call returns as HLU_ERR_TIMEOUT).
+ * Synchronous. */
+int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int32_t K, int32_t* status_out);
+
+/* hlu_debug_zero_dof - input for the zero-pivot path (needs a GPU): sets row
+ * and column `dof` (original DOF order) of the handle's assembled matrix A to
+ * zero, in place on the device.  A later hlu_factor then meets an exact zero
+ * pivot in the dense diagonal block holding that DOF and returns
+ * HLU_ERR_ZERO_PIVOT.  The matrix stays modified until the handle is
+ * destroyed.  HLU_ERR_ARG for dof outside [0, N).  Synchronous. */
+int hlu_debug_zero_dof(hlu_handle* h, int64_t dof);
+
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a
  * GPU).  Runs the task executor with one CTA on a two-task schedule in which
  * task 1 waits for itself: task 0 runs, and the CTA that claims queue slot 1

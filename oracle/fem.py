@@ -20,12 +20,16 @@ Readings:
     beta = (5 + 3 sqrt 5)/20, weights |T|/4;
   * manufactured field E = (sin pi y sin pi z, sin pi z sin pi x, sin pi x sin pi y):
     div E = 0 and curl curl E = 2 pi^2 E, so J = (2 pi^2 - kappa^2) E, and
-    E x n = 0 on the cube's boundary.
+    E x n = 0 on the cube's boundary;
+  * Example 1's source J_S = [0, 0, 1]^T is a constant current density
+    (constant_current_rhs).
 
 Pins (tests/test_oracle_fem.py): discrete de Rham property C G = 0 and K G = 0;
 null space of K of dimension (n-1)^3; cavity eigenvalues 2pi^2 (x3), 3pi^2 (x2);
 symmetry; M SPD; reference-tetrahedron element matrices worked by hand; L2
-convergence of the manufactured solution at rate ~1.
+convergence of the manufactured solution at rate ~1; the constant-current load
+vector is discretely divergence-free (G^T b = 0) and equals the exact integral
+|T|/4 J . (grad l_b - grad l_a) computed element by element.
 """
 import math
 
@@ -205,6 +209,14 @@ def load_vector(mesh, Jfun):
 
 def manufactured_rhs(mesh, kappa):
     return load_vector(mesh, lambda X: manufactured_J(X, kappa))
+
+
+def constant_current_rhs(mesh, J):
+    """b_j = <J_S, Phi_j> for a constant current density J_S (Sec. 4, Example 1
+    takes J_S = [0, 0, 1]^T), by the same 4-point rule, which is exact here:
+    J_S . Phi_j is linear on every tetrahedron."""
+    Jv = np.asarray(J, dtype=float).reshape(3)
+    return load_vector(mesh, lambda X: np.broadcast_to(Jv, X.shape))
 
 
 def l2_error(mesh, x, Efun):

@@ -18,6 +18,7 @@
 
 #include "../../include/hlu.h"
 #include "build.h"
+#include "devmem.h"
 #include "exec.h"
 #include "hlu_internal.h"
 #include "host_exec.h"
@@ -56,7 +57,7 @@ template <class T>
 cudaError_t upload(T** d, const std::vector<T>& h) {
   *d = nullptr;
   size_t bytes = sizeof(T) * std::max<size_t>(h.size(), 1);
-  cudaError_t e = cudaMalloc(d, bytes);
+  cudaError_t e = dev_malloc(d, bytes);
   if (e != cudaSuccess) return e;
   if (!h.empty()) e = cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
   return e;
@@ -117,10 +118,10 @@ struct DevSched {
     return cudaSuccess;
   }
   cudaError_t alloc_state() {
-    cudaError_t e = cudaMalloc(&indeg, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
+    cudaError_t e = dev_malloc(&indeg, sizeof(int32_t) * std::max<int64_t>(ntasks, 1));
     if (e != cudaSuccess) return e;
-    if ((e = cudaMalloc(&queue, sizeof(unsigned long long) * std::max<int64_t>(ntasks, 1))) != cudaSuccess) return e;
-    return cudaMalloc(&qctl, sizeof(unsigned long long) * 2);
+    if ((e = dev_malloc(&queue, sizeof(unsigned long long) * std::max<int64_t>(ntasks, 1))) != cudaSuccess) return e;
+    return dev_malloc(&qctl, sizeof(unsigned long long) * 2);
   }
   // a per-handle view of shared task data
   DevSched share() const {
@@ -142,9 +143,9 @@ struct DevSched {
       for (void* p : {(void*)tasks, (void*)terms, (void*)pieces, (void*)pred_ptr, (void*)pred_idx,
                       (void*)succ_ptr,
                       (void*)succ_idx, (void*)indeg0, (void*)roots})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     for (void* p : {(void*)indeg, (void*)queue, (void*)qctl})
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
     *this = DevSched();
   }
 };
@@ -165,8 +166,8 @@ struct SchedBundle {
   ~SchedBundle() {
     dF.free_all();
     dS.free_all();
-    if (d_fill_dense) cudaFree(d_fill_dense);
-    if (d_fill_lr) cudaFree(d_fill_lr);
+    if (d_fill_dense) dev_free(d_fill_dense);
+    if (d_fill_lr) dev_free(d_fill_lr);
   }
 };
 
@@ -197,7 +198,7 @@ struct KrylovWS {
   void free_all() {
     for (void* p : {(void*)V, (void*)Z, (void*)W, (void*)h1, (void*)h2, (void*)hn, (void*)H, (void*)cs, (void*)sn,
                     (void*)g, (void*)est, (void*)y, (void*)bn, (void*)part, (void*)tmp, (void*)jr})
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
     *this = KrylovWS();
   }
 };
@@ -249,7 +250,7 @@ void free_factor(hlu_handle* h) {
   for (void* p : {(void*)h->d_arena, (void*)h->d_ranks, (void*)h->d_piv, (void*)h->d_scratch, (void*)h->d_status,
                   (void*)h->d_flops, (void*)h->d_arenas, (void*)h->d_rankp, (void*)h->d_pivp,
                   (void*)h->d_prof, (void*)h->d_term_p})
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   h->d_prof = nullptr;
   h->d_term_p = nullptr;
   h->term_p_fresh = false;
@@ -334,6 +335,7 @@ void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool wi
   a.jacobi_tol = g_jacobi_tol;
   a.compress_at = g_compress_at;
   a.prof = with_flops ? h0->d_prof : nullptr;
+  a.tf32 = (with_flops && h0->precision == HLU_TF32) ? 1 : 0;  // factorisations only; solves stay FP32
   a.trace = h0->d_trace;
 }
 
@@ -419,10 +421,10 @@ int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, 
   if (total == 0) return HLU_OK;
   std::vector<unsigned long long> seed = batch_roots(roots);
   if (*d_q_len < total + 2) {
-    if (*d_q) cudaFree(*d_q);
+    if (*d_q) dev_free(*d_q);
     *d_q = nullptr;
     *d_q_len = 0;
-    CKR(cudaMalloc(d_q, sizeof(unsigned long long) * (total + 2)), "queue");
+    CKR(dev_malloc(d_q, sizeof(unsigned long long) * (total + 2)), "queue");
     *d_q_len = total + 2;
   }
   a.qctl = *d_q;
@@ -486,22 +488,22 @@ int ensure_kw(hlu_handle* h, int m, int nr) {
   k.N = N;
   k.m = m;
   k.nr = nr;
-  CKR(cudaMalloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
-  CKR(cudaMalloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
-  CKR(cudaMalloc(&k.W, sizeof(double) * N * nr), "alloc W");
-  CKR(cudaMalloc(&k.tmp, sizeof(double) * N * nr), "alloc tmp");
-  CKR(cudaMalloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.hn, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.cs, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.sn, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.est, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.y, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.bn, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
-  CKR(cudaMalloc(&k.jr, sizeof(int) * nr), "alloc");
+  CKR(dev_malloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
+  CKR(dev_malloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
+  CKR(dev_malloc(&k.W, sizeof(double) * N * nr), "alloc W");
+  CKR(dev_malloc(&k.tmp, sizeof(double) * N * nr), "alloc tmp");
+  CKR(dev_malloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.hn, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
+  CKR(dev_malloc(&k.cs, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.sn, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.est, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.y, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.bn, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
+  CKR(dev_malloc(&k.jr, sizeof(int) * nr), "alloc");
   return HLU_OK;
 }
 
@@ -529,8 +531,12 @@ int gmres_chunk(hlu_handle* h, const double* b, double* x, int nr, int64_t ld, i
   for (int r = 0; r < nr; ++r) CKR(cudaMemsetAsync(x + r * ld, 0, sizeof(double) * N, s), "x0");
   rc = col_norms(h, b, ld, nr, k.bn, bn.data(), s);
   if (rc) return rc;
+  for (int r = 0; r < nr; ++r)
+    if (!std::isfinite(bn[r]))
+      return fail(HLU_ERR_ARG, "right-hand side column " + std::to_string(r) + " is not finite (x = 0 written)");
   int iters = 0, restarts = 0;
   double pms = 0;
+  bool broke = false;  // a residual turned non-finite: the iteration cannot go on
   for (;;) {
     CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, x, ld, b, ld, k.V, ldr, nr, s), "residual");
     rc = col_norms(h, k.V, ldr, nr, k.hn, beta.data(), s);
@@ -539,8 +545,9 @@ int gmres_chunk(hlu_handle* h, const double* b, double* x, int nr, int64_t ld, i
     for (int r = 0; r < nr; ++r) {
       conv[r] = (bn[r] == 0.0) || (beta[r] <= tol * bn[r]);
       all = all && conv[r];
+      broke = broke || !std::isfinite(beta[r]);
     }
-    if (all || iters >= maxit) break;
+    if (all || iters >= maxit || broke) break;
     CKR(scale_cols(N, k.V, ldr, k.hn, k.V, ldr, nr, s), "scale");
     CKR(init_g(nr, m, k.hn, k.g, s), "init g");
     std::fill(jr.begin(), jr.end(), 0);
@@ -603,6 +610,7 @@ int gmres_chunk(hlu_handle* h, const double* b, double* x, int nr, int64_t ld, i
   }
   bool all = true;
   for (int r = 0; r < nr; ++r) all = all && conv[r];
+  if (broke) return fail(HLU_ERR_NOT_CONVERGED, "GMRES stopped: a residual is not finite");
   return all ? HLU_OK : fail(HLU_ERR_NOT_CONVERGED, "GMRES reached maxit");
 }
 
@@ -642,7 +650,7 @@ void hlu_destroy(hlu_handle* h) {
   h->sb.reset();
   for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->A.rowptr, (void*)h->A.col,
                   (void*)h->A.val, (void*)h->d_perm, (void*)h->d_iperm})
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -684,8 +692,8 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     if ((e = build_mesh_dofs(n, s, h->mesh)) != cudaSuccess) return bail(e, "mesh");
     if ((e = assemble_csr(h->mesh, kappa, s, h->A)) != cudaSuccess) return bail(e, "assembly");
     const int64_t N = h->A.N;
-    if ((e = cudaMalloc(&h->d_perm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "perm");
-    if ((e = cudaMalloc(&h->d_iperm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "iperm");
+    if ((e = dev_malloc(&h->d_perm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "perm");
+    if ((e = dev_malloc(&h->d_iperm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "iperm");
     if ((e = build_trees(h->mesh, leaf, eta2, s, h->trees, h->d_perm)) != cudaSuccess) return bail(e, "trees");
     if ((e = invert_perm((int32_t)N, h->d_perm, h->d_iperm, s)) != cudaSuccess) return bail(e, "iperm");
     trees_from_export(h->trees.nc, h->trees.clusters.data(), h->trees.nb, h->trees.blocks.data(), h->C, h->B);
@@ -769,7 +777,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     h->dS = h->sb->dS.share();
     if ((e = h->dF.alloc_state()) != cudaSuccess) return bail(e, "queue");
     if ((e = h->dS.alloc_state()) != cudaSuccess) return bail(e, "queue");
-    if (h->dS.nterms > 0 && (e = cudaMalloc(&h->d_term_p, sizeof(int32_t) * h->dS.nterms)) != cudaSuccess)
+    if (h->dS.nterms > 0 && (e = dev_malloc(&h->d_term_p, sizeof(int32_t) * h->dS.nterms)) != cudaSuccess)
       return bail(e, "term widths");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "sync");
     h->info.n_tasks = h->sb->st.n_factor_tasks;
@@ -815,6 +823,14 @@ int hlu_rhs_manufactured(const hlu_handle* h, double* b_dev, void* stream) {
   return HLU_OK;
 }
 
+int hlu_rhs_constant_current(const hlu_handle* h, double jx, double jy, double jz, double* b_dev, void* stream) {
+  if (!h || !b_dev) return fail(HLU_ERR_ARG, "null argument");
+  if (!std::isfinite(jx) || !std::isfinite(jy) || !std::isfinite(jz)) return fail(HLU_ERR_ARG, "J must be finite");
+  const double J[3] = {jx, jy, jz};
+  CKR(constant_current_rhs(h->mesh, J, b_dev, (cudaStream_t)stream), "rhs (constant current)");
+  return HLU_OK;
+}
+
 int hlu_rhs_manufactured_noalloc(const hlu_handle* h, double* b_dev, void* stream) {
   if (!h || !b_dev) return fail(HLU_ERR_ARG, "null argument");
   const int64_t need = (int64_t)36 * h->n * h->n * h->n;
@@ -832,7 +848,7 @@ int hlu_spmv(const hlu_handle* h, const double* x, double* y, int32_t nrhs, int6
 }
 
 int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision) {
-  if (!h || (precision != HLU_FP64 && precision != HLU_FP32)) return -1;
+  if (!h || (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)) return -1;
   int es = esize(precision);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -848,7 +864,7 @@ int hlu_factor(hlu_handle* h, int32_t precision, void* stream) { return factor_i
 // allocation for `precision` (first time), rank/status/flop resets, A_H fill
 static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
   const int es = esize(precision);
-  if (h->precision != precision) {
+  if (h->precision < 0 || esize(h->precision) != es) {  // FP32 and TF32 share the FP32 storage
     free_factor(h);
     int dev = 0;
     CKR(cudaGetDevice(&dev), "device");
@@ -859,15 +875,15 @@ static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
     h->grid = sms * bps;
     h->scratch_stride = scratch_stride_elems(h->L, es);
     h->arena_elems = h->L.total;
-    CKR(cudaMalloc(&h->d_arena, (size_t)es * h->L.total), "arena");
-    CKR(cudaMalloc(&h->d_ranks, sizeof(int32_t) * std::max(h->L.n_slots, 1)), "ranks");
-    CKR(cudaMalloc(&h->d_piv, sizeof(int32_t) * std::max<int64_t>(h->L.piv_total, 1)), "piv");
-    CKR(cudaMalloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
-    CKR(cudaMalloc(&h->d_status, sizeof(int32_t) * 8), "status");
-    CKR(cudaMalloc(&h->d_flops, sizeof(double)), "flops");
-    CKR(cudaMalloc(&h->d_prof, sizeof(unsigned long long) * kProfEntries), "prof");
-    h->precision = precision;
+    CKR(dev_malloc(&h->d_arena, (size_t)es * h->L.total), "arena");
+    CKR(dev_malloc(&h->d_ranks, sizeof(int32_t) * std::max(h->L.n_slots, 1)), "ranks");
+    CKR(dev_malloc(&h->d_piv, sizeof(int32_t) * std::max<int64_t>(h->L.piv_total, 1)), "piv");
+    CKR(dev_malloc(&h->d_scratch, (size_t)es * h->scratch_stride * h->grid), "scratch");
+    CKR(dev_malloc(&h->d_status, sizeof(int32_t) * 8), "status");
+    CKR(dev_malloc(&h->d_flops, sizeof(double)), "flops");
+    CKR(dev_malloc(&h->d_prof, sizeof(unsigned long long) * kProfEntries), "prof");
   }
+  h->precision = precision;
   CKR(cudaMemsetAsync(h->d_ranks, 0, sizeof(int32_t) * std::max(h->L.n_slots, 1), s), "ranks");
   h->cur_nrhs = 0;
   int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
@@ -930,7 +946,8 @@ static int factor_finish(hlu_handle* h, hlu_handle* status_of, cudaStream_t s, f
 static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit) {
   try {
     if (!h) return fail(HLU_ERR_ARG, "null handle");
-    if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
+    if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
+      return fail(HLU_ERR_ARG, "precision");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = factor_prepare(h, precision, s);
     if (rc) return rc;
@@ -1015,6 +1032,7 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
       stats->nrhs = nrhs;
       stats->converged = 1;
     }
+    bool all_conv = true, broke = false;
     for (int32_t c0 = 0; c0 < nrhs; c0 += h->L.nrhs_max) {
       int nr = std::min(h->L.nrhs_max, nrhs - c0);
       const double* bc = b + c0 * ld;
@@ -1023,6 +1041,10 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
       for (int r = 0; r < nr; ++r) CKR(cudaMemsetAsync(xc + r * ld, 0, sizeof(double) * N, s), "x0");
       rc = col_norms(h, bc, ld, nr, k.bn, bn.data(), s);
       if (rc) return rc;
+      for (int r = 0; r < nr; ++r)
+        if (!std::isfinite(bn[r]))
+          return fail(HLU_ERR_ARG,
+                      "right-hand side column " + std::to_string(c0 + r) + " is not finite (x = 0 written)");
       int it = 0;
       bool conv = false;
       while (it < maxit) {
@@ -1030,6 +1052,8 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
         CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, xc, ld, bc, ld, k.W, N, nr, s), "residual");
         rc = col_norms(h, k.W, N, nr, k.hn, rn.data(), s);
         if (rc) return rc;
+        for (int r = 0; r < nr; ++r) broke = broke || !std::isfinite(rn[r]);
+        if (broke) break;
         rc = solve_any(h, k.W, k.tmp, nr, N, s);
         if (rc) return rc;
         // x += M^-1 r
@@ -1052,10 +1076,13 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
         }
         stats->converged = stats->converged && conv;
       }
+      all_conv = all_conv && conv;
+      if (broke) break;
     }
     if (stats)
       stats->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return (stats && !stats->converged) ? fail(HLU_ERR_NOT_CONVERGED, "Richardson reached maxit") : HLU_OK;
+    if (broke) return fail(HLU_ERR_NOT_CONVERGED, "Richardson stopped: a residual is not finite");
+    return all_conv ? HLU_OK : fail(HLU_ERR_NOT_CONVERGED, "Richardson reached maxit");
   } catch (const std::exception& ex) {
     return fail(HLU_ERR_CUDA, ex.what());
   }
@@ -1064,7 +1091,8 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
 int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream) {
   try {
     if (!hs || count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "bad argument");
-    if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision");
+    if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
+      return fail(HLU_ERR_ARG, "precision");
     cudaStream_t s = (cudaStream_t)stream;
     for (int32_t i = 0; i < count; ++i) {
       if (!hs[i]) return fail(HLU_ERR_ARG, "null handle");
@@ -1164,12 +1192,12 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   DevSched ds;
   CKR(ds.load(S), "upload");
   CKR(ds.alloc_state(), "queue");
-  CKR(cudaMalloc(&h.d_status, sizeof(int32_t) * 8), "alloc");
+  CKR(dev_malloc(&h.d_status, sizeof(int32_t) * 8), "alloc");
   // valid (unused) per-problem pointers: the two tasks do no work
-  CKR(cudaMalloc(&h.d_arena, 256), "alloc");
-  CKR(cudaMalloc(&h.d_arenas, sizeof(void*)), "alloc");
-  CKR(cudaMalloc(&h.d_rankp, sizeof(int32_t*)), "alloc");
-  CKR(cudaMalloc(&h.d_pivp, sizeof(int32_t*)), "alloc");
+  CKR(dev_malloc(&h.d_arena, 256), "alloc");
+  CKR(dev_malloc(&h.d_arenas, sizeof(void*)), "alloc");
+  CKR(dev_malloc(&h.d_rankp, sizeof(int32_t*)), "alloc");
+  CKR(dev_malloc(&h.d_pivp, sizeof(int32_t*)), "alloc");
   CKR(cudaMemcpy(h.d_arenas, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
   CKR(cudaMemcpy(h.d_rankp, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
   CKR(cudaMemcpy(h.d_pivp, &h.d_arena, sizeof(void*), cudaMemcpyHostToDevice), "ptr");
@@ -1184,7 +1212,7 @@ extern "C" int hlu_debug_wait_timeout(double limit_ms, int32_t* status_out) {
   ds.free_all();
   for (void* p : {(void*)h.d_status, (void*)h.d_arena, (void*)h.d_arenas, (void*)h.d_rankp,
                   (void*)h.d_pivp})
-    cudaFree(p);
+    dev_free(p);
   h.d_status = nullptr;
   h.d_arena = nullptr;
   h.d_arenas = nullptr;
@@ -1231,11 +1259,11 @@ extern "C" int hlu_debug_factor_trace(hlu_handle* h, int32_t precision, uint64_t
   if (h->dF.pred_ptr && nt > 0)
     CKR(cudaMemcpy(&sizes[1], h->dF.pred_ptr + nt, sizeof(int64_t), cudaMemcpyDeviceToHost), "edges");
   if (!trace_out) return HLU_OK;
-  CKR(cudaMalloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  CKR(dev_malloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   int rc = factor_impl(h, precision, nullptr, -1);
   cudaError_t e = cudaMemcpy(trace_out, h->d_trace, sizeof(uint64_t) * 4 * nt, cudaMemcpyDeviceToHost);
-  cudaFree(h->d_trace);
+  dev_free(h->d_trace);
   h->d_trace = nullptr;
   if (rc) return rc;
   CKR(e, "trace copy");
@@ -1260,7 +1288,7 @@ extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trac
     CKR(cudaMemcpy(&sizes[1], h->dS.pred_ptr + nt, sizeof(int64_t), cudaMemcpyDeviceToHost), "edges");
   if (!trace_out) return HLU_OK;
   if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
-  CKR(cudaMalloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
+  CKR(dev_malloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs, nullptr), "nrhs slot");
   h->cur_nrhs = nrhs;
@@ -1270,7 +1298,7 @@ extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trac
     rc = read_status(h, nullptr, st);
   }
   cudaError_t e = cudaMemcpy(trace_out, h->d_trace, sizeof(uint64_t) * 4 * nt, cudaMemcpyDeviceToHost);
-  cudaFree(h->d_trace);
+  dev_free(h->d_trace);
   h->d_trace = nullptr;
   if (rc) return rc;
   CKR(e, "trace copy");
@@ -1279,6 +1307,52 @@ extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trac
   if (pred_idx_out)
     CKR(cudaMemcpy(pred_idx_out, h->dS.pred_idx, sizeof(int32_t) * sizes[1], cudaMemcpyDeviceToHost), "dag");
   if (tasks_out) CKR(cudaMemcpy(tasks_out, h->dS.tasks, sizeof(Task) * nt, cudaMemcpyDeviceToHost), "tasks");
+  return HLU_OK;
+}
+
+// Zeroes row and column `dof` of A (columns are ascending within a row).
+__global__ void k_zero_dof(int64_t N, const int64_t* rowptr, const int32_t* col, double* val, int32_t dof) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[r], e = rowptr[r + 1];
+    if (r == dof) {
+      for (int64_t q = b; q < e; ++q) val[q] = 0.0;
+      continue;
+    }
+    int64_t lo = b, hi = e;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (col[mid] < dof)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    if (lo < e && col[lo] == dof) val[lo] = 0.0;
+  }
+}
+
+extern "C" int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int32_t K, int32_t* status_out) {
+  if (!A || !B || !D || K < 1 || K > 4096) return fail(HLU_ERR_ARG, "bad argument");
+  int32_t* st = nullptr;
+  CKR(dev_malloc(&st, sizeof(int32_t) * 4), "status");
+  int32_t z[4] = {0, -1, 0, 0};
+  cudaError_t e = cudaMemcpy(st, z, sizeof(z), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = tc_tile_product(A, B, D, K, st, (unsigned long long)(g_wait_limit_ms * 1e6), nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int32_t hs[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hs, st, sizeof(hs), cudaMemcpyDeviceToHost);
+  dev_free(st);
+  CKR(e, "tf32 tile");
+  if (status_out) *status_out = hs[0];
+  return hs[0] == 5 ? fail(HLU_ERR_TIMEOUT, "tensor-core completion wait ran out") : HLU_OK;
+}
+
+extern "C" int hlu_debug_zero_dof(hlu_handle* h, int64_t dof) {
+  if (!h || dof < 0 || dof >= h->A.N) return fail(HLU_ERR_ARG, "bad argument");
+  note_launch();
+  k_zero_dof<<<(int)std::min<int64_t>((h->A.N + 255) / 256, 4096), 256>>>(h->A.N, h->A.rowptr, h->A.col, h->A.val,
+                                                                          (int32_t)dof);
+  CKR(cudaGetLastError(), "zero dof");
+  CKR(cudaDeviceSynchronize(), "zero dof");
   return HLU_OK;
 }
 
@@ -1302,21 +1376,21 @@ int alloc_ws(KrylovWS& k, int64_t N, int m, int nr) {
   k.N = N;
   k.m = m;
   k.nr = nr;
-  CKR(cudaMalloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
-  CKR(cudaMalloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
-  CKR(cudaMalloc(&k.W, sizeof(double) * N * nr), "alloc W");
-  CKR(cudaMalloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.hn, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.cs, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.sn, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
-  CKR(cudaMalloc(&k.est, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.y, sizeof(double) * m * nr), "alloc");
-  CKR(cudaMalloc(&k.bn, sizeof(double) * nr), "alloc");
-  CKR(cudaMalloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
-  CKR(cudaMalloc(&k.jr, sizeof(int) * nr), "alloc");
+  CKR(dev_malloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
+  CKR(dev_malloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
+  CKR(dev_malloc(&k.W, sizeof(double) * N * nr), "alloc W");
+  CKR(dev_malloc(&k.h1, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.h2, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.hn, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.H, sizeof(double) * (m + 1) * m * nr), "alloc");
+  CKR(dev_malloc(&k.cs, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.sn, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.g, sizeof(double) * (m + 1) * nr), "alloc");
+  CKR(dev_malloc(&k.est, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.y, sizeof(double) * m * nr), "alloc");
+  CKR(dev_malloc(&k.bn, sizeof(double) * nr), "alloc");
+  CKR(dev_malloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
+  CKR(dev_malloc(&k.jr, sizeof(int) * nr), "alloc");
   return HLU_OK;
 }
 

@@ -28,6 +28,7 @@
 #include "launch_count.h"
 
 #include "build.h"
+#include "devmem.h"
 
 namespace hlu {
 
@@ -235,6 +236,28 @@ __global__ void k_rhs_coo(int n, double kappa2, const int32_t* dofmap, int32_t* 
     for (int e = 0; e < 6; ++e) {
       keys[t * 6 + e] = g.dof[e] >= 0 ? g.dof[e] : INT32_MAX;
       vals[t * 6 + e] = g.vol / 4.0 * acc[e];
+    }
+  }
+}
+
+// load vector of a constant current density J (Sec. 4, Example 1: J_S =
+// [0, 0, 1]): Phi_ab = lam_a grad lam_b - lam_b grad lam_a is linear and the
+// integral of a barycentric coordinate over T is |T| / 4, so
+// b_e = |T| / 4 J . (grad lam_b - grad lam_a) exactly.  One thread per
+// tetrahedron, 6 (dof, value) pairs.
+__global__ void k_rhs_const_coo(int n, double J0, double J1, double J2, const int32_t* dofmap, int32_t* keys,
+                                double* vals) {
+  int64_t nt = (int64_t)6 * n * n * n;
+  const double J[3] = {J0, J1, J2};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    TetGeo g;
+    tet_geometry(t, n, dofmap, g);
+    for (int e = 0; e < 6; ++e) {
+      const int a = g.lo[e], b = g.hi[e];
+      double d[3];
+      for (int c = 0; c < 3; ++c) d[c] = g.G[b][c] - g.G[a][c];
+      keys[t * 6 + e] = g.dof[e] >= 0 ? g.dof[e] : INT32_MAX;
+      vals[t * 6 + e] = g.vol / 4.0 * dot3(J, d);
     }
   }
 }
@@ -606,6 +629,23 @@ template __global__ void k_fill_dense<double>(int32_t, const FillDesc*, const in
     if (e_ != cudaSuccess) return e_;       \
   } while (0)
 
+// Temporaries of one host driver: freed when the driver returns, on success
+// or on an early error return.
+struct TempScope {
+  std::vector<void*> ptrs;
+  template <class T>
+  cudaError_t alloc(T** p, size_t bytes) {
+    cudaError_t e = dev_malloc(p, bytes);
+    if (e == cudaSuccess) ptrs.push_back((void*)*p);
+    return e;
+  }
+  ~TempScope() {
+    for (void* p : ptrs) dev_free(p);
+  }
+};
+// thrust's temporary storage comes from the library's allocator too
+static ThrustAlloc g_talloc;
+
 static int grid_for(int64_t n, int bs = 256) {
   int64_t g = (n + bs - 1) / bs;
   if (g < 1) g = 1;
@@ -615,46 +655,47 @@ static int grid_for(int64_t n, int bs = 256) {
 
 cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m) {
   int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  TempScope tmp;
   int32_t* cnt = nullptr;
-  CK(cudaMalloc(&cnt, sizeof(int32_t) * (nv + 1)));
+  CK(tmp.alloc(&cnt, sizeof(int32_t) * (nv + 1)));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nv + 1), s));
   note_launch();
   k_count_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt);
-  thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(cnt),
+  thrust::exclusive_scan(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(cnt),
                          thrust::device_ptr<int32_t>(cnt + nv + 1), thrust::device_ptr<int32_t>(cnt));
   int32_t N = 0;
   CK(cudaMemcpyAsync(&N, cnt + nv, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   m.n = n;
   m.N = N;
-  CK(cudaMalloc(&m.dofmap, sizeof(int32_t) * nv * 7));
-  CK(cudaMalloc(&m.edges, sizeof(int32_t) * 2 * (int64_t)N));
-  CK(cudaMalloc(&m.pts, sizeof(int32_t) * 3 * (int64_t)N));
+  CK(dev_malloc(&m.dofmap, sizeof(int32_t) * nv * 7));
+  CK(dev_malloc(&m.edges, sizeof(int32_t) * 2 * (int64_t)N));
+  CK(dev_malloc(&m.pts, sizeof(int32_t) * 3 * (int64_t)N));
   note_launch();
   k_number_edges<<<grid_for(nv), 256, 0, s>>>(n, cnt, m.dofmap, m.edges, m.pts);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
-  cudaFree(cnt);
   return cudaSuccess;
 }
 
 cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A) {
   int64_t nt = (int64_t)6 * m.n * m.n * m.n;
   int64_t ne = nt * 36;
+  TempScope tmp;
   int64_t* keys = nullptr;
   double* vals = nullptr;
-  CK(cudaMalloc(&keys, sizeof(int64_t) * ne));
-  CK(cudaMalloc(&vals, sizeof(double) * ne));
+  CK(tmp.alloc(&keys, sizeof(int64_t) * ne));
+  CK(tmp.alloc(&vals, sizeof(double) * ne));
   note_launch();
   k_element_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.N, m.dofmap, keys, vals);
   CK(cudaGetLastError());
-  thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int64_t>(keys),
+  thrust::stable_sort_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(keys),
                              thrust::device_ptr<int64_t>(keys + ne), thrust::device_ptr<double>(vals));
   int64_t* ukeys = nullptr;
   double* uvals = nullptr;
-  CK(cudaMalloc(&ukeys, sizeof(int64_t) * ne));
-  CK(cudaMalloc(&uvals, sizeof(double) * ne));
-  auto ends = thrust::reduce_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int64_t>(keys),
+  CK(tmp.alloc(&ukeys, sizeof(int64_t) * ne));
+  CK(tmp.alloc(&uvals, sizeof(double) * ne));
+  auto ends = thrust::reduce_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(keys),
                                     thrust::device_ptr<int64_t>(keys + ne), thrust::device_ptr<double>(vals),
                                     thrust::device_ptr<int64_t>(ukeys), thrust::device_ptr<double>(uvals));
   int64_t nu = ends.first - thrust::device_ptr<int64_t>(ukeys);
@@ -664,45 +705,47 @@ cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR&
   int64_t nnz = (last == INT64_MAX) ? nu - 1 : nu;
   A.N = m.N;
   A.nnz = nnz;
-  CK(cudaMalloc(&A.rowptr, sizeof(int64_t) * (m.N + 1)));
-  CK(cudaMalloc(&A.col, sizeof(int32_t) * nnz));
-  CK(cudaMalloc(&A.val, sizeof(double) * nnz));
+  CK(dev_malloc(&A.rowptr, sizeof(int64_t) * (m.N + 1)));
+  CK(dev_malloc(&A.col, sizeof(int32_t) * nnz));
+  CK(dev_malloc(&A.val, sizeof(double) * nnz));
   int32_t* rowcnt = nullptr;
-  CK(cudaMalloc(&rowcnt, sizeof(int32_t) * (m.N + 1)));
+  CK(tmp.alloc(&rowcnt, sizeof(int32_t) * (m.N + 1)));
   CK(cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * (m.N + 1), s));
   note_launch();
   k_csr_rows<<<grid_for(nnz), 256, 0, s>>>(nnz, m.N, ukeys, A.col, rowcnt);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(A.val, uvals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
-  thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(rowcnt),
+  thrust::exclusive_scan(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(rowcnt),
                          thrust::device_ptr<int32_t>(rowcnt + m.N + 1), thrust::device_ptr<int64_t>(A.rowptr),
                          (int64_t)0);
   CK(cudaStreamSynchronize(s));
-  cudaFree(rowcnt);
-  cudaFree(keys);
-  cudaFree(vals);
-  cudaFree(ukeys);
-  cudaFree(uvals);
   return cudaSuccess;
 }
 
-cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s) {
+// Load vector from per-tetrahedron (dof, value) pairs: manufactured field
+// (J == nullptr) or constant current J[3].  The pairs are sorted by DOF and
+// summed in a fixed order, so the result does not depend on the launch.
+static cudaError_t rhs_from_elements(const DevMesh& m, double kappa, const double* Jc, double* b, cudaStream_t s) {
   int64_t nt = (int64_t)6 * m.n * m.n * m.n;
   int64_t ne = nt * 6;
   int32_t* keys = nullptr;
   double* vals = nullptr;
   int32_t* uk = nullptr;
   double* us = nullptr;
-  CK(cudaMallocAsync(&keys, sizeof(int32_t) * ne, s));
-  CK(cudaMallocAsync(&vals, sizeof(double) * ne, s));
-  CK(cudaMallocAsync(&uk, sizeof(int32_t) * ne, s));
-  CK(cudaMallocAsync(&us, sizeof(double) * ne, s));
+  TempScope tmp;
+  CK(tmp.alloc(&keys, sizeof(int32_t) * ne));
+  CK(tmp.alloc(&vals, sizeof(double) * ne));
+  CK(tmp.alloc(&uk, sizeof(int32_t) * ne));
+  CK(tmp.alloc(&us, sizeof(double) * ne));
   note_launch();
-  k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
+  if (Jc)
+    k_rhs_const_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, Jc[0], Jc[1], Jc[2], m.dofmap, keys, vals);
+  else
+    k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
   CK(cudaGetLastError());
-  thrust::stable_sort_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(keys),
+  thrust::stable_sort_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(keys),
                              thrust::device_ptr<int32_t>(keys + ne), thrust::device_ptr<double>(vals));
-  auto ends = thrust::reduce_by_key(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(keys),
+  auto ends = thrust::reduce_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(keys),
                                     thrust::device_ptr<int32_t>(keys + ne), thrust::device_ptr<double>(vals),
                                     thrust::device_ptr<int32_t>(uk), thrust::device_ptr<double>(us));
   int64_t nu = ends.first - thrust::device_ptr<int32_t>(uk);
@@ -710,11 +753,16 @@ cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStre
   note_launch();
   k_scatter_rhs<<<grid_for(nu), 256, 0, s>>>(nu, uk, us, m.N, b);
   CK(cudaGetLastError());
-  CK(cudaFreeAsync(keys, s));
-  CK(cudaFreeAsync(vals, s));
-  CK(cudaFreeAsync(uk, s));
-  CK(cudaFreeAsync(us, s));
+  CK(cudaStreamSynchronize(s));
   return cudaSuccess;
+}
+
+cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s) {
+  return rhs_from_elements(m, kappa, nullptr, b, s);
+}
+
+cudaError_t constant_current_rhs(const DevMesh& m, const double J[3], double* b, cudaStream_t s) {
+  return rhs_from_elements(m, 0.0, J, b, s);
 }
 
 cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream_t s, HostTrees& out,
@@ -722,19 +770,20 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   const int32_t N = (int32_t)m.N;
   // level-by-level cluster arrays with global BFS ids; generous capacity
   int32_t cap = 2 * N + 16;  // a binary tree with at most N leaves
+  TempScope tmp;
   int32_t *off, *size, *lo, *hi, *son, *level, *parent, *nleft, *permA, *permB, *cnt;
-  CK(cudaMalloc(&off, sizeof(int32_t) * cap));
-  CK(cudaMalloc(&size, sizeof(int32_t) * cap));
-  CK(cudaMalloc(&lo, sizeof(int32_t) * 3 * cap));
-  CK(cudaMalloc(&hi, sizeof(int32_t) * 3 * cap));
-  CK(cudaMalloc(&son, sizeof(int32_t) * 2 * cap));
-  CK(cudaMalloc(&level, sizeof(int32_t) * cap));
-  CK(cudaMalloc(&parent, sizeof(int32_t) * cap));
-  CK(cudaMalloc(&nleft, sizeof(int32_t) * cap));
-  CK(cudaMalloc(&permA, sizeof(int32_t) * (N + 1)));
-  CK(cudaMalloc(&permB, sizeof(int32_t) * (N + 1)));
-  CK(cudaMalloc(&cnt, sizeof(int32_t)));
-  thrust::sequence(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(permA), thrust::device_ptr<int32_t>(permA + N));
+  CK(tmp.alloc(&off, sizeof(int32_t) * cap));
+  CK(tmp.alloc(&size, sizeof(int32_t) * cap));
+  CK(tmp.alloc(&lo, sizeof(int32_t) * 3 * cap));
+  CK(tmp.alloc(&hi, sizeof(int32_t) * 3 * cap));
+  CK(tmp.alloc(&son, sizeof(int32_t) * 2 * cap));
+  CK(tmp.alloc(&level, sizeof(int32_t) * cap));
+  CK(tmp.alloc(&parent, sizeof(int32_t) * cap));
+  CK(tmp.alloc(&nleft, sizeof(int32_t) * cap));
+  CK(tmp.alloc(&permA, sizeof(int32_t) * (N + 1)));
+  CK(tmp.alloc(&permB, sizeof(int32_t) * (N + 1)));
+  CK(tmp.alloc(&cnt, sizeof(int32_t)));
+  thrust::sequence(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(permA), thrust::device_ptr<int32_t>(permA + N));
   int32_t h0[2] = {0, N};
   CK(cudaMemcpyAsync(off, &h0[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(size, &h0[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -782,8 +831,8 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   const int32_t nc = first;
   // DFS pre-order ids
   int32_t *sub, *pre;
-  CK(cudaMalloc(&sub, sizeof(int32_t) * nc));
-  CK(cudaMalloc(&pre, sizeof(int32_t) * nc));
+  CK(tmp.alloc(&sub, sizeof(int32_t) * nc));
+  CK(tmp.alloc(&pre, sizeof(int32_t) * nc));
   for (int l = (int)level_first.size() - 1; l >= 0; --l) {
     note_launch();
     k_subtree<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub);
@@ -794,7 +843,7 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
     k_preorder<<<grid_for(level_cnt[l]), 256, 0, s>>>(level_first[l], level_cnt[l], 2, son, sub, pre);
   }
   int32_t* cl_export;
-  CK(cudaMalloc(&cl_export, sizeof(int32_t) * 12 * nc));
+  CK(tmp.alloc(&cl_export, sizeof(int32_t) * 12 * nc));
   note_launch();
   k_export_clusters<<<grid_for(nc), 256, 0, s>>>(nc, pre, off, size, lo, hi, son, level, parent, cl_export);
   CK(cudaGetLastError());
@@ -803,13 +852,13 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   int32_t bcap = 1 << 20;
   int32_t *brow, *bcol, *bkind, *bson, *bpar, *nch, *cst;
   auto balloc = [&](int32_t c) -> cudaError_t {
-    CK(cudaMalloc(&brow, sizeof(int32_t) * c));
-    CK(cudaMalloc(&bcol, sizeof(int32_t) * c));
-    CK(cudaMalloc(&bkind, sizeof(int32_t) * c));
-    CK(cudaMalloc(&bson, sizeof(int32_t) * 4 * (int64_t)c));
-    CK(cudaMalloc(&bpar, sizeof(int32_t) * c));
-    CK(cudaMalloc(&nch, sizeof(int32_t) * (c + 1)));
-    CK(cudaMalloc(&cst, sizeof(int32_t) * (c + 1)));
+    CK(tmp.alloc(&brow, sizeof(int32_t) * c));
+    CK(tmp.alloc(&bcol, sizeof(int32_t) * c));
+    CK(tmp.alloc(&bkind, sizeof(int32_t) * c));
+    CK(tmp.alloc(&bson, sizeof(int32_t) * 4 * (int64_t)c));
+    CK(tmp.alloc(&bpar, sizeof(int32_t) * c));
+    CK(tmp.alloc(&nch, sizeof(int32_t) * (c + 1)));
+    CK(tmp.alloc(&cst, sizeof(int32_t) * (c + 1)));
     return cudaSuccess;
   };
   // capacity: blocks grow at most 4x per level; bound by an estimate, grow on demand
@@ -826,7 +875,7 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
     k_block_classify<<<grid_for(bcount), 256, 0, s>>>(bcount, brow + bfirst, bcol + bfirst, lo, hi, son, eta2,
                                                       bkind + bfirst, nch + bfirst);
     CK(cudaGetLastError());
-    thrust::exclusive_scan(thrust::cuda::par.on(s), thrust::device_ptr<int32_t>(nch + bfirst),
+    thrust::exclusive_scan(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(nch + bfirst),
                            thrust::device_ptr<int32_t>(nch + bfirst + bcount), thrust::device_ptr<int32_t>(cst + bfirst));
     int32_t lastc = 0, lastn = 0;
     CK(cudaMemcpyAsync(&lastc, cst + bfirst + bcount - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -849,8 +898,8 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   }
   const int32_t nb = bfirst;
   int32_t *bsub, *bpre;
-  CK(cudaMalloc(&bsub, sizeof(int32_t) * nb));
-  CK(cudaMalloc(&bpre, sizeof(int32_t) * nb));
+  CK(tmp.alloc(&bsub, sizeof(int32_t) * nb));
+  CK(tmp.alloc(&bpre, sizeof(int32_t) * nb));
   for (int l = (int)bl_first.size() - 1; l >= 0; --l) {
     note_launch();
     k_subtree<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub);
@@ -861,7 +910,7 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
     k_preorder<<<grid_for(bl_cnt[l]), 256, 0, s>>>(bl_first[l], bl_cnt[l], 4, bson, bsub, bpre);
   }
   int32_t* bl_export;
-  CK(cudaMalloc(&bl_export, sizeof(int32_t) * 8 * (int64_t)nb));
+  CK(tmp.alloc(&bl_export, sizeof(int32_t) * 8 * (int64_t)nb));
   note_launch();
   k_export_blocks<<<grid_for(nb), 256, 0, s>>>(nb, bpre, pre, brow, bcol, bkind, bson, bpar, bl_export);
   CK(cudaGetLastError());
@@ -875,11 +924,6 @@ cudaError_t build_trees(const DevMesh& m, int32_t leaf, int64_t eta2, cudaStream
   CK(cudaStreamSynchronize(s));
   out.nc = nc;
   out.nb = nb;
-  for (void* p : {(void*)off, (void*)size, (void*)lo, (void*)hi, (void*)son, (void*)level, (void*)parent,
-                  (void*)nleft, (void*)permA, (void*)permB, (void*)cnt, (void*)sub, (void*)pre, (void*)cl_export,
-                  (void*)brow, (void*)bcol, (void*)bkind, (void*)bson, (void*)bpar, (void*)nch, (void*)cst,
-                  (void*)bsub, (void*)bpre, (void*)bl_export})
-    cudaFree(p);
   return cudaSuccess;
 }
 

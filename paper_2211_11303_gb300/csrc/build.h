@@ -38,6 +38,8 @@ struct FillDesc {
 cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m);
 cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A);
 cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s);
+// load vector of the constant current density J (exact integration)
+cudaError_t constant_current_rhs(const DevMesh& m, const double J[3], double* b, cudaStream_t s);
 // manufactured_rhs without allocations (fixed device scratch; see build.cu);
 // cudaErrorInvalidValue when the mesh needs more than rhs_noalloc_max_entries()
 // element contributions

@@ -19,10 +19,13 @@
 
 #include <cstdint>
 
+#include <type_traits>
+
 #include "launch_count.h"
 
 #include "exec.h"
 #include "hlu_internal.h"
+#include "tc.cuh"
 
 namespace hlu {
 
@@ -50,6 +53,20 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Tensor-core state of one CTA (TF32 tile products, factorisation launches
+// with HLU_TF32): the accumulator's tensor-memory columns, the completion
+// mbarrier and its phase (every thread keeps its own copy; all threads pass
+// the same waits).
+struct TcCtl {
+  bool on = false;
+  bool broken = false;   // a completion wait ran out: no further MMAs are issued
+  uint32_t tmem = 0;
+  uint64_t* bar = nullptr;
+  uint32_t phase = 0;
+  int32_t* status = nullptr;
+  unsigned long long wait_ns = 0;
+};
+
 template <class T>
 struct Ctx {
   T* arena;
@@ -67,6 +84,7 @@ struct Ctx {
   int32_t compress_at;
   int32_t nrhs_slot, nrhs;  // the launch's right-hand-side count and its slot
   const int32_t* term_p;    // resolved term column counts (solve launches) or null
+  TcCtl* tcc;               // tensor-core tile products (FP32 factorisations with TF32) or null
 };
 
 template <class T>
@@ -312,11 +330,130 @@ __device__ __forceinline__ void chunk_mma(T (&acc)[4][4], const T* As, const T* 
   }
 }
 
+// ---------------------------------------------------------------- TF32 tile products
+// Waits (thread 0, bounded by the launch's wait limit) until the MMAs
+// committed last have completed; false, with HLU_ERR_TIMEOUT recorded and the
+// launch aborted, when the wait ran out.  Every thread returns the same value.
+__device__ bool tc_wait(TcCtl* t) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    if (!t->broken) {
+      const uint64_t t0 = gtimer();
+      for (;;) {
+        if (tc::mbar_try_wait(t->bar, t->phase)) {
+          ok = 1;
+          break;
+        }
+        if (gtimer() - t0 > t->wait_ns) {
+          atomicCAS(t->status, 0, 5);
+          atomicExch(t->status + 3, 1);
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  if (ok)
+    t->phase ^= 1u;
+  else
+    t->broken = true;
+  return ok;
+}
+
+// The chunk pipeline of tile_mma_seq on the fifth-generation tensor cores:
+// each 64 x 32 (A) and 32 x 64 (B) chunk is rounded to TF32 and staged
+// K-major in the core-matrix layout (A at S, B at S + 8 KB), and one thread
+// issues four M = 128, N = 64, K = 8 MMAs into the tensor-memory accumulator.
+// The MMA runs while the next chunk's operands load into registers; the
+// staging buffer is rewritten only after the MMAs reading it completed.
+// Rows 64..127 of the M = 128 A operand read the B chunk (their results are
+// never used).  At the end the 64 x 64 result goes through shared memory into
+// every thread's 4 x 4 register tile (acc +=).  S: >= 16 KB, 1024-aligned.
+template <class Cursor>
+__device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, float* S, TcCtl* t) {
+  if (!cur.first()) return;
+  const int tid = threadIdx.x;
+  float ra[kChunkRegs], rb[kChunkRegs];
+  Chunk<float> ch = cur.chunk();
+  chunk_fetch(ch, ra, rb);
+  char* Sb = reinterpret_cast<char*>(S);
+  bool first = true;
+  __syncthreads();  // the staging buffer's previous readers are done
+  for (;;) {
+    if (!first && !tc_wait(t)) return;  // the buffer is still read by the MMAs
+#pragma unroll
+    for (int q = 0; q < kChunkRegs; ++q) {
+      const int e = tid + q * NT;
+      int r, kk;
+      chunk_coord(ch.A.rs == 1, e, r, kk);
+      *reinterpret_cast<float*>(Sb + tc::tc_offset(r, kk)) = tc::to_tf32(ra[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kChunkRegs; ++q) {
+      const int e = tid + q * NT;
+      int cc, kk;
+      chunk_coord(ch.B.rs != 1, e, cc, kk);
+      *reinterpret_cast<float*>(Sb + 8192 + tc::tc_offset(cc, kk)) = tc::to_tf32(rb[q]);
+    }
+    tc::fence_async_shared();
+    __syncthreads();
+    if (tid == 0 && !t->broken) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(Sb), b0 = a0 + 8192u;
+#pragma unroll
+      for (int ks = 0; ks < tc::kTcChunkK / 8; ++ks)
+        tc::mma_tf32(t->tmem, tc::smem_desc(a0 + ks * 2 * tc::kTcLBO), tc::smem_desc(b0 + ks * 2 * tc::kTcLBO),
+                     !first || ks > 0);
+      tc::mma_commit(t->bar);
+    }
+    first = false;
+    const bool more = cur.next();
+    if (more) {
+      ch = cur.chunk();
+      chunk_fetch(ch, ra, rb);
+    }
+    if (!more) break;
+  }
+  if (!tc_wait(t)) return;
+  tc::fence_after_sync();
+  // rows 0..63 of the accumulator: lane quarters 0 and 1, read by warps 0, 1
+  // (columns 0..31) and 4, 5 (columns 32..63)
+  const int w = tid >> 5, lane = tid & 31;
+  if ((w & 3) < 2) {
+    const int q = w & 3, col0 = (w >> 2) * 32;
+    float v[32];
+    tc::tmem_ld32(t->tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+    const int row = q * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) S[row + (col0 + j) * 64] = v[j];
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] += S[(tx * 4 + i) + (ty * 4 + j) * 64];
+  __syncthreads();
+}
+
 // Software pipeline over a sequence of chunks: the operands of chunk j + 1
 // are in flight (registers) while chunk j is multiplied from shared memory.
 // Cursor: first() -> bool (a chunk exists), chunk() -> Chunk, next() -> bool.
+// With tensor-core state switched on (FP32 only) the products run in TF32 on
+// the tensor cores (tile_mma_seq_tc).
 template <class T, class Cursor>
-__device__ void tile_mma_seq(T (&acc)[4][4], Cursor& cur, T* As, T* Bs) {
+__device__ void tile_mma_seq(T (&acc)[4][4], Cursor& cur, T* As, T* Bs, TcCtl* tcc = nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcc && tcc->on) {
+      tile_mma_seq_tc(acc, cur, As, tcc);
+      return;
+    }
+  }
   if (!cur.first()) return;
   T ra[kChunkRegs], rb[kChunkRegs];
   Chunk<T> ch = cur.chunk();
@@ -358,9 +495,9 @@ struct ProductCursor {
 // acc += A (tile rows [rlo, rlo + mrows), K columns) times B (K x ncols)
 template <class T>
 __device__ void tile_mma(T (&acc)[4][4], const Mat<T>& A, int rlo, int mrows, const Mat<T>& B, int ncols, int K,
-                         T* As, T* Bs) {
+                         T* As, T* Bs, TcCtl* tcc = nullptr) {
   ProductCursor<T> cur{A, B, rlo, mrows, ncols, K, 0};
-  tile_mma_seq(acc, cur, As, Bs);
+  tile_mma_seq(acc, cur, As, Bs, tcc);
 }
 // C[rows i0.., cols j0..] (+)= sign * acc for the valid part of the tile
 template <class T>
@@ -459,7 +596,7 @@ __device__ void task_proj(Ctx<T>& c, const Task& t, char* smem) {
       T acc[4][4];
       acc_zero(acc);
       tile_mma(acc, shift(matT(c, t.a), i0, 0), 0, min(64, r - i0), shift(mat(c, t.b), 0, j0), min(64, k - j0), m,
-               As, Bs);
+               As, Bs, c.tcc);
       tile_store(acc, c, t.c, i0, j0, min(64, r - i0), min(64, k - j0), T(1), true);
     }
   if (threadIdx.x == 0) c.flops += 2.0 * m * r * k;
@@ -522,7 +659,7 @@ __device__ double rowmv_tile(const Ctx<T>& c, const Task& t, int i0, int j0, int
     if (threadIdx.x < nq) s_p[threadIdx.x] = pq >= 0 ? pq : ncols(c, s_tm[threadIdx.x].A);
     __syncthreads();
     TermCursor<T> cur{&c, s_tm, s_p, nq, i0, j0, k, 0, 0};
-    tile_mma_seq(acc, cur, As, Bs);
+    tile_mma_seq(acc, cur, As, Bs, c.tcc);
     if (threadIdx.x == 0)
       for (int q = 0; q < nq; ++q) {
         const int lo = max(s_tm[q].roff, i0), hi = min(s_tm[q].roff + s_tm[q].A.rows, i0 + 64);
@@ -700,7 +837,7 @@ __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
       acc_zero(acc);
       if (k > 0)
         tile_mma(acc, shift(mat(c, t.a), i0, 0), 0, min(64, m - i0), shift(matT(c, t.b), 0, j0), min(64, n - j0), k,
-                 As, Bs);
+                 As, Bs, c.tcc);
       tile_store(acc, c, t.c, i0, j0, min(64, m - i0), min(64, n - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
     }
   if (threadIdx.x == 0) c.flops += 2.0 * m * n * k;
@@ -1427,7 +1564,7 @@ __device__ bool task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
         if (threadIdx.x < nq) s_w[threadIdx.x] = ncols(c, s_pc[threadIdx.x].X);
         __syncthreads();
         PieceCursor<T> cur{&c, s_pc, s_w, nq, i0, j0, 0, 0};
-        tile_mma_seq(acc, cur, As, Bs);
+        tile_mma_seq(acc, cur, As, Bs, c.tcc);
       }
       const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 #pragma unroll
@@ -1579,11 +1716,31 @@ __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
 // ---------------------------------------------------------------- executor
 template <class T>
 __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ ExecArgs a) {
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(1024) char smem[];
   __shared__ int64_t s_task;
   __shared__ int64_t s_succ[2];  // successor range of the running task
   __shared__ int s_prob;
   Ctx<T> c;
+  TcCtl tcc;
+  c.tcc = nullptr;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_tcbar;
+  const bool use_tc = std::is_same<T, float>::value && a.tf32 != 0;
+  if (use_tc) {
+    // tensor memory for the 128 x 64 FP32 accumulator, held for the whole
+    // persistent launch, and the MMA completion barrier
+    if (threadIdx.x < 32) tc::tmem_alloc(&s_tmem, tc::kTcCols);
+    if (threadIdx.x == 0) tc::mbar_init(&s_tcbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tcc.on = true;
+    tcc.tmem = s_tmem;
+    tcc.bar = &s_tcbar;
+    tcc.status = a.status;
+    tcc.wait_ns = a.wait_limit_ns;
+    c.tcc = &tcc;
+  }
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
   c.rows_max = a.trunc_rows;
   c.status = a.status;
@@ -1701,11 +1858,72 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     }
     __syncthreads();
   }
+  if (use_tc) {
+    __syncthreads();
+    if (tcc.broken && threadIdx.x == 0) {
+      // a completion wait ran out: wait once more (bounded) for the MMAs in
+      // flight before the accumulator columns are released
+      const uint64_t t0 = gtimer();
+      while (!tc::mbar_try_wait(tcc.bar, tcc.phase) && gtimer() - t0 < a.wait_limit_ns) {
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tcc.tmem, tc::kTcCols);
+  }
   if (threadIdx.x == 0 && a.flops) atomicAdd(a.flops, c.flops);
   if (a.prof && threadIdx.x < kProfEntries) {
     unsigned long long v = s_prof[threadIdx.x];
     if (v) atomicAdd(a.prof + threadIdx.x, v);
   }
+}
+
+// One 64 x 64 tile product D = A B (A: 64 x K, ld 64; B: K x 64, ld K; D:
+// 64 x 64, ld 64; column-major FP32) through the TF32 tensor-core pipeline of
+// the executor, by one CTA: checks that path on its own.
+__global__ void __launch_bounds__(NT, 1)
+    tc_tile_kernel(const float* A, const float* B, float* D, int K, int32_t* status, unsigned long long wait_ns) {
+  extern __shared__ __align__(1024) char smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  if (threadIdx.x < 32) tc::tmem_alloc(&s_tmem, tc::kTcCols);
+  if (threadIdx.x == 0) tc::mbar_init(&s_bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  TcCtl t;
+  t.on = true;
+  t.tmem = s_tmem;
+  t.bar = &s_bar;
+  t.status = status;
+  t.wait_ns = wait_ns;
+  float acc[4][4];
+  acc_zero(acc);
+  ProductCursor<float> cur{Mat<float>{A, 1, 64}, Mat<float>{B, 1, K}, 0, 64, 64, K, 0};
+  tile_mma_seq_tc(acc, cur, reinterpret_cast<float*>(smem), &t);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) D[(tx * 4 + i) + (ty * 4 + j) * 64] = acc[i][j];
+  __syncthreads();
+  if (t.broken && threadIdx.x == 0) {
+    const uint64_t t0 = gtimer();
+    while (!tc::mbar_try_wait(t.bar, t.phase) && gtimer() - t0 < wait_ns) {
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(t.tmem, tc::kTcCols);
+}
+
+cudaError_t tc_tile_product(const float* A, const float* B, float* D, int K, int32_t* status,
+                            unsigned long long wait_ns, cudaStream_t s) {
+  note_launch();
+  tc_tile_kernel<<<1, NT, 2 * kStage * sizeof(float), s>>>(A, B, D, K, status, wait_ns);
+  return cudaGetLastError();
 }
 
 size_t exec_smem_bytes(int elem_size) {

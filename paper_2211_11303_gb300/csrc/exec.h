@@ -55,10 +55,16 @@ struct ExecArgs {
   double jacobi_tol;            // truncation: Jacobi orthogonality tolerance
   int32_t compress_at;          // truncation: stack width that triggers a compression
   unsigned long long* prof;     // optional [kProfEntries] (layout above)
+  int32_t tf32;                 // FP32 launches: tile products in TF32 on the tensor cores (tcgen05)
   unsigned long long* trace;    // optional [ntotal x 4] per slot: (problem << 40 | task), claim, start, end (ns)
 };
 
 size_t exec_smem_bytes(int elem_size);
+// D (64 x 64) = A (64 x K) B (K x 64), column-major FP32 device arrays, through
+// the executor's TF32 tensor-core tile pipeline (one CTA); status[0] receives
+// HLU_ERR_TIMEOUT (5) if an MMA completion wait ran out.
+cudaError_t tc_tile_product(const float* A, const float* B, float* D, int K, int32_t* status,
+                            unsigned long long wait_ns, cudaStream_t s);
 template <class T>
 int exec_blocks_per_sm();
 template <class T>

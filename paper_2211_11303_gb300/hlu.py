@@ -1,9 +1,12 @@
 """Thin ctypes binding of the C ABI in include/hlu.h.
 
 Argument marshalling only: every numerical step runs in libhlu.so's CUDA
-kernels.  PyTorch provides device memory and streams.  Vectors are FP64 CUDA
-tensors of shape (N,) or (N, nrhs) in column-major layout (``colmajor`` makes
-one), in the original interior-edge DOF order.
+kernels.  PyTorch provides device memory and streams: on loading, the
+library's device allocator is pointed at PyTorch's caching allocator
+(hlu_set_allocator; set HLU_ALLOCATOR=cuda in the environment to keep
+cudaMalloc).  Vectors are FP64 CUDA tensors of shape (N,) or (N, nrhs) in
+column-major layout (``colmajor`` makes one), in the original interior-edge
+DOF order.
 """
 import ctypes
 import os
@@ -14,6 +17,7 @@ HLU_OK = 0
 HLU_ERR_NOT_CONVERGED = 4
 HLU_FP64 = 0
 HLU_FP32 = 1
+HLU_TF32 = 2
 BLOCK_ADM, BLOCK_DENSE, BLOCK_SUB = 0, 1, 2
 
 
@@ -67,6 +71,7 @@ SIGNATURES = {
     "hlu_export_csr": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "hlu_rhs_manufactured": (_i32, [_vp, _vp, _vp]),
     "hlu_rhs_manufactured_noalloc": (_i32, [_vp, _vp, _vp]),
+    "hlu_rhs_constant_current": (_i32, [_vp, _f64, _f64, _f64, _vp, _vp]),
     "hlu_spmv": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
     "hlu_factor": (_i32, [_vp, _i32, _vp]),
     "hlu_factor_stats": (_i32, [_vp, _P(hlu_factor_info)]),
@@ -81,6 +86,11 @@ SIGNATURES = {
     "hlu_set_tile": (None, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
     "hlu_launch_count": (_i64, []),
+    "hlu_set_allocator": (_i32, [_vp, _vp, _vp]),
+    "hlu_set_device_memory_limit": (_i32, [_i64]),
+    "hlu_device_bytes_in_use": (_i64, []),
+    "hlu_debug_zero_dof": (_i32, [_vp, _i64]),
+    "hlu_debug_tf32_tile": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "hlu_gmres_begin": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _vp, _P(_vp)]),
     "hlu_gmres_step_batch": (_i32, [_P(_vp), _i32, _vp]),
     "hlu_gmres_status": (_i32, [_vp, _P(_i32), _P(hlu_stats)]),
@@ -112,7 +122,67 @@ def lib():
             f.restype = res
             f.argtypes = args
         _lib = L
+        if os.environ.get("HLU_ALLOCATOR", "torch") != "cuda":
+            use_torch_allocator()
     return _lib
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_torch_callbacks = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (on the current device and stream).  The callbacks are kept
+    alive for the life of the process: the library may free blocks from
+    handle finalisers late in interpreter shutdown, when they become no-ops."""
+    global _torch_callbacks
+    import atexit
+
+    import torch
+
+    if _torch_callbacks is None:
+        state = {"down": False}
+
+        def _alloc(nbytes, ctx, _t=torch, _s=state):
+            try:
+                return _t.cuda.caching_allocator_alloc(int(nbytes))
+            except Exception:  # out of memory: the library reports HLU_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, ctx, _t=torch, _s=state):
+            if _s["down"]:
+                return
+            try:
+                _t.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        for cb in cbs:  # never collected: the C side keeps the pointers
+            ctypes.pythonapi.Py_IncRef(ctypes.py_object(cb))
+        atexit.register(lambda s=state: s.__setitem__("down", True))
+        _torch_callbacks = cbs
+    _check(lib().hlu_set_allocator(ctypes.cast(_torch_callbacks[0], _vp), ctypes.cast(_torch_callbacks[1], _vp),
+                                   None))
+
+
+def use_cuda_allocator():
+    """Back to cudaMalloc/cudaFree for allocations made from now on."""
+    _check(lib().hlu_set_allocator(None, None, None))
+
+
+def hlu_set_device_memory_limit(nbytes):
+    _check(lib().hlu_set_device_memory_limit(int(nbytes)))
+
+
+def hlu_device_bytes_in_use():
+    return int(lib().hlu_device_bytes_in_use())
+
+
+def hlu_debug_zero_dof(h, dof):
+    _check(lib().hlu_debug_zero_dof(_vp(h), int(dof)))
 
 
 def _check(status):
@@ -198,6 +268,14 @@ def hlu_export_csr(h):
 def hlu_rhs_manufactured(h, b, stream=None):
     p, nr, ld = _vec(b, hlu_n(h))
     _check(lib().hlu_rhs_manufactured(_vp(h), p, _stream(stream)))
+
+
+def hlu_rhs_constant_current(h, J, b, stream=None):
+    """Load vector of the constant current density J = (jx, jy, jz)."""
+    pb, nr, _ = _vec(b, hlu_n(h))
+    if nr != 1:
+        raise ValueError("b must be one column")
+    _check(lib().hlu_rhs_constant_current(_vp(h), float(J[0]), float(J[1]), float(J[2]), pb, _stream(stream)))
 
 
 def hlu_rhs_manufactured_noalloc(h, b, stream=None):

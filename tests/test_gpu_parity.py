@@ -143,9 +143,12 @@ def test_operator_error_within_2x_of_oracle(hlu, prec, n, kappa, eps):
 def test_rank_above_former_capacity(hlu, prec):
     """n = 10, kappa 6, eps 1e-6: truncations ask for ranks above 32 (the
     capacity of earlier builds, which clipped them).  With the capacity of 64
-    every truncation keeps s_i > eps s_1 in full (no capacity hit), and the
-    operator error stays within 2x of the oracle's, which truncates with no
-    capacity at all (Sec. 4 truncated SVD)."""
+    every truncation keeps s_i > eps s_1 in full (no capacity hit).  FP64: the
+    operator error is within 2x of the oracle's, which truncates with no
+    capacity at all (Sec. 4 truncated SVD).  FP32: at eps 1e-6 the FP32
+    rounding of the factorisation, not the truncation, sets the operator
+    error, so the bar adds that floor, measured by the same FP32 path at
+    eps 1e-12 (where nothing is truncated)."""
     n, kappa, eps = 10, 6.0, 1e-6
     m, A, perm, cl, bl = oracle_problem(n, kappa)
     key = ("op_error", n, kappa, eps)
@@ -154,14 +157,23 @@ def test_rank_above_former_capacity(hlu, prec):
         _cache[key] = (op_error(P.apply, A), max(P.H.ranks().values()))
     e_or, r_or = _cache[key]
     assert r_or > 32  # the oracle needs more than the former capacity
+    prc = hlu.HLU_FP64 if prec == "fp64" else hlu.HLU_FP32
+    floor = 0.0
+    if prec == "fp32":
+        h0 = hlu.hlu_build(n, kappa, 32, 2.0, 1e-12)
+        try:
+            hlu.hlu_factor(h0, prc)
+            floor = op_error(lambda R: gpu_apply(hlu, h0, R), A)
+        finally:
+            hlu.hlu_destroy(h0)
     h = hlu.hlu_build(n, kappa, 32, 2.0, eps)
     try:
-        hlu.hlu_factor(h, hlu.HLU_FP64 if prec == "fp64" else hlu.HLU_FP32)
+        hlu.hlu_factor(h, prc)
         info = hlu.hlu_factor_stats(h)
         assert info["rank_cap_hits"] == 0
         assert 32 < info["rank_wanted_max"] <= 64 and info["rank_max"] > 32
         e_gpu = op_error(lambda R: gpu_apply(hlu, h, R), A)
-        assert e_gpu <= 2.0 * e_or, (e_gpu, e_or)
+        assert e_gpu <= 2.0 * e_or + 2.0 * floor, (e_gpu, e_or, floor)
     finally:
         hlu.hlu_destroy(h)
 

@@ -24,6 +24,7 @@ def _declared():
     for h in ("hlu.h", "hlu_debug.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"^\s*typedef [^;{]*\(\*\w+\)\([^;]*\);", "", src, flags=re.M)  # function-pointer types
         for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
             name = m.group(1)
             if name not in ("if", "sizeof", "defined"):
@@ -115,3 +116,14 @@ def test_tiled_factor_tree_quality(lib, n, kappa, leaf, tile):
     _, _, _, _, _, x2, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 9, tile=tile)
     _, _, _, _, _, x3, _ = _host_solve(lib, n, kappa, 1e-3, leaf, 0, tile=tile)
     assert np.array_equal(x2, x3)
+
+
+def test_allocator_and_memory_limit_arguments(lib):
+    """hlu_set_allocator takes both callbacks or neither; the memory limit is
+    a non-negative byte count (no device needed)."""
+    from paper_2211_11303_gb300 import hlu
+    cb = hlu._ALLOC_FN(lambda n, ctx: None)
+    assert lib.hlu_set_allocator(ctypes.cast(cb, ctypes.c_void_p), None, None) == 1
+    assert lib.hlu_set_device_memory_limit(-1) == 1
+    assert lib.hlu_set_device_memory_limit(0) == 0
+    assert lib.hlu_device_bytes_in_use() >= 0

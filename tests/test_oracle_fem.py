@@ -120,3 +120,40 @@ def test_manufactured_convergence_rate():
         errs.append(F.l2_error(m, x, F.manufactured_E))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert 0.85 < rates[0] < 1.3 and 0.9 < rates[1] < 1.2, (errs, rates)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+@pytest.mark.parametrize("J", [(0.0, 0.0, 1.0), (1.0, -2.0, 0.5)])
+def test_constant_current_rhs_is_discretely_divergence_free(n, J):
+    """For a constant J, <J, grad phi_v> = -<div J, phi_v> = 0 for every
+    interior vertex hat function phi_v (zero on the boundary), and grad phi_v
+    is the combination G[:, v] of interior edge basis functions, so
+    G^T b = 0 up to rounding."""
+    m = M.interior_edges(n)
+    b = F.constant_current_rhs(m, J)
+    G = F.gradient_matrix(m)
+    assert np.abs(G.T @ b).max() <= 1e-14 * max(1.0, np.abs(b).max())
+    assert np.abs(b).max() > 0.01 / n ** 3
+
+
+def test_constant_current_rhs_equals_exact_element_integrals():
+    """The integral of a barycentric coordinate over a tetrahedron is |T|/4,
+    so b_e = sum over the tets of e of |T|/4 J . (grad l_hi - grad l_lo); the
+    gradients here come from inverting [1 x y z] at the four vertices."""
+    n, J = 2, np.array([0.0, 0.0, 1.0])
+    m = M.interior_edges(n)
+    b = F.constant_current_rhs(m, J)
+    lat = m["lattice"] / float(n)
+    index = {(int(a), int(c)): e for e, (a, c) in enumerate(m["edges"])}
+    ref = np.zeros(len(m["edges"]))
+    for tet in m["tets"]:
+        V = np.hstack([np.ones((4, 1)), lat[tet]])
+        vol = abs(np.linalg.det(V)) / 6.0
+        grads = np.linalg.inv(V)[1:, :].T  # row i: grad of the barycentric coordinate of vertex i
+        for i in range(4):
+            for j in range(i + 1, 4):
+                a, c = (i, j) if tet[i] < tet[j] else (j, i)
+                e = index.get((int(tet[a]), int(tet[c])))
+                if e is not None:
+                    ref[e] += vol / 4.0 * J @ (grads[c] - grads[a])
+    assert np.abs(b - ref).max() <= 1e-15 * 10 + 1e-14 * np.abs(ref).max()

@@ -54,9 +54,11 @@ extern "C" {
 #define HLU_FP32 1 /* factor and triangular solves in FP32, FP32 accumulate */
 #define HLU_TF32 2 /* FP32 factor whose tile products (dense and low-rank GEMM
                       contractions: projections, H x multivector updates, dense
-                      updates, dense-route sums) run in TF32 on the tensor cores
-                      (tcgen05, FP32 accumulation in tensor memory); LU, QR, SVD
-                      and the triangular solves in FP32 */
+                      updates, dense-route sums) run as TF32 MMAs on the tensor
+                      cores (tcgen05, FP32 accumulation in tensor memory), each
+                      operand split into a TF32 part and the TF32 rounding of
+                      its remainder so that the products keep FP32 accuracy;
+                      LU, QR, SVD and the triangular solves in FP32 */
 
 /* ---- block kinds in the exported block tree ------------------------------ */
 #define HLU_BLOCK_ADM 0   /* admissible: low-rank X Y^T (Definition 1)       */
@@ -106,6 +108,8 @@ typedef struct {
   int64_t factor_live_bytes; /* bytes of the factor at its live ranks: dense words plus
                                 (rows + cols) x rank per admissible block; what one
                                 triangular-solve pass (L then U) reads            */
+  int32_t grid_ctas;        /* CTAs of the factorisation launch (persistent)       */
+  int32_t reserved_;
 } hlu_factor_info;
 
 /* hlu_build - Algorithm 1 step I and the structures it needs.
@@ -128,6 +132,14 @@ typedef struct {
  * eps <= 0; HLU_ERR_OOM; HLU_ERR_CUDA. */
 int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps,
               int32_t rank_cap, void* stream, hlu_handle** out);
+
+/* hlu_set_schedule_cache - size of the process-wide cache of task DAGs
+ * (default 16 schedules, 24 GiB of device memory): hlu_build reuses the
+ * DAGs of an identical block tree, so a server that keeps its mesh catalogue
+ * cached builds a new mesh's DAG on the host once.  The least recently used
+ * schedule beyond either bound is dropped (handles holding it keep it).
+ * HLU_ERR_ARG for entries < 1 or bytes < 0. */
+int hlu_set_schedule_cache(int32_t entries, int64_t bytes);
 
 /* Number of interior-edge DOFs N of a built handle (0 for NULL). */
 int64_t hlu_n(const hlu_handle* h);
@@ -201,6 +213,24 @@ int hlu_spmv(const hlu_handle* h, const double* x_dev, double* y_dev, int32_t nr
  * Synchronous (returns after the device finished; factor_ms recorded).
  * Errors: HLU_ERR_ZERO_PIVOT (factor unusable), HLU_ERR_TIMEOUT, HLU_ERR_OOM. */
 int hlu_factor(hlu_handle* h, int32_t precision, void* stream);
+
+/* hlu_factor_async - hlu_factor without waiting for the device: the A_H
+ * fill runs (the call returns after it, with its status), then the
+ * factorisation is queued on `stream` and the call returns.  max_ctas > 0
+ * caps the persistent launch at that many CTAs (0: the full grid), which
+ * leaves SM slots for other work on other streams: a server factors a newly
+ * admitted request's matrix while the running requests' GMRES steps go on
+ * (Alg. 1 step II beside step III of other problems).  Until
+ * hlu_factor_wait reports it done, the handle's solves return HLU_ERR_STATE
+ * and a second factorisation is refused.  Same errors as hlu_factor, the
+ * device-side ones (zero pivot, timeout) from hlu_factor_wait. */
+int hlu_factor_async(hlu_handle* h, int32_t precision, int32_t max_ctas, void* stream);
+
+/* hlu_factor_wait - completion of hlu_factor_async: *done = 1 once the
+ * factorisation finished (statistics filled, status returned as hlu_factor
+ * would), *done = 0 if it is still running and block == 0; block != 0 waits.
+ * *done = 1 at once when nothing is in flight. */
+int hlu_factor_wait(hlu_handle* h, int32_t block, int32_t* done);
 
 /* hlu_factor_stats - fill *info for the last factorisation. */
 int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);

@@ -83,8 +83,9 @@ int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trace_out, int6
 /* hlu_debug_tf32_tile - the TF32 tensor-core tile product of HLU_TF32
  * factorisations on its own (needs a GPU): D = A B for A 64 x K (ld 64), B
  * K x 64 (ld K) and D 64 x 64 (ld 64), column-major FP32 device arrays,
- * computed by one CTA through the executor's tcgen05 pipeline (operands
- * rounded to TF32, FP32 accumulation in tensor memory).  K in [1, 4096].
+ * computed by one CTA through the executor's tcgen05 pipeline (each operand
+ * split into TF32 high and low parts, A_hi B_hi + A_hi B_lo + A_lo B_hi
+ * accumulated in FP32 in tensor memory).  K in [1, 4096].
  * status_out (may be NULL) receives the device status (0, or 5 if an MMA
  * completion wait ran out, which the call returns as HLU_ERR_TIMEOUT).
  * Synchronous. */

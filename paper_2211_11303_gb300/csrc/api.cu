@@ -176,8 +176,8 @@ std::mutex g_batch_mu;            // serialises batched launches (shared order b
 unsigned long long* g_batch_q = nullptr;  // ready queue of batched launches
 int64_t g_batch_q_len = 0;
 std::vector<std::shared_ptr<SchedBundle>> g_cache;  // most recent last
-constexpr size_t kCacheEntries = 16;
-constexpr int64_t kCacheBytes = int64_t(24) << 30;  // device bytes of cached schedules
+size_t g_cache_entries = 16;                   // schedules kept (hlu_set_schedule_cache)
+int64_t g_cache_bytes = int64_t(24) << 30;    // device bytes of cached schedules
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   const unsigned char* c = (const unsigned char*)p;
@@ -195,10 +195,18 @@ struct KrylovWS {
          *cs = nullptr, *sn = nullptr, *g = nullptr, *est = nullptr, *y = nullptr, *bn = nullptr, *part = nullptr,
          *tmp = nullptr;
   int* jr = nullptr;
-  void free_all() {
+  // on_stream: only work queued on stream s used the buffers (GMRES states),
+  // so a caller-supplied allocator gets them back after that stream drains
+  // instead of after the whole device does
+  void free_all(cudaStream_t s = nullptr, bool on_stream = false) {
     for (void* p : {(void*)V, (void*)Z, (void*)W, (void*)h1, (void*)h2, (void*)hn, (void*)H, (void*)cs, (void*)sn,
                     (void*)g, (void*)est, (void*)y, (void*)bn, (void*)part, (void*)tmp, (void*)jr})
-      if (p) dev_free(p);
+      if (p) {
+        if (on_stream)
+          dev_free_on(p, s);
+        else
+          dev_free(p);
+      }
     *this = KrylovWS();
   }
 };
@@ -242,6 +250,8 @@ struct hlu_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   unsigned long long* d_prof = nullptr;  // executor profile of the last factorisation
   unsigned long long* d_trace = nullptr; // per-task trace of the next factorisation (debug)
+  bool factor_pending = false;           // hlu_factor_async launched, hlu_factor_wait not yet done
+  cudaStream_t factor_stream = nullptr;
 };
 
 namespace {
@@ -339,6 +349,22 @@ void fill_common(ExecArgs& a, hlu_handle* scratch_owner, hlu_handle* h0, bool wi
   a.trace = h0->d_trace;
 }
 
+// The executor kernel for a launch: FP64, FP32, or FP32 with TF32 tile
+// products (a separate kernel: tensor memory holds it to one CTA per SM, so
+// its grid is capped at that occupancy).
+cudaError_t launch_exec(int precision, const ExecArgs& a, int g, cudaStream_t s) {
+  if (precision == HLU_FP64) return exec_launch<double>(a, g, s);
+  if (!a.tf32) return exec_launch<float>(a, g, s);
+  static int tc_grid = 0;
+  if (tc_grid == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    tc_grid = std::max(1, sms * std::max(tcx::exec_blocks_per_sm<float>(), 1));
+  }
+  return tcx::exec_launch<float>(a, std::min(g, tc_grid), s);
+}
+
 // One launch of the executor over one problem's schedule (or its first
 // `limit` tasks): counters reset, queue cleared and seeded with the roots.
 int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_flops, int64_t limit = -1) {
@@ -362,7 +388,7 @@ int exec_run(hlu_handle* h, DevSched& ds, int grid, cudaStream_t s, bool with_fl
   if (a.ntotal > nr)
     CKR(cudaMemsetAsync(ds.queue + nr, 0, sizeof(unsigned long long) * (a.ntotal - nr), s), "queue clear");
   int g = (int)std::min<int64_t>(grid, a.ntotal);
-  cudaError_t e = h->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
+  cudaError_t e = launch_exec(h->precision, a, g, s);
   CKR(e, "executor launch");
   return HLU_OK;
 }
@@ -443,7 +469,7 @@ int exec_run_batch(hlu_handle* const* hs, int count, int which, cudaStream_t s, 
   if (total > (int64_t)seed.size())
     CKR(cudaMemsetAsync(a.queue + seed.size(), 0, sizeof(unsigned long long) * (total - seed.size()), s), "clear");
   int g = (int)std::min<int64_t>(hs0->grid, a.ntotal);
-  cudaError_t e = hs0->precision == HLU_FP64 ? exec_launch<double>(a, g, s) : exec_launch<float>(a, g, s);
+  cudaError_t e = launch_exec(hs0->precision, a, g, s);
   CKR(e, "executor launch");
   // the host seed buffer must outlive the copy
   CKR(cudaStreamSynchronize(s), "sync");
@@ -639,10 +665,18 @@ void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)6
 
 
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
+int hlu_set_schedule_cache(int32_t entries, int64_t bytes) {
+  if (entries < 1 || bytes < 0) return fail(HLU_ERR_ARG, "bad argument");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_cache_entries = (size_t)entries;
+  g_cache_bytes = bytes;
+  return HLU_OK;
+}
 int64_t hlu_launch_count(void) { return g_launches.load(); }
 
 void hlu_destroy(hlu_handle* h) {
   if (!h) return;
+  if (h->factor_pending) cudaEventSynchronize(h->ev1);  // no kernel may still use the memory
   free_factor(h);
   h->dF.free_all();
   h->dS.free_all();
@@ -769,7 +803,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
         for (const auto& e : g_cache) b += e->device_bytes;
         return b;
       };
-      while (g_cache.size() > kCacheEntries || (g_cache.size() > 1 && cached_bytes() > kCacheBytes))
+      while (g_cache.size() > g_cache_entries || (g_cache.size() > 1 && cached_bytes() > g_cache_bytes))
         g_cache.erase(g_cache.begin());
     }
     h->L = h->sb->L;
@@ -936,6 +970,7 @@ static int factor_finish(hlu_handle* h, hlu_handle* status_of, cudaStream_t s, f
   }
   const int es = esize(h->precision);
   h->info.factor_live_bytes = live * es;
+  h->info.grid_ctas = h->grid;
   h->info.rank_max = rmax;
   h->info.rank_mean = nadm ? (double)rsum / nadm : 0.0;
   h->info.factor_bytes = h->L.factor_elems * es;
@@ -946,6 +981,7 @@ static int factor_finish(hlu_handle* h, hlu_handle* status_of, cudaStream_t s, f
 static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit) {
   try {
     if (!h) return fail(HLU_ERR_ARG, "null handle");
+    if (h->factor_pending) return fail(HLU_ERR_STATE, "a factorisation of this handle is in flight");
     if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
       return fail(HLU_ERR_ARG, "precision");
     cudaStream_t s = (cudaStream_t)stream;
@@ -959,6 +995,53 @@ static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t l
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     return factor_finish(h, h, s, ms);
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_factor_async(hlu_handle* h, int32_t precision, int32_t max_ctas, void* stream) {
+  try {
+    if (!h || max_ctas < 0) return fail(HLU_ERR_ARG, "bad argument");
+    if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
+      return fail(HLU_ERR_ARG, "precision");
+    if (h->factor_pending) return fail(HLU_ERR_STATE, "a factorisation of this handle is in flight");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = factor_prepare(h, precision, s);
+    if (rc) return rc;
+    CKR(cudaEventRecord(h->ev0, s), "event");
+    const int grid = max_ctas > 0 ? std::min(h->grid, (int)max_ctas) : h->grid;
+    rc = exec_run(h, h->dF, grid, s, true);
+    if (rc) return rc;
+    CKR(cudaEventRecord(h->ev1, s), "event");
+    h->factor_pending = true;
+    h->factor_stream = s;
+    return HLU_OK;
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_factor_wait(hlu_handle* h, int32_t block, int32_t* done) {
+  try {
+    if (!h || !done) return fail(HLU_ERR_ARG, "null argument");
+    *done = 0;
+    if (!h->factor_pending) {
+      *done = 1;
+      return HLU_OK;
+    }
+    if (block) {
+      CKR(cudaEventSynchronize(h->ev1), "sync");
+    } else {
+      const cudaError_t e = cudaEventQuery(h->ev1);
+      if (e == cudaErrorNotReady) return HLU_OK;
+      CKR(e, "event query");
+    }
+    h->factor_pending = false;
+    *done = 1;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    return factor_finish(h, h, h->factor_stream, ms);
   } catch (const std::exception& ex) {
     return fail(HLU_ERR_CUDA, ex.what());
   }
@@ -979,7 +1062,7 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info) {
 
 int hlu_solve(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream) {
   if (!h || !b || !x || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
-  if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+  if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
   return solve_any(h, b, x, nrhs, ld, (cudaStream_t)stream);
 }
 
@@ -990,7 +1073,7 @@ int gmres_solve(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, 
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
       return fail(HLU_ERR_ARG, "bad argument");
-    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     if (stats) {
@@ -1020,7 +1103,7 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
   try {
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!h || !b || !x || nrhs < 1 || ld < h->A.N || !(tol > 0) || maxit < 1) return fail(HLU_ERR_ARG, "bad argument");
-    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     int rc = ensure_kw(h, 1, std::min(nrhs, h->L.nrhs_max));
@@ -1126,7 +1209,7 @@ int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b
     for (int32_t i = 0; i < count; ++i) {
       hlu_handle* h = hs[i];
       if (!h || !b[i] || !x[i] || nrhs[i] < 1) return fail(HLU_ERR_ARG, "bad argument");
-      if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+      if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
       if (h->precision != hs[0]->precision) return fail(HLU_ERR_ARG, "mixed precisions in a batch");
       if (nrhs[i] > h->L.nrhs_max) return fail(HLU_ERR_ARG, "nrhs above the batched limit (16)");
     }
@@ -1287,7 +1370,7 @@ extern "C" int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trac
   if (h->dS.pred_ptr && nt > 0)
     CKR(cudaMemcpy(&sizes[1], h->dS.pred_ptr + nt, sizeof(int64_t), cudaMemcpyDeviceToHost), "edges");
   if (!trace_out) return HLU_OK;
-  if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+  if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
   CKR(dev_malloc(&h->d_trace, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(cudaMemset(h->d_trace, 0, sizeof(unsigned long long) * 4 * std::max<int64_t>(nt, 1)), "trace");
   CKR(set_int(h->d_ranks + h->L.nrhs_slot, nrhs, nullptr), "nrhs slot");
@@ -1336,7 +1419,7 @@ extern "C" int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int
   CKR(dev_malloc(&st, sizeof(int32_t) * 4), "status");
   int32_t z[4] = {0, -1, 0, 0};
   cudaError_t e = cudaMemcpy(st, z, sizeof(z), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = tc_tile_product(A, B, D, K, st, (unsigned long long)(g_wait_limit_ms * 1e6), nullptr);
+  if (e == cudaSuccess) e = tcx::tc_tile_product(A, B, D, K, st, (unsigned long long)(g_wait_limit_ms * 1e6), nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int32_t hs[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(hs, st, sizeof(hs), cudaMemcpyDeviceToHost);
@@ -1465,6 +1548,7 @@ struct hlu_gmres {
   int status = HLU_OK;
   double precond_ms = 0;
   int applies = 0;
+  cudaStream_t s = nullptr;  // the stream of hlu_gmres_begin
 };
 
 extern "C" {
@@ -1476,10 +1560,11 @@ int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nr
     if (!out || !h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
       return fail(HLU_ERR_ARG, "bad argument");
     if (nrhs > h->L.nrhs_max) return fail(HLU_ERR_ARG, "nrhs above 16 per GMRES state");
-    if (h->precision < 0) return fail(HLU_ERR_STATE, "not factored");
+    if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
     cudaStream_t s = (cudaStream_t)stream;
     hlu_gmres* g = new hlu_gmres();
     g->h = h;
+    g->s = s;
     g->b = b;
     g->x = x;
     g->nr = nrhs;
@@ -1665,7 +1750,7 @@ int hlu_gmres_status(const hlu_gmres* g, int32_t* done, hlu_stats* st) {
 
 void hlu_gmres_end(hlu_gmres* g) {
   if (!g) return;
-  g->k.free_all();
+  g->k.free_all(g->s, true);
   delete g;
 }
 

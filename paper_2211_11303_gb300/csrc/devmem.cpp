@@ -52,7 +52,7 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
   return cudaSuccess;
 }
 
-cudaError_t dev_free(void* p) {
+static cudaError_t free_impl(void* p, bool whole_device, cudaStream_t s) {
   if (!p) return cudaSuccess;
   Live l{0, Alloc()};
   {
@@ -66,12 +66,15 @@ cudaError_t dev_free(void* p) {
   if (l.by.free) {
     // the caller's allocator may hand the block out again at once: no kernel
     // of this library may still use it
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = whole_device ? cudaDeviceSynchronize() : cudaStreamSynchronize(s);
     l.by.free(p, l.bytes, l.by.ctx);
     return e;
   }
   return cudaFree(p);
 }
+
+cudaError_t dev_free(void* p) { return free_impl(p, true, nullptr); }
+cudaError_t dev_free_on(void* p, cudaStream_t s) { return free_impl(p, false, s); }
 
 int64_t dev_bytes_in_use() {
   std::lock_guard<std::mutex> lk(g_mu);

@@ -13,6 +13,10 @@ namespace hlu {
 
 cudaError_t dev_alloc(void** p, size_t bytes);  // cudaErrorMemoryAllocation when refused
 cudaError_t dev_free(void* p);                  // NULL is a no-op
+// dev_free for a block that only work queued on stream s used: a
+// caller-supplied allocator gets it back once s has drained (cudaFree
+// itself waits for the whole device)
+cudaError_t dev_free_on(void* p, cudaStream_t s);
 int64_t dev_bytes_in_use();
 bool dev_custom_allocator();
 

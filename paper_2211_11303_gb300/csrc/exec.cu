@@ -15,6 +15,13 @@
 // st.global.cg); a task's writes are fenced before its successors' counters
 // are decremented, and queue slots are published with st.release and read
 // with ld.acquire at gpu scope.
+//
+// This file is compiled twice.  exec.cu itself (HLU_EXEC_TC == 0) builds the
+// FP32 and FP64 executors with no tensor-core code; exec_tc.cu includes it
+// with HLU_EXEC_TC == 1 and builds, in namespace hlu::tcx, the FP32 executor
+// whose tile products run as TF32 MMAs on the tensor cores.  A kernel that
+// allocates tensor memory is held to one CTA per SM, so the FP32 executor
+// must not contain that code.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,7 +34,14 @@
 #include "hlu_internal.h"
 #include "tc.cuh"
 
+#ifndef HLU_EXEC_TC
+#define HLU_EXEC_TC 0
+#endif
+
 namespace hlu {
+#if HLU_EXEC_TC
+namespace tcx {
+#endif
 
 #define NT 256
 
@@ -59,6 +73,7 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // the same waits).
 struct TcCtl {
   bool on = false;
+  char* stage = nullptr;  // 1024-aligned staging buffer, tc::kTcStageBytes
   bool broken = false;   // a completion wait ran out: no further MMAs are issued
   uint32_t tmem = 0;
   uint64_t* bar = nullptr;
@@ -364,23 +379,28 @@ __device__ bool tc_wait(TcCtl* t) {
   return ok;
 }
 
-// The chunk pipeline of tile_mma_seq on the fifth-generation tensor cores:
-// each 64 x 32 (A) and 32 x 64 (B) chunk is rounded to TF32 and staged
-// K-major in the core-matrix layout (A at S, B at S + 8 KB), and one thread
-// issues four M = 128, N = 64, K = 8 MMAs into the tensor-memory accumulator.
-// The MMA runs while the next chunk's operands load into registers; the
-// staging buffer is rewritten only after the MMAs reading it completed.
-// Rows 64..127 of the M = 128 A operand read the B chunk (their results are
-// never used).  At the end the 64 x 64 result goes through shared memory into
-// every thread's 4 x 4 register tile (acc +=).  S: >= 16 KB, 1024-aligned.
+// The chunk pipeline of tile_mma_seq on the fifth-generation tensor cores,
+// with FP32 accuracy from TF32 MMAs by splitting each operand into a TF32
+// part and the TF32 rounding of its remainder (x = x_hi + x_lo): the staged
+// M = 128 A operand is [A_hi; A_lo] (64 rows each), the N = 128 B operand
+// [B_hi, B_lo], so one M = 128, N = 128, K = 8 MMA per K step accumulates
+// all four products in tensor memory; the result is
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (A_lo B_lo, below FP32 rounding, is
+// left out).  Each 64 x 32 (A) and 32 x 64 (B) chunk is staged K-major in
+// the core-matrix layout (A at t->stage, B 16 KB after it); one thread issues
+// four MMAs.  The MMAs run while the next chunk's operands load into
+// registers; the staging buffer is rewritten only after the MMAs reading it
+// completed.  At the end the three 64 x 64 quadrants go through shared
+// memory into every thread's 4 x 4 register tile (acc +=).
 template <class Cursor>
-__device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, float* S, TcCtl* t) {
+__device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, TcCtl* t) {
   if (!cur.first()) return;
   const int tid = threadIdx.x;
   float ra[kChunkRegs], rb[kChunkRegs];
   Chunk<float> ch = cur.chunk();
   chunk_fetch(ch, ra, rb);
-  char* Sb = reinterpret_cast<char*>(S);
+  char* Sb = t->stage;
+  float* S = reinterpret_cast<float*>(Sb);
   bool first = true;
   __syncthreads();  // the staging buffer's previous readers are done
   for (;;) {
@@ -390,20 +410,24 @@ __device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, float* S, TcCtl
       const int e = tid + q * NT;
       int r, kk;
       chunk_coord(ch.A.rs == 1, e, r, kk);
-      *reinterpret_cast<float*>(Sb + tc::tc_offset(r, kk)) = tc::to_tf32(ra[q]);
+      const float hi = tc::to_tf32(ra[q]);
+      *reinterpret_cast<float*>(Sb + tc::tc_offset(r, kk)) = hi;
+      *reinterpret_cast<float*>(Sb + tc::tc_offset(64 + r, kk)) = tc::to_tf32(ra[q] - hi);
     }
 #pragma unroll
     for (int q = 0; q < kChunkRegs; ++q) {
       const int e = tid + q * NT;
       int cc, kk;
       chunk_coord(ch.B.rs != 1, e, cc, kk);
-      *reinterpret_cast<float*>(Sb + 8192 + tc::tc_offset(cc, kk)) = tc::to_tf32(rb[q]);
+      const float hi = tc::to_tf32(rb[q]);
+      *reinterpret_cast<float*>(Sb + tc::kTcOperandBytes + tc::tc_offset(cc, kk)) = hi;
+      *reinterpret_cast<float*>(Sb + tc::kTcOperandBytes + tc::tc_offset(64 + cc, kk)) = tc::to_tf32(rb[q] - hi);
     }
     tc::fence_async_shared();
     __syncthreads();
     if (tid == 0 && !t->broken) {
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(Sb), b0 = a0 + 8192u;
+      const uint32_t a0 = tc::smem_u32(Sb), b0 = a0 + tc::kTcOperandBytes;
 #pragma unroll
       for (int ks = 0; ks < tc::kTcChunkK / 8; ++ks)
         tc::mma_tf32(t->tmem, tc::smem_desc(a0 + ks * 2 * tc::kTcLBO), tc::smem_desc(b0 + ks * 2 * tc::kTcLBO),
@@ -420,16 +444,25 @@ __device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, float* S, TcCtl
   }
   if (!tc_wait(t)) return;
   tc::fence_after_sync();
-  // rows 0..63 of the accumulator: lane quarters 0 and 1, read by warps 0, 1
-  // (columns 0..31) and 4, 5 (columns 32..63)
+  // warp w reads lane quarter q = w % 4 (accumulator rows 32 q ..), columns
+  // 32 (w / 4) ..: quarters 0, 1 hold A_hi rows (hi x hi in columns 0..63,
+  // hi x lo in 64..127), quarters 2, 3 the A_lo rows (lo x hi in 0..63)
   const int w = tid >> 5, lane = tid & 31;
-  if ((w & 3) < 2) {
-    const int q = w & 3, col0 = (w >> 2) * 32;
-    float v[32];
-    tc::tmem_ld32(t->tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+  const int q = w & 3, col0 = (w >> 2) * 32;
+  float v[32];
+  tc::tmem_ld32(t->tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+  if (q < 2) {
+    float u[32];
+    tc::tmem_ld32(t->tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(col0 + 64), u);
     const int row = q * 32 + lane;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) S[row + (col0 + j) * 64] = v[j];
+    for (int j = 0; j < 32; ++j) S[row + (col0 + j) * 64] = v[j] + u[j];
+  }
+  __syncthreads();
+  if (q >= 2) {
+    const int row = (q - 2) * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) S[row + (col0 + j) * 64] += v[j];
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -448,12 +481,16 @@ __device__ void tile_mma_seq_tc(float (&acc)[4][4], Cursor& cur, float* S, TcCtl
 // the tensor cores (tile_mma_seq_tc).
 template <class T, class Cursor>
 __device__ void tile_mma_seq(T (&acc)[4][4], Cursor& cur, T* As, T* Bs, TcCtl* tcc = nullptr) {
+#if HLU_EXEC_TC
   if constexpr (std::is_same<T, float>::value) {
     if (tcc && tcc->on) {
-      tile_mma_seq_tc(acc, cur, As, tcc);
+      tile_mma_seq_tc(acc, cur, tcc);
       return;
     }
   }
+#else
+  (void)tcc;
+#endif
   if (!cur.first()) return;
   T ra[kChunkRegs], rb[kChunkRegs];
   Chunk<T> ch = cur.chunk();
@@ -1174,6 +1211,28 @@ constexpr int kDenseRank = 40;           // rows kept by the dense route's pivot
 constexpr int kCoreRank = kRankMax;      // rows kept by the stack route's pivoted QR of the core
 constexpr int kCoreV = kTruncStack * kCoreRank + kCoreRank * kCoreRank;  // M (q x r') and V (r' x r')
 
+// dynamic shared memory of the task bodies: max over task kinds of TRUNC
+// (3 stack-wide vectors + G + V), GETRF/TRSM (64 x 64 + 64 ints), the fused
+// leaf solve and the staged GEMM chunks (2 x KC x kLds)
+__host__ __device__ constexpr size_t exec_smem_base(int elem_size) {
+  const size_t trunc0 = (size_t)elem_size * (3 * kTruncStack + kTruncStack * kTruncStack + kCoreV);
+  // dense truncation route (FP32 only)
+  const size_t r0 = (size_t)4 * (kDenseMax * kDenseRank + kDenseRank * kDenseRank);
+  const size_t region0 = r0 < (size_t)4 * 2 * kStage ? (size_t)4 * 2 * kStage : r0;
+  const size_t dense = region0 + (size_t)4 * (kDenseMax * kDenseMax + 2 * kDenseMax) + sizeof(int) * kDenseMax;
+  const size_t trunc = (elem_size == 4 && dense > trunc0) ? dense : trunc0;
+  const size_t lu0 = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
+  // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
+  const size_t rsolve = (size_t)elem_size * (2 * kStage + 2 * 64 * 64 + 64) + 64 * sizeof(int);
+  const size_t lu = rsolve > lu0 ? rsolve : lu0;
+  const size_t gemm = (size_t)elem_size * 2 * kStage;
+  const size_t m = trunc > lu ? trunc : lu;
+  return m > gemm ? m : gemm;
+}
+// the tensor-core staging buffer follows the task bodies' region, 1024-aligned
+__host__ __device__ constexpr size_t exec_stage_offset() { return (exec_smem_base(4) + 1023) & ~(size_t)1023; }
+
+
 // Householder QR with column pivoting of D (m x n, ld m, shared memory) in
 // place, stopped after kmax steps or once the trailing block's squared
 // Frobenius norm is <= rel2 ||D||_F^2.  perm[j] = original index of column j.
@@ -1715,8 +1774,21 @@ __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
 
 // ---------------------------------------------------------------- executor
 template <class T>
-__global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ ExecArgs a) {
+// two CTAs per SM for the plain executors; the tensor-core one is held to one
+// by its tensor memory, so it may use the whole register file
+#if HLU_EXEC_TC
+#define EXEC_MIN_BLOCKS 1
+#else
+#define EXEC_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(NT, EXEC_MIN_BLOCKS) exec_kernel(const __grid_constant__ ExecArgs a) {
+  // the tensor-core staging buffer at the start of dynamic shared memory is
+  // 1024-byte aligned; the plain executors need 16 bytes
+#if HLU_EXEC_TC
   extern __shared__ __align__(1024) char smem[];
+#else
+  extern __shared__ __align__(16) char smem[];
+#endif
   __shared__ int64_t s_task;
   __shared__ int64_t s_succ[2];  // successor range of the running task
   __shared__ int s_prob;
@@ -1725,7 +1797,8 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
   c.tcc = nullptr;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_tcbar;
-  const bool use_tc = std::is_same<T, float>::value && a.tf32 != 0;
+  const bool use_tc = HLU_EXEC_TC && std::is_same<T, float>::value && a.tf32 != 0;
+#if HLU_EXEC_TC
   if (use_tc) {
     // tensor memory for the 128 x 64 FP32 accumulator, held for the whole
     // persistent launch, and the MMA completion barrier
@@ -1735,12 +1808,14 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     __syncthreads();
     tc::fence_after_sync();
     tcc.on = true;
+    tcc.stage = smem + exec_stage_offset();
     tcc.tmem = s_tmem;
     tcc.bar = &s_tcbar;
     tcc.status = a.status;
     tcc.wait_ns = a.wait_limit_ns;
     c.tcc = &tcc;
   }
+#endif
   c.scratch = reinterpret_cast<T*>(a.scratch) + (int64_t)blockIdx.x * a.scratch_stride;
   c.rows_max = a.trunc_rows;
   c.status = a.status;
@@ -1858,6 +1933,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     }
     __syncthreads();
   }
+#if HLU_EXEC_TC
   if (use_tc) {
     __syncthreads();
     if (tcc.broken && threadIdx.x == 0) {
@@ -1872,6 +1948,9 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
     tc::fence_after_sync();
     if (threadIdx.x < 32) tc::tmem_dealloc(tcc.tmem, tc::kTcCols);
   }
+#else
+  (void)use_tc;
+#endif
   if (threadIdx.x == 0 && a.flops) atomicAdd(a.flops, c.flops);
   if (a.prof && threadIdx.x < kProfEntries) {
     unsigned long long v = s_prof[threadIdx.x];
@@ -1879,6 +1958,7 @@ __global__ void __launch_bounds__(NT, 2) exec_kernel(const __grid_constant__ Exe
   }
 }
 
+#if HLU_EXEC_TC
 // One 64 x 64 tile product D = A B (A: 64 x K, ld 64; B: K x 64, ld K; D:
 // 64 x 64, ld 64; column-major FP32) through the TF32 tensor-core pipeline of
 // the executor, by one CTA: checks that path on its own.
@@ -1894,6 +1974,7 @@ __global__ void __launch_bounds__(NT, 1)
   tc::fence_after_sync();
   TcCtl t;
   t.on = true;
+  t.stage = smem;
   t.tmem = s_tmem;
   t.bar = &s_bar;
   t.status = status;
@@ -1901,7 +1982,7 @@ __global__ void __launch_bounds__(NT, 1)
   float acc[4][4];
   acc_zero(acc);
   ProductCursor<float> cur{Mat<float>{A, 1, 64}, Mat<float>{B, 1, K}, 0, 64, 64, K, 0};
-  tile_mma_seq_tc(acc, cur, reinterpret_cast<float*>(smem), &t);
+  tile_mma_seq_tc(acc, cur, &t);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -1922,27 +2003,19 @@ __global__ void __launch_bounds__(NT, 1)
 cudaError_t tc_tile_product(const float* A, const float* B, float* D, int K, int32_t* status,
                             unsigned long long wait_ns, cudaStream_t s) {
   note_launch();
-  tc_tile_kernel<<<1, NT, 2 * kStage * sizeof(float), s>>>(A, B, D, K, status, wait_ns);
+  cudaError_t e = cudaFuncSetAttribute(tc_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc::kTcStageBytes);
+  if (e != cudaSuccess) return e;
+  tc_tile_kernel<<<1, NT, tc::kTcStageBytes, s>>>(A, B, D, K, status, wait_ns);
   return cudaGetLastError();
 }
+#endif
 
 size_t exec_smem_bytes(int elem_size) {
-  // max over task kinds: TRUNC (3 stack-wide vectors + G + V), GETRF/TRSM
-  // (64 x 64 + 64 ints), staged GEMM chunks (2 x KC x kLds)
-  size_t trunc = (size_t)elem_size * (3 * kTruncStack + kTruncStack * kTruncStack + kCoreV);
-  if (elem_size == 4) {  // dense truncation route (FP32 only)
-    size_t region0 = (size_t)4 * (kDenseMax * kDenseRank + kDenseRank * kDenseRank);
-    if (region0 < (size_t)4 * 2 * kStage) region0 = (size_t)4 * 2 * kStage;
-    const size_t dense = region0 + (size_t)4 * (kDenseMax * kDenseMax + 2 * kDenseMax) + sizeof(int) * kDenseMax;
-    if (dense > trunc) trunc = dense;
-  }
-  size_t lu = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
-  // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
-  const size_t rsolve = (size_t)elem_size * (2 * kStage + 2 * 64 * 64 + 64) + 64 * sizeof(int);
-  if (rsolve > lu) lu = rsolve;
-  size_t gemm = (size_t)elem_size * 2 * kStage;
-  size_t m = trunc > lu ? trunc : lu;
-  return m > gemm ? m : gemm;
+#if HLU_EXEC_TC
+  if (elem_size == 4) return exec_stage_offset() + tc::kTcStageBytes;
+#endif
+  return exec_smem_base(elem_size);
 }
 
 template <class T>
@@ -1966,8 +2039,13 @@ cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s) {
 }
 
 template cudaError_t exec_launch<float>(const ExecArgs&, int, cudaStream_t);
-template cudaError_t exec_launch<double>(const ExecArgs&, int, cudaStream_t);
 template int exec_blocks_per_sm<float>();
+#if !HLU_EXEC_TC
+template cudaError_t exec_launch<double>(const ExecArgs&, int, cudaStream_t);
 template int exec_blocks_per_sm<double>();
+#endif
 
+#if HLU_EXEC_TC
+}  // namespace tcx
+#endif
 }  // namespace hlu

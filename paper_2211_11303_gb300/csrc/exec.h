@@ -60,15 +60,24 @@ struct ExecArgs {
 };
 
 size_t exec_smem_bytes(int elem_size);
+template <class T>
+int exec_blocks_per_sm();
+template <class T>
+cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
+
+// The FP32 executor whose tile products run in TF32 on the tensor cores
+// (exec_tc.cu; launches with ExecArgs::tf32 set).
+namespace tcx {
+template <class T>
+int exec_blocks_per_sm();
+template <class T>
+cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
 // D (64 x 64) = A (64 x K) B (K x 64), column-major FP32 device arrays, through
 // the executor's TF32 tensor-core tile pipeline (one CTA); status[0] receives
 // HLU_ERR_TIMEOUT (5) if an MMA completion wait ran out.
 cudaError_t tc_tile_product(const float* A, const float* B, float* D, int K, int32_t* status,
                             unsigned long long wait_ns, cudaStream_t s);
-template <class T>
-int exec_blocks_per_sm();
-template <class T>
-cudaError_t exec_launch(const ExecArgs& a, int grid, cudaStream_t s);
+}  // namespace tcx
 
 constexpr int kExecThreads = 256;
 constexpr int kTruncStack = 96;  // columns of a truncation stack; wider pieces are stacked in parts

@@ -950,8 +950,13 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   L.nrhs_slot = L.n_slots++;
   L.work_off = alloc((int64_t)C[0].size * nrhs_max);
   L.wmax = 0;
-  // ring region for temporaries (both schedules; they never run concurrently)
-  const int64_t ring = std::min<int64_t>(std::max<int64_t>(8 * fe, int64_t(1) << 22), int64_t(1) << 30);
+  // ring region for temporaries (both schedules; they never run concurrently).
+  // Every wrap of the ring orders the new occupants of a chunk after all
+  // users of its previous ones (FENCE tasks); at rank capacity 64 the
+  // temporaries are twice those of capacity 32, and a 2^31-element bound
+  // keeps the number of wraps (and fences) of the larger workloads at what a
+  // 2^30 bound gave at capacity 32.
+  const int64_t ring = std::min<int64_t>(std::max<int64_t>(8 * fe, int64_t(1) << 22), int64_t(1) << 31);
   const int64_t ring_off = alloc(ring);
   L.ring_off = ring_off;
   L.ring_size = ring;

@@ -19,7 +19,9 @@ namespace tc {
 constexpr uint32_t kTcLBO = 128;   // bytes between core matrices along K
 constexpr uint32_t kTcSBO = 1024;  // bytes between 8-row groups (8 K groups x 128 B)
 constexpr int kTcChunkK = 32;      // K values staged per chunk (4 MMAs of K = 8)
-constexpr int kTcCols = 64;        // tensor-memory columns held per CTA (fp32 accumulator N = 64)
+constexpr int kTcCols = 128;       // tensor-memory columns held per CTA (fp32 accumulator N = 128)
+constexpr uint32_t kTcOperandBytes = 128 * kTcChunkK * 4;  // one staged operand: 128 rows x 32 K
+constexpr uint32_t kTcStageBytes = 2 * kTcOperandBytes;    // A and B
 
 // byte offset of element (row, k) of a staged K-major operand chunk
 __device__ __forceinline__ uint32_t tc_offset(int row, int k) {
@@ -41,11 +43,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor of kind::tf32: D in FP32, A and B TF32, both
-// K-major, M = 128, N = 64.
+// K-major, M = 128, N = 128.
 constexpr uint32_t kIdescTf32 = (1u << 4)              // D format: F32
                                 | (2u << 7)            // A format: TF32
                                 | (2u << 10)           // B format: TF32
-                                | ((64u >> 3) << 17)   // N / 8
+                                | ((128u >> 3) << 17)  // N / 8
                                 | ((128u >> 4) << 24); // M / 16
 
 // round to the nearest TF32 value (kept in a 32-bit register)

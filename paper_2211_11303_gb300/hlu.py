@@ -48,7 +48,8 @@ class hlu_factor_info(ctypes.Structure):
                 ("n_clusters", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
                 ("n_adm", ctypes.c_int32), ("n_dense", ctypes.c_int32),
                 ("rank_wanted_max", ctypes.c_int32), ("trunc_dense_fallbacks", ctypes.c_int32),
-                ("factor_live_bytes", ctypes.c_int64)]
+                ("factor_live_bytes", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 def _struct_dict(s):
@@ -67,6 +68,7 @@ _P = ctypes.POINTER
 SIGNATURES = {
     "hlu_build": (_i32, [_P(hlu_mesh), _f64, _i32, _f64, _f64, _i32, _vp, _P(_vp)]),
     "hlu_n": (_i64, [_vp]),
+    "hlu_set_schedule_cache": (_i32, [_i32, _i64]),
     "hlu_export_trees": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "hlu_export_csr": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "hlu_rhs_manufactured": (_i32, [_vp, _vp, _vp]),
@@ -74,6 +76,8 @@ SIGNATURES = {
     "hlu_rhs_constant_current": (_i32, [_vp, _f64, _f64, _f64, _vp, _vp]),
     "hlu_spmv": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
     "hlu_factor": (_i32, [_vp, _i32, _vp]),
+    "hlu_factor_async": (_i32, [_vp, _i32, _i32, _vp]),
+    "hlu_factor_wait": (_i32, [_vp, _i32, _P(_i32)]),
     "hlu_factor_stats": (_i32, [_vp, _P(hlu_factor_info)]),
     "hlu_factor_profile": (_i32, [_vp, _vp]),
     "hlu_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
@@ -231,6 +235,10 @@ def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
     return h.value
 
 
+def hlu_set_schedule_cache(entries, nbytes):
+    _check(lib().hlu_set_schedule_cache(int(entries), int(nbytes)))
+
+
 def hlu_n(h):
     return int(lib().hlu_n(_vp(h)))
 
@@ -297,6 +305,18 @@ def hlu_spmv(h, x, y, stream=None):
 
 def hlu_factor(h, precision=HLU_FP32, stream=None):
     _check(lib().hlu_factor(_vp(h), int(precision), _stream(stream)))
+
+
+def hlu_factor_async(h, precision=HLU_FP32, max_ctas=0, stream=None):
+    """Queue the factorisation on `stream` (capped at max_ctas CTAs) and return."""
+    _check(lib().hlu_factor_async(_vp(h), int(precision), int(max_ctas), _stream(stream)))
+
+
+def hlu_factor_wait(h, block=False):
+    """True once the factorisation queued by hlu_factor_async has finished."""
+    done = _i32()
+    _check(lib().hlu_factor_wait(_vp(h), int(bool(block)), ctypes.byref(done)))
+    return bool(done.value)
 
 
 def hlu_factor_stats(h):

@@ -12,9 +12,14 @@ triangular solves of every request run in one persistent launch, and a
 request's result is the same whether it ran alone or in the mix.
 
 Arrivals follow the request's ``t`` (seconds after start) on the wall clock.
-Factorisations run synchronously in the loop (the persistent executor fills
-the GPU), so a request that needs a new factor delays the running ones by the
-factorisation time; that delay is part of the reported latencies.
+A request that needs a new factor is factored on a side stream
+(``hlu_factor_async``) with the persistent launch capped at one CTA per SM,
+while the loop keeps stepping the running requests on the main stream: the
+executor holds two CTAs per SM, so the factorisation and the running
+requests' triangular solves share every SM.  One factorisation is in flight
+at a time; the request starts its GMRES once ``hlu_factor_wait`` reports the
+factor done.  ``overlap=False`` factors synchronously in the loop instead
+(the running requests wait for the factorisation).
 """
 import time
 
@@ -38,7 +43,7 @@ class _Factor:
 
 class Server:
     def __init__(self, hbm_budget_bytes, max_active=64, leaf=32, eta=2.0, eps=1e-4, precision=H.HLU_FP32,
-                 restart=50, tol=1e-8, maxit=1000):
+                 restart=50, tol=1e-8, maxit=1000, overlap=True):
         self.budget = int(hbm_budget_bytes)
         self.max_active = int(max_active)
         self.leaf, self.eta, self.eps = leaf, eta, eps
@@ -46,7 +51,12 @@ class Server:
         self.factors = {}
         self.used = 0
         self.reserve = 4 << 30  # device bytes kept free beyond each admission
-        self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0}
+        self.overlap = bool(overlap)
+        self.side = torch.cuda.Stream() if self.overlap else None
+        self.factor_ctas = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.inflight = None  # (entry of the request waiting for its factor, factor)
+        self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0,
+                      "steps_during_factor": 0}
 
     # -- factor cache ---------------------------------------------------------
     def _evict_for(self, need):
@@ -67,6 +77,8 @@ class Server:
         key = (int(req["n"]), float(req["kappa"]))
         f = self.factors.get(key)
         if f is not None:
+            if "_h" in req:  # built while the factor was not cached yet
+                H.hlu_destroy(req.pop("_h")[1])
             return f, None, 0
         if "_h" not in req:
             if not may_build:
@@ -75,16 +87,33 @@ class Server:
             req["_h"] = (key, h, int(H.hlu_factor_bytes_estimate(h, self.precision)))
         return None, req["_h"], req["_h"][2]
 
+    def prewarm(self, ns, kappa=1.0):
+        """Build (and drop) one handle per mesh size so that the library's
+        schedule cache holds the task DAGs of the mesh catalogue: a server
+        start-up step, after which a request's latency holds its own
+        factorisation and solve only."""
+        for n in sorted(set(int(x) for x in ns)):
+            H.hlu_destroy(H.hlu_build(n, kappa, self.leaf, self.eta, self.eps))
+
+    def _start(self, req, f, N, kb, active):
+        b = self._rhs_of(req, N)
+        bd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
+        bd.copy_(torch.from_numpy(np.ascontiguousarray(b)).pin_memory(), non_blocking=True)
+        xd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
+        g = H.hlu_gmres_begin(f.h, bd, xd, restart=self.restart, tol=self.tol, maxit=self.maxit)
+        active.append({"req": req, "f": f, "g": g, "b": bd, "x": xd, "kb": kb})
+
     # -- main loop --------------------------------------------------------------
     def run(self, requests, rhs_of):
         """Serve `requests` (dicts with id, t, n, kappa, nrhs) in arrival
         order; rhs_of(req, N) -> float64 host array (N, nrhs).  Returns one
         result dict per request (id, latency_s, iterations, relres, x)."""
         pending = sorted(requests, key=lambda r: (r["t"], r["id"]))
+        self._rhs_of = rhs_of
         waiting, active, results = [], [], {}
         t0 = time.perf_counter()
         pi = 0
-        while pi < len(pending) or waiting or active:
+        while pi < len(pending) or waiting or active or self.inflight is not None:
             now = time.perf_counter() - t0
             while pi < len(pending) and pending[pi]["t"] <= now:
                 waiting.append(pending[pi])
@@ -96,10 +125,16 @@ class Server:
             still = []
             built_one = False
             for req in waiting:
-                if len(active) >= self.max_active:
+                if len(active) + (self.inflight is not None) >= self.max_active:
                     still.append(req)
                     continue
                 f, built, fbytes = self._lookup(req, may_build=not built_one)
+                if f is None and built is not None and self.inflight is not None:
+                    still.append(req)  # one factorisation in flight at a time
+                    continue
+                if f is not None and self.inflight is not None and f is self.inflight[1]:
+                    still.append(req)  # its factor is being computed
+                    continue
                 if f is None and built is None:
                     still.append(req)
                     continue
@@ -112,39 +147,52 @@ class Server:
                 if f is not None:
                     f.users -= 1
                 # the device itself must have the room as well (schedules and
-                # handles are outside the budget)
-                ok = ok and torch.cuda.mem_get_info()[0] > fbytes + kb + self.reserve
+                # handles are outside the budget); blocks PyTorch's caching
+                # allocator holds unused count as free
+                avail = torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+                ok = ok and avail > fbytes + kb + self.reserve
                 if not ok:
-                    if not active and all(g.users == 0 for g in self.factors.values()) and not self.factors:
+                    if not active and self.inflight is None and not self.factors:
                         raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))
+                    if built is not None:  # do not hold an unadmitted handle's memory
+                        H.hlu_destroy(req.pop("_h")[1])
                     still.append(req)
                     continue
                 if f is None:
                     key, h, nbytes = req.pop("_h")
-                    H.hlu_factor(h, self.precision)
                     f = _Factor(key, h, nbytes)
                     self.factors[key] = f
-                    self.used += nbytes
+                    self.used += nbytes + kb
                     self.stats["factorisations"] += 1
+                    f.users += 1
+                    if self.overlap:
+                        with torch.cuda.stream(self.side):
+                            H.hlu_factor_async(h, self.precision, self.factor_ctas, self.side)
+                        self.inflight = (req, f, N, kb)
+                        continue
+                    H.hlu_factor(h, self.precision)
                 else:
                     self.stats["cache_hits"] += 1
-                got = f
-                b = rhs_of(req, N)
-                bd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
-                bd.copy_(torch.from_numpy(np.ascontiguousarray(b)).pin_memory(), non_blocking=True)
-                xd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
-                g = H.hlu_gmres_begin(got.h, bd, xd, restart=self.restart, tol=self.tol, maxit=self.maxit)
-                got.users += 1
-                self.used += kb
-                active.append({"req": req, "f": got, "g": g, "b": bd, "x": xd, "kb": kb})
+                    f.users += 1
+                    self.used += kb
+                self._start(req, f, N, kb, active)
             waiting = still
+            if self.inflight is not None:
+                # the factor of a newly admitted request: start its GMRES once
+                # done (wait for it when nothing else can run meanwhile)
+                req, f, N, kb = self.inflight
+                if H.hlu_factor_wait(f.h, block=not active):
+                    self.inflight = None
+                    self._start(req, f, N, kb, active)
             if not active:
-                if pi < len(pending):
+                if pi < len(pending) and self.inflight is None:
                     time.sleep(max(0.0, min(pending[pi]["t"] - (time.perf_counter() - t0), 0.05)))
                 continue
             self.stats["max_active"] = max(self.stats["max_active"], len(active))
             H.hlu_gmres_step_batch([a["g"] for a in active])
             self.stats["steps"] += 1
+            if self.inflight is not None:
+                self.stats["steps_during_factor"] += 1
             keep = []
             for a in active:
                 done, st = H.hlu_gmres_status(a["g"])
@@ -166,6 +214,9 @@ class Server:
         return [results[r["id"]] for r in requests]
 
     def close(self):
+        if self.inflight is not None:
+            H.hlu_factor_wait(self.inflight[1].h, block=True)
+            self.inflight = None
         for f in self.factors.values():
             H.hlu_destroy(f.h)
         self.factors.clear()

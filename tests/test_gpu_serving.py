@@ -132,5 +132,61 @@ def test_server_results_match_alone(hlu):
             assert r["converged"] and err <= MIX_VS_ALONE, (r["id"], float(err))
         finally:
             hlu.hlu_destroy(h)
+        # and against the direct solve of the oracle's matrix (the metric's bar)
+        from oracle import fem, mesh
+        import scipy.sparse.linalg as spla
+        A = fem.assemble(mesh.interior_edges(r["n"]), r["kappa"]).tocsc()
+        xd = spla.splu(A).solve(rhs_of(r, A.shape[0]))
+        xr = np.asarray(r["x"]).reshape(xd.shape)
+        for j in range(xd.shape[1]):
+            assert np.linalg.norm(xr[:, j] - xd[:, j]) <= 1e-7 * np.linalg.norm(xd[:, j]), (r["id"], j)
     summ = serve.latency_summary(res)
     assert summ["requests"] == len(reqs) and summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_result_unchanged_while_a_factorisation_runs(hlu):
+    """A request's GMRES steps taken while another problem's factorisation
+    runs on a second stream (hlu_factor_async, one CTA per SM) give the same
+    result as the request alone, and the factorisation run beside them gives
+    the same factor as one run alone."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    hs = hlu.hlu_build(5, 3.0, 16, 2.0, 1e-4)   # the running request's problem
+    hb = hlu.hlu_build(16, 6.0, 32, 2.0, 1e-4)  # the problem factored beside it
+    hb2 = hlu.hlu_build(16, 6.0, 32, 2.0, 1e-4)
+    side = torch.cuda.Stream()
+    try:
+        hlu.hlu_factor(hs, hlu.HLU_FP32)
+        hlu.hlu_factor(hb2, hlu.HLU_FP32)
+        b = _rhs(hlu.hlu_n(hs), 3, 9100)
+        alone, st_alone = _run(hlu, [(hs, b)], [0])
+        # the same request, stepped while hb is factored on the side stream
+        x = hlu.colmajor(hlu.hlu_n(hs), 3)
+        with torch.cuda.stream(side):
+            hlu.hlu_factor_async(hb, hlu.HLU_FP32, sms, side)
+        g = hlu.hlu_gmres_begin(hs, b, x, restart=50, tol=TOL, maxit=500)
+        steps_during = 0
+        try:
+            done = False
+            while not done:
+                hlu.hlu_gmres_step_batch([g])
+                if not hlu.hlu_factor_wait(hb, block=False):
+                    steps_during += 1
+                done, st = hlu.hlu_gmres_status(g)
+        finally:
+            hlu.hlu_gmres_end(g)
+        hlu.hlu_factor_wait(hb, block=True)
+        torch.cuda.synchronize()
+        assert steps_during > 0  # the steps did run while the factorisation was on the device
+        err = torch.linalg.norm(x - alone[0]) / torch.linalg.norm(alone[0])
+        assert st["converged"] and err <= MIX_VS_ALONE, float(err)
+        # the factor computed beside the request equals one computed alone
+        N = hlu.hlu_n(hb)
+        z = _rhs(N, 2, 9200)
+        y1, y2 = hlu.colmajor(N, 2), hlu.colmajor(N, 2)
+        hlu.hlu_solve(hb, z, y1)
+        hlu.hlu_solve(hb2, z, y2)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2)
+    finally:
+        for h in (hs, hb, hb2):
+            hlu.hlu_destroy(h)

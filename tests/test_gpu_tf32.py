@@ -1,9 +1,9 @@
 """The TF32 tensor-core path (HLU_TF32, tcgen05 MMAs with the accumulator in
-tensor memory) through the C ABI.  The tile product on its own equals the
-product of the TF32-rounded operands up to FP32 accumulation; factorisations
-whose tile products run on the tensor cores meet the oracle's operator-error
-bar where the truncation, not TF32 rounding, sets the error, and FGMRES
-brings their solutions to 1e-7 of the direct solve."""
+tensor memory, each operand split into TF32 high and low parts) through the
+C ABI.  The tile product on its own equals the split product up to FP32
+accumulation; factorisations whose tile products run on the tensor cores
+meet the oracle's operator-error bar and stay close to the FP32 path, and
+FGMRES brings their solutions to 1e-7 of the direct solve."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -37,6 +37,11 @@ def tf32_round(x):
 
 @pytest.mark.parametrize("K", [1, 5, 32, 33, 100, 256])
 def test_tf32_tile_product(hlu, K):
+    """D = A B from the tensor cores with each operand split into a TF32 part
+    and the TF32 rounding of its remainder: D equals
+    A_hi B_hi + A_hi B_lo + A_lo B_hi up to FP32 accumulation, and A B (the
+    FP32 product) to about 2^-21 relative, far closer than the plain TF32
+    product A_hi B_hi."""
     import ctypes
     rng = np.random.default_rng(K)
     A = rng.standard_normal((64, K)).astype(np.float32)
@@ -49,14 +54,17 @@ def test_tf32_tile_product(hlu, K):
                                         ctypes.c_void_p(dD.data_ptr()), K, st)
     assert rc == 0 and st[0] == 0
     D = dD.cpu().numpy().reshape(64, 64, order="F").astype(np.float64)
-    rA, rB = tf32_round(A).astype(np.float64), tf32_round(B).astype(np.float64)
-    ref = rA @ rB
-    scale = np.abs(rA) @ np.abs(rB)
-    # the TF32 products are exact in FP32; only the FP32 accumulation rounds
-    assert np.all(np.abs(D - ref) <= (K + 1) * 2.0 ** -23 * scale + 1e-30)
-    # and the TF32 rounding is really applied (differs from the FP32 product)
-    if K >= 32:
-        assert np.abs(D - A.astype(np.float64) @ B.astype(np.float64)).max() > 2.0 ** -20 * scale.max()
+    Ah, Bh = tf32_round(A), tf32_round(B)
+    Al, Bl = tf32_round(A - Ah), tf32_round(B - Bh)  # A - A_hi is exact in FP32
+    Ah, Bh, Al, Bl = (x.astype(np.float64) for x in (Ah, Bh, Al, Bl))
+    ref = Ah @ Bh + Ah @ Bl + Al @ Bh
+    scale = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+    # the partial products are exact in FP32; only the FP32 accumulation rounds
+    assert np.all(np.abs(D - ref) <= (K + 2) * 2.0 ** -23 * scale + 1e-30)
+    exact = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.all(np.abs(D - exact) <= (K + 4) * 2.0 ** -21 * scale + 1e-30)
+    if K >= 32:  # the split matters: the plain TF32 product is much further off
+        assert np.abs(Ah @ Bh - exact).max() > 16 * np.abs(D - exact).max()
 
 
 def _op_error(apply, A, nvec=3, seed=11):
@@ -76,7 +84,7 @@ def _gpu_apply(hlu, h, X):
     return x.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,kappa,eps", [(6, 4.0, 1e-2), (8, 8.0, 1e-2)])
+@pytest.mark.parametrize("n,kappa,eps", [(6, 4.0, 1e-2), (8, 8.0, 1e-3), (10, 6.0, 1e-4)])
 def test_tf32_factor_within_2x_of_oracle(hlu, n, kappa, eps):
     m = mesh.interior_edges(n)
     A = fem.assemble(m, kappa).tocsr()
@@ -92,7 +100,7 @@ def test_tf32_factor_within_2x_of_oracle(hlu, n, kappa, eps):
         # the FP32 path on the same handle gives a comparable preconditioner
         hlu.hlu_factor(h, hlu.HLU_FP32)
         e_32 = _op_error(lambda R: _gpu_apply(hlu, h, R), A)
-        assert e_tf <= 2.0 * e_32 + 1e-3, (e_tf, e_32)
+        assert e_tf <= 1.5 * e_32, (e_tf, e_32)
     finally:
         hlu.hlu_destroy(h)
 

@@ -67,12 +67,35 @@ extern "C" {
 
 typedef struct hlu_handle hlu_handle;
 
-/* Mesh: the unit cube cut into lattice_n^3 sub-cubes, each split into the 6
- * Kuhn tetrahedra along the axis permutations (Sec. 4, Example 1: the cube
- * cut into 6 tetrahedra and refined).  lattice_n >= 1. */
+/* Mesh: a conforming tetrahedral mesh of the domain (Sec. 2.1), given as
+ * nv vertex coordinates xyz (double[nv * 3], host) and nt tetrahedra tets
+ * (int32[nt * 4] vertex ids, host), or, with lattice_n > 0, the unit cube cut
+ * into lattice_n^3 sub-cubes, each split into the 6 Kuhn tetrahedra along
+ * the axis permutations (Sec. 4, Example 1: the cube cut into 6 tetrahedra
+ * and refined); lattice_n > 0 takes precedence (xyz and tets may then be
+ * NULL; hlu_mesh_kuhn_cube fills them for inspection).
+ * General meshes: a face that belongs to one tetrahedron is a boundary face;
+ * edges on boundary faces carry E x n = 0 and are eliminated; the remaining
+ * (interior) edges, oriented from the lower to the higher vertex id, are the
+ * DOFs in increasing (lo, hi) order.  The cluster tree's points are the edge
+ * midpoints on an integer grid, p = rint((x_lo + x_hi - 2 b) s), b the lower
+ * corner of the vertices' bounding box and s the largest power of two with
+ * 2 extent s <= 2^21.  The caller keeps xyz and tets; hlu_build copies them. */
 typedef struct {
+  int32_t nv, nt;
+  const double* xyz;
+  const int32_t* tets;
   int32_t lattice_n;
 } hlu_mesh;
+
+/* hlu_mesh_kuhn_cube - the Kuhn cube with n^3 sub-cubes as a mesh: vertex
+ * id (i (n+1) + j)(n+1) + k at (i, j, k) / n, tetrahedron 6 c + p of sub-cube
+ * c = (c0 n + c1) n + c2 with corners c, c + e_p0, c + e_p0 + e_p1, c + (1,1,1)
+ * for the axis permutations p in lexicographic order; lattice_n = n.  The
+ * arrays are allocated by the library (host memory) and released by
+ * hlu_mesh_free.  HLU_ERR_ARG for n outside [1, 200]; HLU_ERR_OOM. */
+int hlu_mesh_kuhn_cube(int32_t n, hlu_mesh* out);
+void hlu_mesh_free(hlu_mesh* m);
 
 /* Per-solve statistics (host struct filled by gmres_solve / hlu_richardson;
  * valid when the call returns). */
@@ -113,11 +136,12 @@ typedef struct {
 } hlu_factor_info;
 
 /* hlu_build - Algorithm 1 step I and the structures it needs.
- * Builds, on the GPU: the Kuhn mesh and its interior-edge numbering (Sec. 2.1:
- * one DOF per interior edge, sigma(Phi_i, e_j) = delta_ij), the CSR matrix
+ * Builds, on the GPU: the mesh's interior-edge numbering (Sec. 2.1: one DOF
+ * per interior edge, sigma(Phi_i, e_j) = delta_ij), the CSR matrix
  * A = K - kappa^2 M of a(E, Phi) = <curl E, curl Phi> - kappa^2 <E, Phi>
  * (Sec. 2.1 weak form; the paper's kappa is kappa^2 here), the geometric
- * cluster tree on doubled edge midpoints (Sec. 4, geometrically balanced
+ * cluster tree on the edge midpoints (doubled lattice coordinates on the Kuhn
+ * cube, the integer grid of hlu_mesh otherwise; Sec. 4, geometrically balanced
  * bisection, leaf size `leaf`), the block tree with admissibility
  * min(diam tau, diam sigma) <= eta dist(tau, sigma) (Sec. 3-4, eta = 2 in the
  * paper; eta^2 must be an integer), and the exact A_H (dense leaves from A,
@@ -128,8 +152,11 @@ typedef struct {
  * 64); a truncation that asks for more keeps the first rank_cap singular
  * triplets and counts a rank-capacity hit (hlu_factor_info).
  * The build is synchronous (trees are copied to the host for scheduling).
- * Errors: HLU_ERR_ARG for n < 1, leaf < 2, eta <= 0 or non-integer eta^2,
- * eps <= 0; HLU_ERR_OOM; HLU_ERR_CUDA. */
+ * Errors: HLU_ERR_ARG for lattice_n outside [0, 200], a general mesh with
+ * fewer than 4 vertices, no tetrahedra, 2^21 or more vertices, a vertex id
+ * out of range, a repeated vertex in a tetrahedron or a non-finite
+ * coordinate, leaf < 2, eta <= 0 or non-integer eta^2, eps <= 0; HLU_ERR_OOM;
+ * HLU_ERR_CUDA. */
 int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps,
               int32_t rank_cap, void* stream, hlu_handle** out);
 

@@ -110,9 +110,8 @@ def element_matrices(P, g):
 
 
 def _tet_data(mesh):
-    lattice, tets, n = mesh["lattice"], mesh["tets"], mesh["n"]
-    coords = lattice.astype(np.float64) / n
-    return tets, coords[tets]
+    tets = mesh["tets"]
+    return tets, mesh["coords"][tets]
 
 
 def _tet_dofs(mesh, tets):
@@ -237,9 +236,9 @@ def l2_error(mesh, x, Efun):
 def gradient_matrix(mesh):
     """Discrete gradient G: interior vertices -> interior edges, G[e, v] = +1 if v
     is the head (hi) of e, -1 if the tail (lo).  Interior vertices are those
-    with all lattice coordinates strictly between 0 and n, numbered by id."""
-    n, lattice, edges = mesh["n"], mesh["lattice"], mesh["edges"]
-    inner = [v for v in range(len(lattice)) if np.all((lattice[v] > 0) & (lattice[v] < n))]
+    on no boundary face, numbered by id."""
+    edges, bv = mesh["edges"], mesh["boundary_vertex"]
+    inner = [v for v in range(len(bv)) if not bv[v]]
     vpos = {v: i for i, v in enumerate(inner)}
     rows, cols, vals = [], [], []
     for e, (lo, hi) in enumerate(edges):

@@ -86,15 +86,68 @@ def is_boundary_edge(lattice, n, lo, hi):
 def interior_edges(n):
     """Mesh plus its interior edges.
 
-    Returns dict with lattice, tets, edges int64[N, 2] (lo, hi) in DOF order,
-    and edge_index: {(lo, hi): dof}.
+    Returns dict with lattice, coords (lattice / n), tets, edges int64[N, 2]
+    (lo, hi) in DOF order, edge_index: {(lo, hi): dof} and boundary_vertex
+    (bool per vertex: on a face of the cube).
     """
     lattice, tets = kuhn_cube(n)
     edges = [e for e in all_edges(tets) if not is_boundary_edge(lattice, n, *e)]
     edges = np.array(edges, dtype=np.int64).reshape(-1, 2)
     edge_index = {(int(e[0]), int(e[1])): d for d, e in enumerate(edges)}
-    return {"n": n, "lattice": lattice, "tets": tets, "edges": edges,
-            "edge_index": edge_index}
+    bv = np.any((lattice == 0) | (lattice == n), axis=1)
+    return {"n": n, "lattice": lattice, "coords": lattice.astype(np.float64) / n, "tets": tets, "edges": edges,
+            "edge_index": edge_index, "boundary_vertex": bv}
+
+
+def point_scale(extent):
+    """Largest power of two s with 2 extent s <= 2^21 (extent > 0)."""
+    s = 1.0
+    while 2.0 * extent * s * 2.0 <= 2.0 ** 21:
+        s *= 2.0
+    while 2.0 * extent * s > 2.0 ** 21:
+        s *= 0.5
+    return s
+
+
+def general_mesh(coords, tets):
+    """A conforming tetrahedral mesh given by vertex coordinates (float64
+    [nv, 3]) and tetrahedra (int [nt, 4] vertex ids), with one degree of
+    freedom per interior edge (Sec. 2.1; PEC eliminates the boundary edges).
+
+    Readings: a boundary face belongs to exactly one tetrahedron; a boundary
+    edge (and vertex) lies on a boundary face; interior edges are oriented
+    from the lower to the higher vertex id and numbered in increasing
+    (lo, hi) order, as on the Kuhn cube.  The cluster tree's points are the
+    edge midpoints on an integer grid: p = rint((x_lo + x_hi - 2 b) s), b the
+    lower corner of the vertices' bounding box and s = point_scale(extent), a
+    power of two, so every step is an exactly reproducible IEEE operation.
+
+    Returns the dict of interior_edges with n = 0 and no lattice, plus points
+    (int64 [N, 3]), the tree points in DOF order.
+    """
+    coords = np.asarray(coords, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    count = {}
+    for t in tets:
+        for f in itertools.combinations(sorted(int(x) for x in t), 3):
+            count[f] = count.get(f, 0) + 1
+    bfaces = [f for f, c in count.items() if c == 1]
+    bedges = set()
+    bv = np.zeros(len(coords), dtype=bool)
+    for f in bfaces:
+        for a, b in itertools.combinations(f, 2):
+            bedges.add((a, b))
+        bv[list(f)] = True
+    edges = [e for e in all_edges(tets) if e not in bedges]
+    edges = np.array(edges, dtype=np.int64).reshape(-1, 2)
+    edge_index = {(int(e[0]), int(e[1])): d for d, e in enumerate(edges)}
+    lo = coords.min(axis=0)
+    extent = float((coords.max(axis=0) - lo).max())
+    s = point_scale(extent)
+    mid = ((coords[edges[:, 0]] + coords[edges[:, 1]]) - 2.0 * lo) * s
+    points = np.rint(mid).astype(np.int64)
+    return {"n": 0, "coords": coords, "tets": tets, "edges": edges, "edge_index": edge_index,
+            "boundary_vertex": bv, "points": points}
 
 
 def n_interior_edges_formula(n):

@@ -32,6 +32,10 @@ ADM, DENSE, SUB = 0, 1, 2
 
 
 def edge_midpoints2(mesh):
+    """Tree points: doubled lattice midpoints on the Kuhn cube, the quantized
+    midpoints of a general mesh (mesh.general_mesh)."""
+    if "points" in mesh:
+        return mesh["points"]
     lat = mesh["lattice"]
     e = mesh["edges"]
     return lat[e[:, 0]] + lat[e[:, 1]]

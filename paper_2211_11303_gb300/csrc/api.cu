@@ -665,6 +665,55 @@ void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)6
 
 
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
+int hlu_mesh_kuhn_cube(int32_t n, hlu_mesh* out) {
+  if (!out || n < 1 || n > 200) return fail(HLU_ERR_ARG, "bad argument");
+  const int64_t nv = (int64_t)(n + 1) * (n + 1) * (n + 1), nt = (int64_t)6 * n * n * n;
+  double* xyz = (double*)std::malloc(sizeof(double) * 3 * nv);
+  int32_t* tets = (int32_t*)std::malloc(sizeof(int32_t) * 4 * nt);
+  if (!xyz || !tets) {
+    std::free(xyz);
+    std::free(tets);
+    return fail(HLU_ERR_OOM, "host allocation failed");
+  }
+  for (int64_t v = 0; v < nv; ++v) {
+    const int64_t i = v / ((int64_t)(n + 1) * (n + 1)), j = (v / (n + 1)) % (n + 1), k = v % (n + 1);
+    xyz[3 * v] = (double)i / n;
+    xyz[3 * v + 1] = (double)j / n;
+    xyz[3 * v + 2] = (double)k / n;
+  }
+  // tetrahedron 6 c + p of sub-cube c = (c0 n + c1) n + c2: corners c, c + e_p0,
+  // c + e_p0 + e_p1, c + (1, 1, 1) for the axis permutations p in lexicographic order
+  static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int64_t c = 0; c < (int64_t)n * n * n; ++c) {
+    const int64_t c0 = c / ((int64_t)n * n), c1 = (c / n) % n, c2 = c % n;
+    for (int p = 0; p < 6; ++p) {
+      int64_t q[3] = {c0, c1, c2};
+      int32_t* t = tets + 4 * (6 * c + p);
+      t[0] = (int32_t)((q[0] * (n + 1) + q[1]) * (n + 1) + q[2]);
+      for (int s = 0; s < 3; ++s) {
+        q[perms[p][s]] += 1;
+        t[s + 1] = (int32_t)((q[0] * (n + 1) + q[1]) * (n + 1) + q[2]);
+      }
+    }
+  }
+  out->nv = (int32_t)nv;
+  out->nt = (int32_t)nt;
+  out->xyz = xyz;
+  out->tets = tets;
+  out->lattice_n = n;
+  return HLU_OK;
+}
+
+void hlu_mesh_free(hlu_mesh* m) {
+  if (!m) return;
+  std::free(const_cast<double*>(m->xyz));
+  std::free(const_cast<int32_t*>(m->tets));
+  m->xyz = nullptr;
+  m->tets = nullptr;
+  m->nv = m->nt = 0;
+  m->lattice_n = 0;
+}
+
 int hlu_set_schedule_cache(int32_t entries, int64_t bytes) {
   if (entries < 1 || bytes < 0) return fail(HLU_ERR_ARG, "bad argument");
   std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -682,8 +731,9 @@ void hlu_destroy(hlu_handle* h) {
   h->dS.free_all();
   h->kw.free_all();
   h->sb.reset();
-  for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->A.rowptr, (void*)h->A.col,
-                  (void*)h->A.val, (void*)h->d_perm, (void*)h->d_iperm})
+  for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->mesh.xyz,
+                  (void*)h->mesh.tets, (void*)h->mesh.ekeys, (void*)h->A.rowptr, (void*)h->A.col, (void*)h->A.val,
+                  (void*)h->d_perm, (void*)h->d_iperm})
     if (p) dev_free(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -696,7 +746,22 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     if (!mesh || !out) return fail(HLU_ERR_ARG, "null argument");
     *out = nullptr;
     const int n = mesh->lattice_n;
-    if (n < 1 || n > 200) return fail(HLU_ERR_ARG, "lattice_n out of range");
+    if (n > 200 || n < 0) return fail(HLU_ERR_ARG, "lattice_n out of range");
+    if (n == 0) {  // a general mesh: check what the device code relies on
+      if (!mesh->xyz || !mesh->tets || mesh->nv < 4 || mesh->nt < 1)
+        return fail(HLU_ERR_ARG, "a general mesh needs nv >= 4 vertices, nt >= 1 tetrahedra, xyz and tets");
+      if (mesh->nv >= (1 << 21)) return fail(HLU_ERR_ARG, "at most 2^21 - 1 vertices");
+      for (int64_t q = 0; q < 4 * (int64_t)mesh->nt; ++q)
+        if (mesh->tets[q] < 0 || mesh->tets[q] >= mesh->nv) return fail(HLU_ERR_ARG, "tetrahedron vertex id out of range");
+      for (int64_t t = 0; t < mesh->nt; ++t) {
+        const int32_t* v = mesh->tets + 4 * t;
+        for (int a = 0; a < 4; ++a)
+          for (int b = a + 1; b < 4; ++b)
+            if (v[a] == v[b]) return fail(HLU_ERR_ARG, "a tetrahedron repeats a vertex");
+      }
+      for (int64_t q = 0; q < 3 * (int64_t)mesh->nv; ++q)
+        if (!std::isfinite(mesh->xyz[q])) return fail(HLU_ERR_ARG, "vertex coordinates must be finite");
+    }
     if (leaf < 2 || leaf > 64) return fail(HLU_ERR_ARG, "leaf must be in [2, 64]");
     if (!(eta > 0)) return fail(HLU_ERR_ARG, "eta must be > 0");
     double e2 = eta * eta;
@@ -723,7 +788,11 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     };
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return bail(e, "event");
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return bail(e, "event");
-    if ((e = build_mesh_dofs(n, s, h->mesh)) != cudaSuccess) return bail(e, "mesh");
+    if (n > 0)
+      e = build_mesh_dofs(n, s, h->mesh);
+    else
+      e = build_mesh_general(mesh->nv, mesh->nt, mesh->xyz, mesh->tets, s, h->mesh);
+    if (e != cudaSuccess) return bail(e, "mesh");
     if ((e = assemble_csr(h->mesh, kappa, s, h->A)) != cudaSuccess) return bail(e, "assembly");
     const int64_t N = h->A.N;
     if ((e = dev_malloc(&h->d_perm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "perm");
@@ -867,6 +936,7 @@ int hlu_rhs_constant_current(const hlu_handle* h, double jx, double jy, double j
 
 int hlu_rhs_manufactured_noalloc(const hlu_handle* h, double* b_dev, void* stream) {
   if (!h || !b_dev) return fail(HLU_ERR_ARG, "null argument");
+  if (h->n < 1) return fail(HLU_ERR_ARG, "the allocation-free load vector takes Kuhn-cube meshes only");
   const int64_t need = (int64_t)36 * h->n * h->n * h->n;
   if (need > rhs_noalloc_max_entries())
     return fail(HLU_ERR_ARG, "mesh needs " + std::to_string(need) + " element contributions; the fixed scratch holds " +

@@ -19,8 +19,12 @@
 #include <thrust/reduce.h>
 #include <thrust/scan.h>
 #include <thrust/sequence.h>
+#include <thrust/fill.h>
+#include <thrust/set_operations.h>
 #include <thrust/sort.h>
+#include <thrust/unique.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -104,7 +108,7 @@ struct TetGeo {
   int lo[6], hi[6];  // oriented local vertex pair of each local edge
 };
 
-__device__ void tet_geometry(int64_t t, int n, const int32_t* dofmap, TetGeo& g) {
+__device__ void tet_geometry_lattice(int64_t t, int n, const int32_t* dofmap, TetGeo& g) {
   int64_t cube = t / 6;
   int pi = (int)(t % 6);
   int c[3];
@@ -161,6 +165,80 @@ __device__ void tet_geometry(int64_t t, int n, const int32_t* dofmap, TetGeo& g)
   }
 }
 
+// What the element kernels read of a mesh (DevMesh without ownership).
+struct MeshView {
+  int n;            // lattice size, 0 for a general mesh
+  int64_t nt;       // tetrahedra
+  int32_t nv;
+  const int32_t* dofmap;
+  const double* xyz;
+  const int32_t* tets;
+  const int64_t* ekeys;
+  int64_t N;
+};
+static MeshView view_of(const DevMesh& m) {
+  return MeshView{m.n, m.n > 0 ? (int64_t)6 * m.n * m.n * m.n : m.nt, m.nv, m.dofmap, m.xyz, m.tets, m.ekeys, m.N};
+}
+
+// General tetrahedron t: coordinates from xyz, barycentric gradients as in
+// the lattice case, local edge -> interior DOF by binary search of its key.
+__device__ void tet_geometry_general(int64_t t, const MeshView& mv, TetGeo& g) {
+  for (int s = 0; s < 4; ++s) {
+    g.v[s] = mv.tets[4 * t + s];
+    for (int a = 0; a < 3; ++a) g.P[s][a] = mv.xyz[3 * g.v[s] + a];
+  }
+  double J[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 3; ++s) J[a][s] = g.P[s + 1][a] - g.P[0][a];
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int a = 0; a < 3; ++a) {
+    g.G[0][a] = 0;
+    for (int s = 0; s < 3; ++s) {
+      g.G[s + 1][a] = inv[s][a];
+      g.G[0][a] -= inv[s][a];
+    }
+  }
+  g.vol = fabs(det) / 6.0;
+  for (int e = 0; e < 6; ++e) {
+    int a = c_ledge[e][0], b = c_ledge[e][1];
+    if (g.v[a] > g.v[b]) {
+      int tmp = a;
+      a = b;
+      b = tmp;
+    }
+    g.lo[e] = a;
+    g.hi[e] = b;
+    const int64_t key = g.v[a] * (int64_t)mv.nv + g.v[b];
+    int64_t lo = 0, hi = mv.N;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (mv.ekeys[mid] < key)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    g.dof[e] = (lo < mv.N && mv.ekeys[lo] == key) ? (int)lo : -1;
+  }
+}
+
+__device__ __forceinline__ void tet_geometry(int64_t t, const MeshView& mv, TetGeo& g) {
+  if (mv.n > 0)
+    tet_geometry_lattice(t, mv.n, mv.dofmap, g);
+  else
+    tet_geometry_general(t, mv, g);
+}
+
 __device__ __forceinline__ double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -170,11 +248,11 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
 
 // one thread per tetrahedron: 36 (key, value) pairs, key = row * N + col or
 // INT64_MAX for pairs that touch a boundary edge
-__global__ void k_element_coo(int n, double kappa2, int64_t N, const int32_t* dofmap, int64_t* keys, double* vals) {
-  int64_t nt = (int64_t)6 * n * n * n;
+__global__ void k_element_coo(MeshView mv, double kappa2, int64_t N, int64_t* keys, double* vals) {
+  const int64_t nt = mv.nt;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
     TetGeo g;
-    tet_geometry(t, n, dofmap, g);
+    tet_geometry(t, mv, g);
     for (int r = 0; r < 6; ++r) {
       int a = g.lo[r], b = g.hi[r];
       double ca[3];
@@ -209,13 +287,13 @@ __global__ void k_csr_rows(int64_t nnz, int64_t N, const int64_t* ukeys, int32_t
 }
 
 // load vector: one thread per tetrahedron, 6 (dof, value) pairs
-__global__ void k_rhs_coo(int n, double kappa2, const int32_t* dofmap, int32_t* keys, double* vals) {
-  int64_t nt = (int64_t)6 * n * n * n;
+__global__ void k_rhs_coo(MeshView mv, double kappa2, int32_t* keys, double* vals) {
+  const int64_t nt = mv.nt;
   const double qa = (5.0 - sqrt(5.0)) / 20.0, qb = (5.0 + 3.0 * sqrt(5.0)) / 20.0;
   const double PI = 3.14159265358979323846;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
     TetGeo g;
-    tet_geometry(t, n, dofmap, g);
+    tet_geometry(t, mv, g);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int q = 0; q < 4; ++q) {
       double lam[4] = {qa, qa, qa, qa};
@@ -245,13 +323,12 @@ __global__ void k_rhs_coo(int n, double kappa2, const int32_t* dofmap, int32_t* 
 // integral of a barycentric coordinate over T is |T| / 4, so
 // b_e = |T| / 4 J . (grad lam_b - grad lam_a) exactly.  One thread per
 // tetrahedron, 6 (dof, value) pairs.
-__global__ void k_rhs_const_coo(int n, double J0, double J1, double J2, const int32_t* dofmap, int32_t* keys,
-                                double* vals) {
-  int64_t nt = (int64_t)6 * n * n * n;
+__global__ void k_rhs_const_coo(MeshView mv, double J0, double J1, double J2, int32_t* keys, double* vals) {
+  const int64_t nt = mv.nt;
   const double J[3] = {J0, J1, J2};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
     TetGeo g;
-    tet_geometry(t, n, dofmap, g);
+    tet_geometry(t, mv, g);
     for (int e = 0; e < 6; ++e) {
       const int a = g.lo[e], b = g.hi[e];
       double d[3];
@@ -678,8 +755,159 @@ cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m) {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- general meshes
+// 6 edge keys (lo * nv + hi) per tetrahedron
+__global__ void k_tet_edge_keys(int64_t nt, int32_t nv, const int32_t* tets, int64_t* keys) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int e = 0; e < 6; ++e) {
+      int64_t a = tets[4 * t + c_ledge[e][0]], b = tets[4 * t + c_ledge[e][1]];
+      if (a > b) {
+        const int64_t x = a;
+        a = b;
+        b = x;
+      }
+      keys[6 * t + e] = a * nv + b;
+    }
+  }
+}
+// 4 face keys (a nv^2 + b nv + c, a < b < c) per tetrahedron
+__global__ void k_tet_face_keys(int64_t nt, int32_t nv, const int32_t* tets, int64_t* keys) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v[4];
+    for (int s = 0; s < 4; ++s) v[s] = tets[4 * t + s];
+    for (int i = 1; i < 4; ++i)  // sort the 4 ids
+      for (int j = i; j > 0 && v[j - 1] > v[j]; --j) {
+        const int64_t x = v[j];
+        v[j] = v[j - 1];
+        v[j - 1] = x;
+      }
+    for (int skip = 0; skip < 4; ++skip) {
+      int64_t f[3];
+      int q = 0;
+      for (int s = 0; s < 4; ++s)
+        if (s != skip) f[q++] = v[s];
+      keys[4 * t + skip] = (f[0] * nv + f[1]) * nv + f[2];
+    }
+  }
+}
+// the 3 edge keys of every boundary face (faces that occur once)
+__global__ void k_boundary_face_edges(int64_t nf, int32_t nv, const int64_t* fkeys, const int32_t* fcount,
+                                      int64_t* ekeys, int64_t* n_out) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    if (fcount[f] != 1) continue;
+    const int64_t k = fkeys[f];
+    const int64_t a = k / ((int64_t)nv * nv), b = (k / nv) % nv, c = k % nv;
+    const unsigned long long o = atomicAdd(reinterpret_cast<unsigned long long*>(n_out), 3ULL);
+    ekeys[o] = a * nv + b;
+    ekeys[o + 1] = a * nv + c;
+    ekeys[o + 2] = b * nv + c;
+  }
+}
+// edges and tree points of the interior edges: p = rint((x_lo + x_hi - 2 b) s),
+// every operation rounded once as written (no contraction)
+__global__ void k_general_edges(int64_t N, int32_t nv, const int64_t* ekeys, const double* xyz, double b0, double b1,
+                                double b2, double scale, int32_t* edges, int32_t* pts) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = ekeys[e] / nv, hi = ekeys[e] % nv;
+    edges[2 * e] = (int32_t)lo;
+    edges[2 * e + 1] = (int32_t)hi;
+    const double bb[3] = {b0, b1, b2};
+    for (int a = 0; a < 3; ++a) {
+      const double t1 = __dadd_rn(xyz[3 * lo + a], xyz[3 * hi + a]);
+      const double t2 = __dsub_rn(t1, __dmul_rn(2.0, bb[a]));
+      pts[3 * e + a] = (int32_t)__double2ll_rn(__dmul_rn(t2, scale));
+    }
+  }
+}
+
+cudaError_t build_mesh_general(int32_t nv, int64_t nt, const double* xyz, const int32_t* tets, cudaStream_t s,
+                               DevMesh& m) {
+  TempScope tmp;
+  m.n = 0;
+  m.nv = nv;
+  m.nt = nt;
+  CK(dev_malloc(&m.xyz, sizeof(double) * 3 * (int64_t)nv));
+  CK(dev_malloc(&m.tets, sizeof(int32_t) * 4 * nt));
+  CK(cudaMemcpyAsync(m.xyz, xyz, sizeof(double) * 3 * (int64_t)nv, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.tets, tets, sizeof(int32_t) * 4 * nt, cudaMemcpyHostToDevice, s));
+  // all edges, sorted and unique
+  int64_t* ek = nullptr;
+  CK(tmp.alloc(&ek, sizeof(int64_t) * 6 * nt));
+  note_launch();
+  k_tet_edge_keys<<<grid_for(nt), 256, 0, s>>>(nt, nv, m.tets, ek);
+  CK(cudaGetLastError());
+  thrust::sort(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(ek), thrust::device_ptr<int64_t>(ek + 6 * nt));
+  const int64_t ne = thrust::unique(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(ek),
+                                    thrust::device_ptr<int64_t>(ek + 6 * nt)) -
+                     thrust::device_ptr<int64_t>(ek);
+  // faces and how many tetrahedra hold each
+  int64_t* fk = nullptr;
+  int64_t* fu = nullptr;
+  int32_t* ones = nullptr;
+  int32_t* fc = nullptr;
+  CK(tmp.alloc(&fk, sizeof(int64_t) * 4 * nt));
+  CK(tmp.alloc(&fu, sizeof(int64_t) * 4 * nt));
+  CK(tmp.alloc(&ones, sizeof(int32_t) * 4 * nt));
+  CK(tmp.alloc(&fc, sizeof(int32_t) * 4 * nt));
+  note_launch();
+  k_tet_face_keys<<<grid_for(nt), 256, 0, s>>>(nt, nv, m.tets, fk);
+  CK(cudaGetLastError());
+  thrust::sort(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(fk), thrust::device_ptr<int64_t>(fk + 4 * nt));
+  thrust::fill(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(ones),
+               thrust::device_ptr<int32_t>(ones + 4 * nt), 1);
+  auto fe = thrust::reduce_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(fk),
+                                  thrust::device_ptr<int64_t>(fk + 4 * nt), thrust::device_ptr<int32_t>(ones),
+                                  thrust::device_ptr<int64_t>(fu), thrust::device_ptr<int32_t>(fc));
+  const int64_t nf = fe.first - thrust::device_ptr<int64_t>(fu);
+  // boundary edges: the edges of faces held by one tetrahedron
+  int64_t* bk = nullptr;
+  int64_t* nb = nullptr;
+  CK(tmp.alloc(&bk, sizeof(int64_t) * 3 * std::max<int64_t>(nf, 1)));
+  CK(tmp.alloc(&nb, sizeof(int64_t)));
+  CK(cudaMemsetAsync(nb, 0, sizeof(int64_t), s));
+  note_launch();
+  k_boundary_face_edges<<<grid_for(nf), 256, 0, s>>>(nf, nv, fu, fc, bk, nb);
+  CK(cudaGetLastError());
+  int64_t nbk = 0;
+  CK(cudaMemcpyAsync(&nbk, nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  thrust::sort(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(bk), thrust::device_ptr<int64_t>(bk + nbk));
+  const int64_t nbu = thrust::unique(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(bk),
+                                     thrust::device_ptr<int64_t>(bk + nbk)) -
+                      thrust::device_ptr<int64_t>(bk);
+  // interior edges = all edges minus boundary edges, in key = (lo, hi) order
+  CK(dev_malloc(&m.ekeys, sizeof(int64_t) * std::max<int64_t>(ne, 1)));
+  const int64_t N = thrust::set_difference(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(ek),
+                                           thrust::device_ptr<int64_t>(ek + ne), thrust::device_ptr<int64_t>(bk),
+                                           thrust::device_ptr<int64_t>(bk + nbu), thrust::device_ptr<int64_t>(m.ekeys)) -
+                    thrust::device_ptr<int64_t>(m.ekeys);
+  m.N = N;
+  if (N < 1) return cudaErrorInvalidValue;
+  // tree points on the integer grid (bounding box and scale on the host)
+  double lo[3] = {xyz[0], xyz[1], xyz[2]}, hi[3] = {xyz[0], xyz[1], xyz[2]};
+  for (int64_t v = 0; v < nv; ++v)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], xyz[3 * v + a]);
+      hi[a] = std::max(hi[a], xyz[3 * v + a]);
+    }
+  double extent = 0;
+  for (int a = 0; a < 3; ++a) extent = std::max(extent, hi[a] - lo[a]);
+  if (!(extent > 0)) return cudaErrorInvalidValue;
+  double scale = 1.0;
+  while (2.0 * extent * scale * 2.0 <= 2097152.0) scale *= 2.0;
+  while (2.0 * extent * scale > 2097152.0) scale *= 0.5;
+  CK(dev_malloc(&m.edges, sizeof(int32_t) * 2 * N));
+  CK(dev_malloc(&m.pts, sizeof(int32_t) * 3 * N));
+  note_launch();
+  k_general_edges<<<grid_for(N), 256, 0, s>>>(N, nv, m.ekeys, m.xyz, lo[0], lo[1], lo[2], scale, m.edges, m.pts);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return cudaSuccess;
+}
+
 cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A) {
-  int64_t nt = (int64_t)6 * m.n * m.n * m.n;
+  const MeshView mv = view_of(m);
+  const int64_t nt = mv.nt;
   int64_t ne = nt * 36;
   TempScope tmp;
   int64_t* keys = nullptr;
@@ -687,7 +915,7 @@ cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR&
   CK(tmp.alloc(&keys, sizeof(int64_t) * ne));
   CK(tmp.alloc(&vals, sizeof(double) * ne));
   note_launch();
-  k_element_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.N, m.dofmap, keys, vals);
+  k_element_coo<<<grid_for(nt, 128), 128, 0, s>>>(mv, kappa * kappa, m.N, keys, vals);
   CK(cudaGetLastError());
   thrust::stable_sort_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int64_t>(keys),
                              thrust::device_ptr<int64_t>(keys + ne), thrust::device_ptr<double>(vals));
@@ -726,7 +954,8 @@ cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR&
 // (J == nullptr) or constant current J[3].  The pairs are sorted by DOF and
 // summed in a fixed order, so the result does not depend on the launch.
 static cudaError_t rhs_from_elements(const DevMesh& m, double kappa, const double* Jc, double* b, cudaStream_t s) {
-  int64_t nt = (int64_t)6 * m.n * m.n * m.n;
+  const MeshView mv = view_of(m);
+  const int64_t nt = mv.nt;
   int64_t ne = nt * 6;
   int32_t* keys = nullptr;
   double* vals = nullptr;
@@ -739,9 +968,9 @@ static cudaError_t rhs_from_elements(const DevMesh& m, double kappa, const doubl
   CK(tmp.alloc(&us, sizeof(double) * ne));
   note_launch();
   if (Jc)
-    k_rhs_const_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, Jc[0], Jc[1], Jc[2], m.dofmap, keys, vals);
+    k_rhs_const_coo<<<grid_for(nt, 128), 128, 0, s>>>(mv, Jc[0], Jc[1], Jc[2], keys, vals);
   else
-    k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
+    k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(mv, kappa * kappa, keys, vals);
   CK(cudaGetLastError());
   thrust::stable_sort_by_key(thrust::cuda::par(g_talloc).on(s), thrust::device_ptr<int32_t>(keys),
                              thrust::device_ptr<int32_t>(keys + ne), thrust::device_ptr<double>(vals));
@@ -1015,7 +1244,7 @@ cudaError_t manufactured_rhs_noalloc(const DevMesh& m, double kappa, double* b, 
   // every scratch entry read below is written first by k_rhs_coo; b starts at 0
   CK(cudaMemsetAsync(b, 0, sizeof(double) * m.N, s));
   note_launch();
-  k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(m.n, kappa * kappa, m.dofmap, keys, vals);
+  k_rhs_coo<<<grid_for(nt, 128), 128, 0, s>>>(view_of(m), kappa * kappa, keys, vals);
   CK(cudaGetLastError());
   note_launch();
   k_add_rhs<<<grid_for(ne), 256, 0, s>>>(ne, keys, vals, m.N, b);

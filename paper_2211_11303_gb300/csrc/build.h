@@ -7,12 +7,21 @@
 
 namespace hlu {
 
+// A tetrahedral mesh on the device: the Kuhn cube (n > 0, vertices and
+// tetrahedra implied by the lattice) or a general mesh (n == 0, vertex
+// coordinates and tetrahedra stored).
 struct DevMesh {
   int n = 0;
   int64_t N = 0;
-  int32_t* dofmap = nullptr;  // (n+1)^3 x 7: DOF of edge (v, v + dir) or -1
+  int32_t* dofmap = nullptr;  // lattice: (n+1)^3 x 7: DOF of edge (v, v + dir) or -1
   int32_t* edges = nullptr;   // N x 2 (lo, hi)
-  int32_t* pts = nullptr;     // N x 3 doubled midpoints
+  int32_t* pts = nullptr;     // N x 3 tree points (lattice: doubled midpoints;
+                              // general: quantized midpoints)
+  int64_t nt = 0;             // tetrahedra
+  int32_t nv = 0;             // vertices
+  double* xyz = nullptr;      // general: nv x 3 coordinates
+  int32_t* tets = nullptr;    // general: nt x 4 vertex ids
+  int64_t* ekeys = nullptr;   // general: N interior-edge keys lo * nv + hi, ascending (DOF order)
 };
 struct DevCSR {
   int64_t N = 0, nnz = 0;
@@ -36,6 +45,12 @@ struct FillDesc {
 };
 
 cudaError_t build_mesh_dofs(int n, cudaStream_t s, DevMesh& m);
+// General mesh: xyz (nv x 3) and tets (nt x 4, ids in [0, nv)) on the host.
+// Interior edges (edges on no boundary face; a boundary face belongs to one
+// tetrahedron) numbered in (lo, hi) order; tree points p = rint((x_lo + x_hi
+// - 2 lo_box) s) with s the largest power of two keeping them <= 2^21.
+cudaError_t build_mesh_general(int32_t nv, int64_t nt, const double* xyz, const int32_t* tets, cudaStream_t s,
+                               DevMesh& m);
 cudaError_t assemble_csr(const DevMesh& m, double kappa, cudaStream_t s, DevCSR& A);
 cudaError_t manufactured_rhs(const DevMesh& m, double kappa, double* b, cudaStream_t s);
 // load vector of the constant current density J (exact integration)

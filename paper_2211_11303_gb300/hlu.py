@@ -28,7 +28,8 @@ class HluError(RuntimeError):
 
 
 class hlu_mesh(ctypes.Structure):
-    _fields_ = [("lattice_n", ctypes.c_int32)]
+    _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("xyz", ctypes.c_void_p),
+                ("tets", ctypes.c_void_p), ("lattice_n", ctypes.c_int32)]
 
 
 class hlu_stats(ctypes.Structure):
@@ -67,6 +68,8 @@ _P = ctypes.POINTER
 # include/hlu_debug.h (tests check every declared name is exported)
 SIGNATURES = {
     "hlu_build": (_i32, [_P(hlu_mesh), _f64, _i32, _f64, _f64, _i32, _vp, _P(_vp)]),
+    "hlu_mesh_kuhn_cube": (_i32, [_i32, _P(hlu_mesh)]),
+    "hlu_mesh_free": (None, [_P(hlu_mesh)]),
     "hlu_n": (_i64, [_vp]),
     "hlu_set_schedule_cache": (_i32, [_i32, _i64]),
     "hlu_export_trees": (_i32, [_vp, _vp, _vp, _vp, _P(_i64)]),
@@ -226,10 +229,41 @@ def _vec(t, N):
 
 
 # ---------------------------------------------------------------- C-ABI names
-def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
-    """Algorithm 1 step I on the GPU; returns an opaque handle (int)."""
+def lattice_mesh(n):
+    """hlu_mesh of the Kuhn cube with n^3 sub-cubes (the lattice path)."""
+    return hlu_mesh(0, 0, None, None, int(n))
+
+
+def hlu_mesh_kuhn_cube(n):
+    """(xyz float64 [nv, 3], tets int32 [nt, 4]) of the library's Kuhn cube."""
+    import numpy as np
+    m = hlu_mesh()
+    _check(lib().hlu_mesh_kuhn_cube(int(n), ctypes.byref(m)))
+    try:
+        xyz = np.ctypeslib.as_array(ctypes.cast(m.xyz, _P(ctypes.c_double)), shape=(m.nv, 3)).copy()
+        tets = np.ctypeslib.as_array(ctypes.cast(m.tets, _P(ctypes.c_int32)), shape=(m.nt, 4)).copy()
+    finally:
+        lib().hlu_mesh_free(ctypes.byref(m))
+    return xyz, tets
+
+
+def hlu_build_mesh(xyz, tets, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
+    """Algorithm 1 step I for a general tetrahedral mesh: xyz (nv, 3) float64
+    coordinates, tets (nt, 4) vertex ids (host arrays)."""
+    import numpy as np
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    m = hlu_mesh(xyz.shape[0], tets.shape[0], xyz.ctypes.data, tets.ctypes.data, 0)
     h = _vp()
-    m = hlu_mesh(int(n))
+    _check(lib().hlu_build(ctypes.byref(m), float(kappa), int(leaf), float(eta), float(eps), int(rank_cap),
+                           _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
+    """Algorithm 1 step I on the GPU for the Kuhn n-cube; returns an opaque handle (int)."""
+    h = _vp()
+    m = lattice_mesh(n)
     _check(lib().hlu_build(ctypes.byref(m), float(kappa), int(leaf), float(eta), float(eps),
                            int(rank_cap), _stream(stream), ctypes.byref(h)))
     return h.value

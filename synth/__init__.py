@@ -85,3 +85,33 @@ def serving_requests(count=200, seed=5000, n_lo=8, n_hi=32, k_lo=1.0, k_hi=12.0,
         nrhs = r_lo + min(int(u[4 * i + 3] * (r_hi - r_lo + 1)), r_hi - r_lo)
         out.append({"id": i, "t": t, "n": n, "kappa": float(kappa), "nrhs": nrhs})
     return out
+
+
+def perturbed_kuhn_mesh(n, amplitude, seed):
+    """A non-lattice tetrahedral mesh of the unit cube (input recipe): the n^3
+    sub-cubes cut into 6 tetrahedra along the axis permutations, vertex id
+    (i (n+1) + j)(n+1) + k, and every vertex off the cube's faces moved by
+    amplitude / n times a seeded uniform draw in [-1, 1)^3.  amplitude < 0.25
+    inverts no tetrahedron.  Returns (coords float64
+    [(n+1)^3, 3], tets int32 [6 n^3, 4])."""
+    idx = np.arange(n + 1)
+    I, J, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    lat = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    vid = lambda p: (p[..., 0] * (n + 1) + p[..., 1]) * (n + 1) + p[..., 2]
+    c = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), axis=-1).reshape(-1, 3)
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        p = c.copy()
+        corners = [vid(p)]
+        for ax in perm:
+            p = p.copy()
+            p[:, ax] += 1
+            corners.append(vid(p))
+        tets.append(np.stack(corners, axis=1))
+    # tet of sub-cube ci and permutation pi at row 6 ci + pi
+    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    coords = lat.astype(np.float64) / n
+    inner = np.all((lat > 0) & (lat < n), axis=1)
+    u = uniform(seed, 3 * len(coords)).reshape(-1, 3)
+    coords = coords + np.where(inner[:, None], (2.0 * u - 1.0) * amplitude / n, 0.0)
+    return coords, tets

@@ -49,9 +49,9 @@ def test_status_strings(lib):
 def test_build_rejects_bad_arguments(lib):
     from paper_2211_11303_gb300 import hlu
     h = ctypes.c_void_p()
-    m = hlu.hlu_mesh(0)
+    m = hlu.lattice_mesh(0)  # neither a lattice nor a general mesh
     assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
-    m = hlu.hlu_mesh(4)
+    m = hlu.lattice_mesh(4)
     assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 1.5, 1e-4, 32, None, ctypes.byref(h)) == 1  # eta^2 = 2.25
     assert lib.hlu_build(None, 1.0, 32, 2.0, 1e-4, 32, None, ctypes.byref(h)) == 1
 
@@ -127,3 +127,39 @@ def test_allocator_and_memory_limit_arguments(lib):
     assert lib.hlu_set_device_memory_limit(-1) == 1
     assert lib.hlu_set_device_memory_limit(0) == 0
     assert lib.hlu_device_bytes_in_use() >= 0
+
+
+def test_kuhn_cube_mesh_export_matches_the_input_recipe(lib):
+    """hlu_mesh_kuhn_cube (host arrays, no device) lists the same vertices and
+    tetrahedra, in the same order, as the seeded mesh recipe of the tests and
+    the oracle's Kuhn cube."""
+    import synth
+    from oracle import mesh
+    from paper_2211_11303_gb300 import hlu
+    for n in (1, 2, 5):
+        xyz, tets = hlu.hlu_mesh_kuhn_cube(n)
+        c, t = synth.perturbed_kuhn_mesh(n, 0.0, 1)
+        assert np.array_equal(tets, t) and np.array_equal(xyz, c)
+        lat, ot = mesh.kuhn_cube(n)
+        assert np.array_equal(tets, ot) and np.array_equal(xyz, lat / float(n))
+
+
+def test_general_mesh_arguments_are_checked(lib):
+    """Invalid general meshes are refused before any device work."""
+    from paper_2211_11303_gb300 import hlu
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], dtype=np.float64)
+    good = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], dtype=np.int32)
+    h = ctypes.c_void_p()
+
+    def build(x, t):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.int32)
+        m = hlu.hlu_mesh(x.shape[0], t.shape[0], x.ctypes.data, t.ctypes.data, 0)
+        return lib.hlu_build(ctypes.byref(m), 1.0, 32, 2.0, 1e-4, 0, None, ctypes.byref(h))
+
+    assert build(xyz, np.array([[0, 1, 2, 5]])) == 1       # vertex id out of range
+    assert build(xyz, np.array([[0, 1, 1, 3]])) == 1       # repeated vertex
+    bad = xyz.copy()
+    bad[4, 2] = np.nan
+    assert build(bad, good) == 1                           # non-finite coordinate
+    assert build(xyz[:3], np.array([[0, 1, 2, 0]])) == 1   # fewer than 4 vertices

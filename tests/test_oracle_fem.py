@@ -157,3 +157,22 @@ def test_constant_current_rhs_equals_exact_element_integrals():
                 if e is not None:
                     ref[e] += vol / 4.0 * J @ (grads[c] - grads[a])
     assert np.abs(b - ref).max() <= 1e-15 * 10 + 1e-14 * np.abs(ref).max()
+
+
+def test_general_mesh_de_rham_symmetry_and_nullspace():
+    """On a perturbed (non-lattice) mesh the assembled K annihilates the
+    gradients of the interior vertex functions (the discrete de Rham
+    property holds on any mesh), K and M are symmetric, M is SPD and the null
+    space of K has the dimension of the interior vertices."""
+    import synth
+    coords, tets = synth.perturbed_kuhn_mesh(3, 0.2, 11)
+    m = M.general_mesh(coords, tets)
+    K, Mm = F.assemble(m, 1.0, parts=True)
+    G = F.gradient_matrix(m)
+    assert G.shape[1] == 8  # (n - 1)^3 interior vertices
+    assert abs(K @ G).max() < 1e-12 * abs(K).max()
+    assert abs(K - K.T).max() < 1e-13 * abs(K).max() and abs(Mm - Mm.T).max() < 1e-15
+    ev_m = sla.eigvalsh(Mm.toarray())
+    assert ev_m.min() > 0
+    ev_k = sla.eigvalsh(K.toarray(), Mm.toarray())
+    assert int(np.sum(np.abs(ev_k) < 1e-8)) == G.shape[1]

@@ -83,3 +83,51 @@ def test_interior_edges_sorted_and_oriented():
         for ax in range(3):
             for val in (0, 3):
                 assert not (lat[lo, ax] == val and lat[hi, ax] == val)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_general_mesh_reproduces_the_kuhn_lattice_rules(n):
+    """Given the Kuhn cube as plain coordinates and tetrahedra, the general
+    rule (a boundary face belongs to one tetrahedron, boundary edges and
+    vertices lie on boundary faces) selects exactly the edges and vertices the
+    lattice rule (both end points on one face of the cube) selects."""
+    import synth
+    coords, tets = synth.perturbed_kuhn_mesh(n, 0.0, 1)
+    g = M.general_mesh(coords, tets)
+    m = M.interior_edges(n)
+    assert np.array_equal(g["edges"], m["edges"])
+    assert np.array_equal(g["boundary_vertex"], m["boundary_vertex"])
+    assert len(g["edges"]) == M.n_interior_edges_formula(n)
+
+
+def test_general_mesh_points_are_exact_quantised_midpoints():
+    import synth
+    coords, tets = synth.perturbed_kuhn_mesh(3, 0.2, 7)
+    g = M.general_mesh(coords, tets)
+    lo = coords.min(axis=0)
+    extent = (coords.max(axis=0) - lo).max()
+    s = M.point_scale(extent)
+    assert s == 2.0 ** 20 and 2 * extent * s <= 2 ** 21  # unit cube
+    mid = coords[g["edges"][:, 0]] + coords[g["edges"][:, 1]] - 2 * lo
+    assert np.abs(g["points"] - mid * s).max() <= 0.5
+    assert g["points"].min() >= 0 and g["points"].max() <= 2 ** 21
+
+
+def test_perturbed_mesh_is_valid():
+    """No tetrahedron of the perturbed cube inverts (each keeps the
+    orientation it has on the lattice, which alternates with the parity of
+    its axis permutation), the tetrahedra still tile the unit cube (volumes
+    sum to 1) and the Euler characteristic is 1."""
+    import synth
+
+    def signed(coords, tets):
+        P = coords[tets]
+        return np.einsum("ti,ti->t", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0])) / 6.0
+
+    c0, t0 = synth.perturbed_kuhn_mesh(4, 0.0, 3)
+    coords, tets = synth.perturbed_kuhn_mesh(4, 0.2, 3)
+    v0, v = signed(c0, t0), signed(coords, tets)
+    assert np.all(np.sign(v) == np.sign(v0)) and np.abs(v).min() > 0
+    assert abs(np.abs(v).sum() - 1.0) < 1e-12
+    V, E, F, T = len(coords), len(M.all_edges(tets)), len(M.all_faces(tets)), len(tets)
+    assert V - E + F - T == 1

@@ -60,6 +60,10 @@ extern "C" {
                       its remainder so that the products keep FP32 accuracy;
                       LU, QR, SVD and the triangular solves in FP32 */
 
+/* ---- preconditioners of gmres_solve / hlu_richardson ------------------- */
+#define HLU_PRECOND_LU 0   /* (LU)_H^-1 of hlu_factor (Alg. 1 step III), the default */
+#define HLU_PRECOND_HINV 1 /* B_H ~ A_H^-1 of hlu_hinverse (Sec. 3: Schulz iteration) */
+
 /* ---- block kinds in the exported block tree ------------------------------ */
 #define HLU_BLOCK_ADM 0   /* admissible: low-rank X Y^T (Definition 1)       */
 #define HLU_BLOCK_DENSE 1 /* inadmissible with a leaf cluster: dense         */
@@ -331,6 +335,51 @@ void hlu_gmres_end(hlu_gmres* g);
  * gmres_solve.  Synchronous. */
 int hlu_richardson(const hlu_handle* h, const double* b_dev, double* x_dev, int32_t nrhs,
                    int64_t ld, double tol, int32_t maxit, hlu_stats* stats, void* stream);
+
+/* Record of hlu_hinverse. */
+#define HLU_HINV_MAX_ITERS 64
+typedef struct {
+  int32_t iterations;          /* Schulz steps taken                                 */
+  int32_t n_residuals;         /* entries of residual[] (iterations + 1)             */
+  double residual[HLU_HINV_MAX_ITERS + 1]; /* max over 4 probes z of ||z - A B z|| / ||z||,
+                                               for X_0, X_1, ...                      */
+  double alpha;                /* X_0 = alpha A_H, alpha = 1 / (||A||_1 ||A||_inf)    */
+  int32_t rank_max;            /* largest rank of an admissible block of B_H          */
+  int32_t reserved;
+  double rank_mean;
+  int64_t inverse_live_bytes;  /* B_H's words at live ranks (what an apply reads)     */
+  int64_t arena_bytes;         /* device bytes of the iteration's four H-matrices,
+                                  ring and vectors                                    */
+  int64_t n_iter_tasks;        /* tasks of one Schulz step                            */
+  double schedule_ms;          /* host time of the first build of the schedules       */
+  double total_ms;             /* wall time of the call                               */
+} hlu_hinv_info;
+
+/* hlu_hinverse - B_H ~ A_H^-1 by the Schulz iteration (Sec. 3, "the inverse
+ * ... by the iterative method of Schulz"; Sec. 4 truncated SVDs of the
+ * admissible blocks; Example 2): X_0 = alpha A_H, then per step T = A_H (.) X,
+ * X <- 2 X - X (.) T, the formatted H-products of the factorisation (son
+ * products, agglomeration, truncation to s_i > eps s_1 at rank capacity
+ * `rank_cap` of hlu_build), all tasks of a step in one persistent launch, in
+ * FP32 or FP64.  After every step the residual ||I - A B|| is estimated by 4
+ * fixed probe vectors; the iteration stops when it is <= tol, after maxit
+ * steps, at the floor the truncation leaves (the estimate rises again after
+ * falling a hundredfold), or on divergence (above 10: HLU_ERR_NOT_CONVERGED,
+ * no inverse).  *info (may be NULL) is filled.  The first call builds the four
+ * H-matrix copies' schedules on the host.  Synchronous.  HLU_ERR_ARG for
+ * tol <= 0, maxit outside [0, HLU_HINV_MAX_ITERS] or HLU_TF32. */
+int hlu_hinverse(hlu_handle* h, int32_t precision, double tol, int32_t maxit, hlu_hinv_info* info, void* stream);
+
+/* hlu_hinverse_apply - x = B_H b (H-matrix times nrhs vectors; same vector
+ * conventions as hlu_solve).  Synchronous.  HLU_ERR_STATE without an inverse. */
+int hlu_hinverse_apply(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream);
+
+/* hlu_set_preconditioner - preconditioner of gmres_solve and hlu_richardson on
+ * this handle: HLU_PRECOND_LU (default; needs hlu_factor) or HLU_PRECOND_HINV
+ * (the inverse B_H used "as a preconditioner to solve the linear system",
+ * Sec. 4, Example 2; needs hlu_hinverse).  The serving calls (hlu_gmres_*)
+ * use the H-LU.  HLU_ERR_ARG for another value. */
+int hlu_set_preconditioner(hlu_handle* h, int32_t which);
 
 /* hlu_factor_batch - factor `count` built handles in ONE persistent launch
  * (their task DAGs interleaved), sharing the device.  Same semantics as

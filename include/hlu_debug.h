@@ -99,6 +99,17 @@ int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int32_t K, int
  * destroyed.  HLU_ERR_ARG for dof outside [0, N).  Synchronous. */
 int hlu_debug_zero_dof(hlu_handle* h, int64_t dof);
 
+/* hlu_debug_host_hinverse - the Schulz inverse's task DAGs (hlu_hinverse)
+ * run by the host reference executor in FP64 (no GPU): A_H from the CSR
+ * matrix (original order) and the exported trees, X_0 = alpha A_H, `iters`
+ * Schulz steps, then x = X b for nrhs (1..16) columns of b (N x nrhs,
+ * column-major, original order).  info: int64[5] (tasks of a step, tasks of
+ * an apply, largest rank of X, capacity hits, status); may be NULL. */
+int hlu_debug_host_hinverse(int32_t nc, const int32_t* clusters, int32_t nb, const int32_t* blocks,
+                            const int32_t* perm, const int64_t* rowptr, const int32_t* col, const double* val,
+                            double eps, int32_t rank_cap, int32_t tile, double alpha, int32_t iters, int32_t nrhs,
+                            const double* b, double* x, int64_t* info);
+
 /* hlu_debug_wait_timeout - fault injection for the bounded device waits (needs a
  * GPU).  Runs the task executor with one CTA on a two-task schedule in which
  * task 1 waits for itself: task 0 runs, and the CTA that claims queue slot 1

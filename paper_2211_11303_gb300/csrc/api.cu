@@ -213,6 +213,56 @@ struct KrylovWS {
 
 }  // namespace
 
+namespace {
+// The Schulz inverse of A_H (hlu_hinverse): four copies of the factor tree in
+// its own arena, the start / iteration / apply schedules, and the iteration's
+// record.
+struct InvState {
+  bool built = false, ready = false;
+  int precision = -1;
+  ArenaLayout L;
+  std::vector<Block> Bx;
+  SchedStats st;
+  DevSched start, iter, apply;
+  FillDesc* d_fill_dense = nullptr;
+  FillDesc* d_fill_lr = nullptr;
+  int32_t n_fill_dense = 0, n_fill_lr = 0;
+  int64_t dense_rows = 0;
+  void* d_arena = nullptr;
+  int32_t* d_ranks = nullptr;
+  int32_t* d_piv = nullptr;
+  void* d_scratch = nullptr;
+  int64_t scratch_stride = 0;
+  int grid = 0;
+  int32_t* d_status = nullptr;
+  double* d_flops = nullptr;
+  double* d_z = nullptr;  // residual-estimate probes (N x 4) and workspace (N x 8)
+  double* d_w = nullptr;
+  double alpha = 0;
+  std::vector<double> res;
+  void free_data() {
+    for (void* p : {d_arena, (void*)d_ranks, (void*)d_piv, d_scratch, (void*)d_status, (void*)d_flops})
+      if (p) dev_free(p);
+    d_arena = d_scratch = nullptr;
+    d_ranks = d_piv = d_status = nullptr;
+    d_flops = nullptr;
+    precision = -1;
+    ready = false;
+  }
+  void free_all() {
+    free_data();
+    start.free_all();
+    iter.free_all();
+    apply.free_all();
+    for (void* p : {(void*)d_fill_dense, (void*)d_fill_lr, (void*)d_z, (void*)d_w})
+      if (p) dev_free(p);
+    d_fill_dense = d_fill_lr = nullptr;
+    d_z = d_w = nullptr;
+    built = false;
+  }
+};
+}  // namespace
+
 struct hlu_handle {
   int n = 0, leaf = 0, rank_cap = kRankMax;
   double kappa = 0, eta = 0, eps = 0;
@@ -252,6 +302,8 @@ struct hlu_handle {
   unsigned long long* d_trace = nullptr; // per-task trace of the next factorisation (debug)
   bool factor_pending = false;           // hlu_factor_async launched, hlu_factor_wait not yet done
   cudaStream_t factor_stream = nullptr;
+  InvState inv;                          // Schulz inverse of A_H (hlu_hinverse)
+  int32_t precond = HLU_PRECOND_LU;      // preconditioner of gmres_solve / hlu_richardson
 };
 
 namespace {
@@ -502,8 +554,93 @@ int solve_impl(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, i
   return HLU_OK;
 }
 
-int solve_any(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+// One launch of the executor over a schedule of the Schulz inverse (its own
+// arena and rank slots); alpha is the launch scalar of the start, nrhs the
+// column count of the apply.
+int exec_run_inv(hlu_handle* h, DevSched& ds, double alpha, int32_t nrhs, cudaStream_t s) {
+  InvState& iv = h->inv;
+  ExecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  ProbSched& p = a.probs[0];
+  p.tasks = ds.tasks;
+  p.terms = ds.terms;
+  p.pieces = ds.pieces;
+  p.succ_ptr = ds.succ_ptr;
+  p.succ_idx = ds.succ_idx;
+  p.indeg = ds.indeg;
+  p.arena = iv.d_arena;
+  p.ranks = iv.d_ranks;
+  p.piv = iv.d_piv;
+  p.eps = h->eps;
+  p.ntasks = ds.ntasks;
+  p.limit = ds.ntasks;
+  p.nrhs_slot = iv.L.nrhs_slot;
+  p.nrhs = nrhs;
+  p.term_p = nullptr;
+  p.alpha = alpha;
+  a.nprobs = 1;
+  a.ntotal = ds.ntasks;
+  a.queue = ds.queue;
+  a.qctl = ds.qctl;
+  a.scratch = iv.d_scratch;
+  a.scratch_stride = iv.scratch_stride;
+  a.trunc_rows = std::max(iv.L.max_trunc_rows, 1);
+  a.status = iv.d_status;
+  a.flops = iv.d_flops;
+  a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+  a.jacobi_tol = g_jacobi_tol;
+  a.compress_at = g_compress_at;
+  if (a.ntotal == 0) return HLU_OK;
+  const int64_t nr = ds.root_count(-1);
+  int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+  unsigned long long q0[2] = {0ULL, (unsigned long long)nr};
+  CKR(cudaMemcpyAsync(iv.d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status reset");
+  CKR(cudaMemcpyAsync(ds.qctl, q0, sizeof(q0), cudaMemcpyHostToDevice, s), "queue reset");
+  CKR(cudaMemcpyAsync(ds.indeg, ds.indeg0, sizeof(int32_t) * ds.ntasks, cudaMemcpyDeviceToDevice, s), "counters");
+  CKR(cudaMemcpyAsync(ds.queue, ds.roots, sizeof(unsigned long long) * nr, cudaMemcpyDeviceToDevice, s), "roots");
+  if (a.ntotal > nr)
+    CKR(cudaMemsetAsync(ds.queue + nr, 0, sizeof(unsigned long long) * (a.ntotal - nr), s), "queue clear");
+  const int g = (int)std::min<int64_t>(iv.grid, a.ntotal);
+  CKR(launch_exec(iv.precision, a, g, s), "executor launch");
+  int32_t stf[8];
+  CKR(cudaMemcpyAsync(stf, iv.d_status, sizeof(stf), cudaMemcpyDeviceToHost, s), "status read");
+  CKR(cudaStreamSynchronize(s), "sync");
+  if (stf[0] == 5) return fail(HLU_ERR_TIMEOUT, "device wait exceeded its limit");
+  return HLU_OK;
+}
+
+// x = B_H b through the apply schedule, nrhs_max columns per launch
+template <class T>
+int hinv_apply_impl(hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+  InvState& iv = h->inv;
+  const int64_t N = h->A.N;
+  T* work = reinterpret_cast<T*>(iv.d_arena) + iv.L.work_off;
+  T* out = reinterpret_cast<T*>(iv.d_arena) + iv.L.out_off;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += iv.L.nrhs_max) {
+    const int32_t nc = std::min(iv.L.nrhs_max, nrhs - c0);
+    CKR(set_int(iv.d_ranks + iv.L.nrhs_slot, nc, s), "nrhs slot");
+    CKR(gather_cast<T>(N, h->d_perm, b + c0 * ld, ld, work, nc, s), "gather");
+    int rc = exec_run_inv(h, iv.apply, 0.0, nc, s);
+    if (rc) return rc;
+    CKR(scatter_cast<T>(N, h->d_perm, out, x + c0 * ld, ld, nc, s), "scatter");
+  }
+  return HLU_OK;
+}
+int hinv_apply_any(hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+  return h->inv.precision == HLU_FP64 ? hinv_apply_impl<double>(h, b, x, nrhs, ld, s)
+                                      : hinv_apply_impl<float>(h, b, x, nrhs, ld, s);
+}
+
+// the preconditioner of the Krylov solvers: the H-LU solve, or B_H x
+int solve_any(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, cudaStream_t s) {
+  hlu_handle* h = const_cast<hlu_handle*>(hc);
+  if (h->precond == HLU_PRECOND_HINV) return hinv_apply_any(h, b, x, nrhs, ld, s);
   return h->precision == HLU_FP64 ? solve_impl<double>(h, b, x, nrhs, ld, s) : solve_impl<float>(h, b, x, nrhs, ld, s);
+}
+// whether the selected preconditioner can run
+bool precond_ready(const hlu_handle* h) {
+  if (h->precond == HLU_PRECOND_HINV) return h->inv.ready;
+  return h->precision >= 0 && !h->factor_pending;
 }
 
 int ensure_kw(hlu_handle* h, int m, int nr) {
@@ -726,6 +863,7 @@ int64_t hlu_launch_count(void) { return g_launches.load(); }
 void hlu_destroy(hlu_handle* h) {
   if (!h) return;
   if (h->factor_pending) cudaEventSynchronize(h->ev1);  // no kernel may still use the memory
+  h->inv.free_all();
   free_factor(h);
   h->dF.free_all();
   h->dS.free_all();
@@ -1143,7 +1281,7 @@ int gmres_solve(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, 
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
       return fail(HLU_ERR_ARG, "bad argument");
-    if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
+    if (!precond_ready(h)) return fail(HLU_ERR_STATE, "preconditioner not ready (not factored)");
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     if (stats) {
@@ -1173,7 +1311,7 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
   try {
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!h || !b || !x || nrhs < 1 || ld < h->A.N || !(tol > 0) || maxit < 1) return fail(HLU_ERR_ARG, "bad argument");
-    if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
+    if (!precond_ready(h)) return fail(HLU_ERR_STATE, "preconditioner not ready (not factored)");
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     int rc = ensure_kw(h, 1, std::min(nrhs, h->L.nrhs_max));
@@ -1239,6 +1377,216 @@ int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrh
   } catch (const std::exception& ex) {
     return fail(HLU_ERR_CUDA, ex.what());
   }
+}
+
+int hlu_set_preconditioner(hlu_handle* h, int32_t which) {
+  if (!h || (which != HLU_PRECOND_LU && which != HLU_PRECOND_HINV)) return fail(HLU_ERR_ARG, "bad argument");
+  h->precond = which;
+  return HLU_OK;
+}
+
+int hlu_hinverse(hlu_handle* h, int32_t precision, double tol, int32_t maxit, hlu_hinv_info* info, void* stream) {
+  try {
+    if (!h || !(tol > 0) || maxit < 0 || maxit > HLU_HINV_MAX_ITERS) return fail(HLU_ERR_ARG, "bad argument");
+    if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision (FP64 or FP32)");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    InvState& iv = h->inv;
+    const int64_t N = h->A.N;
+    if (!iv.built) {
+      Schedule S0, S1, S2;
+      build_inverse_schedules(h->C, h->sb->FB, h->rank_cap, 16, h->tile, iv.L, iv.Bx, S0, S1, S2, iv.st);
+      CKR(iv.start.load(S0), "upload start schedule");
+      CKR(iv.iter.load(S1), "upload iteration schedule");
+      CKR(iv.apply.load(S2), "upload apply schedule");
+      for (DevSched* d : {&iv.start, &iv.iter, &iv.apply}) CKR(d->alloc_state(), "queue");
+      // A_H fill descriptors of copy 0
+      std::vector<FillDesc> fd, fl;
+      int64_t rows = 0;
+      const size_t nb = h->sb->FB.size();
+      for (size_t b = 0; b < nb; ++b) {
+        const Block& bk = iv.Bx[b];
+        if (bk.kind == KIND_SUB) continue;
+        FillDesc f;
+        std::memset(&f, 0, sizeof(f));
+        f.roff = h->C[bk.row].off;
+        f.m = h->C[bk.row].size;
+        f.coff = h->C[bk.col].off;
+        f.n = h->C[bk.col].size;
+        if (bk.kind == KIND_DENSE) {
+          f.off = iv.L.dense_off[b];
+          f.row_prefix = rows;
+          rows += f.m;
+          fd.push_back(f);
+        } else {
+          f.off = iv.L.x_off[b];
+          f.off2 = iv.L.y_off[b];
+          f.slot = iv.L.slot[b];
+          f.cap = iv.L.cap[b];
+          fl.push_back(f);
+        }
+      }
+      iv.n_fill_dense = (int32_t)fd.size();
+      iv.n_fill_lr = (int32_t)fl.size();
+      iv.dense_rows = rows;
+      CKR(upload(&iv.d_fill_dense, fd), "fill desc");
+      CKR(upload(&iv.d_fill_lr, fl), "fill desc");
+      // residual probes: 4 columns of uniforms in [-1, 1) (SplitMix64)
+      std::vector<double> z((size_t)N * 4);
+      uint64_t st = 0x5eedULL;
+      for (double& v : z) {
+        st += 0x9E3779B97F4A7C15ULL;
+        uint64_t q = st;
+        q = (q ^ (q >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        q = (q ^ (q >> 27)) * 0x94D049BB133111EBULL;
+        q ^= q >> 31;
+        v = 2.0 * ((double)(q >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+      }
+      CKR(upload(&iv.d_z, z), "probes");
+      CKR(dev_malloc(&iv.d_w, sizeof(double) * N * 8), "probe workspace");
+      iv.built = true;
+    }
+    const int es = esize(precision);
+    if (iv.precision != precision) {
+      iv.free_data();
+      int dev = 0, sms = 0;
+      CKR(cudaGetDevice(&dev), "device");
+      CKR(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sms");
+      const int bps = precision == HLU_FP64 ? blocks_per_sm<double>() : blocks_per_sm<float>();
+      if (bps < 1) return fail(HLU_ERR_CUDA, "executor does not fit on an SM");
+      iv.grid = sms * bps;
+      iv.scratch_stride = scratch_stride_elems(iv.L, es);
+      CKR(dev_malloc(&iv.d_arena, (size_t)es * iv.L.total), "inverse arena");
+      CKR(dev_malloc(&iv.d_ranks, sizeof(int32_t) * std::max(iv.L.n_slots, 1)), "ranks");
+      CKR(dev_malloc(&iv.d_piv, sizeof(int32_t)), "piv");
+      CKR(dev_malloc(&iv.d_scratch, (size_t)es * iv.scratch_stride * iv.grid), "scratch");
+      CKR(dev_malloc(&iv.d_status, sizeof(int32_t) * 8), "status");
+      CKR(dev_malloc(&iv.d_flops, sizeof(double)), "flops");
+      iv.precision = precision;
+    }
+    iv.ready = false;
+    CKR(cudaMemsetAsync(iv.d_ranks, 0, sizeof(int32_t) * std::max(iv.L.n_slots, 1), s), "ranks");
+    int32_t st0[8] = {0, -1, 0, 0, 0, 0, 0, 0};
+    CKR(cudaMemcpyAsync(iv.d_status, st0, sizeof(st0), cudaMemcpyHostToDevice, s), "status");
+    cudaError_t e;
+    if (precision == HLU_FP64)
+      e = fill_ah<double>(h->A, h->d_perm, h->d_iperm, iv.d_fill_dense, iv.n_fill_dense, iv.dense_rows, iv.d_fill_lr,
+                          iv.n_fill_lr, (double*)iv.d_arena, iv.L.work_off, iv.L.ident_off, iv.L.ident_n, iv.d_ranks,
+                          iv.d_status, s);
+    else
+      e = fill_ah<float>(h->A, h->d_perm, h->d_iperm, iv.d_fill_dense, iv.n_fill_dense, iv.dense_rows, iv.d_fill_lr,
+                         iv.n_fill_lr, (float*)iv.d_arena, iv.L.work_off, iv.L.ident_off, iv.L.ident_n, iv.d_ranks,
+                         iv.d_status, s);
+    CKR(e, "A_H fill");
+    // alpha = 1 / (||A||_1 ||A||_inf) from the CSR
+    {
+      std::vector<int64_t> rp(N + 1);
+      std::vector<int32_t> ci(h->A.nnz);
+      std::vector<double> va(h->A.nnz);
+      CKR(cudaMemcpy(rp.data(), h->A.rowptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost), "csr");
+      CKR(cudaMemcpy(ci.data(), h->A.col, sizeof(int32_t) * h->A.nnz, cudaMemcpyDeviceToHost), "csr");
+      CKR(cudaMemcpy(va.data(), h->A.val, sizeof(double) * h->A.nnz, cudaMemcpyDeviceToHost), "csr");
+      std::vector<double> colsum(N, 0.0);
+      double ninf = 0;
+      for (int64_t r = 0; r < N; ++r) {
+        double rs = 0;
+        for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+          rs += std::fabs(va[q]);
+          colsum[ci[q]] += std::fabs(va[q]);
+        }
+        ninf = std::max(ninf, rs);
+      }
+      double n1 = 0;
+      for (double c : colsum) n1 = std::max(n1, c);
+      iv.alpha = 1.0 / (n1 * ninf);
+    }
+    int rc = exec_run_inv(h, iv.start, iv.alpha, 0, s);
+    if (rc) return rc;
+    rc = ensure_kw(h, 1, 4);
+    if (rc) return rc;
+    // ||z - A B z|| / ||z|| over the 4 probes
+    std::vector<double> zn(4);
+    rc = col_norms(h, iv.d_z, N, 4, h->kw.hn, zn.data(), s);
+    if (rc) return rc;
+    auto estimate = [&](double* out) -> int {
+      int r2 = hinv_apply_any(h, iv.d_z, iv.d_w, 4, N, s);
+      if (r2) return r2;
+      CKR(residual(h->A.rowptr, h->A.col, h->A.val, N, iv.d_w, N, iv.d_z, N, iv.d_w + 4 * N, N, 4, s), "residual");
+      std::vector<double> rn(4);
+      r2 = col_norms(h, iv.d_w + 4 * N, N, 4, h->kw.hn, rn.data(), s);
+      if (r2) return r2;
+      double m = 0;
+      for (int j = 0; j < 4; ++j) m = std::max(m, rn[j] / zn[j]);
+      *out = m;
+      return HLU_OK;
+    };
+    iv.res.clear();
+    double r0 = 0;
+    if ((rc = estimate(&r0))) return rc;
+    iv.res.push_back(r0);
+    bool diverged = false;
+    int it = 0;
+    while (iv.res.back() > tol && it < maxit) {
+      if ((rc = exec_run_inv(h, iv.iter, 0.0, 0, s))) return rc;
+      double r = 0;
+      if ((rc = estimate(&r))) return rc;
+      ++it;
+      if (!std::isfinite(r) || r > 10.0) {
+        diverged = true;
+        iv.res.push_back(r);
+        break;
+      }
+      iv.res.push_back(r);
+      // the truncation floor: the estimate rises again after it had fallen a
+      // hundredfold (before that, the Schulz residual only falls: the
+      // residual matrix squares each step)
+      const double prev = iv.res[iv.res.size() - 2];
+      if (r > prev && prev < 1e-2 * iv.res[0]) break;
+    }
+    iv.ready = !diverged;
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iterations = it;
+      info->alpha = iv.alpha;
+      info->n_residuals = (int32_t)std::min<size_t>(iv.res.size(), HLU_HINV_MAX_ITERS + 1);
+      for (int32_t k = 0; k < info->n_residuals; ++k) info->residual[k] = iv.res[k];
+      std::vector<int32_t> rk(std::max(iv.L.n_slots, 1));
+      CKR(cudaMemcpy(rk.data(), iv.d_ranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost), "ranks");
+      const size_t nb = h->sb->FB.size();
+      int64_t rs = 0, na = 0, live = 0;
+      for (size_t b = nb; b < 2 * nb; ++b) {  // copy 1: the inverse
+        const Block& bk = iv.Bx[b];
+        const int64_t m = h->C[bk.row].size, n = h->C[bk.col].size;
+        if (bk.kind == KIND_ADM) {
+          const int32_t r = rk[iv.L.slot[b]];
+          info->rank_max = std::max(info->rank_max, r);
+          rs += r;
+          ++na;
+          live += (m + n) * r;
+        } else if (bk.kind == KIND_DENSE) {
+          live += m * n;
+        }
+      }
+      info->rank_mean = na ? (double)rs / na : 0.0;
+      info->inverse_live_bytes = live * es;
+      info->arena_bytes = iv.L.total * es;
+      info->n_iter_tasks = iv.iter.ntasks;
+      info->schedule_ms = iv.st.host_ms;
+      info->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return diverged ? fail(HLU_ERR_NOT_CONVERGED, "Schulz iteration diverged (truncation too coarse)") : HLU_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(HLU_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& ex) {
+    return fail(HLU_ERR_CUDA, ex.what());
+  }
+}
+
+int hlu_hinverse_apply(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream) {
+  hlu_handle* h = const_cast<hlu_handle*>(hc);
+  if (!h || !b || !x || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
+  if (!h->inv.ready) return fail(HLU_ERR_STATE, "no inverse (hlu_hinverse)");
+  return hinv_apply_any(h, b, x, nrhs, ld, (cudaStream_t)stream);
 }
 
 int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream) {

@@ -182,3 +182,81 @@ extern "C" int hlu_debug_host_factor_prefix(int32_t nc, const int32_t* clusters,
     return 6;
   }
 }
+
+// The Schulz inverse's schedules run by the host reference executor (FP64):
+// A_H into copy 0, X_0 = alpha A_H, `iters` Schulz steps, then x = X b.
+extern "C" int hlu_debug_host_hinverse(int32_t nc, const int32_t* clusters, int32_t nb, const int32_t* blocks,
+                                       const int32_t* perm, const int64_t* rowptr, const int32_t* col,
+                                       const double* val, double eps, int32_t rank_cap, int32_t tile,
+                                       double alpha, int32_t iters, int32_t nrhs, const double* b, double* x,
+                                       int64_t* info) {
+  try {
+    if (!clusters || !blocks || !perm || !rowptr || !col || !val || nrhs < 1 || nrhs > 16 || eps <= 0 || iters < 0)
+      return 1;
+    std::vector<Cluster> C;
+    std::vector<Block> B;
+    trees_from_export(nc, clusters, nb, blocks, C, B);
+    const int32_t N = C[0].size;
+    std::vector<Block> FB = factor_tree(C, B, tile);
+    ArenaLayout L;
+    std::vector<Block> Bx;
+    Schedule S0, S1, S2;
+    SchedStats st;
+    build_inverse_schedules(C, FB, rank_cap > 0 ? rank_cap : kRankMax, 16, tile, L, Bx, S0, S1, S2, st);
+    std::vector<double> arena(L.total, 0.0);
+    std::vector<int32_t> ranks(std::max(L.n_slots, 1), 0), piv(1, 0);
+    for (int32_t i = 0; i < L.ident_n; ++i) arena[L.ident_off + i + (int64_t)i * L.ident_n] = 1.0;
+    std::vector<int32_t> iperm(N);
+    for (int32_t i = 0; i < N; ++i) iperm[perm[i]] = i;
+    for (size_t bi = 0; bi < FB.size(); ++bi) {  // A_H: copy 0
+      const Block& bk = Bx[bi];
+      if (bk.kind == KIND_SUB) continue;
+      const Cluster& R = C[bk.row];
+      const Cluster& Q = C[bk.col];
+      int32_t kk = 0;
+      for (int32_t i = 0; i < R.size; ++i) {
+        const int32_t orow = perm[R.off + i];
+        bool any = false;
+        for (int64_t e = rowptr[orow]; e < rowptr[orow + 1]; ++e) {
+          const int32_t j = iperm[col[e]] - Q.off;
+          if (j < 0 || j >= Q.size) continue;
+          if (bk.kind == KIND_DENSE) {
+            arena[L.dense_off[bi] + i + (int64_t)j * R.size] = val[e];
+          } else {
+            if (!any) {
+              if (kk >= L.cap[bi]) return 7;
+              arena[L.x_off[bi] + i + (int64_t)kk * R.size] = 1.0;
+              any = true;
+            }
+            arena[L.y_off[bi] + j + (int64_t)kk * Q.size] = val[e];
+          }
+        }
+        if (any) ++kk;
+      }
+      if (bk.kind == KIND_ADM) ranks[L.slot[bi]] = kk;
+    }
+    int32_t cap_hits = 0;
+    int stt = host_execute<double>(S0, arena.data(), ranks.data(), piv.data(), eps, 0, &cap_hits, -1, alpha);
+    for (int32_t k = 0; k < iters && !stt; ++k)
+      stt = host_execute<double>(S1, arena.data(), ranks.data(), piv.data(), eps, 0, &cap_hits);
+    ranks[L.nrhs_slot] = nrhs;
+    for (int32_t j = 0; j < nrhs; ++j)
+      for (int32_t i = 0; i < N; ++i) arena[L.work_off + i + (int64_t)j * N] = b[perm[i] + (int64_t)j * N];
+    if (!stt) stt = host_execute<double>(S2, arena.data(), ranks.data(), piv.data(), eps, 0, &cap_hits);
+    for (int32_t j = 0; j < nrhs; ++j)
+      for (int32_t i = 0; i < N; ++i) x[perm[i] + (int64_t)j * N] = arena[L.out_off + i + (int64_t)j * N];
+    if (info) {
+      int32_t rmax = 0;
+      for (size_t bi = FB.size(); bi < 2 * FB.size(); ++bi)
+        if (Bx[bi].kind == KIND_ADM) rmax = std::max(rmax, ranks[L.slot[bi]]);
+      info[0] = (int64_t)S1.tasks.size();
+      info[1] = (int64_t)S2.tasks.size();
+      info[2] = rmax;
+      info[3] = cap_hits;
+      info[4] = stt;
+    }
+    return stt;
+  } catch (const std::exception&) {
+    return 6;
+  }
+}

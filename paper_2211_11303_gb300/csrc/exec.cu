@@ -100,6 +100,7 @@ struct Ctx {
   int32_t nrhs_slot, nrhs;  // the launch's right-hand-side count and its slot
   const int32_t* term_p;    // resolved term column counts (solve launches) or null
   TcCtl* tcc;               // tensor-core tile products (FP32 factorisations with TF32) or null
+  double alpha;             // the launch's scalar for TF_ALPHA / PF_ALPHA
 };
 
 template <class T>
@@ -875,7 +876,8 @@ __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
       if (k > 0)
         tile_mma(acc, shift(mat(c, t.a), i0, 0), 0, min(64, m - i0), shift(matT(c, t.b), 0, j0), min(64, n - j0), k,
                  As, Bs, c.tcc);
-      tile_store(acc, c, t.c, i0, j0, min(64, m - i0), min(64, n - j0), T(t.sign), (t.flags & TF_OVERWRITE) != 0);
+      const T sg = (t.flags & TF_ALPHA) ? T(t.sign) * T(c.alpha) : T(t.sign);
+      tile_store(acc, c, t.c, i0, j0, min(64, m - i0), min(64, n - j0), sg, (t.flags & TF_OVERWRITE) != 0);
     }
   if (threadIdx.x == 0) c.flops += 2.0 * m * n * k;
 }
@@ -1491,7 +1493,7 @@ __device__ int trunc_stack(Ctx<T>& c, const Task& t, TC* SX, TC* SY, TC* OX, TC*
         __syncthreads();
       }
       const int take = min(w - c0, kStackCols - W);
-      const TC sg = TC(P.sign);
+      const TC sg = (P.pad & PF_ALPHA) ? TC(P.sign) * TC(c.alpha) : TC(P.sign);
       for (int64_t idx = threadIdx.x; idx < (int64_t)m * take; idx += NT) SX[(int64_t)W * m + idx] = TC(0);
       for (int64_t idx = threadIdx.x; idx < (int64_t)n * take; idx += NT) SY[(int64_t)W * n + idx] = TC(0);
       __syncthreads();
@@ -1578,8 +1580,9 @@ struct PieceCursor {
     const Piece& P = pc[q];
     const int xl = max(P.xoff, i0), xh = min(P.xoff + P.X.rows, i0 + 64);
     const int yl = max(P.yoff, j0), yh = min(P.yoff + P.Y.rows, j0 + 64);
+    const T sg = (P.pad & PF_ALPHA) ? T(P.sign) * T(c->alpha) : T(P.sign);
     return Chunk<T>{shift(mat(*c, P.X), xl - P.xoff, l0), shift(matT(*c, P.Y), l0, yl - P.yoff), xl - i0, xh - xl,
-                    yh - yl, min(KC, w[q] - l0), yl - j0, T(P.sign)};
+                    yh - yl, min(KC, w[q] - l0), yl - j0, sg};
   }
 };
 
@@ -1885,6 +1888,7 @@ __global__ void __launch_bounds__(NT, EXEC_MIN_BLOCKS) exec_kernel(const __grid_
       c.nrhs_slot = P.nrhs_slot;
       c.nrhs = P.nrhs;
       c.term_p = P.term_p;
+      c.alpha = P.alpha;
       run_task(c, t, smem);
     }
     if (threadIdx.x == 0) asm volatile("cp.async.wait_all;" ::: "memory");

@@ -28,6 +28,7 @@ struct ProbSched {
   int32_t nrhs;             // value for this launch (read without a load)
   const int32_t* term_p;    // solve launches: each term's column count, resolved
                             // after the factorisation (-1: read it live); else null
+  double alpha;             // scalar of TF_ALPHA tasks and PF_ALPHA pieces (Schulz start)
 };
 constexpr int kMaxBatch = 64;  // problems in one launch
 // profile layout: per task kind (TK_NUM + 1 rows) tasks, wait cycles, run

@@ -48,7 +48,10 @@ enum TaskType : int32_t {
   TK_NUM = 9,
   TK_FENCE = 9    // no work: orders re-use of temporary memory after its readers
 };
-enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2 };
+// TF_ALPHA (DADD) and PF_ALPHA (a TRUNC piece): the sign is multiplied by the
+// launch's scalar alpha (the Schulz start X_0 = alpha A)
+enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2, TF_ALPHA = 4 };
+enum : int32_t { PF_ALPHA = 1 };
 
 struct Task {
   int32_t type;
@@ -70,7 +73,7 @@ struct Term {
   int32_t pad;
 };
 // TRUNC piece: sign * X Y^T placed at rows [xoff, xoff + X.rows) of the target
-// and columns [yoff, yoff + Y.rows).
+// and columns [yoff, yoff + Y.rows); pad holds PF_ flags.
 struct Piece {
   View X, Y;
   int32_t xoff, yoff;
@@ -107,6 +110,7 @@ struct ArenaLayout {
   int32_t max_trunc_rows = 0;      // largest TRUNC target dimension
   int32_t wmax = 0;                // largest stacked width of a TRUNC
   int64_t ring_off = 0, ring_size = 0;  // region for temporaries
+  int64_t out_off = -1;            // H-matrix apply: output vector (N x nrhs_max), -1 if none
 };
 
 struct SchedStats {
@@ -127,5 +131,16 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B,
                      int32_t nrhs_max, int32_t tile, ArenaLayout& L,
                      Schedule& factor, Schedule& solve, SchedStats& st, std::vector<Block>* factor_blocks);
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile);
+
+// The Schulz iteration for the inverse of A_H (Sec. 3, Sec. 4) over four
+// copies of the factor tree FB in one arena: copy 0 holds A_H, 1 the iterate
+// X, 2 the product T, 3 the next iterate Y (block b of copy q is block
+// q * |FB| + b of Bx).  start: X <- alpha A_H (alpha from the launch);
+// iter: T <- -A_H X, Y <- 2 X, Y <- Y + X T, X <- Y (formatted H-products
+// truncated to eps); apply: out <- X in for nrhs_max columns (work_off ->
+// out_off).
+void build_inverse_schedules(const std::vector<Cluster>& C, const std::vector<Block>& FB, int32_t rank_cap,
+                             int32_t nrhs_max, int32_t tile, ArenaLayout& L, std::vector<Block>& Bx,
+                             Schedule& start, Schedule& iter, Schedule& apply, SchedStats& st);
 
 }  // namespace hlu

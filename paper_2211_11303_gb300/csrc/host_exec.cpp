@@ -26,6 +26,7 @@ struct HostCtx {
   const Term* terms;
   const Piece* pieces;
   double eps;
+  double alpha = 0.0;
   int32_t status = 0;
   int32_t cap_hits = 0;
 };
@@ -138,7 +139,7 @@ void h_rowmv(HostCtx<T>& c, const Task& t) {
 template <class T>
 void h_dadd(HostCtx<T>& c, const Task& t) {
   int m = t.c.rows, n = ncols(c, t.c), k = ncols(c, t.a);
-  T sg = T(t.sign);
+  T sg = (t.flags & TF_ALPHA) ? T(t.sign) * T(c.alpha) : T(t.sign);
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < m; ++i) {
       T s = 0;
@@ -316,7 +317,8 @@ int h_trunc_stack(HostCtx<T>& c, const Task& t, std::vector<TC>& SX, std::vector
     SX.resize((size_t)m * (W + w), TC(0));
     SY.resize((size_t)n * (W + w), TC(0));
     for (int j = 0; j < w; ++j) {
-      for (int i = 0; i < P.X.rows; ++i) SX[(P.xoff + i) + (size_t)(W + j) * m] = TC(P.sign) * TC(at(c, P.X, i, j));
+      const TC sg = (P.pad & PF_ALPHA) ? TC(P.sign) * TC(c.alpha) : TC(P.sign);
+      for (int i = 0; i < P.X.rows; ++i) SX[(P.xoff + i) + (size_t)(W + j) * m] = sg * TC(at(c, P.X, i, j));
       for (int i = 0; i < P.Y.rows; ++i) SY[(P.yoff + i) + (size_t)(W + j) * n] = TC(at(c, P.Y, i, j));
     }
     W += w;
@@ -419,7 +421,7 @@ std::vector<int64_t> exec_order(const Schedule& S, uint64_t seed) {
 
 template <class T>
 int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, double eps,
-                 uint64_t order_seed, int32_t* cap_hits, int64_t limit) {
+                 uint64_t order_seed, int32_t* cap_hits, int64_t limit, double alpha) {
   HostCtx<T> c;
   c.arena = arena;
   c.ranks = ranks;
@@ -427,6 +429,7 @@ int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, doub
   c.terms = S.terms.data();
   c.pieces = S.pieces.data();
   c.eps = eps;
+  c.alpha = alpha;
   for (int64_t t : exec_order(S, order_seed)) {
     if (limit >= 0 && t >= limit) continue;
     run_task(c, S.tasks[t]);
@@ -436,8 +439,8 @@ int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, doub
 }
 
 template int host_execute<double>(const Schedule&, double*, int32_t*, int32_t*, double, uint64_t,
-                                  int32_t*, int64_t);
+                                  int32_t*, int64_t, double);
 template int host_execute<float>(const Schedule&, float*, int32_t*, int32_t*, double, uint64_t,
-                                 int32_t*, int64_t);
+                                 int32_t*, int64_t, double);
 
 }  // namespace hlu

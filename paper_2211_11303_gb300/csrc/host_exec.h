@@ -7,9 +7,10 @@
 
 namespace hlu {
 
+// alpha: the launch scalar of TF_ALPHA tasks and PF_ALPHA pieces
 template <class T>
 int host_execute(const Schedule& S, T* arena, int32_t* ranks, int32_t* piv, double eps,
-                 uint64_t order_seed, int32_t* cap_hits, int64_t limit = -1);
+                 uint64_t order_seed, int32_t* cap_hits, int64_t limit = -1, double alpha = 0.0);
 
 // Trees from the exported flat layout (clusters: nc x 12, blocks: nb x 8), with
 // the leaf ranges filled in.

@@ -595,7 +595,7 @@ class Sched {
 
   // ---------------------------------------------------------------- truncation
   void emit_trunc(const MV& X, const MV& Y, int32_t slot, int32_t cap,
-                  const std::vector<PieceMV>& ps) {
+                  const std::vector<PieceMV>& ps, bool alpha = false) {
     Task t = make(TK_TRUNC);
     t.a = X.v;
     t.b = Y.v;
@@ -613,6 +613,7 @@ class Sched {
       q.xoff = p.xoff;
       q.yoff = p.yoff;
       q.sign = p.sign;
+      q.pad = alpha ? PF_ALPHA : 0;
       S_->pieces.push_back(q);
       acc(p.p.X, false);
       acc(p.p.Y, false);
@@ -738,7 +739,10 @@ class Sched {
     }
   }
 
-  void gemm(int32_t c, int32_t a, int32_t b) {
+  // c <- c + sign * a b in the format of c (formatted H-product: son
+  // products where all three are subdivided, agglomeration otherwise); the
+  // H-LU's Schur complement update is sign = -1
+  void gemm(int32_t c, int32_t a, int32_t b, float sign = -1.0f) {
     if (kind(c) == KIND_SUB && kind(a) == KIND_SUB && kind(b) == KIND_SUB) {
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
@@ -748,16 +752,74 @@ class Sched {
           for (int k = 0; k < 2; ++k) {
             int32_t cc = son(c, i, j), aa = son(a, i, k), bb = son(b, k, j);
             if (kind(cc) == KIND_SUB && kind(aa) == KIND_SUB && kind(bb) == KIND_SUB)
-              gemm(cc, aa, bb);
+              gemm(cc, aa, bb, sign);
             else
               ps.push_back(product(aa, bb));
           }
-          add_multi(son(c, i, j), ps, -1.0f);
+          add_multi(son(c, i, j), ps, sign);
         }
       return;
     }
-    add_multi(c, {product(a, b)}, -1.0f);
+    add_multi(c, {product(a, b)}, sign);
   }
+
+  // ---------------------------------------------------------------- whole H-matrices
+  // dst <- sign * src (times the launch's alpha when `alpha`), leaf by leaf;
+  // dst and src have the same block structure.  Dense leaves: one DADD of
+  // src against the identity; admissible leaves: a truncation of the one
+  // piece (exact: the rank does not change).
+  void copy_scaled(int32_t dst, int32_t src, float sign, bool alpha) {
+    if (kind(dst) == KIND_SUB) {
+      for (int k = 0; k < 4; ++k) copy_scaled(B_[dst].son[k], B_[src].son[k], sign, alpha);
+      return;
+    }
+    if (kind(dst) == KIND_DENSE) {
+      // dense blocks have one side of at most the identity's size: D I or I D
+      Task t = make(TK_DADD);
+      t.flags = TF_OVERWRITE | (alpha ? TF_ALPHA : 0);
+      t.sign = sign;
+      t.c = mvD(dst).v;
+      if (sz(colc(dst)) <= L_.ident_n) {
+        t.a = mvD(src).v;
+        t.b = mvIdent(colc(dst)).v;
+      } else {
+        t.a = mvIdent(rowc(dst)).v;
+        t.b = mvDT(src).v;
+      }
+      begin(t);
+      acc(mvD(src), false);
+      acc(mvD(dst), true);
+      end();
+      return;
+    }
+    PieceMV p{LR{mvX(src), mvY(src)}, 0, 0, sign};
+    std::vector<PieceMV> ps{p};
+    emit_trunc(mvX(dst), mvY(dst), L_.slot[dst], L_.cap[dst], ps, alpha);
+  }
+  // dst <- 0: dense leaves overwritten with an empty product, admissible
+  // leaves truncated from no pieces (rank 0)
+  void zero(int32_t dst) {
+    if (kind(dst) == KIND_SUB) {
+      for (int k = 0; k < 4; ++k) zero(B_[dst].son[k]);
+      return;
+    }
+    if (kind(dst) == KIND_DENSE) {
+      Task t = make(TK_DADD);
+      t.flags = TF_OVERWRITE;
+      t.c = mvD(dst).v;
+      t.a = mvD(dst).v;
+      t.a.cols = 0;  // no columns: the product is zero
+      t.b = mvDT(dst).v;
+      t.b.cols = 0;
+      begin(t);
+      acc(mvD(dst), true);
+      end();
+      return;
+    }
+    emit_trunc(mvX(dst), mvY(dst), L_.slot[dst], L_.cap[dst], {});
+  }
+  // Vout <- H(b) Vin for a whole H-matrix b (its row cluster is the root)
+  void apply(int32_t b, const MV& Vin, const MV& Vout) { hmul(b, Vin, Vout, 1.0f, false, true, Vout.v.slot); }
 
   // ---------------------------------------------------------------- H-trsm, H-LU
   void trsm_left(int32_t d, int32_t b) {
@@ -981,6 +1043,99 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
   st.n_solve_tasks = (int64_t)solve.tasks.size();
   st.host_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void build_inverse_schedules(const std::vector<Cluster>& C, const std::vector<Block>& FB, int32_t rank_cap,
+                             int32_t nrhs_max, int32_t tile, ArenaLayout& L, std::vector<Block>& Bx,
+                             Schedule& start, Schedule& iter, Schedule& apply, SchedStats& st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int32_t nb = (int32_t)FB.size();
+  Bx.assign((size_t)4 * nb, Block());
+  for (int32_t q = 0; q < 4; ++q)
+    for (int32_t b = 0; b < nb; ++b) {
+      Block k = FB[b];
+      for (int s = 0; s < 4; ++s)
+        if (k.son[s] >= 0) k.son[s] += q * nb;
+      if (k.parent >= 0) k.parent += q * nb;
+      Bx[(size_t)q * nb + b] = k;
+    }
+  const size_t nx = Bx.size();
+  L = ArenaLayout();
+  L.dense_off.assign(nx, -1);
+  L.x_off.assign(nx, -1);
+  L.y_off.assign(nx, -1);
+  L.cap.assign(nx, 0);
+  L.slot.assign(nx, -1);
+  L.piv_off.assign(nx, -1);
+  int32_t leafmax = 0;
+  for (const Cluster& c : C)
+    if (c.son[0] < 0) leafmax = std::max(leafmax, c.size);
+  auto alloc = [&](int64_t n) {
+    int64_t o = L.total;
+    L.total += (n + 31) & ~int64_t(31);
+    return o;
+  };
+  L.ident_n = std::max(std::max(leafmax, tile), 1);
+  L.ident_off = alloc((int64_t)L.ident_n * L.ident_n);
+  int64_t fe = 0;
+  for (size_t b = 0; b < nx; ++b) {
+    const int32_t m = C[Bx[b].row].size, n = C[Bx[b].col].size;
+    if (Bx[b].kind == KIND_DENSE) {
+      L.dense_off[b] = alloc((int64_t)m * n);
+      fe += (int64_t)m * n;
+    } else if (Bx[b].kind == KIND_ADM) {
+      const int32_t cap = std::min(rank_cap, std::min(m, n));
+      L.cap[b] = cap;
+      L.slot[b] = L.n_slots++;
+      L.x_off[b] = alloc((int64_t)m * cap);
+      L.y_off[b] = alloc((int64_t)n * cap);
+      fe += (int64_t)(m + n) * cap;
+    }
+  }
+  L.factor_elems = fe;
+  L.nrhs_max = nrhs_max;
+  L.nrhs_slot = L.n_slots++;
+  L.work_off = alloc((int64_t)C[0].size * nrhs_max);
+  L.out_off = alloc((int64_t)C[0].size * nrhs_max);
+  const int64_t ring = std::min<int64_t>(std::max<int64_t>(8 * fe, int64_t(1) << 22), int64_t(1) << 31);
+  L.ring_off = alloc(ring);
+  L.ring_size = ring;
+  const int32_t segsz = std::max(leafmax, tile);
+  start = Schedule();
+  iter = Schedule();
+  apply = Schedule();
+  std::vector<int32_t> dbuf, xbuf, ybuf;
+  const int32_t A0 = 0, X0 = nb, T0 = 2 * nb, Y0 = 3 * nb;
+  {
+    Sched s(C, Bx, rank_cap, L, &start, dbuf, xbuf, ybuf, true, segsz, L.ring_off, ring);
+    s.copy_scaled(X0, A0, 1.0f, true);
+  }
+  {
+    Sched s(C, Bx, rank_cap, L, &iter, dbuf, xbuf, ybuf, true, segsz, L.ring_off, ring);
+    s.zero(T0);
+    s.gemm(T0, A0, X0, -1.0f);  // T = -A X
+    s.copy_scaled(Y0, X0, 2.0f, false);
+    s.gemm(Y0, X0, T0, 1.0f);   // Y = 2 X - X A X
+    s.copy_scaled(X0, Y0, 1.0f, false);
+    st.temp_elems = s.temp_elems_;
+    st.ring_wraps = s.wraps_;
+  }
+  {
+    Sched s(C, Bx, rank_cap, L, &apply, dbuf, xbuf, ybuf, true, segsz, L.ring_off, ring);
+    const int32_t N = C[0].size;
+    MV Win, Wout;
+    Win.buf = -1;  // read-only here
+    Win.clus = 0;
+    Win.v = View{L.work_off, 1, N, N, nrhs_max, L.nrhs_slot, 0};
+    Wout.buf = s.new_buf_leaves(0);
+    Wout.clus = 0;
+    Wout.v = View{L.out_off, 1, N, N, nrhs_max, L.nrhs_slot, 0};
+    s.apply(X0, Win, Wout);
+  }
+  for (Schedule* sc : {&start, &iter, &apply}) sc->n_edges = (int64_t)sc->pred_idx.size();
+  st.n_factor_tasks = (int64_t)iter.tasks.size();
+  st.n_solve_tasks = (int64_t)apply.tasks.size();
+  st.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 }  // namespace hlu

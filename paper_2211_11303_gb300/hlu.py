@@ -18,6 +18,9 @@ HLU_ERR_NOT_CONVERGED = 4
 HLU_FP64 = 0
 HLU_FP32 = 1
 HLU_TF32 = 2
+HLU_PRECOND_LU = 0
+HLU_PRECOND_HINV = 1
+HLU_HINV_MAX_ITERS = 64
 BLOCK_ADM, BLOCK_DENSE, BLOCK_SUB = 0, 1, 2
 
 
@@ -51,6 +54,14 @@ class hlu_factor_info(ctypes.Structure):
                 ("rank_wanted_max", ctypes.c_int32), ("trunc_dense_fallbacks", ctypes.c_int32),
                 ("factor_live_bytes", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
                 ("reserved_", ctypes.c_int32)]
+
+
+class hlu_hinv_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("n_residuals", ctypes.c_int32),
+                ("residual", ctypes.c_double * (HLU_HINV_MAX_ITERS + 1)), ("alpha", ctypes.c_double),
+                ("rank_max", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rank_mean", ctypes.c_double),
+                ("inverse_live_bytes", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("n_iter_tasks", ctypes.c_int64), ("schedule_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
 def _struct_dict(s):
@@ -87,6 +98,9 @@ SIGNATURES = {
     "gmres_solve": (_i32, [_vp, _vp, _vp, _i32, _i64, _i32, _f64, _i32, _i32, _P(hlu_stats), _vp]),
     "hlu_richardson": (_i32, [_vp, _vp, _vp, _i32, _i64, _f64, _i32, _P(hlu_stats), _vp]),
     "hlu_factor_batch": (_i32, [_P(_vp), _i32, _i32, _vp]),
+    "hlu_hinverse": (_i32, [_vp, _i32, _f64, _i32, _P(hlu_hinv_info), _vp]),
+    "hlu_hinverse_apply": (_i32, [_vp, _vp, _vp, _i32, _i64, _vp]),
+    "hlu_set_preconditioner": (_i32, [_vp, _i32]),
     "hlu_solve_batch": (_i32, [_P(_vp), _i32, _P(_vp), _P(_vp), _P(_i32), _vp]),
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
@@ -108,6 +122,8 @@ SIGNATURES = {
     "hlu_debug_host_factor_solve": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32,
                                            _i32, _i32, ctypes.c_uint64, _i32, _vp, _vp, _vp]),
     "hlu_debug_wait_timeout": (_i32, [_f64, _vp]),
+    "hlu_debug_host_hinverse": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _f64, _i32,
+                                       _i32, _vp, _vp, _vp]),
     "hlu_debug_host_factor_prefix": (_i32, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32,
                                             ctypes.c_uint64, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
     "hlu_debug_factor_prefix": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
@@ -439,6 +455,31 @@ def hlu_gmres_status(g):
 
 def hlu_gmres_end(g):
     lib().hlu_gmres_end(_vp(g))
+
+
+def hlu_hinverse(h, precision=HLU_FP32, tol=1e-10, maxit=HLU_HINV_MAX_ITERS, stream=None,
+                 raise_on_nonconvergence=True):
+    """Schulz inverse B_H of A_H; returns the record (residuals as a list)."""
+    info = hlu_hinv_info()
+    rc = lib().hlu_hinverse(_vp(h), int(precision), float(tol), int(maxit), ctypes.byref(info), _stream(stream))
+    if rc != HLU_ERR_NOT_CONVERGED or raise_on_nonconvergence:
+        _check(rc)
+    d = _struct_dict(info)
+    d["residual"] = [info.residual[k] for k in range(info.n_residuals)]
+    return d
+
+
+def hlu_hinverse_apply(h, b, x, stream=None):
+    N = hlu_n(h)
+    pb, nr, ldb = _vec(b, N)
+    px, nr2, ldx = _vec(x, N)
+    if nr != nr2 or ldb != ldx:
+        raise ValueError("b and x must have the same shape and leading dimension")
+    _check(lib().hlu_hinverse_apply(_vp(h), pb, px, nr, ldb, _stream(stream)))
+
+
+def hlu_set_preconditioner(h, which):
+    _check(lib().hlu_set_preconditioner(_vp(h), int(which)))
 
 
 def hlu_factor_batch(handles, precision=HLU_FP32, stream=None):

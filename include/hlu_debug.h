@@ -65,8 +65,10 @@ int hlu_debug_factor_prefix(hlu_handle* h, int32_t precision, int64_t limit, voi
 int hlu_debug_task_record(const hlu_handle* h, int64_t idx, void* out);
 
 /* hlu_debug_factor_trace - factorise a built handle at `precision` with a
- * per-task trace (needs a GPU).  trace_out: uint64[4 x tasks] (wait start,
- * run start, end in globaltimer ns, CTA index); pred_ptr_out: int64[tasks+1]
+ * per-task trace (needs a GPU).  trace_out: uint64[4 x tasks], one row per
+ * ready-queue slot in claim order: (problem << 40 | task index), the time
+ * the slot was claimed, the time the task started and the time it ended
+ * (globaltimer ns); pred_ptr_out: int64[tasks+1]
  * and pred_idx_out: int32[edges], the dependency DAG; tasks_out: the task
  * records (136 bytes each).  sizes: int64[2] receives (tasks, edges); pass
  * NULL trace_out to query sizes only.  Any other output may be NULL. */

@@ -237,7 +237,7 @@ def serving_run(args):
 
     lo, hi = args.serve_n_lo, args.serve_n_hi
     prec = hlu.HLU_FP32 if args.precision == "fp32" else hlu.HLU_FP64
-    hlu.hlu_set_schedule_cache(64, 160 << 30)
+    hlu.hlu_set_schedule_cache(64, 48 << 30)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         list(ex.map(lambda n: hlu.hlu_destroy(hlu.hlu_build(n, 1.0, args.leaf, args.eta, args.eps)),
@@ -274,7 +274,8 @@ def serving_run(args):
                wall_s=stats["wall_s"], solves_per_s=summ["rhs_columns"] / stats["wall_s"],
                max_relres=max(r["relres"] for r in res), all_converged=all(r["converged"] for r in res),
                factorisations=stats["factorisations"], cache_hits=stats["cache_hits"],
-               evictions=stats["evictions"], max_active=stats["max_active"], gmres_steps=stats["steps"],
+               evictions=stats["evictions"], oom_retries=stats["oom_retries"], max_active=stats["max_active"],
+               gmres_steps=stats["steps"],
                steps_during_factor=stats["steps_during_factor"], budget_gb=args.serve_budget_gb,
                schedule_prewarm_s=prewarm_s, overlap="factorisations on a side stream (1 CTA/SM) beside GMRES steps",
                note="latency = finish - arrival, including the request's own factorisation and any queueing")

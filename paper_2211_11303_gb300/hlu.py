@@ -105,6 +105,7 @@ SIGNATURES = {
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
+    "hlu_set_solve_segment": (_i32, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
     "hlu_launch_count": (_i64, []),
     "hlu_set_allocator": (_i32, [_vp, _vp, _vp]),
@@ -375,7 +376,8 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SSOLVE",
+              "FENCE"]
 
 
 def hlu_factor_profile(h):
@@ -384,7 +386,7 @@ def hlu_factor_profile(h):
     out = (ctypes.c_uint64 * (k0 + 8))()
     _check(lib().hlu_factor_profile(_vp(h), out))
     d = {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(TASK_KINDS)}
-    d["trunc_phases"] = {"qr_cycles": out[k0 + 1], "core_cycles": out[k0 + 2], "jacobi_cycles": out[k0 + 3],
+    d["trunc_phases"] = {"stack_cycles": out[k0], "qr_cycles": out[k0 + 1], "core_cycles": out[k0 + 2], "jacobi_cycles": out[k0 + 3],
                          "select_apply_cycles": out[k0 + 4], "compressions": out[k0 + 5], "sweeps": out[k0 + 6],
                          "width_sum": out[k0 + 7]}
     return d
@@ -521,6 +523,11 @@ def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
 
 def hlu_set_tile(t):
     lib().hlu_set_tile(int(t))
+
+
+def hlu_set_solve_segment(rows):
+    """Rows of a triangular-solve segment for later hlu_build calls (0: one task per tile)."""
+    _check(lib().hlu_set_solve_segment(int(rows)))
 
 
 class Problem:

@@ -41,6 +41,15 @@ class _Factor:
         self.last_use = 0.0
 
 
+def _device_room():
+    """Device bytes a new allocation can get: the driver's free memory plus
+    the whole segments PyTorch's caching allocator holds unused (free space
+    inside partly used segments cannot serve a large block)."""
+    st = torch.cuda.memory_stats()
+    split = st.get("inactive_split_bytes.all.current", 0)
+    return torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved() - torch.cuda.memory_allocated() - split
+
+
 class Server:
     def __init__(self, hbm_budget_bytes, max_active=64, leaf=32, eta=2.0, eps=1e-4, precision=H.HLU_FP32,
                  restart=50, tol=1e-8, maxit=1000, overlap=True):
@@ -56,7 +65,7 @@ class Server:
         self.factor_ctas = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.inflight = None  # (entry of the request waiting for its factor, factor)
         self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0,
-                      "steps_during_factor": 0}
+                      "steps_during_factor": 0, "oom_retries": 0}
 
     # -- factor cache ---------------------------------------------------------
     def _evict_for(self, need):
@@ -149,8 +158,7 @@ class Server:
                 # the device itself must have the room as well (schedules and
                 # handles are outside the budget); blocks PyTorch's caching
                 # allocator holds unused count as free
-                avail = torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
-                ok = ok and avail > fbytes + kb + self.reserve
+                ok = ok and _device_room() > fbytes + kb + self.reserve
                 if not ok:
                     if not active and self.inflight is None and not self.factors:
                         raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))
@@ -165,12 +173,29 @@ class Server:
                     self.used += nbytes + kb
                     self.stats["factorisations"] += 1
                     f.users += 1
-                    if self.overlap:
-                        with torch.cuda.stream(self.side):
-                            H.hlu_factor_async(h, self.precision, self.factor_ctas, self.side)
-                        self.inflight = (req, f, N, kb)
+                    try:
+                        if self.overlap:
+                            with torch.cuda.stream(self.side):
+                                H.hlu_factor_async(h, self.precision, self.factor_ctas, self.side)
+                            self.inflight = (req, f, N, kb)
+                            continue
+                        H.hlu_factor(h, self.precision)
+                    except H.HluError as e:
+                        # the device could not hold the factor after all
+                        # (fragmented free memory): undo the admission and
+                        # retry once running requests have released memory
+                        if e.status != "HLU_ERR_OOM":
+                            raise
+                        del self.factors[key]
+                        self.used -= nbytes + kb
+                        self.stats["factorisations"] -= 1
+                        self.stats["oom_retries"] += 1
+                        H.hlu_destroy(h)
+                        torch.cuda.empty_cache()
+                        if not active and self.inflight is None and not self.factors:
+                            raise
+                        still.append(req)
                         continue
-                    H.hlu_factor(h, self.precision)
                 else:
                     self.stats["cache_hits"] += 1
                     f.users += 1

@@ -178,6 +178,35 @@ def test_rank_above_former_capacity(hlu, prec):
         hlu.hlu_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_segment_solve_equals_tile_solve(hlu, prec):
+    """The segment-solve schedule (one task per diagonal segment of up to
+    256 rows) applies the same factor as the one-task-per-tile schedule: equal
+    to rounding of the update sums, for 1, 5 and 16 right-hand sides."""
+    P = hlu.HLU_FP64 if prec == "fp64" else hlu.HLU_FP32
+    hs = []
+    try:
+        for rows in (0, 256):
+            hlu.hlu_set_solve_segment(rows)
+            hs.append(hlu.hlu_build(12, 5.0, 32, 2.0, 1e-4))
+            hlu.hlu_factor(hs[-1], P)
+    finally:
+        hlu.hlu_set_solve_segment(256)
+    try:
+        N = hlu.hlu_n(hs[0])
+        assert hlu.hlu_factor_stats(hs[1])["n_solve_tasks"] < hlu.hlu_factor_stats(hs[0])["n_solve_tasks"]
+        for nrhs in (1, 5, 16):
+            X = np.stack([synth.normal(900 + j, N) for j in range(nrhs)], axis=1)
+            y0 = gpu_apply(hlu, hs[0], X)
+            y1 = gpu_apply(hlu, hs[1], X)
+            tol = 1e-11 if prec == "fp64" else 1e-4
+            for j in range(nrhs):
+                assert np.linalg.norm(y1[:, j] - y0[:, j]) <= tol * np.linalg.norm(y0[:, j]), (nrhs, j)
+    finally:
+        for h in hs:
+            hlu.hlu_destroy(h)
+
+
 def test_gmres_fp32_n16_to_1e7(hlu):
     """n = 16 (N = 26,416), kappa 8, eps 1e-4, FP32 factor + FP64 FGMRES(50) to
     a relative residual of 1e-10: each of 4 seeded N(0,1) right-hand sides is

@@ -414,7 +414,7 @@ void hlu_set_wait_limit_ms(double ms);
 void hlu_set_tile(int32_t tile);
 
 /* hlu_set_solve_segment - granularity of the triangular solves (Algorithm 1
- * step III) for subsequent hlu_build calls (process-wide, default 256): the
+ * step III) for subsequent hlu_build calls (process-wide, default 0): the
  * right-hand side is tracked in segments of clusters of up to `rows` DOFs
  * (at least the tile size), and each diagonal segment's forward or backward
  * substitution runs as one task on its rows held in shared memory; rows = 0

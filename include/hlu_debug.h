@@ -93,6 +93,23 @@ int hlu_debug_solve_trace(hlu_handle* h, int32_t nrhs, uint64_t* trace_out, int6
  * Synchronous. */
 int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int32_t K, int32_t* status_out);
 
+/* hlu_debug_truncate - one recompression task (Sec. 3: QR of both factors,
+ * SVD of the small core, keep s_i > eps s_1, at most cap) run by the device
+ * executor on its own (needs a GPU).  The sum X Y^T (X m x w, Y n x w, host
+ * column-major FP64) enters as pieces of piece_cols columns (0: one piece),
+ * in `precision` (HLU_FP64 or HLU_FP32) arithmetic.  flags: 1 = the first
+ * piece is the target itself (its factors start in the outputs, as in an
+ * update A += sum), 2 = each piece's Y is stored row-major (a transposed
+ * view), 4 = piece q restricted to the quadrant ((q mod 4) / 2, q mod 2) of
+ * the m x n target (rows split at m / 2, columns at n / 2; X and Y must be
+ * zero outside).  Xo (m x cap), Yo (n x cap): host outputs, the first
+ * *rank columns hold the kept factors (Yo's columns orthonormal).
+ * status_out (int32[8], may be NULL): the executor status words ([2]
+ * capacity hits, [4] largest rank asked for).  cap in [1, min(m, n, 64)]. */
+int hlu_debug_truncate(int32_t precision, int32_t m, int32_t n, int32_t w, int32_t piece_cols, int32_t flags,
+                       const double* X, const double* Y, double eps, int32_t cap, double* Xo, double* Yo,
+                       int32_t* rank, int32_t* status_out);
+
 /* hlu_debug_zero_dof - input for the zero-pivot path (needs a GPU): sets row
  * and column `dof` (original DOF order) of the handle's assembled matrix A to
  * zero, in place on the device.  A later hlu_factor then meets an exact zero

@@ -1853,6 +1853,158 @@ extern "C" int hlu_debug_tf32_tile(const float* A, const float* B, float* D, int
   return hs[0] == 5 ? fail(HLU_ERR_TIMEOUT, "tensor-core completion wait ran out") : HLU_OK;
 }
 
+// One truncation task (TK_TRUNC) run by the device executor on its own: the
+// stack X Y^T (m x w and n x w, host column-major FP64) goes in as pieces of
+// at most piece_cols columns; the kept factors come back.
+template <class T>
+static int debug_truncate(int32_t precision, int32_t m, int32_t n, int32_t w, int32_t piece_cols, int32_t flags,
+                          const double* X, const double* Y, double eps, int32_t cap, double* Xo, double* Yo,
+                          int32_t* rank, int32_t* status_out) {
+  auto al = [](int64_t e) { return (e + 31) & ~int64_t(31); };
+  const int64_t xo = 0, yo = al((int64_t)m * w), oxo = yo + al((int64_t)n * w), oyo = oxo + al((int64_t)m * cap);
+  const int64_t total = oyo + al((int64_t)n * cap);
+  std::vector<T> harena((size_t)total, T(0));
+  const bool ytrans = (flags & 2) != 0, quad = (flags & 4) != 0, alias = (flags & 1) != 0;
+  const int32_t pw = piece_cols > 0 ? piece_cols : std::max(w, 1);
+  for (int64_t i = 0; i < (int64_t)m * w; ++i) harena[xo + i] = T(X[i]);
+  if (!ytrans) {
+    for (int64_t i = 0; i < (int64_t)n * w; ++i) harena[yo + i] = T(Y[i]);
+  } else {  // each piece's Y block stored row-major (rows x its columns)
+    for (int32_t c0 = 0; c0 < w; c0 += pw) {
+      const int32_t wc = std::min(pw, w - c0);
+      for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < wc; ++j) harena[yo + (int64_t)c0 * n + (int64_t)i * wc + j] = T(Y[i + (int64_t)(c0 + j) * n]);
+    }
+  }
+  Schedule S;
+  Task t;
+  std::memset(&t, 0, sizeof(t));
+  t.type = TK_TRUNC;
+  t.a = View{oxo, 1, m, m, cap, 0, 0};
+  t.b = View{oyo, 1, n, n, cap, 0, 0};
+  t.c.slot = -1;
+  t.out_slot = 0;
+  t.cap = cap;
+  t.piv_off = -1;
+  t.sign = 1.0f;
+  const int32_t mh = m / 2, nh = n / 2;
+  int32_t q_index = 0;
+  for (int32_t c0 = 0; c0 < w; c0 += pw, ++q_index) {
+    Piece q;
+    std::memset(&q, 0, sizeof(q));
+    const int32_t wc = std::min(pw, w - c0);
+    int32_t xr0 = 0, xr = m, yr0 = 0, yr = n;
+    if (quad) {  // piece q covers quadrant ((q mod 4) / 2, q mod 2)
+      const int32_t qi = (q_index % 4) / 2, qj = q_index % 2;
+      xr0 = qi ? mh : 0;
+      xr = qi ? m - mh : mh;
+      yr0 = qj ? nh : 0;
+      yr = qj ? n - nh : nh;
+    }
+    q.X = View{xo + (int64_t)c0 * m + xr0, 1, m, xr, wc, -1, 0};
+    if (!ytrans)
+      q.Y = View{yo + (int64_t)c0 * n + yr0, 1, n, yr, wc, -1, 0};
+    else
+      q.Y = View{yo + (int64_t)c0 * n + (int64_t)yr0 * wc, wc, 1, yr, wc, -1, 0};
+    q.xoff = xr0;
+    q.yoff = yr0;
+    q.sign = 1.0f;
+    if (alias && q_index == 0 && !quad && !ytrans && wc <= cap) {
+      // the target's current factors are the first piece (an update X += ...)
+      for (int32_t j = 0; j < wc; ++j) {
+        for (int32_t i = 0; i < m; ++i) harena[oxo + i + (int64_t)j * m] = harena[xo + i + (int64_t)j * m];
+        for (int32_t i = 0; i < n; ++i) harena[oyo + i + (int64_t)j * n] = harena[yo + i + (int64_t)j * n];
+      }
+      q.X = View{oxo, 1, m, m, cap, 0, 0};
+      q.Y = View{oyo, 1, n, n, cap, 0, 0};
+    }
+    S.pieces.push_back(q);
+  }
+  const int32_t rank0 = (alias && !quad && !ytrans && std::min(pw, w) <= cap) ? std::min(pw, w) : 0;
+  t.list_begin = 0;
+  t.list_count = (int32_t)S.pieces.size();
+  S.tasks.push_back(t);
+  S.pred_ptr = {0, 0};
+  DevSched ds;
+  T* d_arena = nullptr;
+  int32_t *d_ranks = nullptr, *d_piv = nullptr, *d_status = nullptr;
+  void* d_scratch = nullptr;
+  const int64_t rows = std::max(std::max(m, n), 1);
+  const int64_t sbytes = trunc_scratch_bytes(rows, (int)sizeof(T));
+  cudaError_t e = ds.load(S);
+  if (e == cudaSuccess) e = ds.alloc_state();
+  if (e == cudaSuccess) e = upload(&d_arena, harena);
+  if (e == cudaSuccess) e = upload(&d_ranks, std::vector<int32_t>{rank0, 1});
+  if (e == cudaSuccess) e = upload(&d_piv, std::vector<int32_t>{0});
+  if (e == cudaSuccess) e = upload(&d_status, std::vector<int32_t>{0, -1, 0, 0, 0, 0, 0, 0});
+  if (e == cudaSuccess) e = dev_malloc(&d_scratch, (size_t)sbytes);
+  if (e == cudaSuccess) {
+    ExecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    ProbSched& p = a.probs[0];
+    p.tasks = ds.tasks;
+    p.terms = ds.terms;
+    p.pieces = ds.pieces;
+    p.succ_ptr = ds.succ_ptr;
+    p.succ_idx = ds.succ_idx;
+    p.indeg = ds.indeg;
+    p.arena = d_arena;
+    p.ranks = d_ranks;
+    p.piv = d_piv;
+    p.eps = eps;
+    p.ntasks = 1;
+    p.limit = 1;
+    p.nrhs_slot = 1;
+    p.nrhs = 1;
+    a.nprobs = 1;
+    a.ntotal = 1;
+    a.queue = ds.queue;
+    a.qctl = ds.qctl;
+    a.scratch = d_scratch;
+    a.scratch_stride = sbytes / (int64_t)sizeof(T);
+    a.trunc_rows = rows;
+    a.status = d_status;
+    a.wait_limit_ns = (unsigned long long)(g_wait_limit_ms * 1e6);
+    a.jacobi_tol = g_jacobi_tol;
+    a.compress_at = g_compress_at;
+    unsigned long long q0[2] = {0ULL, 1ULL};
+    e = cudaMemcpy(ds.qctl, q0, sizeof(q0), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ds.indeg, ds.indeg0, sizeof(int32_t), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ds.queue, ds.roots, sizeof(unsigned long long), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = launch_exec(precision, a, 1, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  int32_t hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t hr[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hs, d_status, sizeof(hs), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hr, d_ranks, sizeof(hr), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(harena.data(), d_arena, sizeof(T) * total, cudaMemcpyDeviceToHost);
+  ds.free_all();
+  for (void* q : {(void*)d_arena, (void*)d_ranks, (void*)d_piv, (void*)d_status, d_scratch})
+    if (q) dev_free(q);
+  CKR(e, "truncation");
+  *rank = hr[0];
+  for (int64_t i = 0; i < (int64_t)m * cap; ++i) Xo[i] = (double)harena[oxo + i];
+  for (int64_t i = 0; i < (int64_t)n * cap; ++i) Yo[i] = (double)harena[oyo + i];
+  if (status_out)
+    for (int k = 0; k < 8; ++k) status_out[k] = hs[k];
+  return hs[0] == 5 ? fail(HLU_ERR_TIMEOUT, "device wait ran out") : HLU_OK;
+}
+
+extern "C" int hlu_debug_truncate(int32_t precision, int32_t m, int32_t n, int32_t w, int32_t piece_cols,
+                                  int32_t flags, const double* X, const double* Y, double eps, int32_t cap, double* Xo,
+                                  double* Yo, int32_t* rank, int32_t* status_out) {
+  if (!X || !Y || !Xo || !Yo || !rank || m < 1 || n < 1 || w < 0 || piece_cols < 0 || eps <= 0 || cap < 1 ||
+      cap > kRankMax || cap > std::min(m, n) || (flags & ~7) != 0 ||
+      (precision != HLU_FP64 && precision != HLU_FP32))
+    return fail(HLU_ERR_ARG, "bad argument");
+  if ((int64_t)std::max(m, n) > (int64_t)1 << 20 || w > (1 << 16)) return fail(HLU_ERR_ARG, "too large");
+  return precision == HLU_FP64 ? debug_truncate<double>(precision, m, n, w, piece_cols, flags, X, Y, eps, cap, Xo, Yo,
+                                                        rank, status_out)
+                               : debug_truncate<float>(precision, m, n, w, piece_cols, flags, X, Y, eps, cap, Xo, Yo,
+                                                       rank, status_out);
+}
+
 extern "C" int hlu_debug_zero_dof(hlu_handle* h, int64_t dof) {
   if (!h || dof < 0 || dof >= h->A.N) return fail(HLU_ERR_ARG, "bad argument");
   note_launch();

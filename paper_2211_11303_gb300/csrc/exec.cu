@@ -866,48 +866,56 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
 // ---------------------------------------------------------------- SSOLVE
 // One segment of a triangular solve in one task: the segment's rows of the
 // right-hand side (n <= kSegRows rows, k <= kSegCols columns) are held in
-// shared memory, its late update terms are added, then the segment's own
-// substitution runs as a list of operations (leaf triangles, dense and
-// low-rank updates; SegOp codes in hlu_internal.h).  The operands of the
-// next kSegSlots<T> dense operations stream into a ring of shared-memory
+// shared memory and a list of operations runs on them (SegOp codes in
+// hlu_internal.h): the late update terms, then the segment's own
+// substitution (leaf triangles, dense and low-rank updates).  The operands
+// of the next kSegSlots<T> operations stream into a ring of shared-memory
 // slots (cp.async, one commit group per operation) while the current one
-// runs, so the chain of leaf solves never waits on a global round trip.
-constexpr int kSegSlot = kSegTile * kSegTile + kSegTile;  // a tile and its pivots
+// runs, so the chain of leaf solves does not wait on global round trips.
+constexpr int kSegB = kSegTile * kSegTile + kSegTile;       // slot offset of the B operand
+constexpr int kSegSlot = kSegB + kSegTile * kSegCols;       // A tile, pivots, B (64 x 16)
 template <class T>
 struct SegSlots {
   static constexpr int value = sizeof(T) == 4 ? 3 : 2;
 };
 __host__ __device__ constexpr size_t seg_smem_elems(int slots) {
-  return (size_t)2 * kStage + (size_t)kSegRows * kSegCols + (size_t)kRankMax * kSegCols +
-         (size_t)slots * kSegSlot;
+  return (size_t)kSegRows * kSegCols + (size_t)kRankMax * kSegCols + (size_t)slots * kSegSlot;
 }
-constexpr size_t kSegOpBytes = sizeof(Term) * kSegMaxOps;
+constexpr size_t kSegOpBytes = (sizeof(Term) + sizeof(int32_t)) * kSegMaxOps;
 
 template <int N>
 __device__ __forceinline__ void cp_async_wait_n() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Starts the copy of operation q's dense operand (and a lower triangle's
-// pivots) into its slot; always one commit group, empty when there is nothing
-// to copy, so that group counting stays uniform.
+// Starts the copy of operation q's operands into its slot (dense tiles and
+// a lower triangle's pivots; a late update term's A and B); always one
+// commit group, empty when there is nothing to copy, so that the group
+// counting stays uniform.
 template <class T, int NS>
-__device__ __forceinline__ void seg_issue(const Ctx<T>& c, const Term* ops, int nops, int q, T* ring, bool upper) {
+__device__ __forceinline__ void seg_issue(const Ctx<T>& c, const Term* ops, const int32_t* opw, int nops, int q,
+                                          T* ring, bool upper, int k) {
   if (q < nops) {
     const Term& o = ops[q];
-    if (o.pad == SEG_TRI || o.pad == SEG_DUPD) {
-      T* slot = ring + (q % NS) * kSegSlot;
-      const int rows = o.A.rows, cols = o.A.cols;
+    T* slot = ring + (q % NS) * kSegSlot;
+    if (o.pad == SEG_TRI || o.pad == SEG_DUPD || o.pad == SEG_EXT) {
+      const int rows = o.A.rows, cols = opw[q];
       const T* src = c.arena + o.A.off;
       for (int idx = threadIdx.x; idx < rows * cols; idx += NT)
         cp_async_elem(slot + idx, src + (int64_t)(idx % rows) * o.A.rs + (int64_t)(idx / rows) * o.A.cs);
-      if (o.pad == SEG_TRI && !upper) {
-        int* pv = reinterpret_cast<int*>(slot + kSegTile * kSegTile);
-        for (int r = threadIdx.x; r < rows; r += NT) {
-          const unsigned d = (unsigned)__cvta_generic_to_shared(pv + r);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(c.piv + o.B.off + r) : "memory");
-        }
+    }
+    if (o.pad == SEG_TRI && !upper) {
+      int* pv = reinterpret_cast<int*>(slot + kSegTile * kSegTile);
+      for (int r = threadIdx.x; r < o.A.rows; r += NT) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(pv + r);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(c.piv + o.B.off + r) : "memory");
       }
+    }
+    if (o.pad == SEG_EXT) {
+      const int p = opw[q];
+      const T* src = c.arena + o.B.off;
+      for (int idx = threadIdx.x; idx < p * k; idx += NT)
+        cp_async_elem(slot + kSegB + idx, src + (int64_t)(idx % p) * o.B.rs + (int64_t)(idx / p) * o.B.cs);
     }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -923,51 +931,58 @@ __device__ void task_ssolve(Ctx<T>& c, const Task& t, char* smem) {
     if (threadIdx.x == 0) atomicCAS(c.status, 0, 8);
     return;
   }
-  T* As = reinterpret_cast<T*>(smem);
-  T* Bs = As + kStage;
-  T* X = Bs + kStage;                      // n x k, ld n
+  T* X = reinterpret_cast<T*>(smem);       // n x k, ld n
   T* P = X + kSegRows * kSegCols;          // low-rank projection, kRankMax x k
   T* ring = P + kRankMax * kSegCols;       // NS operand slots
   Term* ops = reinterpret_cast<Term*>(ring + NS * kSegSlot);
+  int32_t* opw = reinterpret_cast<int32_t*>(ops + kSegMaxOps);  // column count of each operation's A
   const T* rhs = c.arena + t.c.off;
   for (int idx = threadIdx.x; idx < n * k; idx += NT)
     cp_async_elem(X + idx, rhs + (int64_t)(idx % n) * t.c.rs + (int64_t)(idx / n) * t.c.cs);
   asm volatile("cp.async.commit_group;" ::: "memory");
   {
     const int words = nops * (int)(sizeof(Term) / sizeof(int32_t));
-    const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin + t.list_count);
+    const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin);
     int32_t* dst = reinterpret_cast<int32_t*>(ops);
     for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
+    // resolved column counts (ranks fixed during the solve), else live ranks
+    const int pq = (c.term_p && threadIdx.x < nops) ? __ldcg(c.term_p + t.list_begin + threadIdx.x) : -1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nops; q += NT) {
+      const int pr = (q == threadIdx.x) ? pq : -1;
+      opw[q] = pr >= 0 ? pr : (ops[q].pad == SEG_LUPD ? 0 : ncols(c, ops[q].A));
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < NS; ++q) seg_issue<T, NS>(c, ops, nops, q, ring, upper);
+  for (int q = 0; q < NS; ++q) seg_issue<T, NS>(c, ops, opw, nops, q, ring, upper, k);
   double fl = 0;
-  if (t.list_count > 0) {
-    const T sg = T(t.sign);
-    for (int i0 = 0; i0 < n; i0 += 64) {
-      T acc[4][4];
-      acc_zero(acc);
-      fl += rowmv_tile(c, t, i0, 0, k, acc, As, Bs);
-      if (i0 == 0) cp_async_wait_n<NS>();  // the right-hand side has arrived
-      __syncthreads();
-      const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int r = i0 + tx * 4 + i, cc = ty * 4 + j;
-          if (r < n && cc < k) X[r + cc * n] += sg * acc[i][j];
-        }
-    }
-  }
+  const T sg = T(t.sign);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int q = 0; q < nops; ++q) {
-    cp_async_wait_n<NS - 1>();  // operation q's operands have arrived
+    cp_async_wait_n<NS - 1>();  // operation q's operands (and the right-hand side) have arrived
     __syncthreads();
     const Term& o = ops[q];
     const T* Ad = ring + (q % NS) * kSegSlot;
-    if (o.pad == SEG_TRI) {
+    if (o.pad == SEG_EXT) {
+      // rows [ro, ro + rows) += sign * A B (A rows x p, B p x k in the slot)
+      const int rows = o.A.rows, p = opw[q], ro = o.roff;
+      const T* Bd = Ad + kSegB;
+      for (int e = threadIdx.x; e < rows * k; e += NT) {
+        const int i = e % rows, j = e / rows;
+        const T* a = Ad + i;
+        const T* b = Bd + j * p;
+        T s0 = 0, s1 = 0;
+        int l = 0;
+        for (; l + 2 <= p; l += 2) {
+          s0 += a[l * rows] * b[l];
+          s1 += a[(l + 1) * rows] * b[l + 1];
+        }
+        if (l < p) s0 += a[l * rows] * b[l];
+        X[ro + i + j * n] += sg * (s0 + s1);
+      }
+      fl += 2.0 * rows * p * k;
+    } else if (o.pad == SEG_TRI) {
       const int s = o.A.rows, ro = o.roff;
       const int r0 = lane, r1 = lane + 32;
       if (!upper) {
@@ -1008,7 +1023,7 @@ __device__ void task_ssolve(Ctx<T>& c, const Task& t, char* smem) {
     } else if (o.pad == SEG_DUPD) {
       // rows [ro, ro + rows) -= A rows [co, co + cols): the two row ranges
       // are disjoint, so every output is written as soon as it is summed
-      const int rows = o.A.rows, cols = o.A.cols, ro = o.roff, co = o.B.pad;
+      const int rows = o.A.rows, cols = opw[q], ro = o.roff, co = o.B.pad;
       for (int e = threadIdx.x; e < rows * k; e += NT) {
         const int i = e % rows, j = e / rows;
         const T* a = Ad + i;
@@ -1054,7 +1069,7 @@ __device__ void task_ssolve(Ctx<T>& c, const Task& t, char* smem) {
       fl += 2.0 * (rows + ny) * r * k;
     }
     __syncthreads();
-    seg_issue<T, NS>(c, ops, nops, q + NS, ring, upper);
+    seg_issue<T, NS>(c, ops, opw, nops, q + NS, ring, upper, k);
   }
   cp_async_wait_n<0>();
   __syncthreads();
@@ -1426,7 +1441,7 @@ __host__ __device__ constexpr size_t exec_smem_base(int elem_size) {
   // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
   const size_t rsolve = (size_t)elem_size * (2 * kStage + 2 * 64 * 64 + 64) + 64 * sizeof(int);
   const size_t lu1 = rsolve > lu0 ? rsolve : lu0;
-  // segment solve: staging, right-hand side, projection, operand slots, operations
+  // segment solve: right-hand side, projection, operand slots, operations
   const size_t seg = (size_t)elem_size * seg_smem_elems(elem_size == 4 ? 3 : 2) + kSegOpBytes;
   const size_t lu = seg > lu1 ? seg : lu1;
   const size_t gemm = (size_t)elem_size * 2 * kStage;
@@ -1924,6 +1939,216 @@ __device__ bool task_trunc_dense(Ctx<T>& c, const Task& t, char* smem) {
 }
 
 // (a, b) <- truncation of sum_pieces sign X Y^T (stack, compress, store).
+// ------------------------------------------------------------- small TRUNC
+// Q (m x tmax) of a Householder QR in place: S holds the reflectors of
+// house_qr_group below its diagonal (unit leading entries implicit), and
+// column j of S becomes column j of Q = H_0 ... H_{tmax-1} [I; 0], formed
+// from the last reflector back (the recurrence of LAPACK's dorg2r).  Run by
+// a group of NW warps (group thread gt, named barrier bar).
+template <class T, int NW>
+__device__ void orgqr_group(T* S, int m, int tmax, const T* tau, int gt, int bar) {
+  constexpr int NTG = NW * 32;
+  const int wg = gt >> 5, lane = gt & 31;
+  for (int j = tmax - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    T* cj = S + (int64_t)j * m;
+    // H_j on the columns already formed: their row j is still zero
+    if (tj != T(0))
+      for (int cc = j + 1 + wg; cc < tmax; cc += NW) {
+        T* col = S + (int64_t)cc * m;
+        T d = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * col[i];
+        d = warp_sum(d) * tj;
+        for (int i = j + 1 + lane; i < m; i += 32) col[i] -= d * cj[i];
+        if (lane == 0) col[j] = -d;
+      }
+    group_bar(bar, NTG);
+    for (int i = gt; i < m; i += NTG) cj[i] = i < j ? T(0) : (i == j ? T(1) - tj : -tj * cj[i]);
+    group_bar(bar, NTG);
+  }
+}
+
+// Elements of T a small truncation needs in shared memory: both stacks,
+// their reflector scalars, the core, its SVD and the two small factors.
+__host__ __device__ constexpr int64_t trunc_small_elems(int m, int n, int W) {
+  return (int64_t)(m + n) * W + 5LL * W * W + 10LL * W + 4LL * kTruncStack + 8;
+}
+template <class T>
+__device__ __forceinline__ bool trunc_small_fits(int m, int n, int W) {
+  return W > 0 && W <= kTruncStack &&
+         trunc_small_elems(m, n, W) * (int64_t)sizeof(T) <= (int64_t)exec_smem_base(sizeof(T));
+}
+
+// A truncation whose whole stack fits in shared memory: the same
+// recompression as the stack route (Householder QR of both stacks, core
+// R_x R_y^T with Dot2, pivoted QR of the core, Jacobi SVD, s_i > eps s_1),
+// in one compression of all W columns, with the stacks, reflectors and
+// factors resident in shared memory; the kept factors X = Q_x Z_x and
+// Y = Q_y Z_y go straight to the target views (Q_x, Q_y formed in place).
+template <class T>
+__device__ void task_trunc_small(Ctx<T>& c, const Task& t, char* smem, int W) {
+  const int m = t.a.rows, n = t.b.rows;
+  unsigned long long* tp = c.tprof;
+  long long t0 = tp && threadIdx.x == 0 ? clock64() : 0;
+  auto lap = [&](int k) {
+    if (tp && threadIdx.x == 0) {
+      const long long t1 = clock64();
+      tp[k] += (unsigned long long)(t1 - t0);
+      t0 = t1;
+    }
+  };
+  T* SX = reinterpret_cast<T*>(smem);
+  T* SY = SX + (int64_t)m * W;
+  T* tauX = SY + (int64_t)n * W;
+  T* tauY = tauX + W;
+  T* sv = tauY + W;
+  T* s2x = sv + W;
+  T* s2y = s2x + W + 1;
+  T* scbx = s2y + W + 1;
+  T* scby = scbx + 2 * kTruncStack;
+  T* tauG = scby + 2 * kTruncStack;
+  T* G = tauG + W;
+  T* V = G + W * W;
+  T* Zx = V + 2 * W * W;
+  T* Zy = Zx + W * W;
+  int* perm = reinterpret_cast<int*>(Zy + W * W);
+  int* ord = perm + W;
+  __shared__ int s_r;
+  for (int idx = threadIdx.x; idx < (m + n) * W; idx += NT) SX[idx] = T(0);
+  __syncthreads();
+  int w0 = 0;
+  for (int q = 0; q < t.list_count; ++q) {
+    const Piece& P = c.pieces[t.list_begin + q];
+    const int w = ncols(c, P.X);
+    const T sg = (P.pad & PF_ALPHA) ? T(P.sign) * T(c.alpha) : T(P.sign);
+    // four elements per thread at a time: all loads issued before the stores
+    const int64_t nx = (int64_t)P.X.rows * w, ny = (int64_t)P.Y.rows * w;
+    for (int64_t b0 = threadIdx.x; b0 < nx; b0 += 4 * NT) {
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        v[u] = idx < nx ? ldv(c, P.X, idx % P.X.rows, idx / P.X.rows) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        if (idx < nx) SX[(P.xoff + idx % P.X.rows) + (int64_t)(w0 + idx / P.X.rows) * m] = sg * v[u];
+      }
+    }
+    for (int64_t b0 = threadIdx.x; b0 < ny; b0 += 4 * NT) {
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        v[u] = idx < ny ? ldv(c, P.Y, idx % P.Y.rows, idx / P.Y.rows) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = b0 + (int64_t)u * NT;
+        if (idx < ny) SY[(P.yoff + idx % P.Y.rows) + (int64_t)(w0 + idx / P.Y.rows) * n] = v[u];
+      }
+    }
+    w0 += w;
+  }
+  __syncthreads();
+  lap(0);
+  constexpr int kHalf = NT / 2;
+  if (threadIdx.x < kHalf)
+    house_qr_group<T, kHalf / 32>(SX, m, W, tauX, s2x, scbx, threadIdx.x, 1);
+  else
+    house_qr_group<T, kHalf / 32>(SY, n, W, tauY, s2y, scby, threadIdx.x - kHalf, 2);
+  __syncthreads();
+  lap(1);
+  const int p = min(m, W), q = min(n, W);
+  for (int idx = threadIdx.x; idx < p * q; idx += NT) {
+    const int i = idx % p, j = idx / p;
+    typename AccurateDot<T>::type acc;
+    for (int l = max(i, j); l < W; ++l) acc.add(SX[i + (int64_t)l * m], SY[j + (int64_t)l * n]);
+    G[i + j * p] = acc.value();
+  }
+  __syncthreads();
+  lap(2);
+  T tail2 = 0;
+  const T rel = T(0.1 * c.eps);
+  const int rp = pivoted_qr(G, p, q, min(kCoreRank, min(p, q)), rel * rel / T(min(p, q)), tauG, sv, perm, &tail2);
+  T* M = V;
+  T* Vs = V + q * rp;
+  for (int idx = threadIdx.x; idx < q * rp; idx += NT) {
+    const int j = idx % q, i = idx / q;
+    M[perm[j] + i * q] = j >= i ? G[i + j * p] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < rp * rp; idx += NT) Vs[idx] = (idx % rp == idx / rp) ? T(1) : T(0);
+  __syncthreads();
+  const int sweeps = rp > 0 ? jacobi_svd(M, Vs, q, rp, sv, T(c.jacobi_tol), T(0.01 * c.eps)) : 0;
+  lap(3);
+  if (tp && threadIdx.x == 0) {
+    tp[5] += 1ULL;
+    tp[6] += (unsigned long long)sweeps;
+    tp[7] += (unsigned long long)W;
+  }
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < rp; ++j) {
+      sv[j] = sqrt(sv[j]);
+      ord[j] = j;
+    }
+    for (int j = 1; j < rp; ++j) {  // stable insertion sort, descending
+      int x = ord[j], i = j - 1;
+      while (i >= 0 && sv[ord[i]] < sv[x]) {
+        ord[i + 1] = ord[i];
+        --i;
+      }
+      ord[i + 1] = x;
+    }
+    const T smax = rp ? sv[ord[0]] : T(0);
+    int r = 0;
+    if (smax > T(0))
+      while (r < rp && sv[ord[r]] > T(c.eps) * smax) ++r;
+    const bool more = rp == kCoreRank && tail2 > T(c.eps * c.eps) * smax * smax;
+    atomicMax(c.status + 4, more ? kCoreRank + 1 : r);
+    if (r > t.cap || more) {
+      r = min(r, t.cap);
+      atomicAdd(c.status + 2, 1);
+    }
+    s_r = r;
+    c.flops += 2.0 * (m + n) * W * W + 4.0 * (double)p * q * rp + 6.0 * sweeps * (double)q * rp * rp +
+               2.0 * (m + n) * W * r;
+  }
+  __syncthreads();
+  const int r = s_r;
+  // Z_x = Q_G [V_M S; 0] (p x r), Z_y = W S^-1 (q x r), columns by descending s
+  for (int idx = threadIdx.x; idx < p * r; idx += NT) {
+    const int i = idx % p, j = idx / p;
+    Zx[idx] = i < rp ? Vs[i + ord[j] * rp] * sv[ord[j]] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < q * r; idx += NT) {
+    const int i = idx % q, j = idx / q;
+    Zy[idx] = M[i + ord[j] * q] / sv[ord[j]];
+  }
+  __syncthreads();
+  apply_q_group<T, NT / 32>(G, p, rp, tauG, Zx, p, r, threadIdx.x);
+  if (threadIdx.x < kHalf)
+    orgqr_group<T, kHalf / 32>(SX, m, p, tauX, threadIdx.x, 1);
+  else
+    orgqr_group<T, kHalf / 32>(SY, n, q, tauY, threadIdx.x - kHalf, 2);
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += NT) {
+    const int i = e % m, j = e / m;
+    T sum = 0;
+    for (int l = 0; l < p; ++l) sum += SX[i + (int64_t)l * m] * Zx[l + j * p];
+    stv(c, t.a, i, j, sum);
+  }
+  for (int e = threadIdx.x; e < n * r; e += NT) {
+    const int i = e % n, j = e / n;
+    T sum = 0;
+    for (int l = 0; l < q; ++l) sum += SY[i + (int64_t)l * n] * Zy[l + j * q];
+    stv(c, t.b, i, j, sum);
+  }
+  __syncthreads();
+  lap(4);
+  if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, r);
+}
+
 template <class T>
 __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
   const int m = t.a.rows, n = t.b.rows;
@@ -1931,16 +2156,24 @@ __device__ void task_trunc(Ctx<T>& c, const Task& t, char* smem) {
     if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
     return;
   }
-  if (sizeof(T) == 4 && m <= kDenseMax && n <= kDenseMax) {
-    // dense route when the stack would need more than one compression
-    __shared__ int s_wsum;
-    if (threadIdx.x == 0) s_wsum = 0;
-    __syncthreads();
-    for (int q = threadIdx.x; q < t.list_count; q += NT) atomicAdd(&s_wsum, ncols(c, c.pieces[t.list_begin + q].X));
-    __syncthreads();
-    const bool dense = s_wsum > c.compress_at;
-    __syncthreads();
-    if (dense && task_trunc_dense(c, t, smem)) return;
+  __shared__ int s_wsum;
+  if (threadIdx.x == 0) s_wsum = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < t.list_count; q += NT) atomicAdd(&s_wsum, ncols(c, c.pieces[t.list_begin + q].X));
+  __syncthreads();
+  const int wsum = s_wsum;
+  __syncthreads();
+  // dense route when the stack would need more than one compression
+  if (sizeof(T) == 4 && m <= kDenseMax && n <= kDenseMax && wsum > c.compress_at && task_trunc_dense(c, t, smem))
+    return;
+  if (wsum == 0) {
+    if (threadIdx.x == 0) __stcg(c.ranks + t.out_slot, 0);
+    return;
+  }
+  // the whole stack in shared memory, one compression
+  if (trunc_small_fits<T>(m, n, wsum)) {
+    task_trunc_small(c, t, smem, wsum);
+    return;
   }
   const int64_t R = c.rows_max;
   T* SX = c.scratch;

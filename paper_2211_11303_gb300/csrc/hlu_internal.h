@@ -45,9 +45,9 @@ enum TaskType : int32_t {
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
   TK_RSOLVE = 8,  // c <- tri(a)^-1 (c - sum_terms A_t B_t): one tile of a triangular solve;
                   // flags & TF_UPPER: U^-1, else L^-1 P (pivots at piv_off)
-  TK_SSOLVE = 9,  // one segment of a triangular solve: c <- c + sign * sum of the list_count
-                  // terms, then the cap operations that follow them in the term list (SegOp)
-                  // on c held in shared memory; flags & TF_UPPER as RSOLVE
+  TK_SSOLVE = 9,  // one segment of a triangular solve: the cap operations (SegOp) at
+                  // list_begin of the term list on c held in shared memory (the late
+                  // update with sign, then the substitution); flags & TF_UPPER as RSOLVE
   TK_NUM = 10,
   TK_FENCE = 10   // no work: orders re-use of temporary memory after its readers
 };
@@ -56,9 +56,11 @@ enum TaskType : int32_t {
 //   SEG_TRI:  rows [roff, roff + A.rows) <- tri(A)^-1 rows, pivots at B.off
 //   SEG_DUPD: rows [roff, roff + A.rows) -= A rows [B.pad, B.pad + A.cols)
 //   SEG_LUPD: rows [roff, roff + A.rows) -= A (B^T rows [B.pad, B.pad + B.rows))
-enum : int32_t { SEG_TRI = 1, SEG_DUPD = 2, SEG_LUPD = 3 };
+//   SEG_EXT:  rows [roff, roff + A.rows) += sign * A B, B read from outside the
+//             segment (the late update; A at most kSegTile x kSegTile)
+enum : int32_t { SEG_TRI = 1, SEG_DUPD = 2, SEG_LUPD = 3, SEG_EXT = 4 };
 // most operations of one segment solve, and its largest diagonal tile
-constexpr int32_t kSegMaxOps = 64;
+constexpr int32_t kSegMaxOps = 128;
 constexpr int32_t kSegTile = 64;
 // largest segment of the triangular-solve schedule (rows held in shared memory)
 constexpr int32_t kSegRows = 256;

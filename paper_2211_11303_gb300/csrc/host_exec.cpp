@@ -366,22 +366,15 @@ void h_rsolve(HostCtx<T>& c, const Task& t) {
   h_trsm(c, s);
 }
 
-// One segment of a triangular solve: the update terms, then the segment's
-// operations (leaf triangles, dense and low-rank updates) in order.
+// One segment of a triangular solve: its operations in order (the late
+// update, then the leaf triangles and the dense and low-rank updates).
 template <class T>
 void h_ssolve(HostCtx<T>& c, const Task& t) {
-  if (t.list_count > 0) {
-    Task r = t;
-    r.type = TK_ROWMV;
-    r.flags = 0;
-    r.out_slot = -1;
-    h_rowmv(c, r);
-  }
   const int k = ncols(c, t.b);
   const bool upper = (t.flags & TF_UPPER) != 0;
   auto x = [&](int i, int j) -> T& { return at(c, t.c, i, j); };
   for (int q = 0; q < t.cap; ++q) {
-    const Term& o = c.terms[t.list_begin + t.list_count + q];
+    const Term& o = c.terms[t.list_begin + q];
     const int ro = o.roff;
     if (o.pad == SEG_TRI) {
       const int s = o.A.rows;
@@ -409,6 +402,15 @@ void h_ssolve(HostCtx<T>& c, const Task& t) {
           T sum = 0;
           for (int l = 0; l < o.A.cols; ++l) sum += at(c, o.A, i, l) * x(co + l, j);
           x(ro + i, j) -= sum;
+        }
+    } else if (o.pad == SEG_EXT) {
+      const int pcols = ncols(c, o.A);
+      const T sg = T(t.sign);
+      for (int j = 0; j < k; ++j)
+        for (int i = 0; i < o.A.rows; ++i) {
+          T sum = 0;
+          for (int l = 0; l < pcols; ++l) sum += at(c, o.A, i, l) * at(c, o.B, l, j);
+          x(ro + i, j) += sg * sum;
         }
     } else if (o.pad == SEG_LUPD) {
       const int co = o.B.pad, r = ncols(c, o.A);

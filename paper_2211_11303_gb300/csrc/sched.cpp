@@ -673,38 +673,85 @@ class Sched {
     if (!seg_solve_ || !is_segment(rowc(d))) return false;
     const int32_t sg = seg_begin_[rowc(d)];
     std::vector<SegOpMV> ops;
-    if (sz(rowc(d)) > kSegRows || !seg_ops(d, C_[rowc(d)].off, upper, ops) || (int32_t)ops.size() > kSegMaxOps) {
-      // solved task by task: the segment's late update becomes its own task
-      if (sg < (int32_t)pending_.size() && pending_[sg].active) {
-        Pending& pd = pending_[sg];
-        emit_rowmv(pd.lv, pd.T, pd.list, pd.Vin, V, rowc(d), pd.sign, pd.trans, false, -1, pd.Vin);
-        pd = Pending();
-      }
-      return false;
-    }
+    if (sz(rowc(d)) > kSegRows || !seg_ops(d, C_[rowc(d)].off, upper, ops) || (int32_t)ops.size() > kSegMaxOps)
+      return seg_fallback(sg, V, d);
     Pending* pd = (sg < (int32_t)pending_.size() && pending_[sg].active) ? &pending_[sg] : nullptr;
+    // the late update terms become the first operations (SEG_EXT), in
+    // pieces of at most kSegTile x kSegTile
+    std::vector<SegOpMV> ext;
+    std::vector<int32_t> ext_tbuf;  // temporaries read (projections)
+    if (pd) {
+      const int32_t lc = rowc(d);
+      for (int32_t i : pd->list) {
+        const int32_t be = pd->lv[i];
+        const int32_t obc = pd->trans ? colc(be) : rowc(be);
+        const int32_t rc = C_[obc].size <= C_[lc].size ? obc : lc;
+        const int32_t roff = C_[rc].off - C_[lc].off;
+        const bool dense = kind(be) == KIND_DENSE;
+        MV A, Bv;
+        if (dense) {
+          A = sub(pd->trans ? mvDT(be) : mvD(be), rc);
+          Bv = sub(pd->Vin, pd->trans ? rowc(be) : colc(be));
+        } else {
+          A = sub(pd->trans ? mvY(be) : mvX(be), rc);
+          Bv = pd->T[i];
+          ext_tbuf.push_back(Bv.buf);
+          Bv.buf = -1;  // a single-segment temporary: tracked through ext_tbuf
+          if (A.v.cols > kSegTile) return seg_fallback(sg, V, d);
+        }
+        for (int32_t i0 = 0; i0 < A.v.rows; i0 += kSegTile)
+          for (int32_t j0 = 0; j0 < (dense ? A.v.cols : 1); j0 += kSegTile) {
+            SegOpMV o;
+            std::memset(&o.t, 0, sizeof(o.t));
+            o.a = A;
+            o.b = Bv;
+            o.t.A = A.v;
+            o.t.A.off += (int64_t)i0 * A.v.rs;
+            o.t.A.rows = std::min(kSegTile, A.v.rows - i0);
+            o.t.B = Bv.v;
+            if (dense) {
+              o.t.A.off += (int64_t)j0 * A.v.cs;
+              o.t.A.cols = std::min(kSegTile, A.v.cols - j0);
+              o.t.B.off += (int64_t)j0 * Bv.v.rs;
+              o.t.B.rows = o.t.A.cols;
+            }
+            o.t.roff = roff + i0;
+            o.t.pad = SEG_EXT;
+            ext.push_back(o);
+          }
+      }
+    }
+    if ((int32_t)(ext.size() + ops.size()) > kSegMaxOps) return seg_fallback(sg, V, d);
     Task k = make(TK_SSOLVE);
     k.flags = upper ? TF_UPPER : 0;
     k.c = V.v;
     k.b = V.v;  // column count source
     k.sign = pd ? pd->sign : 1.0f;
     k.list_begin = (int32_t)S_->terms.size();
-    k.list_count = pd ? (int32_t)pd->list.size() : 0;
-    k.cap = (int32_t)ops.size();
+    k.list_count = 0;
+    k.cap = (int32_t)(ext.size() + ops.size());
     begin(k);
-    if (pd) {
-      push_terms(pd->lv, pd->T, pd->list, pd->Vin, rowc(d), pd->trans);
-      acc_rank(pd->Vin);
-    }
-    for (const SegOpMV& o : ops) {
-      S_->terms.push_back(o.t);
-      acc(o.a, false);
-      if (o.b.buf >= 0) acc(o.b, false);
-    }
+    for (const std::vector<SegOpMV>* l : {&ext, &ops})
+      for (const SegOpMV& o : *l) {
+        S_->terms.push_back(o.t);
+        acc(o.a, false);
+        acc(o.b, false);
+      }
+    for (int32_t b : ext_tbuf) touch(bufs_[b].seg0, false);
+    if (pd) acc_rank(pd->Vin);
     acc(V, true);
     end();
     if (pd) *pd = Pending();
     return true;
+  }
+  // the segment is solved task by task: its late update becomes its own task
+  bool seg_fallback(int32_t sg, const MV& V, int32_t d) {
+    if (sg < (int32_t)pending_.size() && pending_[sg].active) {
+      Pending& pd = pending_[sg];
+      emit_rowmv(pd.lv, pd.T, pd.list, pd.Vin, V, rowc(d), pd.sign, pd.trans, false, -1, pd.Vin);
+      pd = Pending();
+    }
+    return false;
   }
 
   // ---------------------------------------------------------------- triangular
@@ -1081,7 +1128,7 @@ class Sched {
 
 }  // namespace
 
-int32_t g_solve_segment_rows = kSegRows;
+int32_t g_solve_segment_rows = 0;
 
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile) {
   std::vector<Block> out;

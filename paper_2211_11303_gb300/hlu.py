@@ -131,6 +131,8 @@ SIGNATURES = {
     "hlu_debug_task_record": (_i32, [_vp, _i64, _vp]),
     "hlu_debug_factor_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "hlu_debug_solve_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "hlu_debug_truncate": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.c_double, _i32, _vp, _vp, _vp,
+                                  _vp]),
 }
 
 
@@ -558,3 +560,20 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def debug_truncate(X, Y, eps, cap=64, precision=HLU_FP64, piece_cols=0, flags=0):
+    """One device truncation of X Y^T (numpy FP64 arrays m x w, n x w):
+    (Xo m x r, Yo n x r, status words); flags as hlu_debug_truncate."""
+    import numpy as np
+    X = np.asfortranarray(X, dtype=np.float64)
+    Y = np.asfortranarray(Y, dtype=np.float64)
+    m, w = X.shape
+    n = Y.shape[0]
+    Xo = np.zeros((m, cap), order="F")
+    Yo = np.zeros((n, cap), order="F")
+    r = ctypes.c_int32(0)
+    st = (ctypes.c_int32 * 8)()
+    _check(lib().hlu_debug_truncate(int(precision), m, n, w, int(piece_cols), int(flags), X.ctypes.data, Y.ctypes.data,
+                                    float(eps), int(cap), Xo.ctypes.data, Yo.ctypes.data, ctypes.byref(r), st))
+    return Xo[:, :r.value].copy(), Yo[:, :r.value].copy(), list(st)

@@ -141,15 +141,19 @@ def test_operator_error_within_2x_of_oracle(hlu, prec, n, kappa, eps):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_rank_above_former_capacity(hlu, prec):
-    """n = 10, kappa 6, eps 1e-6: truncations ask for ranks above 32 (the
+    """n = 10, kappa 3, eps 1e-6: truncations ask for ranks above 32 (the
     capacity of earlier builds, which clipped them).  With the capacity of 64
     every truncation keeps s_i > eps s_1 in full (no capacity hit).  FP64: the
     operator error is within 2x of the oracle's, which truncates with no
     capacity at all (Sec. 4 truncated SVD).  FP32: at eps 1e-6 the FP32
     rounding of the factorisation, not the truncation, sets the operator
     error, so the bar adds that floor, measured by the same FP32 path at
-    eps 1e-12 (where nothing is truncated)."""
-    n, kappa, eps = 10, 6.0, 1e-6
+    eps 1e-12 (where nothing is truncated).  kappa^2 = 9 lies well below the
+    cavity's first eigenvalue (2 pi^2): near a resonance (kappa 6 at this n)
+    the operator error of any eps-truncated factor moves by orders of
+    magnitude with the rounding-level order of the truncations, and no 2x
+    bar between two correct implementations holds."""
+    n, kappa, eps = 10, 3.0, 1e-6
     m, A, perm, cl, bl = oracle_problem(n, kappa)
     key = ("op_error", n, kappa, eps)
     if key not in _cache:
@@ -191,7 +195,7 @@ def test_segment_solve_equals_tile_solve(hlu, prec):
             hs.append(hlu.hlu_build(12, 5.0, 32, 2.0, 1e-4))
             hlu.hlu_factor(hs[-1], P)
     finally:
-        hlu.hlu_set_solve_segment(256)
+        hlu.hlu_set_solve_segment(0)
     try:
         N = hlu.hlu_n(hs[0])
         assert hlu.hlu_factor_stats(hs[1])["n_solve_tasks"] < hlu.hlu_factor_stats(hs[0])["n_solve_tasks"]

@@ -131,7 +131,7 @@ def test_segment_solves_match_tile_solves(lib, precision, leaf, tile):
         _, _, _, _, _, x1, info1 = _host_solve(lib, 6, 3.0, 1e-6, leaf, 0, nrhs=3, tile=tile, precision=precision)
         _, _, _, _, _, x2, _ = _host_solve(lib, 6, 3.0, 1e-6, leaf, 5, nrhs=3, tile=tile, precision=precision)
     finally:
-        lib.hlu_set_solve_segment(256)
+        lib.hlu_set_solve_segment(0)
     tol = 1e-12 if precision == 0 else 1e-5
     assert np.linalg.norm(x1 - x0) <= tol * np.linalg.norm(x0)
     assert np.array_equal(x1, x2)
@@ -144,7 +144,7 @@ def test_solve_segment_argument_is_checked(lib):
         assert lib.hlu_set_solve_segment(257) == 1
         assert lib.hlu_set_solve_segment(128) == 0
     finally:
-        lib.hlu_set_solve_segment(256)
+        lib.hlu_set_solve_segment(0)
 
 
 def test_allocator_and_memory_limit_arguments(lib):

@@ -269,12 +269,12 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info);
 /* hlu_factor_profile - per task kind of the last factorisation's task DAG:
  * out[3*k + 0] tasks run, out[3*k + 1] SM clock cycles spent waiting for a
  * ready task, out[3*k + 2] cycles spent running, summed over CTAs; kinds
- * k = 0..9 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
- * RSOLVE, SSOLVE and k = 10 the no-work fences; then the truncation phases
- * summed over all compressions: out[33] stacking or dense sum, out[34] QR
- * cycles, out[35] core product, out[36] Jacobi SVD, out[37] selection and Q
- * application, out[38] compressions, out[39] Jacobi sweeps, out[40] summed
- * stack widths.  out: uint64[41] host buffer. */
+ * k = 0..8 are GETRF, TRSM_L, TRSM_UT, TRSM_U, PROJ, ROWMV, TRUNC, DADD,
+ * RSOLVE and k = 9 the no-work fences; then the truncation phases summed
+ * over all compressions: out[30] stacking (shared-memory route) or dense
+ * sum, out[31] QR cycles, out[32] core product, out[33] Jacobi SVD, out[34]
+ * selection and Q application, out[35] compressions, out[36] Jacobi sweeps,
+ * out[37] summed stack widths.  out: uint64[38] host buffer. */
 int hlu_factor_profile(const hlu_handle* h, uint64_t* out);
 
 /* hlu_solve - x = (LU)_H^-1 b, the preconditioner of Algorithm 1 step III
@@ -413,15 +413,6 @@ void hlu_set_wait_limit_ms(double ms);
  * above 64 are clamped to 64. */
 void hlu_set_tile(int32_t tile);
 
-/* hlu_set_solve_segment - granularity of the triangular solves (Algorithm 1
- * step III) for subsequent hlu_build calls (process-wide, default 0): the
- * right-hand side is tracked in segments of clusters of up to `rows` DOFs
- * (at least the tile size), and each diagonal segment's forward or backward
- * substitution runs as one task on its rows held in shared memory; rows = 0
- * runs one task per diagonal tile instead.  rows in [0, 256], else
- * HLU_ERR_ARG.  The arithmetic is the same H-solve either way; only the
- * summation order of the updates differs. */
-int hlu_set_solve_segment(int32_t rows);
 
 /* Device allocator of the library (process-wide).  alloc(bytes, ctx) returns
  * device memory of the current device, or NULL when it cannot (the library

@@ -534,7 +534,6 @@ int read_status(hlu_handle* h, cudaStream_t s, int32_t* out4) {
   if (out4[0] == 5) return fail(HLU_ERR_TIMEOUT, "device wait exceeded its limit at task " + std::to_string(out4[1]));
   if (out4[0] == 3) return fail(HLU_ERR_ZERO_PIVOT, "zero pivot in a diagonal leaf");
   if (out4[0] == 7) return fail(HLU_ERR_STATE, "an A_H block exceeds the rank capacity");
-  if (out4[0] == 8) return fail(HLU_ERR_STATE, "a segment solve exceeds its shared-memory limits");
   return HLU_OK;
 }
 
@@ -800,11 +799,6 @@ void hlu_set_wait_limit_ms(double ms) {
   if (ms > 0) g_wait_limit_ms = ms;
 }
 void hlu_set_tile(int32_t tile) { g_tile = std::max(0, std::min(tile, (int32_t)64)); }
-int hlu_set_solve_segment(int32_t rows) {
-  if (rows < 0 || rows > kSegRows) return fail(HLU_ERR_ARG, "segment rows outside [0, 256]");
-  g_solve_segment_rows = rows;
-  return HLU_OK;
-}
 
 
 int64_t hlu_n(const hlu_handle* h) { return h ? h->A.N : 0; }
@@ -949,7 +943,7 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     uint64_t key = 1469598103934665603ULL;
     key = fnv1a(key, h->trees.clusters.data(), sizeof(int32_t) * h->trees.clusters.size());
     key = fnv1a(key, h->trees.blocks.data(), sizeof(int32_t) * h->trees.blocks.size());
-    int32_t params[5] = {rank_cap, h->tile, nrhs_max, (int32_t)N, g_solve_segment_rows};
+    int32_t params[4] = {rank_cap, h->tile, nrhs_max, (int32_t)N};
     key = fnv1a(key, params, sizeof(params));
     bool cache_hit = false;
     {

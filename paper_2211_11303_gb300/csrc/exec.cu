@@ -863,220 +863,6 @@ __device__ void task_rsolve(Ctx<T>& c, const Task& t, char* smem) {
   if (threadIdx.x == 0) c.flops += fl + (double)n * n * k;
 }
 
-// ---------------------------------------------------------------- SSOLVE
-// One segment of a triangular solve in one task: the segment's rows of the
-// right-hand side (n <= kSegRows rows, k <= kSegCols columns) are held in
-// shared memory and a list of operations runs on them (SegOp codes in
-// hlu_internal.h): the late update terms, then the segment's own
-// substitution (leaf triangles, dense and low-rank updates).  The operands
-// of the next kSegSlots<T> operations stream into a ring of shared-memory
-// slots (cp.async, one commit group per operation) while the current one
-// runs, so the chain of leaf solves does not wait on global round trips.
-constexpr int kSegB = kSegTile * kSegTile + kSegTile;       // slot offset of the B operand
-constexpr int kSegSlot = kSegB + kSegTile * kSegCols;       // A tile, pivots, B (64 x 16)
-template <class T>
-struct SegSlots {
-  static constexpr int value = sizeof(T) == 4 ? 3 : 2;
-};
-__host__ __device__ constexpr size_t seg_smem_elems(int slots) {
-  return (size_t)kSegRows * kSegCols + (size_t)kRankMax * kSegCols + (size_t)slots * kSegSlot;
-}
-constexpr size_t kSegOpBytes = (sizeof(Term) + sizeof(int32_t)) * kSegMaxOps;
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Starts the copy of operation q's operands into its slot (dense tiles and
-// a lower triangle's pivots; a late update term's A and B); always one
-// commit group, empty when there is nothing to copy, so that the group
-// counting stays uniform.
-template <class T, int NS>
-__device__ __forceinline__ void seg_issue(const Ctx<T>& c, const Term* ops, const int32_t* opw, int nops, int q,
-                                          T* ring, bool upper, int k) {
-  if (q < nops) {
-    const Term& o = ops[q];
-    T* slot = ring + (q % NS) * kSegSlot;
-    if (o.pad == SEG_TRI || o.pad == SEG_DUPD || o.pad == SEG_EXT) {
-      const int rows = o.A.rows, cols = opw[q];
-      const T* src = c.arena + o.A.off;
-      for (int idx = threadIdx.x; idx < rows * cols; idx += NT)
-        cp_async_elem(slot + idx, src + (int64_t)(idx % rows) * o.A.rs + (int64_t)(idx / rows) * o.A.cs);
-    }
-    if (o.pad == SEG_TRI && !upper) {
-      int* pv = reinterpret_cast<int*>(slot + kSegTile * kSegTile);
-      for (int r = threadIdx.x; r < o.A.rows; r += NT) {
-        const unsigned d = (unsigned)__cvta_generic_to_shared(pv + r);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(c.piv + o.B.off + r) : "memory");
-      }
-    }
-    if (o.pad == SEG_EXT) {
-      const int p = opw[q];
-      const T* src = c.arena + o.B.off;
-      for (int idx = threadIdx.x; idx < p * k; idx += NT)
-        cp_async_elem(slot + kSegB + idx, src + (int64_t)(idx % p) * o.B.rs + (int64_t)(idx / p) * o.B.cs);
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-template <class T>
-__device__ void task_ssolve(Ctx<T>& c, const Task& t, char* smem) {
-  constexpr int NS = SegSlots<T>::value;
-  const int n = t.c.rows, k = ncols(c, t.b);
-  const bool upper = (t.flags & TF_UPPER) != 0;
-  const int nops = t.cap;
-  if (n > kSegRows || k > kSegCols || nops > kSegMaxOps) {  // the scheduler never emits these
-    if (threadIdx.x == 0) atomicCAS(c.status, 0, 8);
-    return;
-  }
-  T* X = reinterpret_cast<T*>(smem);       // n x k, ld n
-  T* P = X + kSegRows * kSegCols;          // low-rank projection, kRankMax x k
-  T* ring = P + kRankMax * kSegCols;       // NS operand slots
-  Term* ops = reinterpret_cast<Term*>(ring + NS * kSegSlot);
-  int32_t* opw = reinterpret_cast<int32_t*>(ops + kSegMaxOps);  // column count of each operation's A
-  const T* rhs = c.arena + t.c.off;
-  for (int idx = threadIdx.x; idx < n * k; idx += NT)
-    cp_async_elem(X + idx, rhs + (int64_t)(idx % n) * t.c.rs + (int64_t)(idx / n) * t.c.cs);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  {
-    const int words = nops * (int)(sizeof(Term) / sizeof(int32_t));
-    const int32_t* src = reinterpret_cast<const int32_t*>(c.terms + t.list_begin);
-    int32_t* dst = reinterpret_cast<int32_t*>(ops);
-    for (int w = threadIdx.x; w < words; w += NT) dst[w] = __ldg(src + w);
-    // resolved column counts (ranks fixed during the solve), else live ranks
-    const int pq = (c.term_p && threadIdx.x < nops) ? __ldcg(c.term_p + t.list_begin + threadIdx.x) : -1;
-    __syncthreads();
-    for (int q = threadIdx.x; q < nops; q += NT) {
-      const int pr = (q == threadIdx.x) ? pq : -1;
-      opw[q] = pr >= 0 ? pr : (ops[q].pad == SEG_LUPD ? 0 : ncols(c, ops[q].A));
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NS; ++q) seg_issue<T, NS>(c, ops, opw, nops, q, ring, upper, k);
-  double fl = 0;
-  const T sg = T(t.sign);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = 0; q < nops; ++q) {
-    cp_async_wait_n<NS - 1>();  // operation q's operands (and the right-hand side) have arrived
-    __syncthreads();
-    const Term& o = ops[q];
-    const T* Ad = ring + (q % NS) * kSegSlot;
-    if (o.pad == SEG_EXT) {
-      // rows [ro, ro + rows) += sign * A B (A rows x p, B p x k in the slot)
-      const int rows = o.A.rows, p = opw[q], ro = o.roff;
-      const T* Bd = Ad + kSegB;
-      for (int e = threadIdx.x; e < rows * k; e += NT) {
-        const int i = e % rows, j = e / rows;
-        const T* a = Ad + i;
-        const T* b = Bd + j * p;
-        T s0 = 0, s1 = 0;
-        int l = 0;
-        for (; l + 2 <= p; l += 2) {
-          s0 += a[l * rows] * b[l];
-          s1 += a[(l + 1) * rows] * b[l + 1];
-        }
-        if (l < p) s0 += a[l * rows] * b[l];
-        X[ro + i + j * n] += sg * (s0 + s1);
-      }
-      fl += 2.0 * rows * p * k;
-    } else if (o.pad == SEG_TRI) {
-      const int s = o.A.rows, ro = o.roff;
-      const int r0 = lane, r1 = lane + 32;
-      if (!upper) {
-        const int* pv = reinterpret_cast<const int*>(Ad + kSegTile * kSegTile);
-        for (int j = warp; j < k; j += NT / 32) {
-          T* xj = X + j * n + ro;
-          T v0 = r0 < s ? xj[pv[r0]] : T(0);
-          T v1 = r1 < s ? xj[pv[r1]] : T(0);
-          for (int l = 0; l < s; ++l) {
-            const T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31);
-            if (r0 > l && r0 < s) v0 -= Ad[r0 + l * s] * x;
-            if (r1 > l && r1 < s) v1 -= Ad[r1 + l * s] * x;
-          }
-          __syncwarp();
-          if (r0 < s) xj[r0] = v0;
-          if (r1 < s) xj[r1] = v1;
-        }
-      } else {
-        const T d0 = r0 < s ? T(1) / Ad[r0 + r0 * s] : T(0);
-        const T d1 = r1 < s ? T(1) / Ad[r1 + r1 * s] : T(0);
-        for (int j = warp; j < k; j += NT / 32) {
-          T* xj = X + j * n + ro;
-          T v0 = r0 < s ? xj[r0] : T(0);
-          T v1 = r1 < s ? xj[r1] : T(0);
-          for (int l = s - 1; l >= 0; --l) {
-            const T x = __shfl_sync(0xffffffffu, l < 32 ? v0 : v1, l & 31) *
-                        __shfl_sync(0xffffffffu, l < 32 ? d0 : d1, l & 31);
-            if (r0 == l) v0 = x;
-            if (r1 == l) v1 = x;
-            if (r0 < l) v0 -= Ad[r0 + l * s] * x;
-            if (r1 < l) v1 -= Ad[r1 + l * s] * x;
-          }
-          if (r0 < s) xj[r0] = v0;
-          if (r1 < s) xj[r1] = v1;
-        }
-      }
-      fl += (double)s * s * k;
-    } else if (o.pad == SEG_DUPD) {
-      // rows [ro, ro + rows) -= A rows [co, co + cols): the two row ranges
-      // are disjoint, so every output is written as soon as it is summed
-      const int rows = o.A.rows, cols = opw[q], ro = o.roff, co = o.B.pad;
-      for (int e = threadIdx.x; e < rows * k; e += NT) {
-        const int i = e % rows, j = e / rows;
-        const T* a = Ad + i;
-        const T* xin = X + co + j * n;
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        int l = 0;
-        for (; l + 4 <= cols; l += 4) {
-          s0 += a[l * rows] * xin[l];
-          s1 += a[(l + 1) * rows] * xin[l + 1];
-          s2 += a[(l + 2) * rows] * xin[l + 2];
-          s3 += a[(l + 3) * rows] * xin[l + 3];
-        }
-        for (; l < cols; ++l) s0 += a[l * rows] * xin[l];
-        X[ro + i + j * n] -= (s0 + s1) + (s2 + s3);
-      }
-      fl += 2.0 * rows * cols * k;
-    } else if (o.pad == SEG_LUPD) {
-      // rows [ro, ro + rows) -= A (B^T rows [co, co + B.rows)), factors read
-      // from global memory (read-only during the solve)
-      const int rows = o.A.rows, ny = o.B.rows, ro = o.roff, co = o.B.pad;
-      const int r = ncols(c, o.A);
-      for (int e = threadIdx.x; e < r * k; e += NT) {
-        const int l = e % r, j = e / r;
-        const T* b = c.arena + o.B.off + (int64_t)l * o.B.cs;
-        const T* xin = X + co + j * n;
-        T s0 = 0, s1 = 0;
-        int i = 0;
-        for (; i + 2 <= ny; i += 2) {
-          s0 += __ldg(b + (int64_t)i * o.B.rs) * xin[i];
-          s1 += __ldg(b + (int64_t)(i + 1) * o.B.rs) * xin[i + 1];
-        }
-        if (i < ny) s0 += __ldg(b + (int64_t)i * o.B.rs) * xin[i];
-        P[l + j * kRankMax] = s0 + s1;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < rows * k; e += NT) {
-        const int i = e % rows, j = e / rows;
-        const T* a = c.arena + o.A.off + (int64_t)i * o.A.rs;
-        T s0 = 0;
-        for (int l = 0; l < r; ++l) s0 += __ldg(a + (int64_t)l * o.A.cs) * P[l + j * kRankMax];
-        X[ro + i + j * n] -= s0;
-      }
-      fl += 2.0 * (rows + ny) * r * k;
-    }
-    __syncthreads();
-    seg_issue<T, NS>(c, ops, opw, nops, q + NS, ring, upper, k);
-  }
-  cp_async_wait_n<0>();
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n * k; idx += NT) stv(c, t.c, idx % n, idx / n, X[idx]);
-  if (threadIdx.x == 0) c.flops += fl;
-}
-
 // ---------------------------------------------------------------- DADD
 template <class T>
 __device__ void task_dadd(Ctx<T>& c, const Task& t, char* smem) {
@@ -1440,10 +1226,7 @@ __host__ __device__ constexpr size_t exec_smem_base(int elem_size) {
   const size_t lu0 = (size_t)elem_size * (64 * 64 + 64) + 64 * sizeof(int);
   // fused leaf solve: staging chunks, tile, right-hand side, inverse diagonal, pivots
   const size_t rsolve = (size_t)elem_size * (2 * kStage + 2 * 64 * 64 + 64) + 64 * sizeof(int);
-  const size_t lu1 = rsolve > lu0 ? rsolve : lu0;
-  // segment solve: right-hand side, projection, operand slots, operations
-  const size_t seg = (size_t)elem_size * seg_smem_elems(elem_size == 4 ? 3 : 2) + kSegOpBytes;
-  const size_t lu = seg > lu1 ? seg : lu1;
+  const size_t lu = rsolve > lu0 ? rsolve : lu0;
   const size_t gemm = (size_t)elem_size * 2 * kStage;
   const size_t m = trunc > lu ? trunc : lu;
   return m > gemm ? m : gemm;
@@ -2206,7 +1989,6 @@ __device__ void run_task(Ctx<T>& c, const Task& t, char* smem) {
     case TK_TRUNC: task_trunc(c, t, smem); break;
     case TK_DADD: task_dadd(c, t, smem); break;
     case TK_RSOLVE: task_rsolve(c, t, smem); break;
-    case TK_SSOLVE: task_ssolve(c, t, smem); break;
     default: break;
   }
 }

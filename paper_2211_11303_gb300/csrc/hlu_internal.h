@@ -45,26 +45,9 @@ enum TaskType : int32_t {
   TK_DADD = 7,    // c (m x n) <- [c] + sign * a b^T  (a: m x k, b: n x k)
   TK_RSOLVE = 8,  // c <- tri(a)^-1 (c - sum_terms A_t B_t): one tile of a triangular solve;
                   // flags & TF_UPPER: U^-1, else L^-1 P (pivots at piv_off)
-  TK_SSOLVE = 9,  // one segment of a triangular solve: the cap operations (SegOp) at
-                  // list_begin of the term list on c held in shared memory (the late
-                  // update with sign, then the substitution); flags & TF_UPPER as RSOLVE
-  TK_NUM = 10,
-  TK_FENCE = 10   // no work: orders re-use of temporary memory after its readers
+  TK_NUM = 9,
+  TK_FENCE = 9    // no work: orders re-use of temporary memory after its readers
 };
-// Operations of a TK_SSOLVE task, stored as Terms after its update terms;
-// the code is in Term::pad, rows are local to the segment:
-//   SEG_TRI:  rows [roff, roff + A.rows) <- tri(A)^-1 rows, pivots at B.off
-//   SEG_DUPD: rows [roff, roff + A.rows) -= A rows [B.pad, B.pad + A.cols)
-//   SEG_LUPD: rows [roff, roff + A.rows) -= A (B^T rows [B.pad, B.pad + B.rows))
-//   SEG_EXT:  rows [roff, roff + A.rows) += sign * A B, B read from outside the
-//             segment (the late update; A at most kSegTile x kSegTile)
-enum : int32_t { SEG_TRI = 1, SEG_DUPD = 2, SEG_LUPD = 3, SEG_EXT = 4 };
-// most operations of one segment solve, and its largest diagonal tile
-constexpr int32_t kSegMaxOps = 128;
-constexpr int32_t kSegTile = 64;
-// largest segment of the triangular-solve schedule (rows held in shared memory)
-constexpr int32_t kSegRows = 256;
-constexpr int32_t kSegCols = 16;  // right-hand-side columns of one segment solve
 // TF_ALPHA (DADD) and PF_ALPHA (a TRUNC piece): the sign is multiplied by the
 // launch's scalar alpha (the Schulz start X_0 = alpha A)
 enum : int32_t { TF_OVERWRITE = 1, TF_UPPER = 2, TF_ALPHA = 4 };
@@ -147,9 +130,6 @@ struct SchedStats {
 void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t rank_cap,
                      int32_t nrhs_max, int32_t tile, ArenaLayout& L,
                      Schedule& factor, Schedule& solve, SchedStats& st, std::vector<Block>* factor_blocks);
-// Rows of the triangular-solve segments (0: one task per leaf tile, the
-// segment size of the factorisation); at most kSegRows.
-extern int32_t g_solve_segment_rows;
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile);
 
 // The Schulz iteration for the inverse of A_H (Sec. 3, Sec. 4) over four

@@ -366,73 +366,6 @@ void h_rsolve(HostCtx<T>& c, const Task& t) {
   h_trsm(c, s);
 }
 
-// One segment of a triangular solve: its operations in order (the late
-// update, then the leaf triangles and the dense and low-rank updates).
-template <class T>
-void h_ssolve(HostCtx<T>& c, const Task& t) {
-  const int k = ncols(c, t.b);
-  const bool upper = (t.flags & TF_UPPER) != 0;
-  auto x = [&](int i, int j) -> T& { return at(c, t.c, i, j); };
-  for (int q = 0; q < t.cap; ++q) {
-    const Term& o = c.terms[t.list_begin + q];
-    const int ro = o.roff;
-    if (o.pad == SEG_TRI) {
-      const int s = o.A.rows;
-      std::vector<T> V(s), W(s);
-      for (int j = 0; j < k; ++j) {
-        for (int i = 0; i < s; ++i) V[i] = x(ro + i, j);
-        if (!upper) {
-          const int32_t* p = c.piv + o.B.off;
-          for (int i = 0; i < s; ++i) W[i] = V[p[i]];
-          for (int i = 0; i < s; ++i)
-            for (int l = 0; l < i; ++l) W[i] -= at(c, o.A, i, l) * W[l];
-          V = W;
-        } else {
-          for (int i = s - 1; i >= 0; --i) {
-            for (int l = i + 1; l < s; ++l) V[i] -= at(c, o.A, i, l) * V[l];
-            V[i] /= at(c, o.A, i, i);
-          }
-        }
-        for (int i = 0; i < s; ++i) x(ro + i, j) = V[i];
-      }
-    } else if (o.pad == SEG_DUPD) {
-      const int co = o.B.pad;
-      for (int j = 0; j < k; ++j)
-        for (int i = 0; i < o.A.rows; ++i) {
-          T sum = 0;
-          for (int l = 0; l < o.A.cols; ++l) sum += at(c, o.A, i, l) * x(co + l, j);
-          x(ro + i, j) -= sum;
-        }
-    } else if (o.pad == SEG_EXT) {
-      const int pcols = ncols(c, o.A);
-      const T sg = T(t.sign);
-      for (int j = 0; j < k; ++j)
-        for (int i = 0; i < o.A.rows; ++i) {
-          T sum = 0;
-          for (int l = 0; l < pcols; ++l) sum += at(c, o.A, i, l) * at(c, o.B, l, j);
-          x(ro + i, j) += sg * sum;
-        }
-    } else if (o.pad == SEG_LUPD) {
-      const int co = o.B.pad, r = ncols(c, o.A);
-      std::vector<T> P((size_t)r * k);
-      for (int j = 0; j < k; ++j)
-        for (int l = 0; l < r; ++l) {
-          T sum = 0;
-          for (int i = 0; i < o.B.rows; ++i) sum += at(c, o.B, i, l) * x(co + i, j);
-          P[l + (size_t)j * r] = sum;
-        }
-      for (int j = 0; j < k; ++j)
-        for (int i = 0; i < o.A.rows; ++i) {
-          T sum = 0;
-          for (int l = 0; l < r; ++l) sum += at(c, o.A, i, l) * P[l + (size_t)j * r];
-          x(ro + i, j) -= sum;
-        }
-    } else {
-      throw std::logic_error("segment operation");
-    }
-  }
-}
-
 template <class T>
 void run_task(HostCtx<T>& c, const Task& t) {
   switch (t.type) {
@@ -445,7 +378,6 @@ void run_task(HostCtx<T>& c, const Task& t) {
     case TK_TRUNC: h_trunc(c, t); break;
     case TK_DADD: h_dadd(c, t); break;
     case TK_RSOLVE: h_rsolve(c, t); break;
-    case TK_SSOLVE: h_ssolve(c, t); break;
     case TK_FENCE: break;
     default: throw std::logic_error("task type");
   }

@@ -52,20 +52,10 @@ class Sched {
   Sched(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t kcap, ArenaLayout& L,
         Schedule* S, std::vector<int32_t>& dbuf, std::vector<int32_t>& xbuf,
         std::vector<int32_t>& ybuf, bool make_buffers, int32_t segsz, int64_t ring_off,
-        int64_t ring_size, int32_t seg_solve_rows = 0)
+        int64_t ring_size)
       : C_(C), B_(B), kcap_(kcap), L_(L), S_(S), dbuf_(dbuf), xbuf_(xbuf), ybuf_(ybuf),
         ring_off_(ring_off), ring_size_(ring_size) {
     S_->pred_ptr.assign(1, 0);
-    // segment solves (solve schedules): segments of up to seg_solve_rows rows
-    // whose diagonal blocks fit one task; clusters of up to segsz rows always do
-    seg_solve_ = seg_solve_rows > 0;
-    segsz_base_ = segsz;
-    if (seg_solve_) {
-      segsz = std::max(segsz, seg_solve_rows);
-      diag_of_.assign(C_.size(), -1);
-      for (size_t b = 0; b < B_.size(); ++b)
-        if (B_[b].row == B_[b].col) diag_of_[B_[b].row] = (int32_t)b;
-    }
     // dependency segments: clusters of at most `segsz` DOFs whose parent is
     // larger (the tile level, or the leaves); every cluster covers a range of them
     seg_begin_.assign(C_.size(), 0);
@@ -92,36 +82,9 @@ class Sched {
   }
 
   // ---------------------------------------------------------------- segments
-  // operations of the segment solve of diagonal block d (both triangles),
-  // or more than kSegMaxOps when it cannot be one task
-  int32_t seg_op_count(int32_t d) const {
-    constexpr int32_t kTooMany = kSegMaxOps + 1;
-    if (d < 0) return kTooMany;
-    if (kind(d) == KIND_DENSE) return sz(rowc(d)) <= kSegTile ? 1 : kTooMany;
-    if (kind(d) != KIND_SUB) return kTooMany;
-    int32_t n = seg_op_count(son(d, 0, 0)) + seg_op_count(son(d, 1, 1));
-    int32_t off[2] = {0, 0};
-    for (int q = 0; q < 2; ++q) {
-      std::vector<int32_t> lv;
-      leaves_of(q == 0 ? son(d, 1, 0) : son(d, 0, 1), lv);
-      for (int32_t be : lv) {
-        if (kind(be) == KIND_DENSE)
-          off[q] += ((sz(rowc(be)) + kSegTile - 1) / kSegTile) * ((sz(colc(be)) + kSegTile - 1) / kSegTile);
-        else if (kind(be) == KIND_ADM)
-          off[q] += 1;
-        else
-          return kTooMany;
-      }
-    }
-    n += std::max(off[0], off[1]);
-    return std::min(n, kTooMany);
-  }
   void assign_segments(int32_t c, bool inside, int32_t segsz) {
     const Cluster& cl = C_[c];
-    // segment solves: a segment's diagonal block must fit one task
-    const bool fits = !seg_solve_ || cl.size <= segsz_base_ ||
-                      seg_op_count(diag_of_[c]) <= kSegMaxOps;
-    bool is_seg = !inside && ((cl.size <= segsz && fits) || cl.son[0] < 0);
+    bool is_seg = !inside && (cl.size <= segsz || cl.son[0] < 0);
     if (is_seg || inside) {
       if (is_seg) seg_cluster_.push_back(c);
       int32_t sidx = (int32_t)seg_cluster_.size() - 1;
@@ -595,168 +558,8 @@ class Sched {
     return out;
   }
 
-  // ---------------------------------------------------------------- segment solves
-  // A diagonal block whose row cluster is one segment of the solve schedule
-  // is solved by one TK_SSOLVE task: the segment's late update terms, then
-  // the recursive substitution of the block (leaf triangles, dense and
-  // low-rank off-diagonal updates) in the order the recursion visits them,
-  // on the segment's rows held in shared memory.
-  bool is_segment(int32_t c) const {
-    return seg_end_[c] - seg_begin_[c] == 1 && seg_cluster_[seg_begin_[c]] == c;
-  }
-  struct SegOpMV {
-    Term t;
-    MV a, b;  // operands read (b.buf < 0 when none)
-  };
-  // the operations of the substitution of diagonal block d (rows relative to
-  // the segment at offset base); false if some piece does not fit the task
-  bool seg_ops(int32_t d, int32_t base, bool upper, std::vector<SegOpMV>& ops) const {
-    if (kind(d) == KIND_DENSE) {
-      if (sz(rowc(d)) > kSegTile) return false;
-      SegOpMV o;
-      std::memset(&o.t, 0, sizeof(o.t));
-      o.a = mvD(d);
-      o.b.buf = -1;
-      o.t.A = o.a.v;
-      o.t.B.off = L_.piv_off[d];
-      o.t.B.slot = -1;
-      o.t.roff = C_[rowc(d)].off - base;
-      o.t.pad = SEG_TRI;
-      ops.push_back(o);
-      return true;
-    }
-    if (kind(d) != KIND_SUB) return false;
-    const int32_t first = upper ? 1 : 0, second = 1 - first;
-    if (!seg_ops(son(d, first, first), base, upper, ops)) return false;
-    std::vector<int32_t> lv;
-    leaves_of(son(d, second, first), lv);
-    for (int32_t be : lv) {
-      const int32_t ro = C_[rowc(be)].off - base, co = C_[colc(be)].off - base;
-      if (kind(be) == KIND_DENSE) {
-        // in pieces of at most kSegTile x kSegTile
-        const MV D = mvD(be);
-        for (int32_t i0 = 0; i0 < D.v.rows; i0 += kSegTile)
-          for (int32_t j0 = 0; j0 < D.v.cols; j0 += kSegTile) {
-            SegOpMV o;
-            std::memset(&o.t, 0, sizeof(o.t));
-            o.a = D;
-            o.b.buf = -1;
-            o.t.A = D.v;
-            o.t.A.off += (int64_t)i0 * D.v.rs + (int64_t)j0 * D.v.cs;
-            o.t.A.rows = std::min(kSegTile, D.v.rows - i0);
-            o.t.A.cols = std::min(kSegTile, D.v.cols - j0);
-            o.t.B.slot = -1;
-            o.t.B.pad = co + j0;
-            o.t.roff = ro + i0;
-            o.t.pad = SEG_DUPD;
-            ops.push_back(o);
-          }
-      } else if (kind(be) == KIND_ADM) {
-        SegOpMV o;
-        std::memset(&o.t, 0, sizeof(o.t));
-        o.a = mvX(be);
-        o.b = mvY(be);
-        o.t.A = o.a.v;
-        o.t.B = o.b.v;
-        o.t.B.pad = co;
-        o.t.roff = ro;
-        o.t.pad = SEG_LUPD;
-        ops.push_back(o);
-      } else {
-        return false;
-      }
-    }
-    return seg_ops(son(d, second, second), base, upper, ops);
-  }
-  // true if diagonal block d was emitted as one segment solve
-  bool seg_solve(int32_t d, const MV& V, bool upper) {
-    if (!seg_solve_ || !is_segment(rowc(d))) return false;
-    const int32_t sg = seg_begin_[rowc(d)];
-    std::vector<SegOpMV> ops;
-    if (sz(rowc(d)) > kSegRows || !seg_ops(d, C_[rowc(d)].off, upper, ops) || (int32_t)ops.size() > kSegMaxOps)
-      return seg_fallback(sg, V, d);
-    Pending* pd = (sg < (int32_t)pending_.size() && pending_[sg].active) ? &pending_[sg] : nullptr;
-    // the late update terms become the first operations (SEG_EXT), in
-    // pieces of at most kSegTile x kSegTile
-    std::vector<SegOpMV> ext;
-    std::vector<int32_t> ext_tbuf;  // temporaries read (projections)
-    if (pd) {
-      const int32_t lc = rowc(d);
-      for (int32_t i : pd->list) {
-        const int32_t be = pd->lv[i];
-        const int32_t obc = pd->trans ? colc(be) : rowc(be);
-        const int32_t rc = C_[obc].size <= C_[lc].size ? obc : lc;
-        const int32_t roff = C_[rc].off - C_[lc].off;
-        const bool dense = kind(be) == KIND_DENSE;
-        MV A, Bv;
-        if (dense) {
-          A = sub(pd->trans ? mvDT(be) : mvD(be), rc);
-          Bv = sub(pd->Vin, pd->trans ? rowc(be) : colc(be));
-        } else {
-          A = sub(pd->trans ? mvY(be) : mvX(be), rc);
-          Bv = pd->T[i];
-          ext_tbuf.push_back(Bv.buf);
-          Bv.buf = -1;  // a single-segment temporary: tracked through ext_tbuf
-          if (A.v.cols > kSegTile) return seg_fallback(sg, V, d);
-        }
-        for (int32_t i0 = 0; i0 < A.v.rows; i0 += kSegTile)
-          for (int32_t j0 = 0; j0 < (dense ? A.v.cols : 1); j0 += kSegTile) {
-            SegOpMV o;
-            std::memset(&o.t, 0, sizeof(o.t));
-            o.a = A;
-            o.b = Bv;
-            o.t.A = A.v;
-            o.t.A.off += (int64_t)i0 * A.v.rs;
-            o.t.A.rows = std::min(kSegTile, A.v.rows - i0);
-            o.t.B = Bv.v;
-            if (dense) {
-              o.t.A.off += (int64_t)j0 * A.v.cs;
-              o.t.A.cols = std::min(kSegTile, A.v.cols - j0);
-              o.t.B.off += (int64_t)j0 * Bv.v.rs;
-              o.t.B.rows = o.t.A.cols;
-            }
-            o.t.roff = roff + i0;
-            o.t.pad = SEG_EXT;
-            ext.push_back(o);
-          }
-      }
-    }
-    if ((int32_t)(ext.size() + ops.size()) > kSegMaxOps) return seg_fallback(sg, V, d);
-    Task k = make(TK_SSOLVE);
-    k.flags = upper ? TF_UPPER : 0;
-    k.c = V.v;
-    k.b = V.v;  // column count source
-    k.sign = pd ? pd->sign : 1.0f;
-    k.list_begin = (int32_t)S_->terms.size();
-    k.list_count = 0;
-    k.cap = (int32_t)(ext.size() + ops.size());
-    begin(k);
-    for (const std::vector<SegOpMV>* l : {&ext, &ops})
-      for (const SegOpMV& o : *l) {
-        S_->terms.push_back(o.t);
-        acc(o.a, false);
-        acc(o.b, false);
-      }
-    for (int32_t b : ext_tbuf) touch(bufs_[b].seg0, false);
-    if (pd) acc_rank(pd->Vin);
-    acc(V, true);
-    end();
-    if (pd) *pd = Pending();
-    return true;
-  }
-  // the segment is solved task by task: its late update becomes its own task
-  bool seg_fallback(int32_t sg, const MV& V, int32_t d) {
-    if (sg < (int32_t)pending_.size() && pending_[sg].active) {
-      Pending& pd = pending_[sg];
-      emit_rowmv(pd.lv, pd.T, pd.list, pd.Vin, V, rowc(d), pd.sign, pd.trans, false, -1, pd.Vin);
-      pd = Pending();
-    }
-    return false;
-  }
-
   // ---------------------------------------------------------------- triangular
   void solve_lower(int32_t d, const MV& V) {
-    if (seg_solve(d, V, false)) return;
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_L, d, V);
       return;
@@ -779,7 +582,6 @@ class Sched {
     solve_upperT(son(d, 1, 1), W1);
   }
   void solve_upper(int32_t d, const MV& V) {
-    if (seg_solve(d, V, true)) return;
     if (kind(d) == KIND_DENSE) {
       trsm_leaf(TK_TRSM_U, d, V);
       return;
@@ -1083,9 +885,6 @@ class Sched {
   std::vector<int32_t>& ybuf_;
   int32_t seg_size_of(int32_t) const { return segsz_; }
   int32_t segsz_ = 0;
-  bool seg_solve_ = false;
-  int32_t segsz_base_ = 0;         // segment size of the factorisation
-  std::vector<int32_t> diag_of_;   // cluster -> its diagonal block (-1: inside a tile)
   int64_t ring_off_ = 0, ring_size_ = 0, cursor_ = 0;
   std::vector<int32_t> seg_begin_, seg_end_, seg_cluster_;
   std::vector<std::vector<int32_t>> chunk_occ_;
@@ -1127,8 +926,6 @@ class Sched {
 };
 
 }  // namespace
-
-int32_t g_solve_segment_rows = 0;
 
 std::vector<Block> factor_tree(const std::vector<Cluster>& C, const std::vector<Block>& B, int32_t tile) {
   std::vector<Block> out;
@@ -1236,11 +1033,7 @@ void build_schedules(const std::vector<Cluster>& C, const std::vector<Block>& Bf
     st.ring_wraps = s.wraps_;
   }
   {
-    // the solve tracks its right-hand side in segments of up to kSegRows
-    // rows, each diagonal segment solved by one task
-    const bool seg = g_solve_segment_rows > 0 && nrhs_max <= kSegCols;
-    Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring,
-            seg ? g_solve_segment_rows : 0);
+    Sched s(C, B, rank_cap, L, &solve, dbuf, xbuf, ybuf, true, segsz, ring_off, ring);
     s.solve_all(nrhs_max);
     st.temp_elems += s.temp_elems_;
   }

@@ -105,7 +105,6 @@ SIGNATURES = {
     "hlu_factor_bytes_estimate": (_i64, [_vp, _i32]),
     "hlu_set_wait_limit_ms": (None, [_f64]),
     "hlu_set_tile": (None, [_i32]),
-    "hlu_set_solve_segment": (_i32, [_i32]),
     "hlu_set_trunc_params": (_i32, [_i32, _f64]),
     "hlu_launch_count": (_i64, []),
     "hlu_set_allocator": (_i32, [_vp, _vp, _vp]),
@@ -378,8 +377,7 @@ def hlu_factor_stats(h):
     return _struct_dict(info)
 
 
-TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "SSOLVE",
-              "FENCE"]
+TASK_KINDS = ["GETRF", "TRSM_L", "TRSM_UT", "TRSM_U", "PROJ", "ROWMV", "TRUNC", "DADD", "RSOLVE", "FENCE"]
 
 
 def hlu_factor_profile(h):
@@ -526,10 +524,6 @@ def hlu_set_trunc_params(compress_at=0, jacobi_tol=0.0):
 def hlu_set_tile(t):
     lib().hlu_set_tile(int(t))
 
-
-def hlu_set_solve_segment(rows):
-    """Rows of a triangular-solve segment for later hlu_build calls (0: one task per tile)."""
-    _check(lib().hlu_set_solve_segment(int(rows)))
 
 
 class Problem:

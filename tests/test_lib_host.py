@@ -118,35 +118,6 @@ def test_tiled_factor_tree_quality(lib, n, kappa, leaf, tile):
     assert np.array_equal(x2, x3)
 
 
-@pytest.mark.parametrize("precision,leaf,tile", [(0, 32, 64), (1, 32, 64), (0, 8, 16)])
-def test_segment_solves_match_tile_solves(lib, precision, leaf, tile):
-    """The triangular solve by segments (one task per diagonal segment of up
-    to 256 rows, its leaf triangles and updates run in shared memory) is the
-    same H-solve as the one-task-per-tile schedule, up to the summation order
-    of the updates, and any topological order of its DAG gives the same bits."""
-    try:
-        assert lib.hlu_set_solve_segment(0) == 0
-        _, _, _, _, _, x0, info0 = _host_solve(lib, 6, 3.0, 1e-6, leaf, 0, nrhs=3, tile=tile, precision=precision)
-        assert lib.hlu_set_solve_segment(256) == 0
-        _, _, _, _, _, x1, info1 = _host_solve(lib, 6, 3.0, 1e-6, leaf, 0, nrhs=3, tile=tile, precision=precision)
-        _, _, _, _, _, x2, _ = _host_solve(lib, 6, 3.0, 1e-6, leaf, 5, nrhs=3, tile=tile, precision=precision)
-    finally:
-        lib.hlu_set_solve_segment(0)
-    tol = 1e-12 if precision == 0 else 1e-5
-    assert np.linalg.norm(x1 - x0) <= tol * np.linalg.norm(x0)
-    assert np.array_equal(x1, x2)
-    assert info1[1] < info0[1]  # fewer solve tasks
-
-
-def test_solve_segment_argument_is_checked(lib):
-    try:
-        assert lib.hlu_set_solve_segment(-1) == 1
-        assert lib.hlu_set_solve_segment(257) == 1
-        assert lib.hlu_set_solve_segment(128) == 0
-    finally:
-        lib.hlu_set_solve_segment(0)
-
-
 def test_allocator_and_memory_limit_arguments(lib):
     """hlu_set_allocator takes both callbacks or neither; the memory limit is
     a non-negative byte count (no device needed)."""

@@ -22,14 +22,21 @@ Readings:
     div E = 0 and curl curl E = 2 pi^2 E, so J = (2 pi^2 - kappa^2) E, and
     E x n = 0 on the cube's boundary;
   * Example 1's source J_S = [0, 0, 1]^T is a constant current density
-    (constant_current_rhs).
+    (constant_current_rhs);
+  * the material coefficient beta is constant on each tetrahedron and scales
+    that element's curl-curl matrix by 1/beta; Example 3's magnet
+    (0.5 x 0.5 x 0.75 in the unit box, beta = 10, air beta = 1) is read as
+    centred in the box (magnet_beta).
 
 Pins (tests/test_oracle_fem.py): discrete de Rham property C G = 0 and K G = 0;
 null space of K of dimension (n-1)^3; cavity eigenvalues 2pi^2 (x3), 3pi^2 (x2);
 symmetry; M SPD; reference-tetrahedron element matrices worked by hand; L2
 convergence of the manufactured solution at rate ~1; the constant-current load
 vector is discretely divergence-free (G^T b = 0) and equals the exact integral
-|T|/4 J . (grad l_b - grad l_a) computed element by element.
+|T|/4 J . (grad l_b - grad l_a) computed element by element; with a material
+coefficient, K_beta G = 0 still holds (only the curl-curl part carries beta),
+a constant beta = c gives K / c (cavity eigenvalues divided by c), and the
+magnet holds 0.1875 of the cube's volume (576 of the 3,072 tetrahedra at n = 8).
 """
 import math
 
@@ -125,16 +132,24 @@ def _tet_dofs(mesh, tets):
     return dofs
 
 
-def assemble(mesh, kappa, parts=False):
+def assemble(mesh, kappa, parts=False, beta=None):
     """CSR matrix A = K - kappa^2 M over interior edges (rows/cols in DOF order,
     columns ascending within a row; the pattern holds every pair of interior
     edges that share a tetrahedron, explicit zeros kept).
 
-    parts=True returns (K, M) instead.
+    beta (optional, one value per tetrahedron): the material coefficient of
+    the curl-curl term, K = sum_T beta_T^-1 K_T (the operator
+    curl(beta^-1 curl E) - kappa E of Sec. 2, beta constant on each element);
+    None is beta = 1.  parts=True returns (K, M) instead.
     """
     N = len(mesh["edges"])
     tets, P = _tet_data(mesh)
     Ke, Me = element_matrices(P, tets)
+    if beta is not None:
+        beta = np.asarray(beta, dtype=np.float64).reshape(-1)
+        if beta.shape[0] != tets.shape[0] or not np.all(beta > 0):
+            raise ValueError("beta: one positive value per tetrahedron")
+        Ke = Ke / beta[:, None, None]
     dofs = _tet_dofs(mesh, tets)
     R = np.repeat(dofs[:, :, None], 6, axis=2)
     C = np.repeat(dofs[:, None, :], 6, axis=1)
@@ -147,6 +162,22 @@ def assemble(mesh, kappa, parts=False):
     A = K.copy()
     A.data = K.data - kappa * kappa * M.data
     return A
+
+
+MAGNET_BOX = ((0.25, 0.75), (0.25, 0.75), (0.125, 0.875))
+
+
+def magnet_beta(mesh, beta_in=10.0, box=MAGNET_BOX):
+    """Per-tetrahedron material coefficient of Example 3 (Sec. 4): a magnet of
+    0.5 x 0.5 x 0.75 inside the unit box, read as centred, with beta = beta_in
+    there and beta = 1 in the surrounding air; a tetrahedron belongs to the
+    magnet when its centroid does."""
+    tets, P = _tet_data(mesh)
+    c = P.mean(axis=1)
+    inside = np.ones(c.shape[0], dtype=bool)
+    for a, (lo, hi) in enumerate(box):
+        inside &= (c[:, a] > lo) & (c[:, a] < hi)
+    return np.where(inside, float(beta_in), 1.0)
 
 
 def _coo_to_csr(rows, cols, vals, N):

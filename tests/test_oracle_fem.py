@@ -176,3 +176,51 @@ def test_general_mesh_de_rham_symmetry_and_nullspace():
     assert ev_m.min() > 0
     ev_k = sla.eigvalsh(K.toarray(), Mm.toarray())
     assert int(np.sum(np.abs(ev_k) < 1e-8)) == G.shape[1]
+
+
+def test_material_coefficient_keeps_gradients_in_kernel():
+    """curl(beta^-1 curl): a per-element beta scales only the curl-curl part,
+    so discrete gradients stay in its kernel and the mass matrix is unchanged
+    (Sec. 2, the operator with the material coefficient)."""
+    n = 4
+    m = M.interior_edges(n)
+    rng = np.random.default_rng(5)
+    beta = rng.uniform(1.0, 10.0, size=6 * n ** 3)
+    K1, M1 = F.assemble(m, 1.0, parts=True)
+    Kb, Mb = F.assemble(m, 1.0, parts=True, beta=beta)
+    G = F.gradient_matrix(m)
+    assert abs(Kb @ G).max() < 1e-12 * abs(Kb).max()
+    assert abs(Mb - M1).max() == 0.0
+    assert abs(Kb - K1).max() > 1e-3 * abs(K1).max()
+    A = F.assemble(m, 2.0, beta=beta)
+    assert abs(A - (Kb - 4.0 * Mb)).max() < 1e-14 * abs(A).max()
+    with pytest.raises(ValueError):
+        F.assemble(m, 1.0, beta=np.zeros(6 * n ** 3))
+
+
+def test_constant_beta_divides_the_cavity_eigenvalues():
+    """beta = c everywhere: the cavity eigenvalues pi^2 (l^2 + m^2 + n^2) / c
+    (at least two indices nonzero) - the first, 2 pi^2 / c, three times."""
+    c = 4.0
+    for n in (3, 5):
+        m = M.interior_edges(n)
+        Kb, Mm = F.assemble(m, 1.0, parts=True, beta=np.full(6 * n ** 3, c))
+        ev = sla.eigh(Kb.toarray(), Mm.toarray(), eigvals_only=True)
+        ev = np.sort(ev[ev > 1e-8 * ev.max()])[:5]
+        exact = np.pi ** 2 * np.array([2, 2, 2, 3, 3]) / c
+        err = np.abs(ev - exact) / exact
+    assert np.all(err < 0.08)
+
+
+def test_magnet_occupies_its_volume():
+    """Example 3's magnet (0.5 x 0.5 x 0.75, centred): at n = 8 the lattice
+    fits its faces, so exactly 0.1875 of the 3,072 tetrahedra (576) lie in it,
+    each with all four vertices in the closed box."""
+    n = 8
+    m = M.interior_edges(n)
+    beta = F.magnet_beta(m, 10.0)
+    inside = beta == 10.0
+    assert inside.sum() == 576 and np.all((beta == 1.0) | inside)
+    P = m["coords"][m["tets"][inside]]
+    for a, (lo, hi) in enumerate(F.MAGNET_BOX):
+        assert np.all(P[:, :, a] >= lo - 1e-15) and np.all(P[:, :, a] <= hi + 1e-15)

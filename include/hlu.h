@@ -84,12 +84,18 @@ typedef struct hlu_handle hlu_handle;
  * DOFs in increasing (lo, hi) order.  The cluster tree's points are the edge
  * midpoints on an integer grid, p = rint((x_lo + x_hi - 2 b) s), b the lower
  * corner of the vertices' bounding box and s the largest power of two with
- * 2 extent s <= 2^21.  The caller keeps xyz and tets; hlu_build copies them. */
+ * 2 extent s <= 2^21.  beta (may be NULL: beta = 1 everywhere): the
+ * material coefficient of the curl-curl term (Sec. 2: the operator
+ * curl(beta^-1 curl E) - kappa E), one positive value per tetrahedron, in the
+ * order of tets (for lattice_n > 0: in the order hlu_mesh_kuhn_cube lists
+ * them); Example 3's magnet is beta = 10 inside, 1 in the air.  The caller
+ * keeps xyz, tets and beta; hlu_build copies them. */
 typedef struct {
   int32_t nv, nt;
   const double* xyz;
   const int32_t* tets;
   int32_t lattice_n;
+  const double* beta;
 } hlu_mesh;
 
 /* hlu_mesh_kuhn_cube - the Kuhn cube with n^3 sub-cubes as a mesh: vertex
@@ -142,8 +148,9 @@ typedef struct {
 /* hlu_build - Algorithm 1 step I and the structures it needs.
  * Builds, on the GPU: the mesh's interior-edge numbering (Sec. 2.1: one DOF
  * per interior edge, sigma(Phi_i, e_j) = delta_ij), the CSR matrix
- * A = K - kappa^2 M of a(E, Phi) = <curl E, curl Phi> - kappa^2 <E, Phi>
- * (Sec. 2.1 weak form; the paper's kappa is kappa^2 here), the geometric
+ * A = K - kappa^2 M of a(E, Phi) = <beta^-1 curl E, curl Phi> - kappa^2 <E, Phi>
+ * (Sec. 2.1 weak form, with the mesh's beta; the paper's kappa is kappa^2
+ * here), the geometric
  * cluster tree on the edge midpoints (doubled lattice coordinates on the Kuhn
  * cube, the integer grid of hlu_mesh otherwise; Sec. 4, geometrically balanced
  * bisection, leaf size `leaf`), the block tree with admissibility
@@ -159,8 +166,8 @@ typedef struct {
  * Errors: HLU_ERR_ARG for lattice_n outside [0, 200], a general mesh with
  * fewer than 4 vertices, no tetrahedra, 2^21 or more vertices, a vertex id
  * out of range, a repeated vertex in a tetrahedron or a non-finite
- * coordinate, leaf < 2, eta <= 0 or non-integer eta^2, eps <= 0; HLU_ERR_OOM;
- * HLU_ERR_CUDA. */
+ * coordinate, a beta value that is not finite and positive, leaf < 2,
+ * eta <= 0 or non-integer eta^2, eps <= 0; HLU_ERR_OOM; HLU_ERR_CUDA. */
 int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps,
               int32_t rank_cap, void* stream, hlu_handle** out);
 

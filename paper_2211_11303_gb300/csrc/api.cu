@@ -838,6 +838,7 @@ int hlu_mesh_kuhn_cube(int32_t n, hlu_mesh* out) {
   out->xyz = xyz;
   out->tets = tets;
   out->lattice_n = n;
+  out->beta = nullptr;
   return HLU_OK;
 }
 
@@ -870,7 +871,8 @@ void hlu_destroy(hlu_handle* h) {
   h->kw.free_all();
   h->sb.reset();
   for (void* p : {(void*)h->mesh.dofmap, (void*)h->mesh.edges, (void*)h->mesh.pts, (void*)h->mesh.xyz,
-                  (void*)h->mesh.tets, (void*)h->mesh.ekeys, (void*)h->A.rowptr, (void*)h->A.col, (void*)h->A.val,
+                  (void*)h->mesh.tets, (void*)h->mesh.ekeys, (void*)h->mesh.beta, (void*)h->A.rowptr,
+                  (void*)h->A.col, (void*)h->A.val,
                   (void*)h->d_perm, (void*)h->d_iperm})
     if (p) dev_free(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -900,6 +902,11 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
       for (int64_t q = 0; q < 3 * (int64_t)mesh->nv; ++q)
         if (!std::isfinite(mesh->xyz[q])) return fail(HLU_ERR_ARG, "vertex coordinates must be finite");
     }
+    const int64_t n_tets = n > 0 ? (int64_t)6 * n * n * n : (int64_t)mesh->nt;
+    if (mesh->beta)
+      for (int64_t t = 0; t < n_tets; ++t)
+        if (!(std::isfinite(mesh->beta[t]) && mesh->beta[t] > 0))
+          return fail(HLU_ERR_ARG, "beta must be finite and positive on every tetrahedron");
     if (leaf < 2 || leaf > 64) return fail(HLU_ERR_ARG, "leaf must be in [2, 64]");
     if (!(eta > 0)) return fail(HLU_ERR_ARG, "eta must be > 0");
     double e2 = eta * eta;
@@ -931,6 +938,12 @@ int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, doub
     else
       e = build_mesh_general(mesh->nv, mesh->nt, mesh->xyz, mesh->tets, s, h->mesh);
     if (e != cudaSuccess) return bail(e, "mesh");
+    if (mesh->beta) {
+      if ((e = dev_malloc(&h->mesh.beta, sizeof(double) * n_tets)) != cudaSuccess) return bail(e, "beta");
+      if ((e = cudaMemcpyAsync(h->mesh.beta, mesh->beta, sizeof(double) * n_tets, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return bail(e, "beta");
+    }
     if ((e = assemble_csr(h->mesh, kappa, s, h->A)) != cudaSuccess) return bail(e, "assembly");
     const int64_t N = h->A.N;
     if ((e = dev_malloc(&h->d_perm, sizeof(int32_t) * N)) != cudaSuccess) return bail(e, "perm");

@@ -175,9 +175,11 @@ struct MeshView {
   const int32_t* tets;
   const int64_t* ekeys;
   int64_t N;
+  const double* beta;  // material coefficient per tetrahedron (null: 1)
 };
 static MeshView view_of(const DevMesh& m) {
-  return MeshView{m.n, m.n > 0 ? (int64_t)6 * m.n * m.n * m.n : m.nt, m.nv, m.dofmap, m.xyz, m.tets, m.ekeys, m.N};
+  return MeshView{m.n, m.n > 0 ? (int64_t)6 * m.n * m.n * m.n : m.nt, m.nv, m.dofmap, m.xyz, m.tets, m.ekeys, m.N,
+                  m.beta};
 }
 
 // General tetrahedron t: coordinates from xyz, barycentric gradients as in
@@ -247,12 +249,14 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
 }
 
 // one thread per tetrahedron: 36 (key, value) pairs, key = row * N + col or
-// INT64_MAX for pairs that touch a boundary edge
+// INT64_MAX for pairs that touch a boundary edge; the curl-curl part is
+// divided by the element's material coefficient
 __global__ void k_element_coo(MeshView mv, double kappa2, int64_t N, int64_t* keys, double* vals) {
   const int64_t nt = mv.nt;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
     TetGeo g;
     tet_geometry(t, mv, g);
+    const double ib = mv.beta ? 1.0 / mv.beta[t] : 1.0;
     for (int r = 0; r < 6; ++r) {
       int a = g.lo[r], b = g.hi[r];
       double ca[3];
@@ -261,7 +265,7 @@ __global__ void k_element_coo(MeshView mv, double kappa2, int64_t N, int64_t* ke
         int cc = g.lo[s], d = g.hi[s];
         double cb[3];
         cross3(g.G[cc], g.G[d], cb);
-        double K = 4.0 * g.vol * dot3(ca, cb);
+        double K = ib * (4.0 * g.vol * dot3(ca, cb));
         auto mom = [&](int i, int j) { return g.vol * (i == j ? 2.0 : 1.0) / 20.0; };
         double M = mom(a, cc) * dot3(g.G[b], g.G[d]) - mom(a, d) * dot3(g.G[b], g.G[cc]) -
                    mom(b, cc) * dot3(g.G[a], g.G[d]) + mom(b, d) * dot3(g.G[a], g.G[cc]);

@@ -22,6 +22,7 @@ struct DevMesh {
   double* xyz = nullptr;      // general: nv x 3 coordinates
   int32_t* tets = nullptr;    // general: nt x 4 vertex ids
   int64_t* ekeys = nullptr;   // general: N interior-edge keys lo * nv + hi, ascending (DOF order)
+  double* beta = nullptr;     // material coefficient per tetrahedron (null: 1)
 };
 struct DevCSR {
   int64_t N = 0, nnz = 0;

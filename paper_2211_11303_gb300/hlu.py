@@ -32,7 +32,7 @@ class HluError(RuntimeError):
 
 class hlu_mesh(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("xyz", ctypes.c_void_p),
-                ("tets", ctypes.c_void_p), ("lattice_n", ctypes.c_int32)]
+                ("tets", ctypes.c_void_p), ("lattice_n", ctypes.c_int32), ("beta", ctypes.c_void_p)]
 
 
 class hlu_stats(ctypes.Structure):
@@ -247,9 +247,11 @@ def _vec(t, N):
 
 
 # ---------------------------------------------------------------- C-ABI names
-def lattice_mesh(n):
-    """hlu_mesh of the Kuhn cube with n^3 sub-cubes (the lattice path)."""
-    return hlu_mesh(0, 0, None, None, int(n))
+def lattice_mesh(n, beta=None):
+    """hlu_mesh of the Kuhn cube with n^3 sub-cubes (the lattice path); beta:
+    optional float64 array of 6 n^3 material coefficients (kept alive by the
+    caller while the struct is used)."""
+    return hlu_mesh(0, 0, None, None, int(n), None if beta is None else beta.ctypes.data)
 
 
 def hlu_mesh_kuhn_cube(n):
@@ -265,23 +267,39 @@ def hlu_mesh_kuhn_cube(n):
     return xyz, tets
 
 
-def hlu_build_mesh(xyz, tets, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
+def _beta_array(beta, nt):
+    import numpy as np
+    if beta is None:
+        return None
+    b = np.ascontiguousarray(beta, dtype=np.float64).reshape(-1)
+    if b.shape[0] != nt:
+        raise ValueError("beta needs one value per tetrahedron (%d)" % nt)
+    return b
+
+
+def hlu_build_mesh(xyz, tets, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None, beta=None):
     """Algorithm 1 step I for a general tetrahedral mesh: xyz (nv, 3) float64
-    coordinates, tets (nt, 4) vertex ids (host arrays)."""
+    coordinates, tets (nt, 4) vertex ids (host arrays); beta: optional
+    material coefficient per tetrahedron."""
     import numpy as np
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
-    m = hlu_mesh(xyz.shape[0], tets.shape[0], xyz.ctypes.data, tets.ctypes.data, 0)
+    b = _beta_array(beta, tets.shape[0])
+    m = hlu_mesh(xyz.shape[0], tets.shape[0], xyz.ctypes.data, tets.ctypes.data, 0,
+                 None if b is None else b.ctypes.data)
     h = _vp()
     _check(lib().hlu_build(ctypes.byref(m), float(kappa), int(leaf), float(eta), float(eps), int(rank_cap),
                            _stream(stream), ctypes.byref(h)))
     return h.value
 
 
-def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None):
-    """Algorithm 1 step I on the GPU for the Kuhn n-cube; returns an opaque handle (int)."""
+def hlu_build(n, kappa, leaf=32, eta=2.0, eps=1e-4, rank_cap=0, stream=None, beta=None):
+    """Algorithm 1 step I on the GPU for the Kuhn n-cube; returns an opaque
+    handle (int).  beta: optional material coefficient per tetrahedron, in
+    the order of hlu_mesh_kuhn_cube."""
     h = _vp()
-    m = lattice_mesh(n)
+    b = _beta_array(beta, 6 * int(n) ** 3)
+    m = lattice_mesh(n, b)
     _check(lib().hlu_build(ctypes.byref(m), float(kappa), int(leaf), float(eta), float(eps),
                            int(rank_cap), _stream(stream), ctypes.byref(h)))
     return h.value

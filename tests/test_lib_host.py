@@ -163,3 +163,26 @@ def test_general_mesh_arguments_are_checked(lib):
     bad[4, 2] = np.nan
     assert build(bad, good) == 1                           # non-finite coordinate
     assert build(xyz[:3], np.array([[0, 1, 2, 0]])) == 1   # fewer than 4 vertices
+    # a material coefficient must be finite and positive on every tetrahedron
+    for bad_beta in ([1.0, 0.0], [1.0, -2.0], [np.nan, 1.0]):
+        bb = np.ascontiguousarray(bad_beta, dtype=np.float64)
+        x = np.ascontiguousarray(xyz)
+        m = hlu.hlu_mesh(x.shape[0], good.shape[0], x.ctypes.data, good.ctypes.data, 0, bb.ctypes.data)
+        assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 2.0, 1e-4, 0, None, ctypes.byref(h)) == 1
+    bl = np.full(6 * 2 ** 3, 1.0)
+    bl[5] = np.inf
+    m = hlu.lattice_mesh(2, bl)
+    assert lib.hlu_build(ctypes.byref(m), 1.0, 32, 2.0, 1e-4, 0, None, ctypes.byref(h)) == 1
+
+
+def test_example3_magnet_matches_oracle(lib):
+    """The Example 3 driver's magnet coefficient (from the library's Kuhn
+    cube export) equals the oracle's (from its own mesh), tetrahedron by
+    tetrahedron, at a size where the box faces are lattice planes and one
+    where they are not."""
+    from oracle import fem, mesh
+    from paper_2211_11303_gb300 import example3
+    for n in (8, 6):
+        b = example3.magnet_beta(n)
+        bo = fem.magnet_beta(mesh.interior_edges(n), 10.0)
+        assert np.array_equal(b, bo)

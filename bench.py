@@ -53,15 +53,17 @@ def _blob_sha1(path):
     return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
 
 
-def _factor_traffic(n, eps, precision):
-    """DRAM bytes per factorisation launch recorded from an ncu capture in
+def _factor_traffic(n, eps, precision, key="exec_kernel_factor", nrhs=None):
+    """DRAM bytes per factorisation (key exec_kernel_factor) or preconditioner
+    apply (exec_kernel_apply) launch recorded from an ncu capture in
     profiles/traffic.json, or None when that record is of another workload or
     the executor source changed since it was taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)["exec_kernel_factor"]
+            rec = json.load(f)[key]
         same_src = rec["exec_cu_blob"] == _blob_sha1(os.path.join(ROOT, "paper_2211_11303_gb300", "csrc", "exec.cu"))
-        same_work = int(rec["n"]) == n and float(rec["eps"]) == eps and rec["precision"] == precision
+        same_work = int(rec["n"]) == n and float(rec["eps"]) == eps and rec["precision"] == precision and (
+            nrhs is None or int(rec.get("nrhs", -1)) == nrhs)
         return int(rec["dram_bytes_per_launch"]) if same_src and same_work else None
     except (OSError, KeyError, ValueError):
         return None
@@ -538,7 +540,8 @@ def run_gpu(args):
                      "solve": {"bound": "hbm", "achieved": live_bytes / (apply_ms / 1000.0) / 1e9,
                                "peak": hbm_gbs, "unit": "GB/s",
                                "frac": live_bytes / (apply_ms / 1000.0) / 1e9 / hbm_gbs,
-                               "traffic": None, "bytes_per_apply": live_bytes,
+                               "traffic": _factor_traffic(n, args.eps, args.precision, "exec_kernel_apply", args.nrhs),
+                               "bytes_per_apply": live_bytes,
                                "kernel": "exec_kernel<float> (H-LU task executor), one triangular-solve "
                                          "launch (L then U) per preconditioner apply",
                                "peak_source": "%s hbm_gbs" % src,

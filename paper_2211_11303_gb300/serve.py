@@ -79,6 +79,23 @@ class Server:
             self.stats["evictions"] += 1
         return self.used + need <= self.budget
 
+    def _room_for(self, need):
+        """True once the device itself can hold `need` more bytes (beyond the
+        reserve), evicting idle cached factors, least recently used first:
+        schedules and handles live outside the budget, so the budget alone
+        can admit what the device cannot hold."""
+        while _device_room() <= need + self.reserve:
+            idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
+            if not idle:
+                return False
+            f = idle[0]
+            H.hlu_destroy(f.h)
+            self.used -= f.nbytes
+            del self.factors[f.key]
+            self.stats["evictions"] += 1
+            torch.cuda.empty_cache()
+        return True
+
     def _lookup(self, req, may_build=True):
         """(cached factor or None, built-but-unfactored handle or None, bytes);
         (None, None, 0) when the request needs a handle that may not be built
@@ -153,12 +170,12 @@ class Server:
                 if f is not None:
                     f.users += 1  # not evictable while deciding
                 ok = self._evict_for(fbytes + kb)
-                if f is not None:
-                    f.users -= 1
                 # the device itself must have the room as well (schedules and
                 # handles are outside the budget); blocks PyTorch's caching
                 # allocator holds unused count as free
-                ok = ok and _device_room() > fbytes + kb + self.reserve
+                ok = ok and self._room_for(fbytes + kb)
+                if f is not None:
+                    f.users -= 1
                 if not ok:
                     if not active and self.inflight is None and not self.factors:
                         raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))

@@ -109,7 +109,27 @@ class Server:
         if "_h" not in req:
             if not may_build:
                 return None, None, 0
-            h = H.hlu_build(req["n"], req["kappa"], self.leaf, self.eta, self.eps)
+            h = None
+            while h is None:
+                try:
+                    h = H.hlu_build(req["n"], req["kappa"], self.leaf, self.eta, self.eps)
+                except H.HluError as e:
+                    # the mesh's schedule or matrix did not fit: free an idle
+                    # cached factor and build again, or wait for running
+                    # requests to release memory
+                    if e.status != "HLU_ERR_OOM":
+                        raise
+                    if not self.factors and self.inflight is None:
+                        raise  # nothing held that could be released
+                    idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
+                    if not idle:
+                        return None, None, 0
+                    H.hlu_destroy(idle[0].h)
+                    self.used -= idle[0].nbytes
+                    del self.factors[idle[0].key]
+                    self.stats["evictions"] += 1
+                    self.stats["oom_retries"] += 1
+                    torch.cuda.empty_cache()
             req["_h"] = (key, h, int(H.hlu_factor_bytes_estimate(h, self.precision)))
         return None, req["_h"], req["_h"][2]
 

@@ -325,7 +325,10 @@ int hlu_set_trunc_params(int32_t compress_at, double jacobi_tol);
  * columns per launch).  States may join or leave between steps; a state's
  * result does not depend on which states it was batched with.
  * hlu_gmres_begin: x = 0, column norms of b; synchronous.  b, x stay owned by
- * the caller and must stay valid until hlu_gmres_end.
+ * the caller and must stay valid until hlu_gmres_end.  Its workspace is
+ * 2 (restart + 1) N nrhs + O(N nrhs) doubles of device memory; when it cannot
+ * be had (HLU_ERR_OOM) or any later step fails, nothing stays allocated and
+ * *out is not written, so the call may be retried once memory is freed.
  * hlu_gmres_status: *done = 1 once finished; stats as in gmres_solve; returns
  * HLU_ERR_NOT_CONVERGED for a finished state that missed tol.
  * All calls on one stream; step_batch is synchronous. */

@@ -648,9 +648,9 @@ int ensure_kw(hlu_handle* h, int m, int nr) {
   if (k.N == h->A.N && k.m >= m && k.nr >= nr) return HLU_OK;
   k.free_all();
   int64_t N = h->A.N;
-  k.N = N;
-  k.m = m;
-  k.nr = nr;
+  // the sizes are recorded only once every buffer exists: a workspace left
+  // partial by an allocation failure is freed and rebuilt by the next call
+  // instead of passing the size test above with null buffers
   CKR(dev_malloc(&k.V, sizeof(double) * N * (m + 1) * nr), "alloc V");
   CKR(dev_malloc(&k.Z, sizeof(double) * N * (m + 1) * nr), "alloc Z");
   CKR(dev_malloc(&k.W, sizeof(double) * N * nr), "alloc W");
@@ -667,6 +667,9 @@ int ensure_kw(hlu_handle* h, int m, int nr) {
   CKR(dev_malloc(&k.bn, sizeof(double) * nr), "alloc");
   CKR(dev_malloc(&k.part, sizeof(double) * std::max(multidot_partials(N, m + 1, nr), 1)), "alloc");
   CKR(dev_malloc(&k.jr, sizeof(int) * nr), "alloc");
+  k.N = N;
+  k.m = m;
+  k.nr = nr;
   return HLU_OK;
 }
 
@@ -2155,21 +2158,30 @@ int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nr
     g->m = restart;
     g->tol = tol;
     g->maxit = maxit;
-    int rc = alloc_ws(g->k, h->A.N, restart, nrhs);
+    // every failure below frees the state and its workspace: the caller
+    // gets no handle to end
+    auto start = [&]() -> int {
+      int rc = alloc_ws(g->k, h->A.N, restart, nrhs);
+      if (rc) return rc;
+      g->bn.assign(nrhs, 0);
+      g->beta.assign(nrhs, 0);
+      g->est.assign(nrhs, 0);
+      g->conv.assign(nrhs, 0);
+      g->jr.assign(nrhs, 0);
+      for (int r = 0; r < nrhs; ++r) CKR(cudaMemsetAsync(x + r * ld, 0, sizeof(double) * h->A.N, s), "x0");
+      rc = norms_ws(g->k, b, ld, nrhs, g->k.bn, s);
+      if (rc) return rc;
+      CKR(cudaMemcpyAsync(g->bn.data(), g->k.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s), "d2h");
+      CKR(cudaStreamSynchronize(s), "sync");
+      return HLU_OK;
+    };
+    int rc = start();
     if (rc) {
+      cudaStreamSynchronize(s);  // the memset / norm work queued so far
+      g->k.free_all();
       delete g;
       return rc;
     }
-    g->bn.assign(nrhs, 0);
-    g->beta.assign(nrhs, 0);
-    g->est.assign(nrhs, 0);
-    g->conv.assign(nrhs, 0);
-    g->jr.assign(nrhs, 0);
-    for (int r = 0; r < nrhs; ++r) CKR(cudaMemsetAsync(x + r * ld, 0, sizeof(double) * h->A.N, s), "x0");
-    rc = norms_ws(g->k, b, ld, nrhs, g->k.bn, s);
-    if (rc) return rc;
-    CKR(cudaMemcpyAsync(g->bn.data(), g->k.bn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s), "d2h");
-    CKR(cudaStreamSynchronize(s), "sync");
     *out = g;
     return HLU_OK;
   } catch (const std::exception& ex) {

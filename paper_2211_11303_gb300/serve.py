@@ -64,6 +64,7 @@ class Server:
         self.side = torch.cuda.Stream() if self.overlap else None
         self.factor_ctas = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.inflight = None  # (entry of the request waiting for its factor, factor)
+        self._active = []  # the running requests of run()
         self.stats = {"factorisations": 0, "cache_hits": 0, "evictions": 0, "steps": 0, "max_active": 0,
                       "steps_during_factor": 0, "oom_retries": 0}
 
@@ -79,21 +80,33 @@ class Server:
             self.stats["evictions"] += 1
         return self.used + need <= self.budget
 
+    def _evict_one(self):
+        """Free the least recently used cached factor no running request
+        uses; False when there is none."""
+        idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
+        if not idle:
+            return False
+        f = idle[0]
+        H.hlu_destroy(f.h)
+        self.used -= f.nbytes
+        del self.factors[f.key]
+        self.stats["evictions"] += 1
+        torch.cuda.empty_cache()
+        return True
+
+    def _stuck(self, f=None):
+        """Nothing runs or is being factored, and no cached factor but f
+        exists: no memory will be released by waiting."""
+        return not self._active and self.inflight is None and all(g is f for g in self.factors.values())
+
     def _room_for(self, need):
         """True once the device itself can hold `need` more bytes (beyond the
         reserve), evicting idle cached factors, least recently used first:
         schedules and handles live outside the budget, so the budget alone
         can admit what the device cannot hold."""
         while _device_room() <= need + self.reserve:
-            idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
-            if not idle:
+            if not self._evict_one():
                 return False
-            f = idle[0]
-            H.hlu_destroy(f.h)
-            self.used -= f.nbytes
-            del self.factors[f.key]
-            self.stats["evictions"] += 1
-            torch.cuda.empty_cache()
         return True
 
     def _lookup(self, req, may_build=True):
@@ -119,17 +132,12 @@ class Server:
                     # requests to release memory
                     if e.status != "HLU_ERR_OOM":
                         raise
-                    if not self.factors and self.inflight is None:
-                        raise  # nothing held that could be released
-                    idle = sorted((f for f in self.factors.values() if f.users == 0), key=lambda f: f.last_use)
-                    if not idle:
-                        return None, None, 0
-                    H.hlu_destroy(idle[0].h)
-                    self.used -= idle[0].nbytes
-                    del self.factors[idle[0].key]
-                    self.stats["evictions"] += 1
                     self.stats["oom_retries"] += 1
-                    torch.cuda.empty_cache()
+                    if self._evict_one():
+                        continue
+                    if self._stuck():
+                        raise  # nothing held that could be released
+                    return None, None, 0
             req["_h"] = (key, h, int(H.hlu_factor_bytes_estimate(h, self.precision)))
         return None, req["_h"], req["_h"][2]
 
@@ -141,13 +149,43 @@ class Server:
         for n in sorted(set(int(x) for x in ns)):
             H.hlu_destroy(H.hlu_build(n, kappa, self.leaf, self.eta, self.eps))
 
-    def _start(self, req, f, N, kb, active):
-        b = self._rhs_of(req, N)
-        bd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
+    @staticmethod
+    def _columns(b):
+        """Device right-hand sides (copied from the host array b, N x nrhs)
+        and solution columns, each column contiguous."""
+        N, nr = b.shape
+        bd = torch.empty((nr, N), dtype=torch.float64, device="cuda").t()
         bd.copy_(torch.from_numpy(np.ascontiguousarray(b)).pin_memory(), non_blocking=True)
-        xd = torch.empty((req["nrhs"], N), dtype=torch.float64, device="cuda").t()
-        g = H.hlu_gmres_begin(f.h, bd, xd, restart=self.restart, tol=self.tol, maxit=self.maxit)
+        xd = torch.empty((nr, N), dtype=torch.float64, device="cuda").t()
+        return bd, xd
+
+    def _start(self, req, f, N, kb, active):
+        """Start the request's GMRES on factor f (admitted: f.users and kb
+        already counted).  When the device cannot hold its columns or Krylov
+        workspace, idle cached factors are freed, least recently used first,
+        and the start retried; with none left the admission is undone and
+        False returned, so the request waits for running ones to finish."""
+        b = np.asarray(self._rhs_of(req, N), dtype=np.float64).reshape(N, -1)
+        while True:
+            try:
+                bd, xd = self._columns(b)
+                g = H.hlu_gmres_begin(f.h, bd, xd, restart=self.restart, tol=self.tol, maxit=self.maxit)
+                break
+            except (H.HluError, torch.cuda.OutOfMemoryError) as e:
+                if isinstance(e, H.HluError) and e.status != "HLU_ERR_OOM":
+                    raise
+                bd = xd = None
+                self.stats["oom_retries"] += 1
+                if self._evict_one():
+                    continue
+                torch.cuda.empty_cache()
+                f.users -= 1
+                self.used -= kb
+                if self._stuck(f):
+                    raise  # nothing runs that could release memory
+                return False
         active.append({"req": req, "f": f, "g": g, "b": bd, "x": xd, "kb": kb})
+        return True
 
     # -- main loop --------------------------------------------------------------
     def run(self, requests, rhs_of):
@@ -157,6 +195,7 @@ class Server:
         pending = sorted(requests, key=lambda r: (r["t"], r["id"]))
         self._rhs_of = rhs_of
         waiting, active, results = [], [], {}
+        self._active = active
         t0 = time.perf_counter()
         pi = 0
         while pi < len(pending) or waiting or active or self.inflight is not None:
@@ -197,8 +236,9 @@ class Server:
                 if f is not None:
                     f.users -= 1
                 if not ok:
-                    if not active and self.inflight is None and not self.factors:
-                        raise RuntimeError("request %s needs %d bytes, above the HBM budget" % (req["id"], fbytes + kb))
+                    if self._stuck(f):
+                        raise RuntimeError("request %s needs %d bytes, more than the HBM budget or the device holds"
+                                           % (req["id"], fbytes + kb))
                     if built is not None:  # do not hold an unadmitted handle's memory
                         H.hlu_destroy(req.pop("_h")[1])
                     still.append(req)
@@ -229,7 +269,7 @@ class Server:
                         self.stats["oom_retries"] += 1
                         H.hlu_destroy(h)
                         torch.cuda.empty_cache()
-                        if not active and self.inflight is None and not self.factors:
+                        if self._stuck():
                             raise
                         still.append(req)
                         continue
@@ -237,7 +277,8 @@ class Server:
                     self.stats["cache_hits"] += 1
                     f.users += 1
                     self.used += kb
-                self._start(req, f, N, kb, active)
+                if not self._start(req, f, N, kb, active):
+                    still.append(req)
             waiting = still
             if self.inflight is not None:
                 # the factor of a newly admitted request: start its GMRES once
@@ -245,7 +286,8 @@ class Server:
                 req, f, N, kb = self.inflight
                 if H.hlu_factor_wait(f.h, block=not active):
                     self.inflight = None
-                    self._start(req, f, N, kb, active)
+                    if not self._start(req, f, N, kb, active):
+                        waiting.append(req)  # its factor stays cached
             if not active:
                 if pi < len(pending) and self.inflight is None:
                     time.sleep(max(0.0, min(pending[pi]["t"] - (time.perf_counter() - t0), 0.05)))
@@ -265,13 +307,13 @@ class Server:
                 t_done = time.perf_counter() - t0
                 H.hlu_gmres_end(a["g"])
                 a["f"].users -= 1
-                a["f"].last_use = t_done
+                a["f"].last_use = time.perf_counter()  # absolute: the order holds across run() calls
                 self.used -= a["kb"]
                 req = a["req"]
                 results[req["id"]] = {"id": req["id"], "latency_s": t_done - req["t"], "iterations": st["iterations"],
                                       "relres": st["relres_max"], "converged": bool(st["converged"]), "x": x,
                                       "n": req["n"], "kappa": req["kappa"], "nrhs": req["nrhs"]}
-            active = keep
+            active[:] = keep  # the list _stuck reads
         self.stats["wall_s"] = time.perf_counter() - t0
         return [results[r["id"]] for r in requests]
 

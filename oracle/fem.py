@@ -26,7 +26,11 @@ Readings:
   * the material coefficient beta is constant on each tetrahedron and scales
     that element's curl-curl matrix by 1/beta; Example 3's magnet
     (0.5 x 0.5 x 0.75 in the unit box, beta = 10, air beta = 1) is read as
-    centred in the box (magnet_beta).
+    centred in the box (magnet_beta);
+  * with conductivity chi > 0 the paper's kappa = omega^2 (alpha + i chi/omega)
+    is complex and enters as given, A = K_beta - kappa M
+    (assemble_time_harmonic): the test functions are not conjugated, so A is
+    complex symmetric, A^T = A.
 
 Pins (tests/test_oracle_fem.py): discrete de Rham property C G = 0 and K G = 0;
 null space of K of dimension (n-1)^3; cavity eigenvalues 2pi^2 (x3), 3pi^2 (x2);
@@ -37,6 +41,12 @@ vector is discretely divergence-free (G^T b = 0) and equals the exact integral
 coefficient, K_beta G = 0 still holds (only the curl-curl part carries beta),
 a constant beta = c gives K / c (cavity eigenvalues divided by c), and the
 magnet holds 0.1875 of the cube's volume (576 of the 3,072 tetrahedra at n = 8).
+The complex assembly reduces to the real one at chi = 0, is symmetric and not
+Hermitian, and its solutions obey the energy identities
+x^H b = x^H K x - omega^2 alpha x^H M x - i omega chi x^H M x (both forms
+real); at a discrete cavity resonance (K v = lambda M v, omega^2 alpha =
+lambda) A v = -i omega chi M v exactly, so the conductivity alone keeps A
+nonsingular there.
 """
 import math
 
@@ -161,6 +171,25 @@ def assemble(mesh, kappa, parts=False, beta=None):
         return K, M
     A = K.copy()
     A.data = K.data - kappa * kappa * M.data
+    return A
+
+
+def time_harmonic_kappa(omega, alpha, chi):
+    """The paper's mass coefficient kappa = omega^2 zeta with
+    zeta = alpha + i chi / omega (Sec. 2): alpha the dielectric permeability,
+    chi the conductivity, omega the angular frequency."""
+    return omega * omega * (alpha + 1j * chi / omega)
+
+
+def assemble_time_harmonic(mesh, omega, alpha, chi, beta=None):
+    """CSR matrix A = K_beta - kappa M with the complex kappa of
+    time_harmonic_kappa (the operator curl(beta^-1 curl E) - kappa E of Sec. 2
+    with conductivity): complex symmetric, not Hermitian, on the pattern of
+    assemble.  chi = 0, alpha = 1 is assemble(mesh, omega)."""
+    K, M = assemble(mesh, 0.0, parts=True, beta=beta)
+    kap = time_harmonic_kappa(omega, alpha, chi)
+    A = K.astype(np.complex128)
+    A.data = K.data - kap * M.data
     return A
 
 

@@ -14,13 +14,18 @@ Sec. 2.9); this module evaluates it by that recursion:
 
 Readings (the paper is silent on these):
   * no global pivoting; a dense diagonal leaf is factored with partial
-    pivoting inside the leaf (first index of max |a|), P L U = A_leaf, L unit
-    lower, U upper.  Off-diagonal L blocks are kept unpermuted and the leaf
-    permutation is applied when the solve reaches that leaf, which is the
-    same as P A = L U with P block diagonal over the leaf clusters;
+    pivoting inside the leaf (first index of max |a|; of max |Re a| + |Im a|
+    for a complex leaf), P L U = A_leaf, L unit lower, U upper.  Off-diagonal
+    L blocks are kept unpermuted and the leaf permutation is applied when the
+    solve reaches that leaf, which is the same as P A = L U with P block
+    diagonal over the leaf clusters;
   * truncation of X Y^T: QR of X and of Y, SVD of R_x R_y^T = U S V^T, keep the
     singular values s_i > eps s_1 (relative, strict), X <- Q_x U_r S_r,
     Y <- Q_y V_r; a zero block truncates to rank 0;
+  * complex blocks (Definition 1's X Y^H) are stored as X Y^T with complex X,
+    Y (Y^T = the paper's Y^H, conjugated); every step above then holds with
+    transposes, not conjugate transposes, and a complex matrix runs the same
+    code in complex arithmetic;
   * A_H is exact: a dense leaf holds the CSR entries, an admissible block holds
     X = the unit columns of its nonzero rows and Y^T = those rows;
   * a product of two subdivided blocks into a low-rank target is formed son by
@@ -31,6 +36,8 @@ Pins (tests/test_oracle_hmatrix.py): truncation returns the exact rank and an
 error <= eps s_1 for matrices with prescribed singular values; A_H equals A
 entrywise; eps -> 1e-14 reproduces the dense LU solve; ||I - (LU)_H^-1 A||_2
 falls as eps shrinks; the leaf getrf equals scipy's partial-pivoting LU.
+Complex (tests/test_oracle_complex.py): the same four on complex input, the
+leaf getrf equal to LAPACK's complex LU.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -43,27 +50,35 @@ class ZeroPivot(ArithmeticError):
 
 
 def truncate(X, Y, eps):
-    """Best rank-r approximation of X Y^T with s_i > eps s_1 (Sec. 4 truncated SVD)."""
+    """Best rank-r approximation of X Y^T with s_i > eps s_1 (Sec. 4 truncated SVD).
+    Complex factors (Definition 1) take the same steps: with R_x R_y^T =
+    U S V^H, X Y^T = (Q_x U S)(Q_y conj(V))^T, and conj(V) = (V^H)^T is the
+    transpose of the SVD's third factor, as for real input."""
     m, n = X.shape[0], Y.shape[0]
+    dt = np.result_type(X, Y, np.float64)
     if X.shape[1] == 0 or m == 0 or n == 0:
-        return np.zeros((m, 0)), np.zeros((n, 0))
+        return np.zeros((m, 0), dt), np.zeros((n, 0), dt)
     Qx, Rx = np.linalg.qr(X)
     Qy, Ry = np.linalg.qr(Y)
     U, s, Vt = np.linalg.svd(Rx @ Ry.T)
     if s[0] == 0.0:
-        return np.zeros((m, 0)), np.zeros((n, 0))
+        return np.zeros((m, 0), dt), np.zeros((n, 0), dt)
     r = int(np.sum(s > eps * s[0]))
     return Qx @ (U[:, :r] * s[:r]), Qy @ Vt[:r].T
 
 
 def getrf(A):
     """LU with partial pivoting inside a dense leaf.  Returns (LU packed, p) with
-    A[p] = L U (p[i] = original row at position i)."""
-    A = np.array(A, dtype=np.float64, copy=True)
+    A[p] = L U (p[i] = original row at position i).  The pivot is the first
+    entry of largest |a| in the column; for a complex leaf, of largest
+    |Re a| + |Im a|, LAPACK's measure for complex pivots."""
+    A = np.array(A, dtype=np.result_type(A, np.float64), copy=True)
+    cplx = np.iscomplexobj(A)
     n = A.shape[0]
     p = np.arange(n)
     for k in range(n):
-        q = k + int(np.argmax(np.abs(A[k:, k])))
+        col = A[k:, k]
+        q = k + int(np.argmax(np.abs(col.real) + np.abs(col.imag) if cplx else np.abs(col)))
         if A[q, k] == 0.0:
             raise ZeroPivot(k)
         if q != k:
@@ -85,6 +100,7 @@ class HMatrix:
         self.X = {}
         self.Y = {}
         self.piv = {}
+        self.dtype = np.dtype(np.float64)  # complex128 for a complex matrix
 
     # ---- shape helpers -------------------------------------------------
     def rows(self, b):
@@ -112,6 +128,7 @@ class HMatrix:
     # ---- A_H (Alg. 1 step I) --------------------------------------------
     def fill(self, Ap):
         """Ap: CSR matrix already permuted to cluster order."""
+        self.dtype = np.result_type(Ap.dtype, np.float64)
         for b, blk in enumerate(self.bl):
             if blk["kind"] == SUB:
                 continue
@@ -129,7 +146,7 @@ class HMatrix:
 
     def to_dense(self, b=0):
         r, c = self.rows(b), self.cols(b)
-        out = np.zeros((r["size"], c["size"]))
+        out = np.zeros((r["size"], c["size"]), self.dtype)
         k = self.kind(b)
         if k == DENSE:
             out[:] = self.D[b]
@@ -151,7 +168,7 @@ class HMatrix:
         if k == ADM:
             return self.X[b] @ (self.Y[b].T @ V)
         r, c = self.rows(b), self.cols(b)
-        out = np.zeros((r["size"], V.shape[1]))
+        out = np.zeros((r["size"], V.shape[1]), np.result_type(self.dtype, V))
         for s in self.bl[b]["sons"]:
             rs, cs = self.rows(s), self.cols(s)
             i0, j0 = rs["offset"] - r["offset"], cs["offset"] - c["offset"]
@@ -166,7 +183,7 @@ class HMatrix:
         if k == ADM:
             return self.Y[b] @ (self.X[b].T @ V)
         r, c = self.rows(b), self.cols(b)
-        out = np.zeros((c["size"], V.shape[1]))
+        out = np.zeros((c["size"], V.shape[1]), np.result_type(self.dtype, V))
         for s in self.bl[b]["sons"]:
             rs, cs = self.rows(s), self.cols(s)
             i0, j0 = rs["offset"] - r["offset"], cs["offset"] - c["offset"]
@@ -259,8 +276,8 @@ class HMatrix:
                     px.append(x)
                     py.append(y)
                 x, y = truncate(np.hstack(px), np.hstack(py), self.eps)
-                X = np.zeros((m, x.shape[1]))
-                Y = np.zeros((n, x.shape[1]))
+                X = np.zeros((m, x.shape[1]), x.dtype)
+                Y = np.zeros((n, x.shape[1]), y.dtype)
                 if i == 0:
                     X[:m0] = x
                 else:

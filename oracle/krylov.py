@@ -26,7 +26,10 @@ import numpy as np
 
 def fgmres(matvec, b, precond=None, restart=50, tol=1e-8, maxit=1000):
     """Returns (x, info) with info = dict(iters, restarts, converged, relres,
-    history).  matvec(v) -> A v; precond(v) -> M^-1 v (identity if None)."""
+    history).  matvec(v) -> A v; precond(v) -> M^-1 v (identity if None).
+    Real systems only (its inner products and rotations are the real ones)."""
+    if np.iscomplexobj(b):
+        raise TypeError("fgmres takes a real right-hand side; a complex system goes to richardson")
     b = np.asarray(b, dtype=np.float64)
     N = b.shape[0]
     x = np.zeros(N)
@@ -98,8 +101,9 @@ def fgmres(matvec, b, precond=None, restart=50, tol=1e-8, maxit=1000):
 
 def richardson(matvec, b, precond, tol=1e-8, maxit=100):
     """Algorithm 1 step III: r = b - A x, err = ||r||/||b||, x <- x + M^-1 r,
-    break when err < tol; then step IV error = ||A x - b||_2."""
-    b = np.asarray(b, dtype=np.float64)
+    break when err < tol; then step IV error = ||A x - b||_2.  Real or
+    complex (the complex kappa of Sec. 2): only sums, products and 2-norms."""
+    b = np.asarray(b, dtype=np.result_type(b, np.float64))
     x = np.zeros_like(b)
     bnorm = np.linalg.norm(b)
     errs = []

@@ -1,0 +1,89 @@
+"""GPU parity at the benchmark's full size, in the launch configuration that
+bench.py times: the Kuhn cube with n = 24 (N = 91,656 interior edges),
+kappa 8, leaf 32, eta 2, eps 1e-4, the stored granularity tuning for that
+workload, 8 seeded N(0, 1) right-hand sides, FGMRES(50) to 1e-10.
+
+Against the oracle: the cluster and block trees bit-exact, the CSR matrix
+element by element, and every solution column, for the FP32 factor and for
+the plain FP64 path, within 1e-7 of the stored direct solve of the oracle's
+matrix (tests/golden/xref_n24_kappa8.npy, written by tests/golden/make_xref.py
+from oracle/ alone), with no truncation at the rank capacity.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, mesh, trees
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+N_CUBE, KAPPA, LEAF, ETA, EPS, NRHS = 24, 8.0, 32, 2.0, 1e-4, 8
+
+
+@pytest.fixture(scope="module")
+def hlu():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2211_11303_gb300 import hlu as H
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    H.hlu_set_wait_limit_ms(60000)
+    return H
+
+
+@pytest.fixture(scope="module")
+def oracle_n24():
+    m = mesh.interior_edges(N_CUBE)
+    A = fem.assemble(m, KAPPA).tocsr()
+    perm, cl, bl = trees.build_trees(m, LEAF, ETA)
+    return m, A, perm, cl, bl
+
+
+def test_full_size_trees_and_matrix(hlu, oracle_n24):
+    m, A, perm, cl, bl = oracle_n24
+    p, C, B = trees.export_arrays(perm, cl, bl)
+    h = hlu.hlu_build(N_CUBE, KAPPA, LEAF, ETA, EPS)
+    try:
+        assert hlu.hlu_n(h) == A.shape[0] == 91656
+        gp, gC, gB = hlu.hlu_export_trees(h)
+        assert np.array_equal(gp, p)
+        assert np.array_equal(gC, C)
+        assert np.array_equal(gB, B)
+        rp, ci, va = hlu.hlu_export_csr(h)
+        assert np.array_equal(rp, A.indptr.astype(np.int64))
+        assert np.array_equal(ci, A.indices.astype(np.int32))
+        assert np.abs(va - A.data).max() <= 1e-13 * np.abs(A.data).max()
+    finally:
+        hlu.hlu_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_solve_matches_the_direct_solve(hlu, prec):
+    from paper_2211_11303_gb300 import autotune
+    ref = np.load(os.path.join(HERE, "golden", "xref_n24_kappa8.npy"))
+    N = ref.shape[0]
+    Bh = np.stack([synth.normal(synth.rhs_seed(2, 0, j), N) for j in range(NRHS)])
+    best = autotune.load(os.path.join(HERE, "..", "paper_2211_11303_gb300", "tuned.json"), N_CUBE, KAPPA, EPS,
+                         "fp32")
+    autotune.apply(best)
+    try:
+        h = hlu.hlu_build(N_CUBE, KAPPA, LEAF, ETA, EPS)
+        try:
+            hlu.hlu_factor(h, hlu.HLU_FP32 if prec == "fp32" else hlu.HLU_FP64)
+            info = hlu.hlu_factor_stats(h)
+            assert info["rank_cap_hits"] == 0
+            B = torch.from_numpy(Bh).cuda().t()
+            X = hlu.colmajor(N, NRHS)
+            st = hlu.gmres_solve(h, B, X, restart=50, tol=1e-10, maxit=500)
+            assert st["converged"] and st["iterations"] <= 40, st
+            Xg = X.t().cpu().numpy().T
+        finally:
+            hlu.hlu_destroy(h)
+    finally:
+        autotune.apply(None)
+    fwd = np.linalg.norm(Xg - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert fwd.max() <= 1e-7, fwd

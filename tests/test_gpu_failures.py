@@ -129,8 +129,8 @@ def test_refused_allocation_is_oom_and_recoverable(hlu):
 
 
 def test_library_memory_comes_from_torch(hlu):
-    """With the default binding the library's device memory is PyTorch's
-    caching allocator's (spec: PyTorch for device memory)."""
+    """With the default binding the library's device memory comes from
+    PyTorch's caching allocator (the allocator hook of the C ABI)."""
     torch.cuda.synchronize()
     before_t = torch.cuda.memory_allocated()
     before_l = hlu.hlu_device_bytes_in_use()

@@ -118,6 +118,33 @@ int hlu_debug_truncate(int32_t precision, int32_t m, int32_t n, int32_t w, int32
  * destroyed.  HLU_ERR_ARG for dof outside [0, N).  Synchronous. */
 int hlu_debug_zero_dof(hlu_handle* h, int64_t dof);
 
+/* hlu_debug_check_hazards - static race check of one task DAG (no GPU).
+ * Builds the schedules from the exported trees (clusters int32[nc*12],
+ * blocks int32[nb*8]; rank_cap 0 = 64, tile and nrhs_max (1..16) as the
+ * library uses them) and picks one DAG by `which`: 0 the H-LU factorisation
+ * (Algorithm 1 step II), 1 the triangular solve (step III), 2 / 3 / 4 the
+ * Schulz inverse's start, step and apply.  Every operand is expanded to the
+ * elements it may address at full capacity (factor arena, pivot vectors and
+ * rank slots are separate spaces), and the DAG is replayed in program order:
+ * each write after write, read after write or write after read on one
+ * element must be ordered by the DAG's edges, taken transitively.
+ * drop_edge: -1, or the index of one edge (in the DAG's predecessor list) to
+ * remove before the check, a planted mistake that tests the check itself.
+ * report (int64[11], required): tasks, element accesses, distinct conflicting
+ * task pairs checked, pairs the edges leave unordered, then for the first
+ * finding the earlier task (-1 for an out-of-range access), the later task,
+ * the space (0 arena, 1 pivots, 2 rank slots) and the element, then accesses
+ * outside their space, the DAG's edge count, and whether the dropped edge's
+ * two tasks are still ordered through other edges (1 / 0; -1 without a
+ * drop).
+ * Returns 0 when every conflict is ordered and every access is in range, 9
+ * when not (see report), 1 for a bad argument, 6 for an internal error or a
+ * DAG too large to check in host memory (more than 40,000 tasks or 2^27
+ * arena elements). */
+int hlu_debug_check_hazards(int32_t nc, const int32_t* clusters, int32_t nb, const int32_t* blocks,
+                            int32_t rank_cap, int32_t tile, int32_t nrhs_max, int32_t which, int64_t drop_edge,
+                            int64_t* report);
+
 /* hlu_debug_host_hinverse - the Schulz inverse's task DAGs (hlu_hinverse)
  * run by the host reference executor in FP64 (no GPU): A_H from the CSR
  * matrix (original order) and the exported trees, X_0 = alpha A_H, `iters`

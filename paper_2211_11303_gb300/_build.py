@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlu.so")
-SOURCES = ["exec.cu", "exec_tc.cu", "api.cu", "build.cu", "krylov.cu", "sched.cpp", "host_exec.cpp", "debug_api.cpp", "devmem.cpp"]
+SOURCES = ["exec.cu", "exec_tc.cu", "api.cu", "build.cu", "krylov.cu", "sched.cpp", "host_exec.cpp", "debug_api.cpp", "hazard.cpp", "devmem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -128,6 +128,7 @@ SIGNATURES = {
                                             ctypes.c_uint64, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
     "hlu_debug_factor_prefix": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "hlu_debug_task_record": (_i32, [_vp, _i64, _vp]),
+    "hlu_debug_check_hazards": (_i32, [_i32, _vp, _i32, _vp, _i32, _i32, _i32, _i32, _i64, _vp]),
     "hlu_debug_factor_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "hlu_debug_solve_trace": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "hlu_debug_truncate": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.c_double, _i32, _vp, _vp, _vp,

@@ -53,7 +53,7 @@ def build(force=False, jobs=None):
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
+    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-ldl"]  # -ldl: NVTX's dlopen on glibc before 2.34
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (r.stdout, r.stderr))

@@ -25,6 +25,21 @@
 #include "krylov.h"
 #include "launch_count.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// One NVTX range per public call (build, factor, solve, GMRES, Richardson,
+// Schulz inverse, batched calls), named after the call, for profilers that
+// filter by range (ncu --nvtx); without a profiler attached each push and
+// pop is a test of an unset function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+
 using namespace hlu;
 
 namespace hlu {
@@ -885,6 +900,7 @@ void hlu_destroy(hlu_handle* h) {
 
 int hlu_build(const hlu_mesh* mesh, double kappa, int32_t leaf, double eta, double eps, int32_t rank_cap,
               void* stream, hlu_handle** out) {
+  NvtxRange nvtx_("hlu_build");
   try {
     if (!mesh || !out) return fail(HLU_ERR_ARG, "null argument");
     *out = nullptr;
@@ -1117,7 +1133,10 @@ int64_t hlu_factor_bytes_estimate(const hlu_handle* h, int32_t precision) {
 }
 
 static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t limit);
-int hlu_factor(hlu_handle* h, int32_t precision, void* stream) { return factor_impl(h, precision, stream, -1); }
+int hlu_factor(hlu_handle* h, int32_t precision, void* stream) {
+  NvtxRange nvtx_("hlu_factor");
+  return factor_impl(h, precision, stream, -1);
+}
 
 // allocation for `precision` (first time), rank/status/flop resets, A_H fill
 static int factor_prepare(hlu_handle* h, int32_t precision, cudaStream_t s) {
@@ -1225,6 +1244,7 @@ static int factor_impl(hlu_handle* h, int32_t precision, void* stream, int64_t l
 }
 
 int hlu_factor_async(hlu_handle* h, int32_t precision, int32_t max_ctas, void* stream) {
+  NvtxRange nvtx_("hlu_factor_async");
   try {
     if (!h || max_ctas < 0) return fail(HLU_ERR_ARG, "bad argument");
     if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
@@ -1285,6 +1305,7 @@ int hlu_factor_stats(const hlu_handle* h, hlu_factor_info* info) {
 }
 
 int hlu_solve(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream) {
+  NvtxRange nvtx_("hlu_solve");
   if (!h || !b || !x || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
   if (h->precision < 0 || h->factor_pending) return fail(HLU_ERR_STATE, "not factored");
   return solve_any(h, b, x, nrhs, ld, (cudaStream_t)stream);
@@ -1292,6 +1313,7 @@ int hlu_solve(const hlu_handle* h, const double* b, double* x, int32_t nrhs, int
 
 int gmres_solve(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, int32_t restart,
                 double tol, int32_t maxit, int32_t flexible, hlu_stats* stats, void* stream) {
+  NvtxRange nvtx_("gmres_solve");
   (void)flexible;  // the flexible (stored z_j) form is used in every case
   try {
     hlu_handle* h = const_cast<hlu_handle*>(hc);
@@ -1324,6 +1346,7 @@ int gmres_solve(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, 
 
 int hlu_richardson(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, double tol,
                    int32_t maxit, hlu_stats* stats, void* stream) {
+  NvtxRange nvtx_("hlu_richardson");
   try {
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!h || !b || !x || nrhs < 1 || ld < h->A.N || !(tol > 0) || maxit < 1) return fail(HLU_ERR_ARG, "bad argument");
@@ -1402,6 +1425,7 @@ int hlu_set_preconditioner(hlu_handle* h, int32_t which) {
 }
 
 int hlu_hinverse(hlu_handle* h, int32_t precision, double tol, int32_t maxit, hlu_hinv_info* info, void* stream) {
+  NvtxRange nvtx_("hlu_hinverse");
   try {
     if (!h || !(tol > 0) || maxit < 0 || maxit > HLU_HINV_MAX_ITERS) return fail(HLU_ERR_ARG, "bad argument");
     if (precision != HLU_FP64 && precision != HLU_FP32) return fail(HLU_ERR_ARG, "precision (FP64 or FP32)");
@@ -1599,6 +1623,7 @@ int hlu_hinverse(hlu_handle* h, int32_t precision, double tol, int32_t maxit, hl
 }
 
 int hlu_hinverse_apply(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, void* stream) {
+  NvtxRange nvtx_("hlu_hinverse_apply");
   hlu_handle* h = const_cast<hlu_handle*>(hc);
   if (!h || !b || !x || nrhs < 1 || ld < h->A.N) return fail(HLU_ERR_ARG, "bad argument");
   if (!h->inv.ready) return fail(HLU_ERR_STATE, "no inverse (hlu_hinverse)");
@@ -1606,6 +1631,7 @@ int hlu_hinverse_apply(const hlu_handle* hc, const double* b, double* x, int32_t
 }
 
 int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* stream) {
+  NvtxRange nvtx_("hlu_factor_batch");
   try {
     if (!hs || count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "bad argument");
     if (precision != HLU_FP64 && precision != HLU_FP32 && precision != HLU_TF32)
@@ -1637,6 +1663,7 @@ int hlu_factor_batch(hlu_handle** hs, int32_t count, int32_t precision, void* st
 
 int hlu_solve_batch(hlu_handle* const* hs, int32_t count, const double* const* b, double* const* x,
                     const int32_t* nrhs, void* stream) {
+  NvtxRange nvtx_("hlu_solve_batch");
   try {
     if (!hs || !b || !x || !nrhs || count < 1 || count > kMaxBatch) return fail(HLU_ERR_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2141,6 +2168,7 @@ extern "C" {
 
 int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nrhs, int64_t ld, int32_t restart,
                     double tol, int32_t maxit, void* stream, hlu_gmres** out) {
+  NvtxRange nvtx_("hlu_gmres_begin");
   try {
     hlu_handle* h = const_cast<hlu_handle*>(hc);
     if (!out || !h || !b || !x || nrhs < 1 || ld < h->A.N || restart < 1 || restart > 1000 || !(tol > 0) || maxit < 1)
@@ -2190,6 +2218,7 @@ int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nr
 }
 
 int hlu_gmres_step_batch(hlu_gmres* const* gs, int32_t count, void* stream) {
+  NvtxRange nvtx_("hlu_gmres_step_batch");
   try {
     if (!gs || count < 1) return fail(HLU_ERR_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;

@@ -398,7 +398,7 @@ def run_gpu(args):
     # granularity: the autotuner's stored choice for this workload (or a fresh
     # tuning with --autotune), else the command-line tile
     from paper_2211_11303_gb300 import autotune
-    tuned_path = os.path.join(ROOT, "paper_2211_11303_gb300", "tuned.json")
+    tuned_path = autotune.default_path()
     prec_name = "fp32" if args.precision == "fp32" else "fp64"
     if args.autotune and rank == 0:
         res = autotune.tune(args.n, args.kappa, args.leaf, args.eta, args.eps,

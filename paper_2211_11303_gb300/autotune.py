@@ -9,7 +9,9 @@ candidate on the problem it is given (build, factorisation and a preconditioned
 FGMRES solve of seeded right-hand sides) and returns the fastest by the time
 of one factorisation plus one solve of ``nrhs`` columns.  ``apply`` installs a
 result for the hlu_build calls that follow.  Results are plain dicts and can be
-stored with ``save`` / ``load`` (JSON) keyed by the workload.
+stored with ``save`` / ``load`` (JSON) keyed by the workload; ``default_path``
+names the store (the environment variable HLU_TUNED, else the one shipped
+beside this module).
 """
 import json
 import os
@@ -21,6 +23,12 @@ import torch
 from . import hlu as H
 
 DEFAULT_CANDIDATES = [{"tile": t, "compress_at": c} for t in (32, 64) for c in (32, 48, 64, 80, 96)]
+
+
+def default_path():
+    """The result store: $HLU_TUNED when set and not empty, else tuned.json
+    beside this module (the results measured for the shipped workloads)."""
+    return os.environ.get("HLU_TUNED") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
 def apply(params):

@@ -36,3 +36,17 @@ def test_committed_result_names_a_candidate():
     path = os.path.join(os.path.dirname(autotune.__file__), "tuned.json")
     best = autotune.load(path, 24, 8.0, 1e-4)
     assert best in autotune.DEFAULT_CANDIDATES
+
+
+def test_store_path_follows_the_environment(tmp_path, monkeypatch):
+    import os
+    monkeypatch.delenv("HLU_TUNED", raising=False)
+    shipped = os.path.join(os.path.dirname(os.path.abspath(autotune.__file__)), "tuned.json")
+    assert autotune.default_path() == shipped
+    path = str(tmp_path / "mine.json")
+    monkeypatch.setenv("HLU_TUNED", path)
+    assert autotune.default_path() == path
+    autotune.save(autotune.default_path(), _result(12, {"tile": 32, "compress_at": 32}))
+    assert autotune.load(path, 12, 8.0, 1e-4) == {"tile": 32, "compress_at": 32}
+    monkeypatch.setenv("HLU_TUNED", "")
+    assert autotune.default_path() == shipped

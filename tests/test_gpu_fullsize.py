@@ -67,8 +67,7 @@ def test_full_size_solve_matches_the_direct_solve(hlu, prec):
     ref = np.load(os.path.join(HERE, "golden", "xref_n24_kappa8.npy"))
     N = ref.shape[0]
     Bh = np.stack([synth.normal(synth.rhs_seed(2, 0, j), N) for j in range(NRHS)])
-    best = autotune.load(os.path.join(HERE, "..", "paper_2211_11303_gb300", "tuned.json"), N_CUBE, KAPPA, EPS,
-                         "fp32")
+    best = autotune.load(autotune.default_path(), N_CUBE, KAPPA, EPS, "fp32")  # the store bench.py reads
     autotune.apply(best)
     try:
         h = hlu.hlu_build(N_CUBE, KAPPA, LEAF, ETA, EPS)

@@ -78,7 +78,9 @@ def test_full_size_solve_matches_the_direct_solve(hlu, prec):
             B = torch.from_numpy(Bh).cuda().t()
             X = hlu.colmajor(N, NRHS)
             st = hlu.gmres_solve(h, B, X, restart=50, tol=1e-10, maxit=500)
-            assert st["converged"] and st["iterations"] <= 40, st
+            # the preconditioner's quality at this size: 7 (FP32) and 8 (FP64)
+            # iterations measured, 6-13 over earlier builds
+            assert st["converged"] and st["iterations"] <= 15, st
             Xg = X.t().cpu().numpy().T
         finally:
             hlu.hlu_destroy(h)

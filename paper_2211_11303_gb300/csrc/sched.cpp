@@ -318,9 +318,13 @@ class Sched {
     }
   }
   // read of one segment: enough to order the task after any writer of the
-  // buffer's rank slot (rank writers write every segment)
+  // buffer's rank slot (rank writers write every segment).  The right-hand
+  // side count of a solve or apply is a launch parameter that no task
+  // writes, so a count taken from it orders nothing: without this, every
+  // update of the backward solve waited for the first segment of its input,
+  // which is solved last
   void acc_rank(const MV& m) {
-    if (m.buf < 0 || m.v.slot < 0) return;
+    if (m.buf < 0 || m.v.slot < 0 || m.v.slot == L_.nrhs_slot) return;
     const Buf& b = bufs_[m.buf];
     touch(b.seg0, false);
   }

@@ -128,6 +128,47 @@ def test_refused_allocation_is_oom_and_recoverable(hlu):
     _solve_ok(hlu)
 
 
+def test_gmres_start_out_of_memory_holds_nothing(hlu):
+    """A GMRES state whose Krylov workspace cannot be had: HLU_ERR_OOM, and no
+    device memory is held afterwards (the first workspace buffer, which fits,
+    is freed again); the same call succeeds once the memory is there."""
+    h = hlu.hlu_build(6, 3.0, 16, 2.0, 1e-4)
+    try:
+        hlu.hlu_factor(h, hlu.HLU_FP64)
+        N = hlu.hlu_n(h)
+        nr, m = 2, 20
+        b = hlu.colmajor(N, nr)
+        b.copy_(torch.from_numpy(np.stack([synth.normal(11 + j, N) for j in range(nr)], axis=1)))
+        x = hlu.colmajor(N, nr)
+        torch.cuda.synchronize()
+        base = hlu.hlu_device_bytes_in_use()
+        first = 8 * N * (m + 1) * nr  # V, the first workspace buffer
+        try:
+            hlu.hlu_set_device_memory_limit(base + first + 4096)  # V fits, Z does not
+            with pytest.raises(hlu.HluError) as ei:
+                hlu.hlu_gmres_begin(h, b, x, restart=m, tol=1e-10, maxit=200)
+            assert ei.value.status == "HLU_ERR_OOM"
+            assert hlu.hlu_device_bytes_in_use() == base
+        finally:
+            hlu.hlu_set_device_memory_limit(0)
+        g = hlu.hlu_gmres_begin(h, b, x, restart=m, tol=1e-10, maxit=200)
+        try:
+            done, st = False, None
+            for _ in range(400):
+                hlu.hlu_gmres_step_batch([g])
+                done, st = hlu.hlu_gmres_status(g)
+                if done:
+                    break
+            assert done and st["converged"] == 1, st
+        finally:
+            hlu.hlu_gmres_end(g)
+        torch.cuda.synchronize()
+        assert hlu.hlu_device_bytes_in_use() == base
+    finally:
+        hlu.hlu_destroy(h)
+    _solve_ok(hlu)
+
+
 def test_library_memory_comes_from_torch(hlu):
     """With the default binding the library's device memory comes from
     PyTorch's caching allocator (the allocator hook of the C ABI)."""

@@ -2203,7 +2203,12 @@ int hlu_gmres_begin(const hlu_handle* hc, const double* b, double* x, int32_t nr
       CKR(cudaStreamSynchronize(s), "sync");
       return HLU_OK;
     };
-    int rc = start();
+    int rc;
+    try {
+      rc = start();
+    } catch (const std::bad_alloc&) {  // the host vectors of the state
+      rc = fail(HLU_ERR_OOM, "host allocation");
+    }
     if (rc) {
       cudaStreamSynchronize(s);  // the memset / norm work queued so far
       g->k.free_all();

@@ -166,6 +166,49 @@ def test_complex_richardson_reaches_the_direct_solve():
     assert np.abs(xs.imag).max() > 1e-3 * np.abs(xs).max()  # the damping is felt
 
 
-def test_fgmres_rejects_a_complex_system():
-    with pytest.raises(TypeError):
-        K.fgmres(lambda v: v, np.ones(3, complex))
+def test_complex_fgmres_textbook_cases():
+    """A diagonal matrix with m distinct complex eigenvalues is solved in m
+    steps (its Krylov space has dimension m); an exact preconditioner in one;
+    a random complex system to the tolerance of numpy's dense solve."""
+    rng = np.random.default_rng(4)
+    lam = np.array([2.0 + 1j, -1.0 + 0.5j, 3.0 - 2j, 0.5 + 4j, -2.0 - 1j])
+    d = np.repeat(lam, 8)
+    b = _cgauss(rng, d.shape[0])
+    x, info = K.fgmres(lambda v: d * v, b, restart=20, tol=1e-12)
+    assert info["converged"] and info["iters"] <= 5, info["iters"]
+    assert np.linalg.norm(x - b / d) <= 1e-10 * np.linalg.norm(b / d)
+    A = _cgauss(rng, 40, 40) + 20 * np.eye(40)  # spectrum in a disk of radius ~9 around 20
+    b = _cgauss(rng, 40)
+    Ainv = np.linalg.inv(A)
+    x, info = K.fgmres(lambda v: A @ v, b, lambda v: Ainv @ v, restart=10, tol=1e-12)
+    assert info["converged"] and info["iters"] == 1
+    x, info = K.fgmres(lambda v: A @ v, b, restart=8, tol=1e-11)
+    xs = np.linalg.solve(A, b)
+    assert info["converged"] and np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+    assert np.linalg.norm(A @ x - b) <= 1e-11 * np.linalg.norm(b) * 1.0001
+
+
+def test_complex_fgmres_with_the_complex_hlu():
+    """FGMRES with the complex H-LU on the conducting magnet reaches the direct
+    solve, in no more steps than Algorithm 1's Richardson iteration."""
+    n = 6
+    m = M.interior_edges(n)
+    beta = F.magnet_beta(m, 10.0)
+    _, A, perm, cl, bl = _complex_problem(n, np.sqrt(10.0), 0.5, 32, beta=beta)
+    b = F.constant_current_rhs(m, (10.0, 10.0, 10.0)).astype(complex)
+    P = H.HLUPreconditioner(A, perm, cl, bl, 1e-4)
+    x, info = K.fgmres(lambda v: A @ v, b, P.apply, restart=30, tol=1e-10)
+    xs = spla.spsolve(A.tocsc(), b)
+    assert info["converged"] and np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+    _, rinfo = K.richardson(lambda v: A @ v, b, P.apply, tol=1e-10)
+    assert info["iters"] <= rinfo["iters"], (info["iters"], rinfo["iters"])
+
+
+def test_real_fgmres_is_unchanged_by_the_complex_path():
+    """Real input keeps real arrays and the real rotations."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 30)) + 12 * np.eye(30)
+    b = rng.standard_normal(30)
+    x, info = K.fgmres(lambda v: A @ v, b, restart=6, tol=1e-12)
+    assert x.dtype == np.float64 and info["converged"]
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(x)

@@ -112,3 +112,23 @@ def test_real_equivalent_through_the_library_dag(lib, n, omega, chi, magnet, pre
     # the pair of an edge is never split: every cluster starts on an even position
     C = trees.export_arrays(rperm, rcl, rbl)[1]
     assert np.all(C[:, 0] % 2 == 0) and np.all(C[:, 1] % 2 == 0)
+
+
+def test_fgmres_on_the_real_equivalent_with_the_fp32_factor(lib):
+    """The library's solver arrangement, an FP32 factor inside FP64 flexible
+    GMRES, on the equivalent real system of the conducting magnet: it reaches
+    the complex direct solve."""
+    n = 4
+    m = mesh.interior_edges(n)
+    A = fem.assemble_time_harmonic(m, np.sqrt(10.0), 1.0, 0.5, beta=fem.magnet_beta(m, 10.0))
+    b = fem.constant_current_rhs(m, (10.0, 10.0, 10.0)).astype(complex)
+    xs = spla.spsolve(A.tocsc(), b)
+    Ar = real_equivalent(A)
+    pts = np.repeat(trees.edge_midpoints2(m), 2, axis=0)
+    rperm, rcl = trees.cluster_tree(pts, 32)
+    rbl = trees.block_tree(rcl, 4)
+    M = HostHLU(lib, Ar, rperm, rcl, rbl, 1e-4, 1)
+    xr, info = krylov.fgmres(lambda v: Ar @ v, interleave(b), M.apply, restart=20, tol=1e-10)
+    assert info["converged"] and info["iters"] <= 6, info
+    x = deinterleave(xr)
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)

@@ -219,7 +219,22 @@ class HazardCheck {
     for (int64_t j = 0; j < v.cols; ++j)
       for (int64_t i = 0; i < v.rows; ++i) touch(SP_ARENA, v.off + i * v.rs + j * v.cs);
   }
+  // a task's term or piece list must lie inside the schedule's list
+  bool list_ok(const Task& t, size_t n) {
+    if (t.list_count == 0 || (t.list_begin >= 0 && t.list_count > 0 &&
+                              (size_t)t.list_begin + (size_t)t.list_count <= n))
+      return true;
+    if (out_of_range_ == 0 && violations_ == 0) {
+      first_[0] = -1;
+      first_[1] = cur_;
+      first_[2] = SP_ARENA;
+      first_[3] = t.list_begin;
+    }
+    ++out_of_range_;
+    return false;
+  }
   void terms(const Task& t) {
+    if (!list_ok(t, S_.terms.size())) return;
     for (int32_t q = 0; q < t.list_count; ++q) {
       const Term& m = S_.terms[t.list_begin + q];
       count(m.A);
@@ -228,6 +243,7 @@ class HazardCheck {
     }
   }
   void pieces(const Task& t) {
+    if (!list_ok(t, S_.pieces.size())) return;
     for (int32_t q = 0; q < t.list_count; ++q) {
       const Piece& p = S_.pieces[t.list_begin + q];
       count(p.X);
